@@ -1,0 +1,172 @@
+/*
+ * ebic.h -- C ABI of the GB300 EBIC population evaluator.
+ *
+ * EBIC (arXiv 1807.09932) is an evolutionary biclustering method. Each generation it scores a
+ * population of candidate biclusters against every row of a float32 matrix. A candidate is an
+ * ordered list of distinct column indices. A row joins the candidate when its values obey the
+ * "greater or equal" relation along that column order, and a candidate's score counts its rows
+ * (Methods, "Handling missing values"). This library evaluates that rule on one GPU
+ * (sm_103a).
+ *
+ * Conventions that hold for every call:
+ *  - Pointer placement is detected per pointer (cudaPointerGetAttributes). Any input or output
+ *    may be host memory (pageable or pinned) or device memory of the current device. Host
+ *    inputs are copied to device scratch that the library allocates stream-ordered and frees on
+ *    the same stream.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). A call whose outputs are
+ *    all in device memory is asynchronous on that stream. A call with any host output
+ *    synchronizes the stream before it returns.
+ *  - The caller owns every buffer it passes. The library owns only ebic_matrix handles and its
+ *    internal scratch.
+ *  - Return values are EBIC_OK (0) or a negative EBIC_ERR_* code. No exception crosses the ABI.
+ *    ebic_last_error() returns a message for the calling thread's last failure.
+ *  - Arguments are checked before any launch. Candidate lists in host memory are checked on
+ *    the host. Candidate lists already in device memory are checked by a device kernel, which
+ *    makes every later kernel of the call do nothing. The failure is then reported by the
+ *    call's return code when the call synchronizes (host outputs), else by
+ *    ebic_matrix_status().
+ *  - Calls on distinct streams may run concurrently, including on the same matrix.
+ *
+ * Bitmap layout: one bitmap per candidate of W = ceil(rows/32) little-endian uint32 words. Bit b
+ * of word w is row 32w+b. Padding bits of the last word are 0. A population's bitmaps are
+ * row-major [n_cand][W].
+ *
+ * Candidate lists are in CSR form. cols holds uint16 column indices. offsets[n_cand+1] holds
+ * uint32 offsets with offsets[0] == 0. Candidate i is cols[offsets[i] .. offsets[i+1]). Its
+ * length L is in [1, 64] and its columns are distinct and < the matrix's column count.
+ */
+#ifndef EBIC_GB300_H
+#define EBIC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define EBIC_OK                  0
+#define EBIC_ERR_INVALID_ARG    -1  /* a size, pointer, flag or candidate list is invalid      */
+#define EBIC_ERR_OOM            -2  /* device or host allocation failed                        */
+#define EBIC_ERR_CUDA           -3  /* a CUDA runtime call failed (message has the CUDA error)   */
+#define EBIC_ERR_DEVICE_TIMEOUT -4  /* a bounded device wait expired; the kernel returned early  */
+#define EBIC_ERR_UNSUPPORTED    -5  /* valid but outside this build's limits (e.g. too many cols)*/
+#define EBIC_ERR_NO_DEVICE      -6  /* no CUDA device is visible                                 */
+
+/* ---- ebic_load_matrix flags ------------------------------------------------------------- */
+/* Missing-value exclusion (Methods, "Handling missing values"). NaN marks a missing value. With
+ * the flag, a row with NaN in any column of a candidate does not match that candidate. Without
+ * it, NaN is replaced by fill_value and compared as a number (the old behaviour). */
+#define EBIC_EXCLUDE_MISSING 0x1u
+
+/* ---- ebic_eval_population / ebic_fitness flags ------------------------------------------- */
+/* Negative trends: a row that is non-increasing along the candidate's order also matches. A row
+ * that is both non-decreasing and non-increasing (constant) is counted once. */
+#define EBIC_NEGATIVE_TRENDS 0x1u
+
+/* Largest supported column count of this build. Rows are limited to 2^31 - 1, the paper's
+ * per-GPU row limit (Methods, "Support for Big Data"). */
+#define EBIC_MAX_COLS 832
+#define EBIC_MAX_CANDIDATE_LEN 64
+
+typedef struct ebic_matrix ebic_matrix;
+
+/*
+ * Load a float32 matrix and build its device-resident rank matrix (one pass).
+ *   x          row-major float32 values, rows x cols, leading dimension ld >= cols (elements);
+ *              host or device memory. The library does not keep x.
+ *   rows       1 .. 2^31-1 (Methods, "Support for Big Data": up to 2^31-1 rows on one GPU)
+ *   cols       1 .. EBIC_MAX_COLS
+ *   flags      EBIC_EXCLUDE_MISSING or 0
+ *   fill_value the number that replaces NaN when exclusion is off. It must not be NaN.
+ *   out        receives the handle; free it with ebic_free_matrix.
+ * The rank transform replaces each value by its dense rank within its row (the number of
+ * distinct non-missing values of the row strictly below it). So x <= y exactly when
+ * rank(x) <= rank(y), which keeps the "greater or equal" relation of Methods, "Handling missing
+ * values" intact. IEEE semantics: -0 == +0, infinities ordered, subnormals exact.
+ * The call returns after the rank matrix is built (the stream is synchronized).
+ */
+int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uint32_t flags,
+                     float fill_value, void* stream, ebic_matrix** out);
+
+/* Free a matrix handle and its device memory. Synchronizes the device. NULL is a no-op. */
+int ebic_free_matrix(ebic_matrix* m);
+
+/*
+ * Shape of a loaded matrix. Any output pointer may be NULL.
+ *   words      W = ceil(rows/32), the bitmap length per candidate
+ *   rank_bits  8 (cols <= 127) or 16: the width of the stored ranks
+ */
+int ebic_matrix_info(const ebic_matrix* m, int64_t* rows, int32_t* cols, int64_t* words,
+                     int32_t* rank_bits);
+
+/*
+ * Copy the dense ranks out, row-major uint16 [rows][cols], 0xFFFF for a missing value
+ * (exclusion on). out is host memory of rows*cols uint16. Synchronous. This call exists to check
+ * the transform; the evaluator never needs it.
+ */
+int ebic_matrix_ranks(const ebic_matrix* m, uint16_t* out, void* stream);
+
+/*
+ * Score a population against every row (the hot path of each EBIC generation; "search is
+ * driven by counting of rows", Methods, "Handling missing values").
+ *   cols, offsets  the population in CSR form (see above); n_cand >= 0 (0 is a no-op)
+ *   flags          EBIC_NEGATIVE_TRENDS or 0
+ *   counts         out: uint32[n_cand], the matched-row count of each candidate
+ *   bitmaps        out: uint32[n_cand][W] row bitmaps, or NULL for counts only
+ * Results are exact integers. They do not depend on the launch configuration.
+ */
+int ebic_eval_population(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                         uint32_t n_cand, uint32_t flags, uint32_t* counts, uint32_t* bitmaps,
+                         void* stream);
+
+/*
+ * Overlap-penalised fitness of a population against an elite archive. This is the project's
+ * reading of the paper's "driven by counting of rows" (Methods, "Handling missing values").
+ *   cols, offsets, n_cand  the population (CSR), as given to ebic_eval_population
+ *   counts, bitmaps        its evaluation: uint32[n_cand] and uint32[n_cand][W]
+ *   arch_cols, arch_offsets, arch_bitmaps, n_arch   the archive: CSR column lists and
+ *                          uint32[n_arch][W] row bitmaps. n_arch may be 0 (pointers then unused).
+ *   fitness                out: uint64[n_cand]
+ *   overlaps               out: uint32[n_cand][n_arch] = popcount(M_c & M_a), or NULL
+ * Definition: o(c,a) = popcount(M_c & M_a). Let p_c = counts[c] minus the largest o(c,a) over
+ * archive members a whose column SET meets c's (0 if there is none). Then
+ * fitness[c] = (uint64)p_c << (min(L_c, 33) - 1).
+ * flags is reserved (pass 0).
+ */
+int ebic_fitness(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                 uint32_t n_cand, const uint32_t* counts, const uint32_t* bitmaps,
+                 const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                 const uint32_t* arch_bitmaps, uint32_t n_arch, uint32_t flags,
+                 uint64_t* fitness, uint32_t* overlaps, void* stream);
+
+/*
+ * Synchronize `stream` and return the deferred device status of `m`, then clear it. That
+ * status is EBIC_OK, EBIC_ERR_INVALID_ARG (a device-resident candidate list failed the device
+ * check) or EBIC_ERR_DEVICE_TIMEOUT (a bounded wait in a kernel expired). The status is shared by
+ * all streams that use `m`.
+ */
+int ebic_matrix_status(ebic_matrix* m, void* stream);
+
+/*
+ * Row-tile height of the evaluator for this matrix, in slabs (1, 2 or 4), or 0 for the
+ * built-in choice. A slab is 512 rows for 8-bit ranks and 256, 128 or 64 rows for 16-bit ranks
+ * (ebic_matrix_get_tile reports it). The tile changes speed only, never results. The autotuner
+ * sets it from timed sweeps. A tile whose shared-memory stage would not fit returns
+ * EBIC_ERR_UNSUPPORTED. Not thread-safe with concurrent evaluations of the same matrix.
+ */
+int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
+/* The tile height in slabs that the next evaluation will use, and the rows per slab. */
+int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab);
+
+/* Message for the calling thread's last failed call ("" if none). Valid until the next call. */
+const char* ebic_last_error(void);
+
+/* ABI version: (major << 16) | minor. */
+int ebic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBIC_GB300_H */

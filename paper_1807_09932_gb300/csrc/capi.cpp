@@ -1,0 +1,615 @@
+// Host runtime and C ABI of the EBIC GB300 library: argument checks, placement of host/device
+// buffers, stream-ordered scratch, tensor-map setup, launch planning and error reporting.
+// Every computational step runs in this library's CUDA kernels; this file only moves data and
+// launches them.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ebic.h"
+#include "ebic_internal.h"
+
+using namespace ebic;
+
+struct ebic_matrix {
+  int device = 0;
+  Layout L;
+  uint32_t flags = 0;
+  float fill = 0.f;
+  uint32_t* ranks = nullptr;   // device rank matrix
+  uint32_t* status = nullptr;  // device deferred-status word
+  int num_sms = 0;
+  std::mutex mu;
+  CUtensorMap tmap[3];         // one per tile height TS = 1, 2, 4
+  bool tmap_ok[3] = {false, false, false};
+  int tile = 0;                // 0: built-in tile choice; else the TS every evaluation uses
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  int code = EBIC_ERR_CUDA;
+  if (e == cudaErrorMemoryAllocation) code = EBIC_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) code = EBIC_ERR_NO_DEVICE;
+  (void)cudaGetLastError();
+  return fail(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define EBIC_CUDA(expr)                                      \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);      \
+  } while (0)
+
+// Current device switched for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { prev = -1; (void)cudaGetLastError(); }
+    if (prev != dev) (void)cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) (void)cudaSetDevice(prev);
+  }
+};
+
+// Stream-ordered scratch freed on the same stream when the call ends.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, s);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) (void)cudaFreeAsync(p, s);
+  }
+};
+
+// true: device (or managed) memory of `dev`; false: host memory (pageable or pinned)
+bool on_device(const void* p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+bool foreign_device(const void* p, int dev) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice && at.device != dev;
+}
+
+template <class T>
+cudaError_t to_device(const T* p, size_t n, int dev, Scratch& sc, const T** out) {
+  if (on_device(p, dev)) { *out = p; return cudaSuccess; }
+  void* d = nullptr;
+  cudaError_t e = sc.alloc(&d, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, sc.s);
+  *out = static_cast<const T*>(d);
+  return e;
+}
+
+template <class T>
+cudaError_t out_buffer(T* p, size_t n, int dev, Scratch& sc, T** out, bool* host) {
+  if (on_device(p, dev)) { *out = p; *host = false; return cudaSuccess; }
+  void* d = nullptr;
+  cudaError_t e = sc.alloc(&d, n * sizeof(T));
+  *out = static_cast<T*>(d);
+  *host = true;
+  return e;
+}
+
+std::once_flag g_pool_once[64];
+void init_pool(int dev) {
+  if (dev < 0 || dev >= 64) return;
+  std::call_once(g_pool_once[dev], [dev] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;  // keep freed scratch in the pool instead of the OS
+      (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    (void)cudaGetLastError();
+  });
+}
+
+// Host-side check of a CSR candidate list: offsets[0] == 0, lengths in [1, 64], columns in
+// range and distinct. Returns an empty string when valid.
+std::string check_candidates_host(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                                  int32_t ncols) {
+  if (offsets[0] != 0) return "offsets[0] must be 0";
+  std::vector<uint32_t> seen((size_t)ncols, 0xFFFFFFFFu);
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t a = offsets[i], b = offsets[i + 1];
+    if (b <= a || b - a > (uint32_t)kMaxLen)
+      return "candidate " + std::to_string(i) + " has length outside [1, 64]";
+    for (uint32_t j = a; j < b; ++j) {
+      const uint16_t c = cols[j];
+      if (c >= (uint32_t)ncols)
+        return "candidate " + std::to_string(i) + " has column " + std::to_string(c) +
+               " >= cols";
+      if (seen[c] == i) return "candidate " + std::to_string(i) + " repeats column " +
+                               std::to_string(c);
+      seen[c] = i;
+    }
+  }
+  return "";
+}
+
+// Tensor map over the rank matrix: dims {32*VEC words, Q slabs, C columns}, box
+// {32*VEC, TS, col_box}. Built once per (matrix, TS) and cached.
+int get_tmap(ebic_matrix* m, int ts, int col_box, const CUtensorMap** out) {
+  const int idx = ts == 1 ? 0 : ts == 2 ? 1 : 2;
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (!m->tmap_ok[idx]) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+      cudaDriverEntryPointQueryResult q;
+      void* fn = nullptr;
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                       cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(EBIC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Layout& L = m->L;
+    const cuuint64_t wps = 32ull * (cuuint64_t)L.vec;
+    cuuint64_t dims[3] = {wps, (cuuint64_t)L.slabs, (cuuint64_t)L.cols};
+    cuuint64_t strides[2] = {wps * 4ull, (cuuint64_t)L.slabs * wps * 4ull};
+    cuuint32_t box[3] = {(cuuint32_t)wps, (cuuint32_t)ts, (cuuint32_t)col_box};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(&m->tmap[idx], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, m->ranks, dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(EBIC_ERR_CUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string(r));
+    m->tmap_ok[idx] = true;
+  }
+  *out = &m->tmap[idx];
+  return EBIC_OK;
+}
+
+int status_code(uint32_t bits, const char* where) {
+  if (bits & kErrTimeout)
+    return fail(EBIC_ERR_DEVICE_TIMEOUT, std::string(where) + ": a bounded device wait expired");
+  if (bits & kErrInvalid)
+    return fail(EBIC_ERR_INVALID_ARG,
+                std::string(where) + ": the device-side check rejected a candidate list");
+  return EBIC_OK;
+}
+
+}  // namespace
+
+namespace ebic {
+
+Layout make_layout(int64_t rows, int32_t cols) {
+  Layout L;
+  L.rows = rows;
+  L.cols = cols;
+  L.words = (rows + 31) / 32;
+  if (cols <= 127) {
+    L.width = 8;
+    L.vec = 4;
+  } else {
+    L.width = 16;
+    L.vec = (int64_t)cols * 512 <= kStageMax ? 4 : (int64_t)cols * 256 <= kStageMax ? 2 : 1;
+  }
+  L.rows_per_group = L.width == 8 ? 128 : 64;
+  L.words_per_group = L.rows_per_group / 32;
+  const int64_t g = (rows + L.rows_per_group - 1) / L.rows_per_group;
+  L.slabs = (g + L.vec - 1) / L.vec;
+  L.groups = L.slabs * L.vec;
+  L.sentinel = L.width == 8 ? 0x7Fu : 0x7FFFu;
+  return L;
+}
+
+static void col_boxes(int32_t cols, int* nb, int* cb) {
+  *nb = (cols + 255) / 256;
+  *cb = (cols + *nb - 1) / *nb;
+}
+
+int default_tile_slabs(const Layout& L) {
+  int nb, cb;
+  col_boxes(L.cols, &nb, &cb);
+  for (int ts = 4; ts >= 1; ts >>= 1) {
+    if (ts > L.slabs && ts > 1) continue;
+    if ((int64_t)nb * cb * ts * 128 * L.vec <= kStageMax) return ts;
+  }
+  return 1;
+}
+
+bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint, int grid,
+               EvalArgs* a) {
+  int nb, cb;
+  col_boxes(L.cols, &nb, &cb);
+  const int64_t col_stride = (int64_t)ts * 128 * L.vec;
+  const int64_t stage = (int64_t)nb * cb * col_stride;
+  const int64_t wpt = (int64_t)ts * L.vec * L.words_per_group;
+  const int64_t wbuf = (int64_t)kEvalWarps * wpt * 4;
+  const int64_t left = kSmemDynMax - 2 * stage - wbuf - 256;
+  if (left < 4 * 64 + 256) return false;
+  int64_t cc_max = std::min<int64_t>(kMaxChunkCols, (left - 132) / 4);
+  cc_max = cc_max / 64 * 64;
+  if (cc_max < 64) return false;
+  const int64_t n_tiles = (L.slabs + ts - 1) / ts;
+  const int64_t total = total_cols_hint > 0 ? total_cols_hint : (int64_t)n_cand * 16;
+  const int64_t want_chunks = std::max<int64_t>(1, (2 * (int64_t)grid + n_tiles - 1) / n_tiles);
+  int64_t cc = (total + want_chunks - 1) / want_chunks;
+  cc = (cc + 63) / 64 * 64;
+  cc = std::max<int64_t>(64, std::min(cc, cc_max));
+  a->cols = L.cols;
+  a->slabs = L.slabs;
+  a->groups = L.groups;
+  a->words = L.words;
+  a->chunk_cols = (int32_t)cc;
+  a->col_box = cb;
+  a->n_col_boxes = nb;
+  a->stage_bytes = (uint32_t)stage;
+  a->smem_bytes = (uint32_t)((2 * stage + wbuf + 2 * (cc + 64) + 2 * (cc + 1) + 15) / 16 * 16);
+  return true;
+}
+
+cudaError_t launch_eval(const EvalConfig& cfg, const CUtensorMap* tmap, const EvalArgs& a,
+                        cudaStream_t s) {
+  if (cfg.width == 8) return launch_eval_w8v4(cfg, tmap, a, s);
+  switch (cfg.vec) {
+    case 4: return launch_eval_w16v4(cfg, tmap, a, s);
+    case 2: return launch_eval_w16v2(cfg, tmap, a, s);
+    case 1: return launch_eval_w16v1(cfg, tmap, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ebic
+
+extern "C" {
+
+int ebic_version(void) { return (1 << 16) | 0; }
+
+const char* ebic_last_error(void) { return g_last_error.c_str(); }
+
+int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uint32_t flags,
+                     float fill_value, void* stream, ebic_matrix** out) {
+  if (!out) return fail(EBIC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!x) return fail(EBIC_ERR_INVALID_ARG, "x is NULL");
+  if (rows < 1 || rows > 2147483647LL)
+    return fail(EBIC_ERR_INVALID_ARG, "rows must be in [1, 2^31-1]");
+  if (cols < 1) return fail(EBIC_ERR_INVALID_ARG, "cols must be >= 1");
+  if (cols > kMaxCols)
+    return fail(EBIC_ERR_UNSUPPORTED, "cols > " + std::to_string(kMaxCols) +
+                                          " is outside this build's limits");
+  if (ld < cols) return fail(EBIC_ERR_INVALID_ARG, "ld must be >= cols");
+  if (flags & ~EBIC_EXCLUDE_MISSING) return fail(EBIC_ERR_INVALID_ARG, "unknown load flag");
+  if (std::isnan(fill_value)) return fail(EBIC_ERR_INVALID_ARG, "fill_value must not be NaN");
+
+  int dev = 0;
+  EBIC_CUDA(cudaGetDevice(&dev));
+  init_pool(dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (foreign_device(x, dev)) return fail(EBIC_ERR_INVALID_ARG, "x is on another device");
+
+  ebic_matrix* m = new ebic_matrix();
+  m->device = dev;
+  m->L = make_layout(rows, cols);
+  m->flags = flags;
+  m->fill = fill_value;
+  auto cleanup = [&](int code) {
+    if (m->ranks) cudaFree(m->ranks);
+    if (m->status) cudaFree(m->status);
+    delete m;
+    return code;
+  };
+  cudaError_t e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaDeviceGetAttribute"));
+  e = cudaMalloc(&m->ranks, m->L.rank_words() * 4);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(rank matrix)"));
+  e = cudaMalloc(&m->status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "status word"));
+
+  {
+    Scratch sc(s);
+    const float* dx = x;
+    int64_t dld = ld;
+    if (!on_device(x, dev)) {
+      void* d = nullptr;
+      e = sc.alloc(&d, (size_t)rows * cols * sizeof(float));
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d, (size_t)cols * sizeof(float), x, (size_t)ld * sizeof(float),
+                              (size_t)cols * sizeof(float), (size_t)rows, cudaMemcpyHostToDevice,
+                              s);
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "copy of x to the device"));
+      dx = static_cast<const float*>(d);
+      dld = cols;
+    }
+    e = launch_rank_transform(m->L, dx, dld, (flags & EBIC_EXCLUDE_MISSING) ? 1 : 0, fill_value,
+                              m->ranks, s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform launch"));
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform"));
+  *out = m;
+  return EBIC_OK;
+}
+
+int ebic_free_matrix(ebic_matrix* m) {
+  if (!m) return EBIC_OK;
+  DeviceGuard g(m->device);
+  cudaError_t e1 = cudaFree(m->ranks);
+  cudaError_t e2 = cudaFree(m->status);
+  delete m;
+  if (e1 != cudaSuccess) return cuda_fail(e1, "cudaFree(rank matrix)");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFree(status)");
+  return EBIC_OK;
+}
+
+int ebic_matrix_info(const ebic_matrix* m, int64_t* rows, int32_t* cols, int64_t* words,
+                     int32_t* rank_bits) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (rows) *rows = m->L.rows;
+  if (cols) *cols = m->L.cols;
+  if (words) *words = m->L.words;
+  if (rank_bits) *rank_bits = m->L.width;
+  return EBIC_OK;
+}
+
+int ebic_matrix_ranks(const ebic_matrix* m, uint16_t* out, void* stream) {
+  if (!m || !out) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  const Layout& L = m->L;
+  std::vector<uint32_t> raw(L.rank_words());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EBIC_CUDA(cudaMemcpyAsync(raw.data(), m->ranks, raw.size() * 4, cudaMemcpyDeviceToHost, s));
+  EBIC_CUDA(cudaStreamSynchronize(s));
+  const uint32_t mask = L.width == 8 ? 0xFFu : 0xFFFFu;
+  for (int64_t r = 0; r < L.rows; ++r) {
+    const int64_t g = r / L.rows_per_group, rr = r % L.rows_per_group;
+    const int64_t lane = rr & 31, k = rr >> 5, q = g / L.vec, j = g % L.vec;
+    for (int32_t c = 0; c < L.cols; ++c) {
+      const size_t w = (((size_t)c * L.slabs + q) * 32 + lane) * L.vec + j;
+      const uint32_t v = (raw[w] >> (L.width * k)) & mask;
+      out[r * L.cols + c] = v == L.sentinel ? 0xFFFFu : (uint16_t)v;
+    }
+  }
+  return EBIC_OK;
+}
+
+int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                         uint32_t n_cand, uint32_t flags, uint32_t* counts, uint32_t* bitmaps,
+                         void* stream) {
+  ebic_matrix* m = const_cast<ebic_matrix*>(cm);
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (flags & ~EBIC_NEGATIVE_TRENDS) return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
+  if (n_cand == 0) return EBIC_OK;
+  if (!cols || !offsets || !counts) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  const int dev = m->device;
+  const Layout& L = m->L;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
+                        (const void*)bitmaps})
+    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+
+  const bool host_lists = !on_device(cols, dev) && !on_device(offsets, dev);
+  int64_t total_hint = 0;
+  if (host_lists) {
+    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+    total_hint = offsets[n_cand];
+  }
+
+  int ts = m->tile ? m->tile : default_tile_slabs(L);
+  while (ts > 1 && ts > L.slabs) ts >>= 1;
+  EvalArgs a;
+  if (!plan_eval(L, ts, n_cand, total_hint, m->num_sms, &a))
+    return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
+  const CUtensorMap* tmap = nullptr;
+  int rc = get_tmap(m, ts, a.col_box, &tmap);
+  if (rc != EBIC_OK) return rc;
+
+  Scratch sc(s);
+  uint32_t* err = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
+  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  const uint16_t* dcols = nullptr;
+  const uint32_t* doffs = nullptr;
+  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
+  // the column count is only known from the offsets; device lists are read by the kernels
+  const size_t ncols_total = host_lists ? offsets[n_cand] : 0;
+  if (on_device(cols, dev)) {
+    dcols = cols;
+  } else {
+    size_t n = ncols_total;
+    if (!host_lists) {  // host columns with device offsets: fetch the total first
+      uint32_t t = 0;
+      EBIC_CUDA(cudaMemcpyAsync(&t, offsets + n_cand, 4, cudaMemcpyDeviceToHost, s));
+      EBIC_CUDA(cudaStreamSynchronize(s));
+      n = t;
+    }
+    EBIC_CUDA(to_device(cols, n, dev, sc, &dcols));
+  }
+  bool counts_host = false, bitmaps_host = false;
+  uint32_t* dcounts = nullptr;
+  uint32_t* dbitmaps = nullptr;
+  EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
+  if (bitmaps)
+    EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbitmaps, &bitmaps_host));
+
+  EBIC_CUDA(launch_prepare(dcols, doffs, n_cand, L.cols, !host_lists, dcounts, n_cand, err,
+                           m->status, s));
+  a.n_cand = n_cand;
+  a.cand_cols = dcols;
+  a.cand_offsets = doffs;
+  a.counts = dcounts;
+  a.bitmaps = dbitmaps;
+  a.err = err;
+  a.err_out = err;
+  a.status = m->status;
+  EvalConfig cfg;
+  cfg.width = L.width;
+  cfg.vec = L.vec;
+  cfg.ts = ts;
+  cfg.negative = (flags & EBIC_NEGATIVE_TRENDS) != 0;
+  cfg.bitmaps = dbitmaps != nullptr;
+  cfg.grid = m->num_sms;
+  EBIC_CUDA(launch_eval(cfg, tmap, a, s));
+
+  if (counts_host || bitmaps_host) {
+    if (counts_host)
+      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
+    if (bitmaps_host)
+      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbitmaps, (size_t)n_cand * L.words * 4,
+                                cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_eval_population");
+  }
+  return EBIC_OK;
+}
+
+int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                 uint32_t n_cand, const uint32_t* counts, const uint32_t* bitmaps,
+                 const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                 const uint32_t* arch_bitmaps, uint32_t n_arch, uint32_t flags,
+                 uint64_t* fitness, uint32_t* overlaps, void* stream) {
+  ebic_matrix* m = const_cast<ebic_matrix*>(cm);
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (flags != 0) return fail(EBIC_ERR_INVALID_ARG, "flags is reserved (pass 0)");
+  if (n_cand == 0) return EBIC_OK;
+  if (!cols || !offsets || !counts || !bitmaps || !fitness)
+    return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  if (n_arch > 0 && (!arch_cols || !arch_offsets || !arch_bitmaps))
+    return fail(EBIC_ERR_INVALID_ARG, "NULL archive argument");
+  DeviceGuard g(m->device);
+  const int dev = m->device;
+  const Layout& L = m->L;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
+                        (const void*)bitmaps, (const void*)arch_cols, (const void*)arch_offsets,
+                        (const void*)arch_bitmaps, (const void*)fitness, (const void*)overlaps})
+    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+
+  const bool host_c = !on_device(cols, dev) && !on_device(offsets, dev);
+  if (host_c) {
+    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+  }
+  const bool host_a = n_arch == 0 || (!on_device(arch_cols, dev) && !on_device(arch_offsets, dev));
+  if (n_arch > 0 && host_a) {
+    std::string why = check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
+  }
+  if ((!host_c && !on_device(cols, dev)) || (!host_c && !on_device(offsets, dev)) ||
+      (n_arch > 0 && !host_a && (!on_device(arch_cols, dev) || !on_device(arch_offsets, dev))))
+    return fail(EBIC_ERR_INVALID_ARG,
+                "a candidate list must have its columns and offsets in the same memory");
+
+  Scratch sc(s);
+  uint32_t* err = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
+  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  const uint16_t *dcols = nullptr, *dacols = nullptr;
+  const uint32_t *doffs = nullptr, *daoffs = nullptr, *dcounts = nullptr, *dbm = nullptr,
+                 *dabm = nullptr;
+  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
+  EBIC_CUDA(to_device(cols, host_c ? (size_t)offsets[n_cand] : 0, dev, sc, &dcols));
+  EBIC_CUDA(to_device(counts, n_cand, dev, sc, &dcounts));
+  EBIC_CUDA(to_device(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm));
+  if (n_arch > 0) {
+    EBIC_CUDA(to_device(arch_offsets, (size_t)n_arch + 1, dev, sc, &daoffs));
+    EBIC_CUDA(to_device(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, dev, sc, &dacols));
+    EBIC_CUDA(to_device(arch_bitmaps, (size_t)n_arch * L.words, dev, sc, &dabm));
+  }
+  bool fit_host = false, ov_host = false;
+  uint64_t* dfit = nullptr;
+  uint32_t* dov = nullptr;
+  EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
+  const size_t n_ov = (size_t)n_cand * n_arch;
+  if (n_arch > 0) {
+    if (overlaps) {
+      EBIC_CUDA(out_buffer(overlaps, n_ov, dev, sc, &dov, &ov_host));
+    } else {
+      EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), n_ov * sizeof(uint32_t)));
+    }
+  }
+  EBIC_CUDA(launch_prepare(dcols, doffs, n_cand, L.cols, !host_c, dov, n_ov, err, m->status, s));
+  if (n_arch > 0)
+    EBIC_CUDA(launch_prepare(dacols, daoffs, n_arch, L.cols, !host_a, nullptr, 0, err, m->status,
+                             s));
+  EBIC_CUDA(launch_overlap(dbm, n_cand, dabm, n_arch, L.words, dov, err, m->num_sms, s));
+  EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
+                                    L.cols, dfit, err, s));
+  if (fit_host || ov_host) {
+    if (fit_host)
+      EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
+    if (ov_host)
+      EBIC_CUDA(cudaMemcpyAsync(overlaps, dov, n_ov * 4, cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_fitness");
+  }
+  return EBIC_OK;
+}
+
+int ebic_matrix_status(ebic_matrix* m, void* stream) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  DeviceGuard g(m->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t bits = 0;
+  EBIC_CUDA(cudaStreamSynchronize(s));
+  EBIC_CUDA(cudaMemcpy(&bits, m->status, 4, cudaMemcpyDeviceToHost));
+  EBIC_CUDA(cudaMemset(m->status, 0, 4));
+  return status_code(bits, "deferred device status");
+}
+
+int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (tile_slabs != 0 && tile_slabs != 1 && tile_slabs != 2 && tile_slabs != 4)
+    return fail(EBIC_ERR_INVALID_ARG, "tile_slabs must be 0, 1, 2 or 4");
+  if (tile_slabs != 0) {
+    int nb = (m->L.cols + 255) / 256, cb = (m->L.cols + nb - 1) / nb;
+    if ((int64_t)nb * cb * tile_slabs * 128 * m->L.vec > kStageMax)
+      return fail(EBIC_ERR_UNSUPPORTED, "tile does not fit in shared memory for this matrix");
+  }
+  m->tile = tile_slabs;
+  return EBIC_OK;
+}
+
+int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  int ts = m->tile ? m->tile : default_tile_slabs(m->L);
+  while (ts > 1 && ts > m->L.slabs) ts >>= 1;
+  if (tile_slabs) *tile_slabs = ts;
+  if (rows_per_slab) *rows_per_slab = (int32_t)m->L.rows_per_slab();
+  return EBIC_OK;
+}
+
+}  // extern "C"

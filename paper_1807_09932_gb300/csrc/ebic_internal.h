@@ -1,0 +1,122 @@
+// Internal declarations of the EBIC GB300 library (not part of the public ABI).
+//
+// Rank-matrix layout in HBM (built once per matrix by the rank transform):
+//   Ranks are dense per-row ranks, stored in WIDTH = 8 bits (cols <= 127) or 16 bits. A 32-bit
+//   "lane word" packs 32/WIDTH rows of one column: byte/half k of the word of lane l in row
+//   group g holds row g*RPG + 32*k + l, where RPG = 32 * (32/WIDTH) rows per group (128 or 64).
+//   VEC consecutive groups form a slab. The matrix is stored column-major over slabs:
+//       word(c, q, l, j) = ((c * Q + q) * 32 + l) * VEC + j,   group g = q * VEC + j
+//   so that one 16-byte load per lane (VEC = 4) fetches four groups of one column, and a 3-D
+//   TMA box {32*VEC words, TS slabs, columns} lands in shared memory column-major with the TS
+//   slabs of one column contiguous.
+//   Rows past the end (padding of the last slab) hold the sentinel in every column.
+//   The sentinel S = 2^(WIDTH-1) - 1 (0x7F or 0x7FFF) marks a missing value; every real rank is
+//   at most cols - 1 <= S - 1, so the top bit of every field is always 0, which the SWAR
+//   compare in the evaluator relies on.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace ebic {
+
+constexpr int kMaxCols = 832;
+constexpr int kMaxLen = 64;
+constexpr int kEvalThreads = 512;  // 16 warps, one CTA per SM
+constexpr int kEvalWarps = kEvalThreads / 32;
+constexpr int kSmemLimit = 232448;            // 227 KB shared memory per CTA (static + dynamic)
+constexpr int kSmemDynMax = kSmemLimit - 2048;  // dynamic part: room for the kernels' static smem
+constexpr int kStageMax = 104 * 1024;         // per pipeline stage (two stages)
+constexpr int kMaxChunkCols = 16384;
+
+// error bits written by kernels into the per-call error word and the matrix status word
+constexpr uint32_t kErrInvalid = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+struct Layout {
+  int32_t width = 8;         // bits per stored rank: 8 or 16
+  int32_t vec = 4;           // groups per slab: 4, 2 or 1
+  int32_t rows_per_group = 128;
+  int32_t words_per_group = 4;  // bitmap words produced by one group
+  int64_t rows = 0;
+  int32_t cols = 0;
+  int64_t groups = 0;        // ceil(rows / rows_per_group), padded up to a whole slab
+  int64_t slabs = 0;         // Q
+  int64_t words = 0;         // W = ceil(rows / 32)
+  uint32_t sentinel = 0x7F;
+  size_t rank_words() const { return (size_t)cols * (size_t)slabs * 32u * (size_t)vec; }
+  int64_t rows_per_slab() const { return (int64_t)rows_per_group * vec; }
+  int64_t words_per_slab() const { return (int64_t)words_per_group * vec; }
+  size_t slab_col_bytes() const { return 128u * (size_t)vec; }  // one column of one slab
+};
+
+// Choose width and VEC for a column count (host).
+Layout make_layout(int64_t rows, int32_t cols);
+
+// ---- rank transform ------------------------------------------------------------------------
+cudaError_t launch_rank_transform(const Layout& L, const float* dX, int64_t ld, int exclude,
+                                  float fill, uint32_t* ranks, cudaStream_t s);
+
+// ---- population preparation (device-side checks, zeroing) ----------------------------------
+// check_offsets: offsets form a CSR list of n candidates of length 1..64 starting at 0.
+// check_columns: (only when err == 0) columns < cols and distinct within a candidate.
+// zero: if non-null, zero[i] = 0 for i < n_zero.
+cudaError_t launch_prepare(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                           int32_t ncols, bool check, uint32_t* zero, size_t n_zero,
+                           uint32_t* err, uint32_t* status, cudaStream_t s);
+
+// ---- population evaluator ------------------------------------------------------------------
+struct EvalArgs {
+  int32_t cols = 0;          // matrix columns
+  int64_t slabs = 0;         // Q
+  int64_t groups = 0;        // groups incl. slab padding (Q * VEC)
+  int64_t words = 0;         // W
+  uint32_t n_cand = 0;
+  const uint16_t* cand_cols = nullptr;     // device CSR
+  const uint32_t* cand_offsets = nullptr;  // device CSR
+  uint32_t* counts = nullptr;              // device, zeroed before the launch
+  uint32_t* bitmaps = nullptr;             // device [n_cand][W] or null
+  int32_t chunk_cols = 0;    // CC: candidate columns staged per chunk
+  int32_t col_box = 0;       // columns per TMA box
+  int32_t n_col_boxes = 0;
+  uint32_t stage_bytes = 0;  // bytes of one pipeline stage
+  uint32_t smem_bytes = 0;   // dynamic shared memory of the launch
+  const uint32_t* err = nullptr;  // per-call error word: non-zero -> do nothing
+  uint32_t* err_out = nullptr;    // where a timeout is reported (per call)
+  uint32_t* status = nullptr;     // matrix status word
+  uint64_t timeout_ns = 1000000000ull;
+};
+
+struct EvalConfig {
+  int width = 8, vec = 4, ts = 1;
+  bool negative = false, bitmaps = true;
+  int grid = 0;
+};
+
+// Tile choice and shared-memory plan for a matrix layout (host).
+int default_tile_slabs(const Layout& L);
+bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint, int grid,
+               EvalArgs* a);
+
+cudaError_t launch_eval(const EvalConfig& cfg, const CUtensorMap* tmap, const EvalArgs& a,
+                        cudaStream_t s);
+// one translation unit per rank layout (width, VEC)
+cudaError_t launch_eval_w8v4(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_w16v4(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_w16v2(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
+cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
+
+// ---- fitness -------------------------------------------------------------------------------
+cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,
+                           uint32_t n_arch, int64_t words, uint32_t* overlaps, const uint32_t* err,
+                           int num_sms, cudaStream_t s);
+cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offsets, uint32_t n_cand,
+                                    const uint32_t* counts, const uint16_t* arch_cols,
+                                    const uint32_t* arch_offsets, uint32_t n_arch,
+                                    const uint32_t* overlaps, int32_t ncols, uint64_t* fitness,
+                                    const uint32_t* err, cudaStream_t s);
+
+}  // namespace ebic

@@ -1,0 +1,302 @@
+// Population evaluator: scores every candidate of a population against every row.
+//
+// What it computes (arXiv 1807.09932, Methods, "Handling missing values"): a row follows a
+// candidate (c_1..c_L) when its values satisfy the "greater or equal" relation along the
+// candidate's column order; a row with a missing value in one of those columns no longer counts
+// when exclusion is on; with the negative-trend option a non-increasing row also follows. The
+// output is each candidate's matched-row count and, optionally, its row bitmap.
+//
+// How (GB300): the rank matrix (see ebic_internal.h for its layout) is streamed through shared
+// memory in row tiles of TS slabs by a 2-stage TMA pipeline (one elected thread issues 3-D
+// cp.async.bulk.tensor loads that complete on an mbarrier; every wait is bounded by the global
+// timer). One CTA per SM is persistent over a contiguous range of work items (candidate chunk,
+// row tile); the candidate chunk's column lists are staged in shared memory. Each warp takes one
+// candidate at a time and checks all TS*VEC row groups of the tile:
+//   * lane l loads one 32-bit word per group and column: 4 rows (8-bit ranks) or 2 rows
+//     (16-bit ranks) of the column, as one 16-byte shared load for four groups (VEC = 4);
+//   * packed-field compare without unpacking: every field is < 2^(WIDTH-1), so
+//     (b | H) - a == b + H - a has no borrow between fields and its top field bit is set
+//     exactly when b >= a (H = the top bit of every field). AND-ing these words along the
+//     chain leaves the top bit of a field set iff that row is non-decreasing along the order;
+//   * exclusion by sentinel: a missing value has the largest code S. A non-decreasing chain that
+//     contains S ends in S, a non-increasing one starts with S, so requiring
+//     last <= S-1 (increasing) and S-1 >= first (decreasing) removes exactly the rows with a
+//     missing value among the candidate's columns; padded rows hold S and never match;
+//   * one __ballot_sync per 32 rows turns the top bits into LSB-first bitmap words; the words
+//     are staged in shared memory and written to HBM as one coalesced run per candidate and
+//     tile; counts are __popc of those words, summed with a warp reduction and one atomicAdd
+//     per candidate and tile.
+#pragma once
+
+#include "device_common.cuh"
+#include "ebic_internal.h"
+
+namespace ebic {
+
+template <int WIDTH>
+struct Swar;
+template <>
+struct Swar<8> {
+  static constexpr uint32_t H = 0x80808080u;       // top bit of each 8-bit field
+  static constexpr uint32_t SP_H = 0xFEFEFEFEu;    // (S-1) + H per field, S = 0x7F
+  static constexpr int WPG = 4;                    // bitmap words per 128-row group
+};
+template <>
+struct Swar<16> {
+  static constexpr uint32_t H = 0x80008000u;
+  static constexpr uint32_t SP_H = 0xFFFEFFFEu;    // (S-1) + H per field, S = 0x7FFF
+  static constexpr int WPG = 2;                    // bitmap words per 64-row group
+};
+
+template <int VEC>
+__device__ __forceinline__ void load_vec(const uint8_t* p, uint32_t* out) {
+  if constexpr (VEC == 4) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else if constexpr (VEC == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    out[0] = v.x; out[1] = v.y;
+  } else {
+    out[0] = *reinterpret_cast<const uint32_t*>(p);
+  }
+}
+
+// The lane's TS*VEC words of one column of the staged tile.
+template <int VEC, int TS>
+__device__ __forceinline__ void load_col(const uint8_t* colbase, uint32_t (&v)[TS * VEC]) {
+#pragma unroll
+  for (int s = 0; s < TS; ++s) load_vec<VEC>(colbase + s * 128 * VEC, v + s * VEC);
+}
+
+// Trend masks of one candidate for the lane's rows of the tile: the top bit of each field of
+// m[g] is set iff that row follows the candidate (increasing, or decreasing when NEG).
+template <int WIDTH, int VEC, int TS, bool NEG>
+__device__ __forceinline__ void trend_masks(const uint8_t* lane_base, uint32_t col_stride,
+                                            const uint16_t* ccols, int L,
+                                            uint32_t (&m)[TS * VEC]) {
+  constexpr int GT = TS * VEC;
+  constexpr uint32_t H = Swar<WIDTH>::H;
+  constexpr uint32_t SP_H = Swar<WIDTH>::SP_H;
+  uint32_t prev[GT], acc[GT], accd[GT];
+  load_col<VEC, TS>(lane_base + (uint32_t)ccols[0] * col_stride, prev);
+#pragma unroll
+  for (int g = 0; g < GT; ++g) {
+    acc[g] = 0xFFFFFFFFu;
+    if (NEG) accd[g] = SP_H - prev[g];  // S-1 >= first: no missing value at the chain's head
+  }
+#pragma unroll 2
+  for (int i = 1; i < L; ++i) {
+    uint32_t cur[GT];
+    load_col<VEC, TS>(lane_base + (uint32_t)ccols[i] * col_stride, cur);
+#pragma unroll
+    for (int g = 0; g < GT; ++g) {
+      acc[g] &= cur[g] + H - prev[g];              // cur >= prev in every field's top bit
+      if (NEG) accd[g] &= prev[g] + H - cur[g];    // prev >= cur
+      prev[g] = cur[g];
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < GT; ++g) {
+    acc[g] &= SP_H - prev[g];  // last <= S-1: no missing value at the chain's tail
+    m[g] = (NEG ? (acc[g] | accd[g]) : acc[g]) & H;
+  }
+}
+
+// Bitmap words of the tile for one candidate: word (g * WPG + k) holds rows
+// g*RPG + 32k + lane, i.e. the tile's words in global LSB-first order.
+template <int WIDTH, int GT>
+__device__ __forceinline__ void ballots_to_smem(const uint32_t (&m)[GT], uint32_t* wb, int lane) {
+#pragma unroll
+  for (int g = 0; g < GT; ++g) {
+    if constexpr (WIDTH == 8) {
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00000080u);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00008000u);
+      const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00800000u);
+      const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x80000000u);
+      if (lane == 0) *reinterpret_cast<uint4*>(wb + 4 * g) = make_uint4(b0, b1, b2, b3);
+    } else {
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00008000u);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x80000000u);
+      if (lane == 0) *reinterpret_cast<uint2*>(wb + 2 * g) = make_uint2(b0, b1);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t n, uint64_t v) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if ((uint64_t)a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Shared-memory plan (dynamic): [stage 0][stage 1][warp word buffers][chunk columns][chunk offsets]
+template <int WIDTH, int VEC, int TS, bool NEG, bool BITMAPS>
+__global__ void __launch_bounds__(kEvalThreads, 1)
+    eval_population_kernel(const __grid_constant__ CUtensorMap tmap, const EvalArgs a) {
+  constexpr int GT = TS * VEC;
+  constexpr int WPT = GT * Swar<WIDTH>::WPG;  // bitmap words per tile
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full_bar[2];
+  __shared__ uint32_t chunk_info[3];
+
+  if (*reinterpret_cast<const volatile uint32_t*>(a.err) != 0) return;  // invalid input
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t total = a.cand_offsets[a.n_cand];
+  const int64_t n_tiles = (a.slabs + TS - 1) / TS;
+  const int64_t n_chunks = ((int64_t)total + a.chunk_cols - 1) / a.chunk_cols;
+  const int64_t n_items = n_chunks * n_tiles;
+  const int64_t i0 = n_items * blockIdx.x / gridDim.x;
+  const int64_t i1 = n_items * (blockIdx.x + 1) / gridDim.x;
+  if (i0 >= i1) return;
+
+  uint8_t* const stage0 = smem;
+  uint8_t* const stage1 = smem + a.stage_bytes;
+  uint32_t* const wbuf = reinterpret_cast<uint32_t*>(smem + 2 * (size_t)a.stage_bytes) + warp * WPT;
+  uint16_t* const ccols =
+      reinterpret_cast<uint16_t*>(smem + 2 * (size_t)a.stage_bytes + kEvalWarps * WPT * 4);
+  uint16_t* const coffs = ccols + a.chunk_cols + 64;
+  const uint32_t col_stride = TS * 128 * VEC;  // bytes of one column in a stage
+
+  auto issue = [&](int64_t item, int s) {
+    const int64_t tile = item % n_tiles;
+    uint8_t* dst = s ? stage1 : stage0;
+    dev::mbar_arrive_expect_tx(&full_bar[s], a.stage_bytes);
+    for (int b = 0; b < a.n_col_boxes; ++b)
+      dev::tma_load_3d(dst + (size_t)b * a.col_box * col_stride, &tmap, &full_bar[s], 0,
+                       (int32_t)(tile * TS), b * a.col_box);
+  };
+
+  if (tid == 0) {
+    dev::prefetch_tensormap(&tmap);
+    dev::mbar_init(&full_bar[0], 1);
+    dev::mbar_init(&full_bar[1], 1);
+    dev::fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(i0, 0);
+    if (i0 + 1 < i1) issue(i0 + 1, 1);
+  }
+
+  int64_t cur_chunk = -1;
+  uint32_t lo = 0, nc = 0;
+  int64_t it = i0;
+  bool timed_out = false;
+  for (; it < i1; ++it) {
+    const int64_t k = it / n_tiles, tile = it % n_tiles;
+    const int s = (int)((it - i0) & 1);
+    const uint32_t parity = (uint32_t)(((it - i0) >> 1) & 1);
+    if (k != cur_chunk) {
+      // stage the column lists of the candidates whose first column lies in
+      // [k*CC, (k+1)*CC): at most CC candidates and CC+63 columns
+      __syncthreads();
+      if (tid == 0) {
+        const uint32_t l = lower_bound_u32(a.cand_offsets, a.n_cand, (uint64_t)k * a.chunk_cols);
+        const uint32_t h =
+            lower_bound_u32(a.cand_offsets, a.n_cand, (uint64_t)(k + 1) * a.chunk_cols);
+        chunk_info[0] = l;
+        chunk_info[1] = h;
+        chunk_info[2] = a.cand_offsets[l];
+      }
+      __syncthreads();
+      lo = chunk_info[0];
+      const uint32_t hi = chunk_info[1], c0 = chunk_info[2];
+      nc = hi - lo;
+      const uint32_t span = a.cand_offsets[hi] - c0;
+      for (uint32_t i = tid; i < span; i += kEvalThreads) ccols[i] = a.cand_cols[c0 + i];
+      for (uint32_t i = tid; i <= nc; i += kEvalThreads)
+        coffs[i] = (uint16_t)(a.cand_offsets[lo + i] - c0);
+      __syncthreads();
+      cur_chunk = k;
+    }
+
+    const bool ok = dev::mbar_wait_bounded(&full_bar[s], parity, a.timeout_ns);
+    if (!__syncthreads_and(ok)) { timed_out = true; break; }
+
+    const uint8_t* lane_base = (s ? stage1 : stage0) + lane * 4 * VEC;
+    const int64_t word0 = tile * WPT;
+    const int64_t g0 = tile * GT;
+    for (uint32_t ci = warp; ci < nc; ci += kEvalWarps) {
+      const int o = coffs[ci];
+      const int L = coffs[ci + 1] - o;
+      uint32_t m[GT];
+      trend_masks<WIDTH, VEC, TS, NEG>(lane_base, col_stride, ccols + o, L, m);
+      const uint32_t cand = lo + ci;
+      uint32_t cnt = 0;
+      if constexpr (BITMAPS) {
+        ballots_to_smem<WIDTH, GT>(m, wbuf, lane);
+        __syncwarp();
+        uint32_t* out = a.bitmaps + (size_t)cand * (size_t)a.words;
+#pragma unroll
+        for (int j = lane; j < WPT; j += 32) {
+          if (word0 + j < a.words) {
+            const uint32_t w = wbuf[j];
+            out[word0 + j] = w;
+            cnt += __popc(w);
+          }
+        }
+        __syncwarp();
+      } else {
+#pragma unroll
+        for (int g = 0; g < GT; ++g)
+          if (g0 + g < a.groups) cnt += __popc(m[g]);
+      }
+      cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+      if (lane == 0 && cnt) atomicAdd(&a.counts[cand], cnt);
+    }
+    __syncthreads();  // every warp is done with stage s
+    if (tid == 0 && it + 2 < i1) issue(it + 2, s);
+  }
+
+  if (timed_out && tid == 0) {
+    atomicOr(a.err_out, kErrTimeout);
+    atomicOr(a.status, kErrTimeout);
+    // wait, again bounded, for the copies still in flight into this CTA's shared memory
+    const int s = (int)((it - i0) & 1);
+    dev::mbar_wait_bounded(&full_bar[s], (uint32_t)(((it - i0) >> 1) & 1), a.timeout_ns);
+    if (it + 1 < i1)
+      dev::mbar_wait_bounded(&full_bar[s ^ 1], (uint32_t)(((it + 1 - i0) >> 1) & 1),
+                             a.timeout_ns);
+  }
+}
+
+template <int WIDTH, int VEC, int TS, bool NEG, bool BITMAPS>
+cudaError_t launch_eval_variant(int grid, const CUtensorMap* tmap, const EvalArgs& a,
+                                cudaStream_t s) {
+  auto kern = eval_population_kernel<WIDTH, VEC, TS, NEG, BITMAPS>;
+  static bool attr_set = false;  // one attribute call per instantiation and process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemDynMax);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  kern<<<grid, kEvalThreads, a.smem_bytes, s>>>(*tmap, a);
+  return cudaGetLastError();
+}
+
+template <int WIDTH, int VEC, int TS>
+cudaError_t launch_eval_ts(const EvalConfig& c, const CUtensorMap* t, const EvalArgs& a,
+                           cudaStream_t s) {
+  if (c.negative)
+    return c.bitmaps ? launch_eval_variant<WIDTH, VEC, TS, true, true>(c.grid, t, a, s)
+                     : launch_eval_variant<WIDTH, VEC, TS, true, false>(c.grid, t, a, s);
+  return c.bitmaps ? launch_eval_variant<WIDTH, VEC, TS, false, true>(c.grid, t, a, s)
+                   : launch_eval_variant<WIDTH, VEC, TS, false, false>(c.grid, t, a, s);
+}
+
+template <int WIDTH, int VEC>
+cudaError_t launch_eval_layout(const EvalConfig& c, const CUtensorMap* t, const EvalArgs& a,
+                               cudaStream_t s) {
+  switch (c.ts) {
+    case 1: return launch_eval_ts<WIDTH, VEC, 1>(c, t, a, s);
+    case 2: return launch_eval_ts<WIDTH, VEC, 2>(c, t, a, s);
+    case 4: return launch_eval_ts<WIDTH, VEC, 4>(c, t, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ebic

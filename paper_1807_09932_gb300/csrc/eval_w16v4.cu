@@ -1,0 +1,9 @@
+// Evaluator instantiations for 16-bit ranks with 4 row group(s) per slab.
+#include "eval_kernel.cuh"
+
+namespace ebic {
+cudaError_t launch_eval_w16v4(const EvalConfig& c, const CUtensorMap* t, const EvalArgs& a,
+                           cudaStream_t s) {
+  return launch_eval_layout<16, 4>(c, t, a, s);
+}
+}  // namespace ebic

@@ -1,0 +1,245 @@
+"""Python binding of the EBIC GB300 C ABI (``include/ebic.h``): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels. This module converts arguments
+(numpy arrays as host buffers, torch tensors as device buffers, torch streams as cudaStream_t)
+and raises ``EbicError`` on a non-zero status. There is no fallback of any kind: if the compiled
+library is missing, importing this module raises.
+
+The functions keep the C names (``ebic_load_matrix``, ``ebic_eval_population``, ...). ``Matrix``,
+``eval_population`` and ``fitness`` are conveniences over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libebic_gb300.so")
+
+EBIC_OK = 0
+EBIC_ERR_INVALID_ARG = -1
+EBIC_ERR_OOM = -2
+EBIC_ERR_CUDA = -3
+EBIC_ERR_DEVICE_TIMEOUT = -4
+EBIC_ERR_UNSUPPORTED = -5
+EBIC_ERR_NO_DEVICE = -6
+EBIC_EXCLUDE_MISSING = 0x1
+EBIC_NEGATIVE_TRENDS = 0x1
+EBIC_MAX_COLS = 832
+EBIC_MAX_CANDIDATE_LEN = 64
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"the EBIC CUDA library is not built ({LIB_PATH} is missing); "
+                      "run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_I32, _I64, _U32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_lib_load = _sig("ebic_load_matrix", [_P, _I64, _I32, _I64, _U32, ctypes.c_float, _P,
+                                      ctypes.POINTER(_P)])
+_lib_free = _sig("ebic_free_matrix", [_P])
+_lib_info = _sig("ebic_matrix_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                                      ctypes.POINTER(_I64), ctypes.POINTER(_I32)])
+_lib_ranks = _sig("ebic_matrix_ranks", [_P, _P, _P])
+_lib_eval = _sig("ebic_eval_population", [_P, _P, _P, _U32, _U32, _P, _P, _P])
+_lib_fitness = _sig("ebic_fitness", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32, _U32, _P, _P,
+                                     _P])
+_lib_status = _sig("ebic_matrix_status", [_P, _P])
+_lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
+_lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
+_lib_last_error = _sig("ebic_last_error", [], ctypes.c_char_p)
+_lib_version = _sig("ebic_version", [])
+
+
+class EbicError(RuntimeError):
+    def __init__(self, code, where):
+        msg = _lib_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _check(code, where):
+    if code != EBIC_OK:
+        raise EbicError(code, where)
+
+
+def _ptr(x):
+    """Raw address of a numpy array (host) or torch tensor (its device or host memory)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def version():
+    return int(_lib_version())
+
+
+# ---- thin C-named wrappers --------------------------------------------------------------------
+
+def ebic_load_matrix(x, rows, cols, ld, flags, fill_value, stream=None):
+    h = _P()
+    _check(_lib_load(_ptr(x), rows, cols, ld, flags, fill_value, _stream(stream),
+                     ctypes.byref(h)), "ebic_load_matrix")
+    return h
+
+
+def ebic_free_matrix(h):
+    _check(_lib_free(h), "ebic_free_matrix")
+
+
+def ebic_matrix_info(h):
+    r, c, w, b = _I64(), _I32(), _I64(), _I32()
+    _check(_lib_info(h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(w), ctypes.byref(b)),
+           "ebic_matrix_info")
+    return r.value, c.value, w.value, b.value
+
+
+def ebic_matrix_ranks(h, out, stream=None):
+    _check(_lib_ranks(h, _ptr(out), _stream(stream)), "ebic_matrix_ranks")
+
+
+def ebic_eval_population(h, cols, offsets, n_cand, flags, counts, bitmaps, stream=None):
+    return _lib_eval(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(counts), _ptr(bitmaps),
+                     _stream(stream))
+
+
+def ebic_fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offsets,
+                 arch_bitmaps, n_arch, flags, fitness, overlaps, stream=None):
+    return _lib_fitness(h, _ptr(cols), _ptr(offsets), n_cand, _ptr(counts), _ptr(bitmaps),
+                        _ptr(arch_cols), _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, flags,
+                        _ptr(fitness), _ptr(overlaps), _stream(stream))
+
+
+def ebic_matrix_status(h, stream=None):
+    return _lib_status(h, _stream(stream))
+
+
+def ebic_matrix_set_tile(h, tile_slabs):
+    _check(_lib_set_tile(h, tile_slabs), "ebic_matrix_set_tile")
+
+
+def ebic_matrix_get_tile(h):
+    t, r = _I32(), _I32()
+    _check(_lib_get_tile(h, ctypes.byref(t), ctypes.byref(r)), "ebic_matrix_get_tile")
+    return t.value, r.value
+
+
+def ebic_last_error():
+    return _lib_last_error().decode(errors="replace")
+
+
+# ---- conveniences -------------------------------------------------------------------------------
+
+def words(rows):
+    return (rows + 31) // 32
+
+
+class Matrix:
+    """A loaded matrix: its device-resident rank matrix stays on the GPU until ``close()``."""
+
+    def __init__(self, X, *, exclude_missing=True, fill_value=0.0, stream=None):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float32)
+        rows, cols = X.shape
+        flags = EBIC_EXCLUDE_MISSING if exclude_missing else 0
+        self.handle = ebic_load_matrix(X, rows, cols, cols, flags, float(fill_value), stream)
+        self.rows, self.cols, self.words, self.rank_bits = ebic_matrix_info(self.handle)
+        self.exclude_missing = exclude_missing
+
+    def close(self):
+        if self.handle:
+            ebic_free_matrix(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def ranks(self):
+        out = np.zeros((self.rows, self.cols), dtype=np.uint16)
+        ebic_matrix_ranks(self.handle, out)
+        return out
+
+    @property
+    def tile(self):
+        return ebic_matrix_get_tile(self.handle)
+
+    def set_tile(self, tile_slabs):
+        ebic_matrix_set_tile(self.handle, tile_slabs)
+
+    def status(self, stream=None):
+        return ebic_matrix_status(self.handle, stream)
+
+
+def eval_population(m: Matrix, cols, offsets, *, negative=False, want_bitmaps=True, counts=None,
+                    bitmaps=None, stream=None):
+    """Counts and bitmaps. Host numpy inputs give host numpy outputs unless buffers are given."""
+    n = len(offsets) - 1
+    if counts is None:
+        counts = np.zeros(n, dtype=np.uint32)
+    if want_bitmaps and bitmaps is None:
+        bitmaps = np.zeros((n, m.words), dtype=np.uint32)
+    if not want_bitmaps:
+        bitmaps = None
+    rc = ebic_eval_population(m.handle, cols, offsets, n,
+                              EBIC_NEGATIVE_TRENDS if negative else 0, counts, bitmaps, stream)
+    _check(rc, "ebic_eval_population")
+    return counts, bitmaps
+
+
+def fitness(m: Matrix, cols, offsets, counts, bitmaps, arch_cols, arch_offsets, arch_bitmaps, *,
+            fitness_out=None, overlaps=None, want_overlaps=True, stream=None):
+    n = len(offsets) - 1
+    k = len(arch_offsets) - 1
+    if fitness_out is None:
+        fitness_out = np.zeros(n, dtype=np.uint64)
+    if want_overlaps and overlaps is None:
+        overlaps = np.zeros((n, k), dtype=np.uint32)
+    rc = ebic_fitness(m.handle, cols, offsets, n, counts, bitmaps, arch_cols, arch_offsets,
+                      arch_bitmaps, k, 0, fitness_out, overlaps if want_overlaps else None,
+                      stream)
+    _check(rc, "ebic_fitness")
+    return fitness_out, overlaps

@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads and exports every symbol its header declares; host-side
+argument checks work without a GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ebic.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1807_09932_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ebic_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("ebic_load_matrix", "ebic_free_matrix", "ebic_eval_population", "ebic_fitness",
+                 "ebic_matrix_info", "ebic_matrix_ranks", "ebic_matrix_status",
+                 "ebic_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_header(lib):
+    from paper_1807_09932_gb300 import ebic
+    for n in declared_functions():
+        if n in ("ebic_version",):
+            continue
+        assert hasattr(ebic, n), n
+
+
+def test_version(lib):
+    lib.ebic_version.restype = ctypes.c_int
+    assert lib.ebic_version() >> 16 == 1
+
+
+def _last_error(lib):
+    lib.ebic_last_error.restype = ctypes.c_char_p
+    return lib.ebic_last_error().decode()
+
+
+def test_load_rejects_bad_arguments_before_touching_cuda(lib):
+    P = ctypes.c_void_p
+    f = lib.ebic_load_matrix
+    f.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                  ctypes.c_float, P, ctypes.POINTER(P)]
+    x = np.zeros((4, 3), np.float32)
+    h = P()
+    xp = x.ctypes.data
+    assert f(None, 4, 3, 3, 1, 0.0, None, ctypes.byref(h)) == -1
+    assert f(xp, 0, 3, 3, 1, 0.0, None, ctypes.byref(h)) == -1          # rows < 1
+    assert f(xp, 2 ** 31, 3, 3, 1, 0.0, None, ctypes.byref(h)) == -1    # rows > 2^31-1
+    assert f(xp, 4, 0, 3, 1, 0.0, None, ctypes.byref(h)) == -1          # cols < 1
+    assert f(xp, 4, 833, 833, 1, 0.0, None, ctypes.byref(h)) == -5     # beyond the build limit
+    assert f(xp, 4, 3, 2, 1, 0.0, None, ctypes.byref(h)) == -1          # ld < cols
+    assert f(xp, 4, 3, 3, 8, 0.0, None, ctypes.byref(h)) == -1          # unknown flag
+    assert f(xp, 4, 3, 3, 0, float("nan"), None, ctypes.byref(h)) == -1  # NaN fill
+    assert "fill_value" in _last_error(lib)
+    assert f(xp, 4, 3, 3, 1, 0.0, None, None) == -1
+
+
+def test_calls_reject_null_matrix(lib):
+    P = ctypes.c_void_p
+    lib.ebic_eval_population.argtypes = [P, P, P, ctypes.c_uint32, ctypes.c_uint32, P, P, P]
+    assert lib.ebic_eval_population(None, None, None, 1, 0, None, None, None) == -1
+    lib.ebic_matrix_info.argtypes = [P, P, P, P, P]
+    assert lib.ebic_matrix_info(None, None, None, None, None) == -1
+    lib.ebic_free_matrix.argtypes = [P]
+    assert lib.ebic_free_matrix(None) == 0
+
+
+def test_no_device_is_reported_not_crashed(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except Exception:
+        pass
+    P = ctypes.c_void_p
+    f = lib.ebic_load_matrix
+    f.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                  ctypes.c_float, P, ctypes.POINTER(P)]
+    x = np.zeros((4, 3), np.float32)
+    h = P()
+    rc = f(x.ctypes.data, 4, 3, 3, 1, 0.0, None, ctypes.byref(h))
+    assert rc in (-6, -3), rc
+    assert not h.value
