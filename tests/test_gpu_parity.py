@@ -109,10 +109,23 @@ def test_long_candidates_and_many_columns(ebic):
     assert c[5] >= 400
 
 
-@pytest.mark.parametrize("tile", [1, 2, 4])
-def test_tile_choice_never_changes_results(ebic, tile):
-    ds, cols, offs = synth.config3(rows=20000)
-    check_eval(ebic, ds.X, cols[:offs[300]], offs[:301], tile=tile)
+@pytest.mark.parametrize("C,tile", [(50, 1), (50, 2), (50, 4), (100, 1), (100, 2), (150, 1),
+                                    (300, 1), (600, 1)])
+def test_tile_choice_never_changes_results(ebic, tile, C):
+    ds = synth.make_dataset(77 + C, 20011, C, kind="beta", planted=[(2000, 8, False)],
+                            nan_frac=0.01)
+    cols, offs = synth.make_population(78, 300, C, 2, 16)
+    check_eval(ebic, ds.X, cols, offs, tile=tile, negative=True)
+
+
+def test_tile_that_does_not_fit_is_rejected(ebic):
+    X = np.zeros((5000, 64), np.float32)
+    with ebic.Matrix(X) as m:
+        with pytest.raises(ebic.EbicError) as ei:
+            m.set_tile(4)  # 64 columns x 4 slabs x 512 B = 128 KB > one pipeline stage
+        assert ei.value.code == ebic.EBIC_ERR_UNSUPPORTED
+        m.set_tile(2)
+        assert m.tile == (2, 512)
 
 
 def test_rank_export_matches_dense_ranks(ebic):
