@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""EBIC population-evaluation benchmark on GB300.
+
+One step = one EBIC generation's device work on one population: the population evaluator
+(counts and row bitmaps of every candidate on every row) followed by the overlap-penalised
+fitness against a device-resident elite archive, both through the C ABI with device buffers.
+The workload is the methylation-shaped matrix (436,444 x 64 Beta(0.5,0.5), 10 planted trend
+biclusters, 0.5% NaN, missing-value exclusion on) with populations of 1,600 candidates of 2-16
+columns (the paper's converging population size, Methods, "Support for Big Data") and an archive
+of 20 biclusters. The rank transform runs once per matrix and is reported separately.
+
+Metric: candidate-row evals/s (one eval = one candidate checked against one row, any length).
+Inputs are resident in HBM when the timed region starts; L2 is flushed (512 MB write) between
+timed steps outside the timed events. ``e2e`` repeats the step through the same public calls
+with the population in pinned host memory and the fitness read back to pinned host memory.
+
+Under torchrun every rank runs the same workload on its own GPU (replicas, no collective on the
+data path); the value is all ranks' evals divided by the slowest rank's time.
+
+``--impl reference`` times the plain CPU oracle (test infrastructure) on the host cores, on a
+bounded sample of the same workload: the comparison arm, not a target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("methylation-shaped: float32 436,444 x 64, Beta(0.5,0.5) background, 10 planted trend "
+            "biclusters (5,000-50,000 rows x 5-16 cols), 0.5% NaN, missing-value exclusion on; "
+            "population 1,600 candidates of 2-16 cols; elite archive of 20")
+N_POPS = 4          # distinct seeded populations, cycled over the steps
+ARCHIVE = 20
+FLUSH_BYTES = 512 << 20
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=50)
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="target wall time of the oracle's bounded sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload():
+    from paper_1807_09932_gb300 import synth
+    ds, cols, offs = synth.config3()
+    pops = [(cols, offs)]
+    for i in range(1, N_POPS):
+        pops.append(synth.make_population(synth.BASE_SEED + 3 + 1000 + 17 * i, 1600, 64, 2, 16))
+    arch_pool = synth.make_population(synth.BASE_SEED + 3 + 5000, 1600, 64, 2, 16)
+    return ds, pops, arch_pool
+
+
+# ---- clocks during the timed region ----------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None,
+                "reasons": reasons}
+
+
+# ---- the oracle arm / CPU baseline -------------------------------------------------------------
+
+def oracle_sample(ds, pops, arch, target_s):
+    """Time the oracle (eval + fitness) on a bounded sample of candidates over all rows."""
+    import oracle
+    X = ds.X
+    R = X.shape[0]
+    cols, offs = pops[0]
+    acols, aoffs, abm = arch
+    threads = oracle.max_threads()
+
+    def run(n):
+        sc = cols[: offs[n]]
+        so = offs[: n + 1]
+        t = time.perf_counter()
+        c, b = oracle.eval_population(X, sc, so, exclude_missing=True, nthreads=threads)
+        oracle.fitness(R, sc, so, c, b, acols, aoffs, abm, want_overlaps=False,
+                       nthreads=threads)
+        return time.perf_counter() - t
+
+    probe = 32
+    t = run(probe)
+    n = int(min(1600, max(probe, probe * target_s / max(t, 1e-6))))
+    return n, threads, run
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    ds, pops, arch_pool = make_workload()
+    import oracle
+    X = ds.X
+    R = X.shape[0]
+    # archive: the 20 best candidates of a separate population, by the oracle itself
+    ac, ao = arch_pool
+    cnt, bm = oracle.eval_population(X, ac, ao, exclude_missing=True)
+    arch = _archive_from(ac, ao, cnt, bm)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    n, threads, run = oracle_sample(ds, pops, arch, min(per_step, args.cpu_seconds))
+    for _ in range(args.warmup):
+        run(n)
+    times = [run(n) for _ in range(args.steps)]
+    ms = 1000 * statistics.mean(times)
+    value = n * R / (ms / 1000)
+    line = {"impl": "reference", "metric": "candidate-row evals/s", "value": value,
+            "unit": "candidate-row evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": R, "cols": X.shape[1],
+                       "population": 1600, "archive": ARCHIVE,
+                       "sample_candidates_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "candidate-row evals/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{n} of 1,600 candidates x all {R} rows per step "
+                                       "(evaluation + fitness vs 20-member archive)"},
+            "e2e": {"value": value, "unit": "candidate-row evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def _archive_from(cols, offs, counts, bitmaps, k=ARCHIVE):
+    """The k candidates with the most rows (ties by index): a stand-in elite archive."""
+    from paper_1807_09932_gb300 import synth
+    order = np.lexsort((np.arange(len(counts)), -counts.astype(np.int64)))[:k]
+    acand = [list(cols[offs[i]:offs[i + 1]]) for i in order]
+    acols, aoffs = synth.population_from_lists(acand)
+    return acols, aoffs, np.ascontiguousarray(bitmaps[order])
+
+
+# ---- our arm -------------------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1807_09932_gb300 import ebic
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ds, pops, arch_pool = make_workload()
+    X = ds.X
+    R, C = X.shape
+
+    def d(a):
+        view = {np.dtype(np.uint16): np.int16, np.dtype(np.uint32): np.int32}[a.dtype]
+        return torch.from_numpy(np.ascontiguousarray(a).view(view)).to(dev)
+
+    # load: rank transform, timed by the library's own events
+    ebic.ebic_timing_enable(True)
+    Xd = torch.from_numpy(X).to(dev)
+    m = ebic.Matrix(Xd, exclude_missing=True)
+    rank_ms, _ = ebic.ebic_timing_read(ebic.EBIC_TIMING_RANK_TRANSFORM)
+    del Xd
+    P = len(pops[0][1]) - 1
+    W = m.words
+
+    # elite archive: the 20 best of a separate population, evaluated on the GPU
+    ac, ao = arch_pool
+    acnt, abm = ebic.eval_population(m, ac, ao)
+    acols, aoffs, abm = _archive_from(ac, ao, acnt, abm)
+    dacols, daoffs, dabm = d(acols), d(aoffs), d(abm)
+    K = len(aoffs) - 1
+
+    dpops = [(d(c), d(o), len(o) - 1) for c, o in pops]
+    counts = torch.empty(P, dtype=torch.int32, device=dev)
+    bitmaps = torch.empty((P, W), dtype=torch.int32, device=dev)
+    fit = torch.empty(P, dtype=torch.int64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    h = m.handle
+    sp = stream.cuda_stream
+
+    def step(i):
+        dc, do, n = dpops[i % N_POPS]
+        rc = ebic.ebic_eval_population(h, dc, do, n, 0, counts, bitmaps, sp)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_eval_population")
+        rc = ebic.ebic_fitness(h, dc, do, n, counts, bitmaps, dacols, daoffs, dabm, K, 0, fit,
+                               None, sp)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_fitness")
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if m.status() != ebic.EBIC_OK:
+        raise SystemExit("device status error after warm-up")
+
+    # ---- timed region: K steps, L2 flushed between steps outside the events ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ebic.ebic_timing_enable(True)
+    launches0 = ebic.ebic_launch_count()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        step(i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = ebic.ebic_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    eval_ms, eval_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_EVALUATE)
+    ov_ms, ov_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_OVERLAP)
+    fin_ms, fin_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_FITNESS)
+    prep_ms, prep_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_PREPARE)
+    ebic.ebic_timing_enable(False)
+    if m.status() != ebic.EBIC_OK:
+        raise SystemExit("device status error in the timed region")
+    my_time = tot_ms / 1000.0
+    if dist:
+        t = torch.tensor([my_time], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        my_time = float(t.item())
+    evals = float(P) * R * args.steps * ws
+    value = evals / my_time
+    ms_per_step = 1000.0 * my_time / args.steps
+
+    # ---- e2e: the same step through the public calls with pinned host inputs/outputs ----
+    e2e = None
+    if args.e2e_steps > 0:
+        hpops = []
+        for c, o in pops:
+            hc = torch.from_numpy(np.ascontiguousarray(c).view(np.int16)).pin_memory()
+            ho = torch.from_numpy(np.ascontiguousarray(o).view(np.int32)).pin_memory()
+            hpops.append((hc, ho, len(o) - 1))
+        hfit = torch.empty(P, dtype=torch.int64).pin_memory()
+        h2d = sum(hc.numel() * 2 + ho.numel() * 4 for hc, ho, _ in hpops) * 2 / N_POPS
+        d2h = P * 8 + 4
+
+        def e2e_step(i):
+            hc, ho, n = hpops[i % N_POPS]
+            rc = ebic.ebic_eval_population(h, hc, ho, n, 0, counts, bitmaps, sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_eval_population")
+            rc = ebic.ebic_fitness(h, hc, ho, n, counts, bitmaps, dacols, daoffs, dabm, K, 0,
+                                   hfit, None, sp)   # host output: synchronizes
+            if rc:
+                raise ebic.EbicError(rc, "ebic_fitness")
+
+        for i in range(3):
+            e2e_step(i)
+        ts = []
+        for i in range(args.e2e_steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step(i)
+            ts.append(time.perf_counter() - t0)
+        et = sum(ts)
+        if dist:
+            t = torch.tensor([et], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": float(P) * R * args.e2e_steps * ws / et,
+               "unit": "candidate-row evals/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * et / args.e2e_steps,
+               "path": "ebic_eval_population + ebic_fitness, population in pinned host memory, "
+                       "fitness read back to pinned host memory"}
+
+    # ---- roofline of the dominant kernel (the evaluator) ----
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    eval_launch_ms = eval_ms / max(eval_n, 1)
+    roof = roofline_eval(pops, R, m, eval_launch_ms, sms, clk, peaks)
+
+    line = {"metric": "candidate-row evals/s", "value": value, "unit": "candidate-row evals/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8" if m.rank_bits == 8 else "u16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": R, "cols": C, "population": P,
+                       "archive": K, "populations_cycled": N_POPS,
+                       "l2": "flushed between timed steps (512 MB write, outside the events)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "rank_bits": m.rank_bits, "tile": list(m.tile)},
+            "roofline": roof,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "kernels_ms_per_step": {"evaluate": eval_ms / args.steps,
+                                    "overlap": ov_ms / args.steps,
+                                    "fitness": fin_ms / args.steps,
+                                    "prepare": prep_ms / args.steps},
+            "rank_transform_ms": rank_ms,
+            "wall_s": wall}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n, threads, run = oracle_sample(ds, pops, (acols, aoffs, abm), args.cpu_seconds)
+        t = run(n)
+        line["cpu_baseline"] = {"value": n * R / t, "unit": "candidate-row evals/s",
+                                "cores": threads, "kind": "oracle",
+                                "sample": f"{n} of 1,600 candidates x all {R} rows "
+                                          "(evaluation + fitness vs 20-member archive), once"}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+
+
+def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
+    """The evaluator against its binding on-chip roof.
+
+    Algorithmic work per launch: every candidate column is one packed-field compare per row,
+    i.e. sum_c L_c * R field compares, done 32/rank_bits rows per 32-bit ALU lane-op; and the
+    same sum_c L_c * R * (rank_bits/8) bytes read from shared memory. Peaks: 64 INT32 ALU lanes
+    and 128 B of shared-memory bandwidth per SM per clock, times the SM count and the median SM
+    clock measured during the timed region (the recipe's unit counts; the HBM figure is the
+    measured copy bandwidth).
+    """
+    sum_l = float(np.mean([int(o[-1]) for _, o in pops]))
+    bytes_per_rank = m.rank_bits / 8
+    fields_per_word = 32 // m.rank_bits
+    clock_hz = (clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0) * 1e6
+    t = launch_ms / 1000.0
+    lane_ops = sum_l * R / fields_per_word          # compares, 32-bit lane ops
+    alu_peak = 64 * sms * clock_hz                   # lane ops / s
+    smem_bytes = sum_l * R * bytes_per_rank
+    smem_peak = 128 * sms * clock_hz
+    hbm_bytes = m.cols * R * bytes_per_rank + 1600 * m.words * 4
+    return {"bound": "alu", "achieved": lane_ops / t / 1e9, "peak": alu_peak / 1e9,
+            "unit": "Gop/s", "frac": (lane_ops / t) / alu_peak, "traffic": None,
+            "kernel": "eval_population_kernel", "launch_ms": launch_ms,
+            "algorithmic_ops_per_launch": lane_ops,
+            "smem": {"achieved_gbs": smem_bytes / t / 1e9, "peak_gbs": smem_peak / 1e9,
+                     "frac": smem_bytes / t / smem_peak},
+            "hbm": {"algorithmic_bytes": hbm_bytes, "achieved_gbs": hbm_bytes / t / 1e9,
+                    "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": (hbm_bytes / t / 1e9) / peaks["hbm_gbs"] if "hbm_gbs" in peaks
+                    else None},
+            "peak_basis": "64 INT32 lanes/SM/clk x SMs x median SM clock in the timed region"}
+
+
+if __name__ == "__main__":
+    main()

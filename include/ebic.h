@@ -159,6 +159,23 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
 /* The tile height in slabs that the next evaluation will use, and the rows per slab. */
 int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab);
 
+/* ---- diagnostics ----------------------------------------------------------------------- */
+/* Kernels launched by this library in this process so far (every launch is counted). */
+int64_t ebic_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded on the stream of each launch, around the
+ * library's own kernel launches. Kinds: */
+#define EBIC_TIMING_RANK_TRANSFORM 0
+#define EBIC_TIMING_PREPARE        1  /* device-side argument checks and output zeroing */
+#define EBIC_TIMING_EVALUATE       2  /* the population evaluator */
+#define EBIC_TIMING_OVERLAP        3  /* bitmap overlaps against the archive */
+#define EBIC_TIMING_FITNESS        4  /* penalised fitness */
+#define EBIC_TIMING_KINDS          5
+/* Enable (1) or disable (0) recording. Either way, the events recorded so far are dropped. */
+int ebic_timing_enable(int on);
+/* Wait for the recorded events of `kind` and return their summed duration and count. */
+int ebic_timing_read(int kind, double* total_ms, int64_t* launches);
+
 /* Message for the calling thread's last failed call ("" if none). Valid until the next call. */
 const char* ebic_last_error(void);
 

@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -194,6 +195,46 @@ int get_tmap(ebic_matrix* m, int ts, int col_box, const CUtensorMap** out) {
   return EBIC_OK;
 }
 
+// ---- diagnostics: launch counter and per-kernel CUDA-event timing --------------------------
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_timing{false};
+std::mutex g_timing_mu;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timed[EBIC_TIMING_KINDS];
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Records a start event before and an end event after the launches in its scope, on the
+// stream they are launched on, when timing is enabled.
+struct Timed {
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Timed(int k, cudaStream_t st) : kind(k), s(st) {
+    if (g_timing.load(std::memory_order_relaxed)) {
+      a = take_event();
+      if (a && cudaEventRecord(a, s) != cudaSuccess) { (void)cudaGetLastError(); a = nullptr; }
+    }
+  }
+  ~Timed() {
+    if (!a) return;
+    cudaEvent_t b = take_event();
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) { (void)cudaGetLastError(); return; }
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timed[kind].emplace_back(a, b);
+  }
+};
+
 int status_code(uint32_t bits, const char* where) {
   if (bits & kErrTimeout)
     return fail(EBIC_ERR_DEVICE_TIMEOUT, std::string(where) + ": a bounded device wait expired");
@@ -206,6 +247,8 @@ int status_code(uint32_t bits, const char* where) {
 }  // namespace
 
 namespace ebic {
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 Layout make_layout(int64_t rows, int32_t cols) {
   Layout L;
@@ -249,11 +292,9 @@ bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint
   col_boxes(L.cols, &nb, &cb);
   const int64_t col_stride = (int64_t)ts * 128 * L.vec;
   const int64_t stage = (int64_t)nb * cb * col_stride;
-  const int64_t wpt = (int64_t)ts * L.vec * L.words_per_group;
-  const int64_t wbuf = (int64_t)kEvalWarps * wpt * 4;
-  const int64_t left = kSmemDynMax - 2 * stage - wbuf - 256;
-  if (left < 4 * 64 + 256) return false;
-  int64_t cc_max = std::min<int64_t>(kMaxChunkCols, (left - 132) / 4);
+  // chunk buffers: (CC + slack) column slots and (CC + 1) offsets, 2 bytes each
+  const int64_t left = kSmemDynMax - 2 * stage - 2 * (kChunkSlack + 1) - 256;
+  int64_t cc_max = std::min<int64_t>(kMaxChunkCols, left / 4);
   cc_max = cc_max / 64 * 64;
   if (cc_max < 64) return false;
   const int64_t n_tiles = (L.slabs + ts - 1) / ts;
@@ -270,7 +311,8 @@ bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint
   a->col_box = cb;
   a->n_col_boxes = nb;
   a->stage_bytes = (uint32_t)stage;
-  a->smem_bytes = (uint32_t)((2 * stage + wbuf + 2 * (cc + 64) + 2 * (cc + 1) + 15) / 16 * 16);
+  a->smem_bytes =
+      (uint32_t)((2 * stage + 2 * (cc + kChunkSlack) + 2 * (cc + 1) + 15) / 16 * 16);
   return true;
 }
 
@@ -348,8 +390,11 @@ int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uin
       dx = static_cast<const float*>(d);
       dld = cols;
     }
-    e = launch_rank_transform(m->L, dx, dld, (flags & EBIC_EXCLUDE_MISSING) ? 1 : 0, fill_value,
-                              m->ranks, s);
+    {
+      Timed t(EBIC_TIMING_RANK_TRANSFORM, s);
+      e = launch_rank_transform(m->L, dx, dld, (flags & EBIC_EXCLUDE_MISSING) ? 1 : 0,
+                                fill_value, m->ranks, s);
+    }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform launch"));
   }
   e = cudaStreamSynchronize(s);
@@ -461,8 +506,19 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
   if (bitmaps)
     EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbitmaps, &bitmaps_host));
 
-  EBIC_CUDA(launch_prepare(dcols, doffs, n_cand, L.cols, !host_lists, dcounts, n_cand, err,
-                           m->status, s));
+  {
+    Timed t(EBIC_TIMING_PREPARE, s);
+    PrepareArgs pa;
+    pa.cols[0] = dcols;
+    pa.offsets[0] = doffs;
+    pa.n[0] = host_lists ? 0 : n_cand;  // host lists were checked on the host
+    pa.ncols = L.cols;
+    pa.zero = dcounts;
+    pa.n_zero = n_cand;
+    pa.err = err;
+    pa.status = m->status;
+    EBIC_CUDA(launch_prepare(pa, s));
+  }
   a.n_cand = n_cand;
   a.cand_cols = dcols;
   a.cand_offsets = doffs;
@@ -478,7 +534,10 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
   cfg.negative = (flags & EBIC_NEGATIVE_TRENDS) != 0;
   cfg.bitmaps = dbitmaps != nullptr;
   cfg.grid = m->num_sms;
-  EBIC_CUDA(launch_eval(cfg, tmap, a, s));
+  {
+    Timed t(EBIC_TIMING_EVALUATE, s);
+    EBIC_CUDA(launch_eval(cfg, tmap, a, s));
+  }
 
   if (counts_host || bitmaps_host) {
     if (counts_host)
@@ -559,13 +618,31 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
       EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), n_ov * sizeof(uint32_t)));
     }
   }
-  EBIC_CUDA(launch_prepare(dcols, doffs, n_cand, L.cols, !host_c, dov, n_ov, err, m->status, s));
-  if (n_arch > 0)
-    EBIC_CUDA(launch_prepare(dacols, daoffs, n_arch, L.cols, !host_a, nullptr, 0, err, m->status,
-                             s));
-  EBIC_CUDA(launch_overlap(dbm, n_cand, dabm, n_arch, L.words, dov, err, m->num_sms, s));
-  EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
-                                    L.cols, dfit, err, s));
+  {
+    Timed t(EBIC_TIMING_PREPARE, s);
+    PrepareArgs pa;
+    pa.cols[0] = dcols;
+    pa.offsets[0] = doffs;
+    pa.n[0] = host_c ? 0 : n_cand;
+    pa.cols[1] = dacols;
+    pa.offsets[1] = daoffs;
+    pa.n[1] = host_a ? 0 : n_arch;
+    pa.ncols = L.cols;
+    pa.zero = dov;
+    pa.n_zero = n_ov;
+    pa.err = err;
+    pa.status = m->status;
+    EBIC_CUDA(launch_prepare(pa, s));
+  }
+  {
+    Timed t(EBIC_TIMING_OVERLAP, s);
+    EBIC_CUDA(launch_overlap(dbm, n_cand, dabm, n_arch, L.words, dov, err, m->num_sms, s));
+  }
+  {
+    Timed t(EBIC_TIMING_FITNESS, s);
+    EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
+                                      L.cols, dfit, err, s));
+  }
   if (fit_host || ov_host) {
     if (fit_host)
       EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
@@ -588,6 +665,40 @@ int ebic_matrix_status(ebic_matrix* m, void* stream) {
   EBIC_CUDA(cudaMemcpy(&bits, m->status, 4, cudaMemcpyDeviceToHost));
   EBIC_CUDA(cudaMemset(m->status, 0, 4));
   return status_code(bits, "deferred device status");
+}
+
+int64_t ebic_launch_count(void) { return g_launches.load(); }
+
+int ebic_timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (auto& v : g_timed)
+    for (auto& pr : v) {
+      g_event_pool.push_back(pr.first);
+      g_event_pool.push_back(pr.second);
+    }
+  for (auto& v : g_timed) v.clear();
+  g_timing.store(on != 0);
+  return EBIC_OK;
+}
+
+int ebic_timing_read(int kind, double* total_ms, int64_t* launches) {
+  if (kind < 0 || kind >= EBIC_TIMING_KINDS || !total_ms || !launches)
+    return fail(EBIC_ERR_INVALID_ARG, "bad timing kind or NULL output");
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> v;
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    v = g_timed[kind];
+  }
+  double tot = 0;
+  for (auto& pr : v) {
+    EBIC_CUDA(cudaEventSynchronize(pr.second));
+    float ms = 0;
+    EBIC_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (int64_t)v.size();
+  return EBIC_OK;
 }
 
 int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs) {

@@ -25,12 +25,11 @@ namespace ebic {
 
 constexpr int kMaxCols = 832;
 constexpr int kMaxLen = 64;
-constexpr int kEvalThreads = 512;  // 16 warps, one CTA per SM
-constexpr int kEvalWarps = kEvalThreads / 32;
 constexpr int kSmemLimit = 232448;            // 227 KB shared memory per CTA (static + dynamic)
 constexpr int kSmemDynMax = kSmemLimit - 2048;  // dynamic part: room for the kernels' static smem
 constexpr int kStageMax = 104 * 1024;         // per pipeline stage (two stages)
 constexpr int kMaxChunkCols = 16384;
+constexpr int kChunkSlack = 72;  // spare column slots past a chunk (candidate tail + prefetch)
 
 // error bits written by kernels into the per-call error word and the matrix status word
 constexpr uint32_t kErrInvalid = 1u;
@@ -53,6 +52,9 @@ struct Layout {
   size_t slab_col_bytes() const { return 128u * (size_t)vec; }  // one column of one slab
 };
 
+// Diagnostics: every kernel launch of the library is counted (defined in capi.cpp).
+void count_launch();
+
 // Choose width and VEC for a column count (host).
 Layout make_layout(int64_t rows, int32_t cols);
 
@@ -60,13 +62,20 @@ Layout make_layout(int64_t rows, int32_t cols);
 cudaError_t launch_rank_transform(const Layout& L, const float* dX, int64_t ld, int exclude,
                                   float fill, uint32_t* ranks, cudaStream_t s);
 
-// ---- population preparation (device-side checks, zeroing) ----------------------------------
-// check_offsets: offsets form a CSR list of n candidates of length 1..64 starting at 0.
-// check_columns: (only when err == 0) columns < cols and distinct within a candidate.
-// zero: if non-null, zero[i] = 0 for i < n_zero.
-cudaError_t launch_prepare(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
-                           int32_t ncols, bool check, uint32_t* zero, size_t n_zero,
-                           uint32_t* err, uint32_t* status, cudaStream_t s);
+// ---- population preparation (device-side argument checks, zeroing) ----------------------------
+// One launch checks up to two CSR candidate lists (n[l] == 0 skips list l) against ncols and
+// zeroes zero[0 .. n_zero). A failed check ORs kErrInvalid into *err and *status.
+struct PrepareArgs {
+  const uint16_t* cols[2] = {nullptr, nullptr};
+  const uint32_t* offsets[2] = {nullptr, nullptr};
+  uint32_t n[2] = {0, 0};
+  int32_t ncols = 0;
+  uint32_t* zero = nullptr;
+  size_t n_zero = 0;
+  uint32_t* err = nullptr;
+  uint32_t* status = nullptr;
+};
+cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s);
 
 // ---- population evaluator ------------------------------------------------------------------
 struct EvalArgs {

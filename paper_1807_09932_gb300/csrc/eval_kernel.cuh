@@ -22,10 +22,11 @@
 //     contains S ends in S, a non-increasing one starts with S, so requiring
 //     last <= S-1 (increasing) and S-1 >= first (decreasing) removes exactly the rows with a
 //     missing value among the candidate's columns; padded rows hold S and never match;
-//   * one __ballot_sync per 32 rows turns the top bits into LSB-first bitmap words; the words
-//     are staged in shared memory and written to HBM as one coalesced run per candidate and
-//     tile; counts are __popc of those words, summed with a warp reduction and one atomicAdd
-//     per candidate and tile.
+//   * bitmap words without ballots: each lane gathers the match bits of up to 8 (16) groups into
+//     one word, and a 5-stage shuffle butterfly transposes the warp's 32x32 bit matrix, so that
+//     every lane holds one LSB-first bitmap word; the words of a tile go to HBM as one coalesced
+//     run per candidate; counts are __popc of those words, summed with a warp reduction and one
+//     atomicAdd per candidate and tile.
 #pragma once
 
 #include "device_common.cuh"
@@ -68,57 +69,97 @@ __device__ __forceinline__ void load_col(const uint8_t* colbase, uint32_t (&v)[T
   for (int s = 0; s < TS; ++s) load_vec<VEC>(colbase + s * 128 * VEC, v + s * VEC);
 }
 
-// Trend masks of one candidate for the lane's rows of the tile: the top bit of each field of
-// m[g] is set iff that row follows the candidate (increasing, or decreasing when NEG).
+// Trend accumulators of one candidate for the lane's rows of the tile: on return, the top bit of
+// each field of acc[g] is set iff that row follows the candidate (increasing, or decreasing when
+// NEG); the other bits are don't-care. The chain is walked two columns per iteration so that
+// each pair of compares costs two 3-input adds and one 3-input AND per word.
 template <int WIDTH, int VEC, int TS, bool NEG>
 __device__ __forceinline__ void trend_masks(const uint8_t* lane_base, uint32_t col_stride,
                                             const uint16_t* ccols, int L,
-                                            uint32_t (&m)[TS * VEC]) {
+                                            uint32_t (&acc)[TS * VEC]) {
   constexpr int GT = TS * VEC;
   constexpr uint32_t H = Swar<WIDTH>::H;
   constexpr uint32_t SP_H = Swar<WIDTH>::SP_H;
-  uint32_t prev[GT], acc[GT], accd[GT];
-  load_col<VEC, TS>(lane_base + (uint32_t)ccols[0] * col_stride, prev);
+  uint32_t a[GT], accd[GT];
+  load_col<VEC, TS>(lane_base + (uint32_t)ccols[0] * col_stride, a);
 #pragma unroll
   for (int g = 0; g < GT; ++g) {
     acc[g] = 0xFFFFFFFFu;
-    if (NEG) accd[g] = SP_H - prev[g];  // S-1 >= first: no missing value at the chain's head
+    if (NEG) accd[g] = SP_H - a[g];  // S-1 >= first: no missing value at the chain's head
   }
-#pragma unroll 2
-  for (int i = 1; i < L; ++i) {
-    uint32_t cur[GT];
-    load_col<VEC, TS>(lane_base + (uint32_t)ccols[i] * col_stride, cur);
+  int i = 1;
+  // column indices of the next pair are read one iteration ahead (the chunk buffer has slack
+  // past its last column, so reading two entries beyond a candidate stays inside it)
+  uint32_t nb = ccols[1], nc = ccols[2];
+#pragma unroll 1
+  for (; i + 1 < L; i += 2) {
+    uint32_t b[GT], c[GT];
+    load_col<VEC, TS>(lane_base + nb * col_stride, b);
+    load_col<VEC, TS>(lane_base + nc * col_stride, c);
+    nb = ccols[i + 2];
+    nc = ccols[i + 3];
 #pragma unroll
     for (int g = 0; g < GT; ++g) {
-      acc[g] &= cur[g] + H - prev[g];              // cur >= prev in every field's top bit
-      if (NEG) accd[g] &= prev[g] + H - cur[g];    // prev >= cur
-      prev[g] = cur[g];
+      acc[g] = acc[g] & (b[g] + H - a[g]) & (c[g] + H - b[g]);            // a <= b <= c
+      if (NEG) accd[g] = accd[g] & (a[g] + H - b[g]) & (b[g] + H - c[g]);  // a >= b >= c
+      a[g] = c[g];
+    }
+  }
+  if (i < L) {
+    uint32_t b[GT];
+    load_col<VEC, TS>(lane_base + nb * col_stride, b);
+#pragma unroll
+    for (int g = 0; g < GT; ++g) {
+      acc[g] &= b[g] + H - a[g];
+      if (NEG) accd[g] &= a[g] + H - b[g];
+      a[g] = b[g];
     }
   }
 #pragma unroll
   for (int g = 0; g < GT; ++g) {
-    acc[g] &= SP_H - prev[g];  // last <= S-1: no missing value at the chain's tail
-    m[g] = (NEG ? (acc[g] | accd[g]) : acc[g]) & H;
+    acc[g] &= SP_H - a[g];  // last <= S-1: no missing value at the chain's tail
+    if (NEG) acc[g] |= accd[g];
   }
 }
 
-// Bitmap words of the tile for one candidate: word (g * WPG + k) holds rows
-// g*RPG + 32k + lane, i.e. the tile's words in global LSB-first order.
+// Gather the match bits of up to WIDTH groups into one word per lane: bit (k*WIDTH + gl) is the
+// top bit of field k of acc[b*WIDTH + gl], i.e. row (group b*WIDTH+gl, sub-row k, this lane).
 template <int WIDTH, int GT>
-__device__ __forceinline__ void ballots_to_smem(const uint32_t (&m)[GT], uint32_t* wb, int lane) {
+__device__ __forceinline__ uint32_t pack_block(const uint32_t (&acc)[GT], int b) {
+  constexpr uint32_t LOWF = WIDTH == 8 ? 0x01010101u : 0x00010001u;  // bit 0 of every field
+  uint32_t x = 0;
 #pragma unroll
-  for (int g = 0; g < GT; ++g) {
-    if constexpr (WIDTH == 8) {
-      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00000080u);
-      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00008000u);
-      const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00800000u);
-      const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x80000000u);
-      if (lane == 0) *reinterpret_cast<uint4*>(wb + 4 * g) = make_uint4(b0, b1, b2, b3);
-    } else {
-      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x00008000u);
-      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, m[g] & 0x80000000u);
-      if (lane == 0) *reinterpret_cast<uint2*>(wb + 2 * g) = make_uint2(b0, b1);
-    }
+  for (int gl = 0; gl < WIDTH; ++gl) {
+    const int g = b * WIDTH + gl;
+    if (g < GT) x |= (acc[g] >> (WIDTH - 1 - gl)) & (LOWF << gl);
+  }
+  return x;
+}
+
+// 32x32 bit transpose across the warp: afterwards bit i of lane j is what bit j of lane i was.
+// Five butterfly stages; in stage s the off-diagonal s x s blocks of every 2s x 2s block swap.
+// rot[t] / sel[t] are the lane's rotation amount and bit mask of stage t (transpose_consts).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, const uint32_t (&rot)[5],
+                                                const uint32_t (&sel)[5]) {
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, 16 >> t);
+    const uint32_t r = __funnelshift_l(y, y, rot[t]);  // rotate left
+    x = (x & ~sel[t]) | (r & sel[t]);
+  }
+  return x;
+}
+
+__device__ __forceinline__ void transpose_consts(int lane, uint32_t (&rot)[5],
+                                                 uint32_t (&sel)[5]) {
+  // bits j with (j & s) != 0, for s = 16, 8, 4, 2, 1
+  const uint32_t right[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int s = 16 >> t;
+    const bool top = (lane & s) == 0;  // top lanes take the partner's left bits into the right
+    rot[t] = top ? (uint32_t)s : (uint32_t)(32 - s);
+    sel[t] = top ? right[t] : ~right[t];
   }
 }
 
@@ -131,11 +172,18 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* a, uint32_t 
   return lo;
 }
 
-// Shared-memory plan (dynamic): [stage 0][stage 1][warp word buffers][chunk columns][chunk offsets]
+// Threads per CTA: 32 warps when the variant's registers fit in 64 per thread (more warps hide
+// the shared-memory load latency of the column chain), else 16.
+template <int GT, bool NEG>
+__host__ __device__ constexpr int eval_threads() { return GT * (NEG ? 3 : 2) <= 16 ? 1024 : 512; }
+
+// Shared-memory plan (dynamic): [stage 0][stage 1][chunk columns][chunk offsets]
 template <int WIDTH, int VEC, int TS, bool NEG, bool BITMAPS>
-__global__ void __launch_bounds__(kEvalThreads, 1)
+__global__ void __launch_bounds__(eval_threads<TS * VEC, NEG>(), 1)
     eval_population_kernel(const __grid_constant__ CUtensorMap tmap, const EvalArgs a) {
   constexpr int GT = TS * VEC;
+  constexpr int THREADS = eval_threads<GT, NEG>();
+  constexpr int WARPS = THREADS / 32;
   constexpr int WPT = GT * Swar<WIDTH>::WPG;  // bitmap words per tile
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full_bar[2];
@@ -144,6 +192,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1)
   if (*reinterpret_cast<const volatile uint32_t*>(a.err) != 0) return;  // invalid input
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t trot[5], tsel[5];
+  transpose_consts(lane, trot, tsel);
   const uint32_t total = a.cand_offsets[a.n_cand];
   const int64_t n_tiles = (a.slabs + TS - 1) / TS;
   const int64_t n_chunks = ((int64_t)total + a.chunk_cols - 1) / a.chunk_cols;
@@ -154,10 +204,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1)
 
   uint8_t* const stage0 = smem;
   uint8_t* const stage1 = smem + a.stage_bytes;
-  uint32_t* const wbuf = reinterpret_cast<uint32_t*>(smem + 2 * (size_t)a.stage_bytes) + warp * WPT;
-  uint16_t* const ccols =
-      reinterpret_cast<uint16_t*>(smem + 2 * (size_t)a.stage_bytes + kEvalWarps * WPT * 4);
-  uint16_t* const coffs = ccols + a.chunk_cols + 64;
+  uint16_t* const ccols = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)a.stage_bytes);
+  uint16_t* const coffs = ccols + a.chunk_cols + kChunkSlack;
   const uint32_t col_stride = TS * 128 * VEC;  // bytes of one column in a stage
 
   auto issue = [&](int64_t item, int s) {
@@ -206,8 +254,8 @@ __global__ void __launch_bounds__(kEvalThreads, 1)
       const uint32_t hi = chunk_info[1], c0 = chunk_info[2];
       nc = hi - lo;
       const uint32_t span = a.cand_offsets[hi] - c0;
-      for (uint32_t i = tid; i < span; i += kEvalThreads) ccols[i] = a.cand_cols[c0 + i];
-      for (uint32_t i = tid; i <= nc; i += kEvalThreads)
+      for (uint32_t i = tid; i < span; i += THREADS) ccols[i] = a.cand_cols[c0 + i];
+      for (uint32_t i = tid; i <= nc; i += THREADS)
         coffs[i] = (uint16_t)(a.cand_offsets[lo + i] - c0);
       __syncthreads();
       cur_chunk = k;
@@ -219,30 +267,30 @@ __global__ void __launch_bounds__(kEvalThreads, 1)
     const uint8_t* lane_base = (s ? stage1 : stage0) + lane * 4 * VEC;
     const int64_t word0 = tile * WPT;
     const int64_t g0 = tile * GT;
-    for (uint32_t ci = warp; ci < nc; ci += kEvalWarps) {
+    for (uint32_t ci = warp; ci < nc; ci += WARPS) {
       const int o = coffs[ci];
       const int L = coffs[ci + 1] - o;
-      uint32_t m[GT];
-      trend_masks<WIDTH, VEC, TS, NEG>(lane_base, col_stride, ccols + o, L, m);
+      uint32_t acc[GT];
+      trend_masks<WIDTH, VEC, TS, NEG>(lane_base, col_stride, ccols + o, L, acc);
       const uint32_t cand = lo + ci;
       uint32_t cnt = 0;
       if constexpr (BITMAPS) {
-        ballots_to_smem<WIDTH, GT>(m, wbuf, lane);
-        __syncwarp();
+        // lane j of transpose block b ends up with bitmap word (b*WIDTH + j%WIDTH)*WPG + j/WIDTH
         uint32_t* out = a.bitmaps + (size_t)cand * (size_t)a.words;
 #pragma unroll
-        for (int j = lane; j < WPT; j += 32) {
-          if (word0 + j < a.words) {
-            const uint32_t w = wbuf[j];
-            out[word0 + j] = w;
+        for (int b = 0; b < (GT + WIDTH - 1) / WIDTH; ++b) {
+          const uint32_t w = transpose32(pack_block<WIDTH, GT>(acc, b), trot, tsel);
+          const int g = b * WIDTH + (lane % WIDTH);
+          const int64_t widx = word0 + g * Swar<WIDTH>::WPG + lane / WIDTH;
+          if (g < GT && widx < a.words) {
+            out[widx] = w;
             cnt += __popc(w);
           }
         }
-        __syncwarp();
       } else {
 #pragma unroll
         for (int g = 0; g < GT; ++g)
-          if (g0 + g < a.groups) cnt += __popc(m[g]);
+          if (g0 + g < a.groups) cnt += __popc(acc[g] & Swar<WIDTH>::H);
       }
       cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
       if (lane == 0 && cnt) atomicAdd(&a.counts[cand], cnt);
@@ -274,7 +322,8 @@ cudaError_t launch_eval_variant(int grid, const CUtensorMap* tmap, const EvalArg
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  kern<<<grid, kEvalThreads, a.smem_bytes, s>>>(*tmap, a);
+  count_launch();
+  kern<<<grid, eval_threads<TS * VEC, NEG>(), a.smem_bytes, s>>>(*tmap, a);
   return cudaGetLastError();
 }
 
@@ -288,14 +337,21 @@ cudaError_t launch_eval_ts(const EvalConfig& c, const CUtensorMap* t, const Eval
                    : launch_eval_variant<WIDTH, VEC, TS, false, false>(c.grid, t, a, s);
 }
 
+// 8-bit ranks (<= 127 columns) can stage 1, 2 or 4 slabs per stage; for 16-bit ranks VEC is
+// already chosen so that one slab fills a stage, so only TS = 1 is instantiated.
 template <int WIDTH, int VEC>
 cudaError_t launch_eval_layout(const EvalConfig& c, const CUtensorMap* t, const EvalArgs& a,
                                cudaStream_t s) {
-  switch (c.ts) {
-    case 1: return launch_eval_ts<WIDTH, VEC, 1>(c, t, a, s);
-    case 2: return launch_eval_ts<WIDTH, VEC, 2>(c, t, a, s);
-    case 4: return launch_eval_ts<WIDTH, VEC, 4>(c, t, a, s);
-    default: return cudaErrorInvalidValue;
+  if constexpr (WIDTH == 8) {
+    switch (c.ts) {
+      case 1: return launch_eval_ts<WIDTH, VEC, 1>(c, t, a, s);
+      case 2: return launch_eval_ts<WIDTH, VEC, 2>(c, t, a, s);
+      case 4: return launch_eval_ts<WIDTH, VEC, 4>(c, t, a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    if (c.ts != 1) return cudaErrorInvalidValue;
+    return launch_eval_ts<WIDTH, VEC, 1>(c, t, a, s);
   }
 }
 

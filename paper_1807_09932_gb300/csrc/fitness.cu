@@ -7,72 +7,112 @@
 //   o(c,a) = popcount(M_c & M_a)                           (rows c shares with a)
 //   p_c    = n_c - max{ o(c,a) : c and a share a column }  (0 when there is none)
 //   F_c    = (uint64) p_c << (min(L_c, 33) - 1)
-// The overlap pass streams each candidate bitmap once per archive member out of L1/L2 with
-// 32-bit AND + popc per word and a warp reduction; the finalize pass builds the candidate's
-// column set as a shared-memory bitset and tests each archive member's columns against it.
+// The overlap pass reads every candidate bitmap from HBM once, against archive words staged in
+// shared memory; the finalize pass builds the candidate's column set as a shared-memory bitset and
+// tests each archive member's columns against it.
 #include "ebic_internal.h"
 
 namespace ebic {
 namespace {
 
-// A valid CSR list: offsets[0] == 0, every length in [1, 64].
-__global__ void check_offsets_kernel(const uint32_t* __restrict__ offsets, uint32_t n,
-                                     uint32_t* err, uint32_t* status) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  bool bad = (i == 0 && offsets[0] != 0u);
-  const uint32_t a = offsets[i], b = offsets[i + 1];
-  bad |= b <= a || b - a > (uint32_t)kMaxLen;
-  if (bad) {
-    atomicOr(err, kErrInvalid);
-    if (status) atomicOr(status, kErrInvalid);
-  }
-}
-
-// Columns in range and distinct within each candidate. Runs only after the offsets passed, so
-// every read stays inside cols[0 .. offsets[n]).
-__global__ void check_columns_kernel(const uint16_t* __restrict__ cols,
-                                     const uint32_t* __restrict__ offsets, uint32_t n,
-                                     int32_t ncols, bool check, uint32_t* __restrict__ zero,
-                                     size_t n_zero, uint32_t* err, uint32_t* status) {
+// Device-side check of up to two CSR candidate lists, and zeroing of one output, in one launch.
+// Thread i checks candidate i of each list: offsets[0] == 0, 1 <= L <= 64, the candidate ends
+// at or before offsets[n] (so its columns lie inside cols[0 .. offsets[n]), the caller's
+// buffer), and its columns are < ncols and distinct. Reads stay in bounds whatever the other
+// candidates' offsets are.
+__global__ void prepare_kernel(PrepareArgs a) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (zero && i < n_zero) zero[i] = 0u;
-  if (!check || i >= n) return;
-  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
-  const uint32_t a = offsets[i], L = offsets[i + 1] - a;
+  if (a.zero && i < a.n_zero) a.zero[i] = 0u;
   bool bad = false;
-  for (uint32_t j = 0; j < L; ++j) {
-    const uint16_t c = cols[a + j];
-    bad |= c >= (uint32_t)ncols;
-    for (uint32_t t = 0; t < j; ++t) bad |= cols[a + t] == c;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    if (i >= a.n[l]) continue;
+    const uint32_t* offs = a.offsets[l];
+    const uint32_t total = offs[a.n[l]];
+    const uint32_t lo = offs[i], hi = offs[i + 1];
+    bool b = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
+    if (!b) {
+      const uint16_t* cols = a.cols[l];
+      for (uint32_t j = lo; j < hi; ++j) {
+        const uint16_t c = cols[j];
+        b |= c >= (uint32_t)a.ncols;
+        for (uint32_t t = lo; t < j; ++t) b |= cols[t] == c;
+      }
+    }
+    bad |= b;
   }
   if (bad) {
-    atomicOr(err, kErrInvalid);
-    if (status) atomicOr(status, kErrInvalid);
+    atomicOr(a.err, kErrInvalid);
+    if (a.status) atomicOr(a.status, kErrInvalid);
   }
 }
 
 constexpr int kOverlapWarps = 8;
-constexpr int kWordsPerSegment = 2048;
+constexpr int kOvCPW = 4;                          // candidates per warp (register blocking)
+constexpr int kOvCands = kOverlapWarps * kOvCPW;   // candidates per block
+constexpr int kOvNPL = 8;                          // words per lane per sub-segment
+constexpr int kOvSub = 32 * kOvNPL;                // words per sub-segment (256)
+constexpr int kOvSubs = 2;                         // sub-segments per block (512 words)
+constexpr int kOvArch = 32;                        // archive members staged per pass
 
-// overlaps[c][a] += popcount(M_c & M_a) over the words of this block's segment.
+// overlaps[c][a] += popcount(M_c & M_a) over this block's words, for the block's 32 candidates
+// and every archive member. The archive's words of each 256-word sub-segment are staged in
+// shared memory once per block and read by all warps; each warp keeps 4 candidates' words in
+// registers, so an archive word read from shared memory serves 4 AND+popc. Partial sums live in
+// shared memory per (candidate, member) and reach HBM as one atomicAdd each per block.
 __global__ void __launch_bounds__(kOverlapWarps * 32)
     overlap_kernel(const uint32_t* __restrict__ bitmaps, uint32_t n_cand,
                    const uint32_t* __restrict__ arch, uint32_t n_arch, int64_t W,
-                   int64_t seg_words, uint32_t* __restrict__ overlaps, const uint32_t* err) {
+                   uint32_t* __restrict__ overlaps, const uint32_t* err) {
+  __shared__ uint32_t arch_s[kOvArch][kOvSub];
+  __shared__ uint32_t part_s[kOvCands][kOvArch];
   if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t c = blockIdx.x * kOverlapWarps + warp;
-  if (c >= n_cand) return;
-  const int64_t w0 = (int64_t)blockIdx.y * seg_words;
-  const int64_t w1 = w0 + seg_words < W ? w0 + seg_words : W;
-  const uint32_t* mc = bitmaps + (size_t)c * W;
-  for (uint32_t a = 0; a < n_arch; ++a) {
-    const uint32_t* ma = arch + (size_t)a * W;
-    uint32_t part = 0;
-    for (int64_t w = w0 + lane; w < w1; w += 32) part += __popc(__ldg(mc + w) & __ldg(ma + w));
-    part = __reduce_add_sync(0xFFFFFFFFu, part);
-    if (lane == 0 && part) atomicAdd(&overlaps[(size_t)c * n_arch + a], part);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t c0 = blockIdx.x * kOvCands + warp * kOvCPW;  // this warp's first candidate
+  const int64_t wblk = (int64_t)blockIdx.y * kOvSub * kOvSubs;
+  for (uint32_t a0 = 0; a0 < n_arch; a0 += kOvArch) {
+    const int na = n_arch - a0 < (uint32_t)kOvArch ? (int)(n_arch - a0) : kOvArch;
+    for (int i = tid; i < kOvCands * kOvArch; i += blockDim.x) (&part_s[0][0])[i] = 0u;
+    for (int sub = 0; sub < kOvSubs; ++sub) {
+      const int64_t ws = wblk + (int64_t)sub * kOvSub;
+      if (ws >= W) break;
+      __syncthreads();
+      for (int i = tid; i < na * kOvSub; i += blockDim.x) {
+        const int a = i / kOvSub, w = i % kOvSub;
+        arch_s[a][w] = ws + w < W ? __ldg(arch + (size_t)(a0 + a) * W + ws + w) : 0u;
+      }
+      __syncthreads();
+      uint32_t cw[kOvCPW][kOvNPL];
+#pragma unroll
+      for (int c = 0; c < kOvCPW; ++c)
+#pragma unroll
+        for (int t = 0; t < kOvNPL; ++t) {
+          const int64_t w = ws + lane + 32 * t;
+          cw[c][t] = (c0 + c < n_cand && w < W) ? __ldg(bitmaps + (size_t)(c0 + c) * W + w) : 0u;
+        }
+      for (int a = 0; a < na; ++a) {
+        uint32_t p[kOvCPW] = {};
+#pragma unroll
+        for (int t = 0; t < kOvNPL; ++t) {
+          const uint32_t x = arch_s[a][lane + 32 * t];
+#pragma unroll
+          for (int c = 0; c < kOvCPW; ++c) p[c] += __popc(cw[c][t] & x);
+        }
+#pragma unroll
+        for (int c = 0; c < kOvCPW; ++c) {
+          const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, p[c]);
+          if (lane == 0) part_s[warp * kOvCPW + c][a] += v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kOvCands * na; i += blockDim.x) {
+      const int c = i / na, a = i % na;
+      const uint32_t v = part_s[c][a];
+      const uint32_t cand = blockIdx.x * kOvCands + c;
+      if (v && cand < n_cand) atomicAdd(&overlaps[(size_t)cand * n_arch + a0 + a], v);
+    }
+    __syncthreads();
   }
 }
 
@@ -122,39 +162,28 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
 
 }  // namespace
 
-cudaError_t launch_prepare(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
-                           int32_t ncols, bool check, uint32_t* zero, size_t n_zero,
-                           uint32_t* err, uint32_t* status, cudaStream_t s) {
-  const int T = 256;
-  if (check && n > 0) {
-    check_offsets_kernel<<<(n + T - 1) / T, T, 0, s>>>(offsets, n, err, status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  const size_t work = (check ? n : 0) > n_zero ? (check ? n : 0) : n_zero;
+cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
+  size_t work = a.n_zero;
+  for (int l = 0; l < 2; ++l) work = a.n[l] > work ? a.n[l] : work;
   if (work == 0) return cudaSuccess;
-  check_columns_kernel<<<(unsigned)((work + T - 1) / T), T, 0, s>>>(cols, offsets, n, ncols,
-                                                                     check, zero, n_zero, err,
-                                                                     status);
+  const int T = 256;
+  count_launch();
+  prepare_kernel<<<(unsigned)((work + T - 1) / T), T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,
                            uint32_t n_arch, int64_t words, uint32_t* overlaps, const uint32_t* err,
                            int num_sms, cudaStream_t s) {
+  (void)num_sms;
   if (n_cand == 0 || n_arch == 0) return cudaSuccess;
-  const unsigned gx = (n_cand + kOverlapWarps - 1) / kOverlapWarps;
-  int64_t nseg = (words + kWordsPerSegment - 1) / kWordsPerSegment;
-  const int64_t want = (4 * (int64_t)num_sms + gx - 1) / gx;  // about 4 blocks per SM
-  if (nseg > want) nseg = want;
-  if (nseg < 1) nseg = 1;
-  if (nseg > 65535) nseg = 65535;
-  int64_t seg = (words + nseg - 1) / nseg;
-  seg = (seg + 31) / 32 * 32;
-  nseg = (words + seg - 1) / seg;
-  dim3 grid(gx, (unsigned)nseg);
+  const int64_t per_block = (int64_t)kOvSub * kOvSubs;
+  const int64_t gy = (words + per_block - 1) / per_block;
+  if (gy > 65535) return cudaErrorInvalidConfiguration;
+  dim3 grid((n_cand + kOvCands - 1) / kOvCands, (unsigned)gy);
+  count_launch();
   overlap_kernel<<<grid, kOverlapWarps * 32, 0, s>>>(bitmaps, n_cand, arch_bitmaps, n_arch, words,
-                                                     seg, overlaps, err);
+                                                     overlaps, err);
   return cudaGetLastError();
 }
 
@@ -166,6 +195,7 @@ cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offset
   (void)ncols;
   if (n_cand == 0) return cudaSuccess;
   const unsigned grid = (n_cand + kFinalizeWarps - 1) / kFinalizeWarps;
+  count_launch();
   fitness_finalize_kernel<<<grid, kFinalizeWarps * 32, 0, s>>>(
       cols, offsets, n_cand, counts, arch_cols, arch_offsets, n_arch, overlaps, fitness, err);
   return cudaGetLastError();

@@ -139,6 +139,7 @@ cudaError_t launch_rank_layout(const Layout& L, const float* dX, int64_t ld, int
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  count_launch();
   kern<<<(unsigned)L.slabs, nwarps * 32, smem, s>>>(dX, L.rows, L.cols, ld, exclude, fill, ranks,
                                                     L.slabs, N, nwarps);
   return cudaGetLastError();

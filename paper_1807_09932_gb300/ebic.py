@@ -59,6 +59,10 @@ _lib_status = _sig("ebic_matrix_status", [_P, _P])
 _lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
 _lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _lib_last_error = _sig("ebic_last_error", [], ctypes.c_char_p)
+_lib_launch_count = _sig("ebic_launch_count", [], ctypes.c_int64)
+_lib_timing_enable = _sig("ebic_timing_enable", [ctypes.c_int])
+_lib_timing_read = _sig("ebic_timing_read", [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(_I64)])
 _lib_version = _sig("ebic_version", [])
 
 
@@ -157,6 +161,24 @@ def ebic_matrix_get_tile(h):
     t, r = _I32(), _I32()
     _check(_lib_get_tile(h, ctypes.byref(t), ctypes.byref(r)), "ebic_matrix_get_tile")
     return t.value, r.value
+
+
+EBIC_TIMING_RANK_TRANSFORM, EBIC_TIMING_PREPARE, EBIC_TIMING_EVALUATE = 0, 1, 2
+EBIC_TIMING_OVERLAP, EBIC_TIMING_FITNESS, EBIC_TIMING_KINDS = 3, 4, 5
+
+
+def ebic_launch_count():
+    return int(_lib_launch_count())
+
+
+def ebic_timing_enable(on):
+    _check(_lib_timing_enable(1 if on else 0), "ebic_timing_enable")
+
+
+def ebic_timing_read(kind):
+    ms, n = ctypes.c_double(), _I64()
+    _check(_lib_timing_read(kind, ctypes.byref(ms), ctypes.byref(n)), "ebic_timing_read")
+    return ms.value, n.value
 
 
 def ebic_last_error():
