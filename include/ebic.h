@@ -121,6 +121,29 @@ int ebic_eval_population(const ebic_matrix* m, const uint16_t* cols, const uint3
                          void* stream);
 
 /*
+ * Allocation-free variant of ebic_eval_population, for callers that cannot allocate device
+ * memory while they evaluate: a serving loop that must not take the allocator's lock or meet an
+ * out-of-memory error mid-request, a process whose device memory is owned by another caching
+ * allocator, or code inside a stream capture. It has no counterpart in the paper; it computes
+ * exactly what ebic_eval_population computes, with the same kernels.
+ *   counts, bitmaps   must be device memory of the matrix's device (no staging buffer exists).
+ *   cols, offsets     device memory (used in place, checked by a device kernel), or host memory
+ *                     (checked on the host and copied into the library's fixed scratch; the
+ *                     offsets rounded up to 256 bytes plus the columns must fit in 1 MiB minus
+ *                     256 bytes, otherwise EBIC_ERR_UNSUPPORTED).
+ * Scratch: a fixed 1 MiB device array inside the library (held by every GPU that loads the
+ * library until exit). Nothing is allocated or freed, by the library or by any library it calls.
+ * The first call on each device looks up that array's device address; make it before any stream
+ * capture. All calls share the array and its previous contents: the call clears its status word
+ * itself, and calls that overlap on the GPU race on the array, so issue one at a time.
+ * Always asynchronous on `stream`: device-side check failures are reported by
+ * ebic_matrix_status().
+ */
+int ebic_eval_population_noalloc(const ebic_matrix* m, const uint16_t* cols,
+                                 const uint32_t* offsets, uint32_t n_cand, uint32_t flags,
+                                 uint32_t* counts, uint32_t* bitmaps, void* stream);
+
+/*
  * Overlap-penalised fitness of a population against an elite archive. This is the project's
  * reading of the paper's "driven by counting of rows" (Methods, "Handling missing values").
  *   cols, offsets, n_cand  the population (CSR), as given to ebic_eval_population

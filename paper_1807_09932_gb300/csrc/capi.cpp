@@ -316,6 +316,39 @@ bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint
   return true;
 }
 
+void matrix_view(const ebic_matrix* m, MatrixView* v) {
+  v->device = m->device;
+  v->L = m->L;
+  v->status = m->status;
+  v->num_sms = m->num_sms;
+}
+
+int matrix_eval_plan(const ebic_matrix* cm, uint32_t n_cand, int64_t total_cols_hint,
+                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap) {
+  ebic_matrix* m = const_cast<ebic_matrix*>(cm);
+  const Layout& L = m->L;
+  int ts = m->tile ? m->tile : default_tile_slabs(L);
+  while (ts > 1 && ts > L.slabs) ts >>= 1;
+  if (!plan_eval(L, ts, n_cand, total_cols_hint, m->num_sms, a))
+    return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
+  int rc = get_tmap(m, ts, a->col_box, tmap);
+  if (rc != EBIC_OK) return rc;
+  cfg->width = L.width;
+  cfg->vec = L.vec;
+  cfg->ts = ts;
+  cfg->grid = m->num_sms;
+  return EBIC_OK;
+}
+
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+
+const char* check_candidates_host_c(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                                    int32_t ncols) {
+  thread_local std::string why;
+  why = check_candidates_host(cols, offsets, n, ncols);
+  return why.c_str();
+}
+
 cudaError_t launch_eval(const EvalConfig& cfg, const CUtensorMap* tmap, const EvalArgs& a,
                         cudaStream_t s) {
   if (cfg.width == 8) return launch_eval_w8v4(cfg, tmap, a, s);

@@ -128,4 +128,29 @@ cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offset
                                     const uint32_t* overlaps, int32_t ncols, uint64_t* fitness,
                                     const uint32_t* err, cudaStream_t s);
 
+// ---- host helpers shared by the C-ABI translation units ------------------------------------
+}  // namespace ebic
+
+struct ebic_matrix;
+
+namespace ebic {
+
+struct MatrixView {
+  int device = 0;
+  Layout L;
+  uint32_t* status = nullptr;
+  int num_sms = 0;
+};
+// Read-only view of a matrix handle's shape and device words.
+void matrix_view(const ebic_matrix* m, MatrixView* v);
+// Tile choice, launch plan and tensor map for evaluating n_cand candidates on m (the same choice
+// ebic_eval_population makes). Returns EBIC_OK or an error code with the last-error message set.
+int matrix_eval_plan(const ebic_matrix* m, uint32_t n_cand, int64_t total_cols_hint,
+                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap);
+// Record the calling thread's last-error message and return `code`.
+int set_last_error(int code, const char* msg);
+// Host-side check of a CSR candidate list; empty string when valid.
+const char* check_candidates_host_c(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                                    int32_t ncols);
+
 }  // namespace ebic

@@ -53,6 +53,7 @@ _lib_info = _sig("ebic_matrix_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_
                                       ctypes.POINTER(_I64), ctypes.POINTER(_I32)])
 _lib_ranks = _sig("ebic_matrix_ranks", [_P, _P, _P])
 _lib_eval = _sig("ebic_eval_population", [_P, _P, _P, _U32, _U32, _P, _P, _P])
+_lib_eval_noalloc = _sig("ebic_eval_population_noalloc", [_P, _P, _P, _U32, _U32, _P, _P, _P])
 _lib_fitness = _sig("ebic_fitness", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32, _U32, _P, _P,
                                      _P])
 _lib_status = _sig("ebic_matrix_status", [_P, _P])
@@ -140,6 +141,12 @@ def ebic_matrix_ranks(h, out, stream=None):
 def ebic_eval_population(h, cols, offsets, n_cand, flags, counts, bitmaps, stream=None):
     return _lib_eval(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(counts), _ptr(bitmaps),
                      _stream(stream))
+
+
+def ebic_eval_population_noalloc(h, cols, offsets, n_cand, flags, counts, bitmaps, stream=None):
+    """Allocation-free evaluation (outputs must be device buffers); see include/ebic.h."""
+    return _lib_eval_noalloc(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(counts),
+                             _ptr(bitmaps), _stream(stream))
 
 
 def ebic_fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offsets,
