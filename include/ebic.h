@@ -152,9 +152,12 @@ int ebic_eval_population_noalloc(const ebic_matrix* m, const uint16_t* cols,
  *                          uint32[n_arch][W] row bitmaps. n_arch may be 0 (pointers then unused).
  *   fitness                out: uint64[n_cand]
  *   overlaps               out: uint32[n_cand][n_arch] = popcount(M_c & M_a), or NULL
- * Definition: o(c,a) = popcount(M_c & M_a). Let p_c = counts[c] minus the largest o(c,a) over
- * archive members a whose column SET meets c's (0 if there is none). Then
- * fitness[c] = (uint64)p_c << (min(L_c, 33) - 1).
+ * Definition: q(x) = (uint64)n_x << (min(L_x, 33) - 1) is the raw quality (n_a of an archive
+ * member is the popcount of its bitmap) and o(c,a) = popcount(M_c & M_a). Let p_c = counts[c]
+ * minus the largest o(c,a) over archive members a whose column SET meets c's and with
+ * q(a) >= q(c) (0 if there is none). Then fitness[c] = (uint64)p_c << (min(L_c, 33) - 1).
+ * Only members at least as good as the candidate penalise it, so improving on an archived
+ * bicluster is not penalised.
  * flags is reserved (pass 0).
  */
 int ebic_fitness(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
@@ -182,6 +185,78 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
 /* The tile height in slabs that the next evaluation will use, and the rows per slab. */
 int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab);
 
+/* ---- the EBIC generation loop (host genetic algorithm over the device evaluator) --------- */
+/*
+ * The paper says EBIC uses evolutionary computation over a population of up to 65,535
+ * candidates, with 1,600 or fewer usually enough to converge (Methods, "Support for Big Data").
+ * It does not define the operators. The ones here are the project's definition: deterministic
+ * given `seed` (a splitmix64 counter generator), tournament selection, an order-preserving
+ * crossover, four mutations (swap, substitute, insert, delete), a tabu list of evaluated column
+ * sequences, and an elite archive of `archive_size` biclusters ranked by raw quality
+ * n << (min(L,33)-1). A candidate enters the archive unless a member sharing a column overlaps
+ * it by more than overlap_threshold x its row count without being strictly worse; strictly worse
+ * members it overlaps that much are replaced by it.
+ * Each generation the population is scored with ebic_eval_population and ebic_fitness against
+ * the current archive (device-resident rank matrix, bitmaps and archive).
+ */
+typedef struct ebic_params {
+  uint32_t population;       /* candidates per generation (default 1600)                      */
+  uint32_t generations;      /* generations to run (default 100)                              */
+  uint32_t archive_size;     /* elite archive size K (default 20)                             */
+  uint32_t elite;            /* best candidates copied unchanged to the next generation (16)  */
+  uint32_t tournament;       /* tournament size (default 4)                                   */
+  uint32_t min_len;          /* shortest candidate (default 2)                                */
+  uint32_t max_init_len;     /* longest initial candidate (default 6)                         */
+  uint32_t max_len;          /* longest candidate (default 64, at most cols)                  */
+  float p_crossover;         /* crossover probability (default 0.5)                           */
+  float p_mutation;          /* mutation probability (default 0.7)                            */
+  float overlap_threshold;   /* archive admission threshold (default 0.5)                     */
+  uint32_t tabu_retries;     /* re-mutations of a tabu child before a random one (default 8)  */
+  uint32_t flags;            /* EBIC_NEGATIVE_TRENDS or 0                                     */
+  uint32_t reserved;
+  uint64_t seed;             /* default 1807099320                                            */
+} ebic_params;
+
+typedef struct ebic_result {
+  uint32_t n;                /* archive members, best first                                   */
+  uint16_t* cols;            /* CSR columns of the members                                    */
+  uint32_t* offsets;         /* [n+1]                                                         */
+  uint32_t* counts;          /* [n] matched rows                                              */
+  uint64_t* quality;         /* [n] counts << (min(L,33)-1): the archive's order key          */
+  uint32_t* bitmaps;         /* [n][W] row bitmaps (NULL from ebic_run_custom)               */
+  int64_t words;             /* W                                                             */
+  uint32_t generations_run;
+  uint64_t candidates_evaluated;
+} ebic_result;
+
+/* Fill *p with the defaults listed above. */
+int ebic_params_default(ebic_params* p);
+
+/* Run EBIC on a loaded matrix; *out receives the archive (free it with ebic_free_result).
+ * stream: the CUDA stream the generations run on. Synchronous. */
+int ebic_run(const ebic_matrix* m, const ebic_params* p, void* stream, ebic_result** out);
+
+/* The same generation loop over caller-supplied evaluation (host buffers throughout). It exists
+ * so the loop can be driven by another implementation of the scoring (a CPU reference) and is
+ * pure host code. Callbacks return 0 on success.
+ *   evaluate:       counts[n], fitness[n] and overlaps[n][n_arch] of the population against the
+ *                   current archive (as last set by set_archive; empty at first)
+ *   pair_overlaps:  out[t][t] = popcount(M_i & M_j) for population indices idx[0..t)
+ *   set_archive:    the new archive, member i = population candidate src[i] if src[i] >= 0,
+ *                   else old archive member -(src[i]+1)
+ */
+typedef struct ebic_evaluator {
+  void* user;
+  int (*evaluate)(void* user, const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                  uint32_t* counts, uint64_t* fitness, uint32_t* overlaps);
+  int (*pair_overlaps)(void* user, const uint32_t* idx, uint32_t t, uint32_t* out);
+  int (*set_archive)(void* user, const int32_t* src, uint32_t k);
+} ebic_evaluator;
+int ebic_run_custom(int64_t rows, int32_t cols, const ebic_params* p, const ebic_evaluator* ev,
+                    ebic_result** out);
+
+int ebic_free_result(ebic_result* r);
+
 /* ---- diagnostics ----------------------------------------------------------------------- */
 /* Kernels launched by this library in this process so far (every launch is counted). */
 int64_t ebic_launch_count(void);
@@ -198,6 +273,11 @@ int64_t ebic_launch_count(void);
 int ebic_timing_enable(int on);
 /* Wait for the recorded events of `kind` and return their summed duration and count. */
 int ebic_timing_read(int kind, double* total_ms, int64_t* launches);
+
+/* Self-test of the failure path of every bounded device wait: launch a kernel whose wait on an
+ * mbarrier can never complete; after timeout_ns (<= 0.1 s) it records the expiry and returns.
+ * Returns EBIC_ERR_DEVICE_TIMEOUT when the path works; the context stays usable. */
+int ebic_selftest_wait_timeout(uint64_t timeout_ns, void* stream);
 
 /* Message for the calling thread's last failed call ("" if none). Valid until the next call. */
 const char* ebic_last_error(void);

@@ -20,8 +20,9 @@
  *  - negative-trend option: a row that is non-increasing along the order also matches, counted
  *    once;
  *  - bitmaps are LSB-first uint32 words, bit b of word w = row 32w+b, padding bits 0;
- *  - fitness: overlap o(c,a) = |rows(c) & rows(a)|; penalty = max o(c,a) over archive members
- *    a that share a column with c (0 if none); F = (n - penalty) << (min(L,33) - 1).
+ *  - fitness: quality q(x) = n_x << (min(L_x,33) - 1); overlap o(c,a) = |rows(c) & rows(a)|;
+ *    penalty = max o(c,a) over archive members a that share a column with c and are at least
+ *    as good (q(a) >= q(c)), 0 if none; F = (n - penalty) << (min(L,33) - 1).
  *
  * Parity status: every function here is pinned by the CPU tests (brute force with sorted(),
  * closed-form match probabilities, invariants, planted recovery, scipy's dense rankdata,
@@ -114,6 +115,12 @@ static uint32_t popcount32(uint32_t x)
     return n;
 }
 
+static uint64_t quality(uint32_t n, uint32_t L)
+{
+    uint32_t shift = (L < 33 ? L : 33) - 1;
+    return (uint64_t)n << shift;
+}
+
 /*
  * Overlap-penalised fitness against an elite archive of K biclusters.
  *   counts[P], bitmaps[P*W]        the population's evaluation
@@ -134,18 +141,21 @@ int oracle_fitness(int64_t R, const uint16_t* cols, const uint32_t* offsets, uin
 #endif
     for (int64_t p = 0; p < (int64_t)P; ++p) {
         uint32_t L = offsets[p + 1] - offsets[p];
+        uint64_t qc = quality(counts[p], L);
         uint32_t penalty = 0;
         for (uint32_t a = 0; a < K; ++a) {
-            uint32_t o = 0;
-            for (int64_t w = 0; w < W; ++w)
+            uint32_t o = 0, na = 0;
+            for (int64_t w = 0; w < W; ++w) {
                 o += popcount32(bitmaps[p * W + w] & abitmaps[(int64_t)a * W + w]);
+                na += popcount32(abitmaps[(int64_t)a * W + w]);
+            }
             if (overlaps) overlaps[p * K + a] = o;
-            int s = share_columns(cols + offsets[p], L, acols + aoffsets[a],
-                                  aoffsets[a + 1] - aoffsets[a]);
-            if (s && o > penalty) penalty = o;
+            uint32_t La = aoffsets[a + 1] - aoffsets[a];
+            int s = share_columns(cols + offsets[p], L, acols + aoffsets[a], La);
+            int at_least_as_good = quality(na, La) >= qc;
+            if (s && at_least_as_good && o > penalty) penalty = o;
         }
-        uint32_t shift = (L < 33 ? L : 33) - 1;
-        fitness[p] = (uint64_t)(counts[p] - penalty) << shift;
+        fitness[p] = quality(counts[p] - penalty, L);
     }
     return 0;
 }

@@ -644,12 +644,14 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
   uint32_t* dov = nullptr;
   EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
   const size_t n_ov = (size_t)n_cand * n_arch;
+  uint32_t* darch_counts = nullptr;  // the archive members' row counts (computed on the device)
   if (n_arch > 0) {
     if (overlaps) {
       EBIC_CUDA(out_buffer(overlaps, n_ov, dev, sc, &dov, &ov_host));
     } else {
       EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), n_ov * sizeof(uint32_t)));
     }
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&darch_counts), n_arch * sizeof(uint32_t)));
   }
   {
     Timed t(EBIC_TIMING_PREPARE, s);
@@ -663,18 +665,21 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
     pa.ncols = L.cols;
     pa.zero = dov;
     pa.n_zero = n_ov;
+    pa.zero2 = darch_counts;
+    pa.n_zero2 = darch_counts ? n_arch : 0;
     pa.err = err;
     pa.status = m->status;
     EBIC_CUDA(launch_prepare(pa, s));
   }
   {
     Timed t(EBIC_TIMING_OVERLAP, s);
-    EBIC_CUDA(launch_overlap(dbm, n_cand, dabm, n_arch, L.words, dov, err, m->num_sms, s));
+    EBIC_CUDA(launch_overlap(dbm, n_cand, dabm, n_arch, L.words, dov, darch_counts, err,
+                             m->num_sms, s));
   }
   {
     Timed t(EBIC_TIMING_FITNESS, s);
     EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
-                                      L.cols, dfit, err, s));
+                                      darch_counts, dfit, err, s));
   }
   if (fit_host || ov_host) {
     if (fit_host)

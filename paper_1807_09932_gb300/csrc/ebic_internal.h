@@ -72,6 +72,8 @@ struct PrepareArgs {
   int32_t ncols = 0;
   uint32_t* zero = nullptr;
   size_t n_zero = 0;
+  uint32_t* zero2 = nullptr;
+  size_t n_zero2 = 0;
   uint32_t* err = nullptr;
   uint32_t* status = nullptr;
 };
@@ -120,13 +122,14 @@ cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalA
 
 // ---- fitness -------------------------------------------------------------------------------
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,
-                           uint32_t n_arch, int64_t words, uint32_t* overlaps, const uint32_t* err,
-                           int num_sms, cudaStream_t s);
+                           uint32_t n_arch, int64_t words, uint32_t* overlaps,
+                           uint32_t* arch_counts, const uint32_t* err, int num_sms,
+                           cudaStream_t s);
 cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offsets, uint32_t n_cand,
                                     const uint32_t* counts, const uint16_t* arch_cols,
                                     const uint32_t* arch_offsets, uint32_t n_arch,
-                                    const uint32_t* overlaps, int32_t ncols, uint64_t* fitness,
-                                    const uint32_t* err, cudaStream_t s);
+                                    const uint32_t* overlaps, const uint32_t* arch_counts,
+                                    uint64_t* fitness, const uint32_t* err, cudaStream_t s);
 
 // ---- host helpers shared by the C-ABI translation units ------------------------------------
 }  // namespace ebic

@@ -4,9 +4,12 @@
 // Fitness (the project's reading of "EBIC search is driven by counting of rows", arXiv
 // 1807.09932, Methods, "Handling missing values"): for candidate c with row count n_c and row
 // bitmap M_c, and archive members a with column sets A_a and bitmaps M_a,
-//   o(c,a) = popcount(M_c & M_a)                           (rows c shares with a)
-//   p_c    = n_c - max{ o(c,a) : c and a share a column }  (0 when there is none)
+//   q(x)   = (uint64) n_x << (min(L_x, 33) - 1)               (raw quality)
+//   o(c,a) = popcount(M_c & M_a)                              (rows c shares with a)
+//   p_c    = n_c - max{ o(c,a) : a shares a column with c and q(a) >= q(c) }   (0 if none)
 //   F_c    = (uint64) p_c << (min(L_c, 33) - 1)
+// Only archive members at least as good as the candidate penalise it, so a candidate that
+// improves on an archived bicluster is not pushed away from it.
 // The overlap pass reads every candidate bitmap from HBM once, against archive words staged in
 // shared memory; the finalize pass builds the candidate's column set as a shared-memory bitset and
 // tests each archive member's columns against it.
@@ -23,6 +26,7 @@ namespace {
 __global__ void prepare_kernel(PrepareArgs a) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a.zero && i < a.n_zero) a.zero[i] = 0u;
+  if (a.zero2 && i < a.n_zero2) a.zero2[i] = 0u;
   bool bad = false;
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
@@ -63,7 +67,8 @@ constexpr int kOvArch = 32;                        // archive members staged per
 __global__ void __launch_bounds__(kOverlapWarps * 32)
     overlap_kernel(const uint32_t* __restrict__ bitmaps, uint32_t n_cand,
                    const uint32_t* __restrict__ arch, uint32_t n_arch, int64_t W,
-                   uint32_t* __restrict__ overlaps, const uint32_t* err) {
+                   uint32_t* __restrict__ overlaps, uint32_t* __restrict__ arch_counts,
+                   const uint32_t* err) {
   __shared__ uint32_t arch_s[kOvArch][kOvSub];
   __shared__ uint32_t part_s[kOvCands][kOvArch];
   if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
@@ -82,6 +87,15 @@ __global__ void __launch_bounds__(kOverlapWarps * 32)
         arch_s[a][w] = ws + w < W ? __ldg(arch + (size_t)(a0 + a) * W + ws + w) : 0u;
       }
       __syncthreads();
+      if (blockIdx.x == 0) {  // the archive's own row counts, once per word segment
+        for (int a = warp; a < na; a += kOverlapWarps) {
+          uint32_t n = 0;
+#pragma unroll
+          for (int t = 0; t < kOvNPL; ++t) n += __popc(arch_s[a][lane + 32 * t]);
+          n = __reduce_add_sync(0xFFFFFFFFu, n);
+          if (lane == 0 && n) atomicAdd(&arch_counts[a0 + a], n);
+        }
+      }
       uint32_t cw[kOvCPW][kOvNPL];
 #pragma unroll
       for (int c = 0; c < kOvCPW; ++c)
@@ -124,8 +138,9 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
                             const uint32_t* __restrict__ counts,
                             const uint16_t* __restrict__ acols,
                             const uint32_t* __restrict__ aoffsets, uint32_t n_arch,
-                            const uint32_t* __restrict__ overlaps, uint64_t* __restrict__ fitness,
-                            const uint32_t* err) {
+                            const uint32_t* __restrict__ overlaps,
+                            const uint32_t* __restrict__ arch_counts,
+                            uint64_t* __restrict__ fitness, const uint32_t* err) {
   __shared__ uint32_t colset[kFinalizeWarps][(kMaxCols + 31) / 32];
   if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -140,9 +155,12 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
     atomicOr(&set[col >> 5], 1u << (col & 31));
   }
   __syncwarp();
+  const uint64_t qc = (uint64_t)counts[c] << ((L < 33u ? L : 33u) - 1u);
   uint32_t best = 0;
   for (uint32_t a = lane; a < n_arch; a += 32) {
     const uint32_t ao = aoffsets[a], al = aoffsets[a + 1] - ao;
+    const uint64_t qa = (uint64_t)arch_counts[a] << ((al < 33u ? al : 33u) - 1u);
+    if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
     bool share = false;
     for (uint32_t j = 0; j < al && !share; ++j) {
       const uint32_t col = acols[ao + j];
@@ -163,7 +181,7 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
 }  // namespace
 
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
-  size_t work = a.n_zero;
+  size_t work = a.n_zero > a.n_zero2 ? a.n_zero : a.n_zero2;
   for (int l = 0; l < 2; ++l) work = a.n[l] > work ? a.n[l] : work;
   if (work == 0) return cudaSuccess;
   const int T = 256;
@@ -173,8 +191,9 @@ cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,
-                           uint32_t n_arch, int64_t words, uint32_t* overlaps, const uint32_t* err,
-                           int num_sms, cudaStream_t s) {
+                           uint32_t n_arch, int64_t words, uint32_t* overlaps,
+                           uint32_t* arch_counts, const uint32_t* err, int num_sms,
+                           cudaStream_t s) {
   (void)num_sms;
   if (n_cand == 0 || n_arch == 0) return cudaSuccess;
   const int64_t per_block = (int64_t)kOvSub * kOvSubs;
@@ -183,21 +202,21 @@ cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint3
   dim3 grid((n_cand + kOvCands - 1) / kOvCands, (unsigned)gy);
   count_launch();
   overlap_kernel<<<grid, kOverlapWarps * 32, 0, s>>>(bitmaps, n_cand, arch_bitmaps, n_arch, words,
-                                                     overlaps, err);
+                                                     overlaps, arch_counts, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offsets, uint32_t n_cand,
                                     const uint32_t* counts, const uint16_t* arch_cols,
                                     const uint32_t* arch_offsets, uint32_t n_arch,
-                                    const uint32_t* overlaps, int32_t ncols, uint64_t* fitness,
-                                    const uint32_t* err, cudaStream_t s) {
-  (void)ncols;
+                                    const uint32_t* overlaps, const uint32_t* arch_counts,
+                                    uint64_t* fitness, const uint32_t* err, cudaStream_t s) {
   if (n_cand == 0) return cudaSuccess;
   const unsigned grid = (n_cand + kFinalizeWarps - 1) / kFinalizeWarps;
   count_launch();
   fitness_finalize_kernel<<<grid, kFinalizeWarps * 32, 0, s>>>(
-      cols, offsets, n_cand, counts, arch_cols, arch_offsets, n_arch, overlaps, fitness, err);
+      cols, offsets, n_cand, counts, arch_cols, arch_offsets, n_arch, overlaps, arch_counts,
+      fitness, err);
   return cudaGetLastError();
 }
 

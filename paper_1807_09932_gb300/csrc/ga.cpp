@@ -1,0 +1,591 @@
+// Host genetic algorithm of EBIC: ebic_run (scoring on the GPU) and ebic_run_custom (scoring by
+// caller callbacks).
+//
+// The paper states that EBIC searches with evolutionary computation over a population (up to
+// 65,535 candidates; 1,600 or fewer usually converge; Methods, "Support for Big Data") and that
+// the search is driven by counting rows (Methods, "Handling missing values"). It does not define
+// the operators. The generation loop below is the project's definition:
+//   * random initial candidates (length uniform in [min_len, max_init_len], distinct columns);
+//   * every generation: score (counts, penalised fitness and overlaps against the archive),
+//     update the archive, then breed the next population: the `elite` best survive unchanged;
+//     the others are tournament winners, crossed over (order-preserving: a prefix of parent A,
+//     then parent B's columns not yet present, in B's order) and mutated (swap, substitute,
+//     insert or delete one column);
+//   * tabu list: a child whose exact column sequence was already evaluated, or already sits in the
+//     new population, is mutated again (up to tabu_retries times), then replaced by a random one;
+//   * archive: the best `archive_size` distinct candidates by quality n << (min(L,33)-1)
+//     (ties: more rows, longer, lexicographically smaller columns). Each generation up to 2K
+//     candidates are offered, best quality first: one is admitted unless a member sharing a
+//     column overlaps it by more than overlap_threshold x its row count without being strictly
+//     worse; strictly worse members it overlaps that much are replaced by it.
+// Every random draw comes from one splitmix64 counter generator seeded with `seed`, and every
+// decision depends only on draws and exact integer scores, so a run is reproducible bit for bit
+// and independent of which evaluator produced the (identical) scores.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "ebic.h"
+#include "ebic_internal.h"
+
+using namespace ebic;
+
+namespace {
+
+struct Rng {  // splitmix64 (Steele, Lea, Flood 2014), as a counter-based generator
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  uint32_t below(uint32_t n) { return (uint32_t)(next() % n); }
+  double unit() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+using Cand = std::vector<uint16_t>;
+
+struct CandHash {
+  size_t operator()(const Cand& c) const {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a
+    for (uint16_t x : c) { h ^= x; h *= 1099511628211ull; }
+    return (size_t)(h ^ c.size());
+  }
+};
+
+uint64_t quality(uint32_t n, size_t L) { return (uint64_t)n << ((L < 33 ? L : 33) - 1); }
+
+// Scoring of one generation, implemented by the GPU (ebic_run) or by callbacks.
+struct Evaluator {
+  virtual ~Evaluator() = default;
+  virtual int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs,
+                       uint32_t n, uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) = 0;
+  virtual int pair_overlaps(const std::vector<uint32_t>& idx, uint32_t* out) = 0;
+  virtual int set_archive(const std::vector<int32_t>& src) = 0;
+  virtual bool has_bitmaps() const { return false; }
+  virtual int archive_bitmaps(uint32_t* out, uint32_t k) { (void)out; (void)k; return EBIC_OK; }
+};
+
+struct Member {
+  Cand cols;
+  uint32_t count;
+  uint64_t q;
+  int32_t src;  // population index (>= 0) or -(old archive index + 1)
+};
+
+bool member_before(const Member& a, const Member& b) {
+  if (a.q != b.q) return a.q > b.q;
+  if (a.count != b.count) return a.count > b.count;
+  if (a.cols.size() != b.cols.size()) return a.cols.size() > b.cols.size();
+  return a.cols < b.cols;
+}
+
+bool shares_column(const Cand& a, const Cand& b) {
+  for (uint16_t x : a)
+    for (uint16_t y : b)
+      if (x == y) return true;
+  return false;
+}
+
+struct Ga {
+  const ebic_params& p;
+  int32_t ncols;
+  Rng rng;
+  std::vector<uint16_t> all_cols;
+
+  Ga(const ebic_params& prm, int32_t nc) : p(prm), ncols(nc), rng{prm.seed} {
+    all_cols.resize((size_t)nc);
+    for (int32_t i = 0; i < nc; ++i) all_cols[(size_t)i] = (uint16_t)i;
+  }
+
+  Cand random_candidate() {
+    const uint32_t L = p.min_len + rng.below(p.max_init_len - p.min_len + 1);
+    for (uint32_t i = 0; i < L; ++i) {  // partial Fisher-Yates over the column list
+      const uint32_t j = i + rng.below((uint32_t)ncols - i);
+      std::swap(all_cols[i], all_cols[j]);
+    }
+    return Cand(all_cols.begin(), all_cols.begin() + L);
+  }
+
+  uint16_t unused_column(const Cand& c) {
+    for (;;) {  // terminates: callers ensure c.size() < ncols
+      const uint16_t x = (uint16_t)rng.below((uint32_t)ncols);
+      if (std::find(c.begin(), c.end(), x) == c.end()) return x;
+    }
+  }
+
+  Cand crossover(const Cand& a, const Cand& b) {
+    const uint32_t cut = 1 + rng.below((uint32_t)a.size());
+    Cand child(a.begin(), a.begin() + cut);
+    for (uint16_t x : b) {
+      if (child.size() >= p.max_len) break;
+      if (std::find(child.begin(), child.end(), x) == child.end()) child.push_back(x);
+    }
+    while (child.size() < p.min_len) child.push_back(unused_column(child));
+    return child;
+  }
+
+  void mutate(Cand& c) {
+    const uint32_t first = rng.below(4);
+    for (uint32_t k = 0; k < 4; ++k) {
+      switch ((first + k) % 4) {
+        case 0:  // swap two positions
+          if (c.size() >= 2) {
+            const uint32_t i = rng.below((uint32_t)c.size());
+            uint32_t j = rng.below((uint32_t)c.size() - 1);
+            if (j >= i) ++j;
+            std::swap(c[i], c[j]);
+            return;
+          }
+          break;
+        case 1:  // substitute a column by an unused one
+          if ((int32_t)c.size() < ncols) {
+            const uint32_t i = rng.below((uint32_t)c.size());
+            c[i] = unused_column(c);
+            return;
+          }
+          break;
+        case 2:  // insert an unused column
+          if (c.size() < p.max_len && (int32_t)c.size() < ncols) {
+            const uint16_t x = unused_column(c);
+            const uint32_t i = rng.below((uint32_t)c.size() + 1);
+            c.insert(c.begin() + i, x);
+            return;
+          }
+          break;
+        default:  // delete a column
+          if (c.size() > p.min_len) {
+            c.erase(c.begin() + rng.below((uint32_t)c.size()));
+            return;
+          }
+          break;
+      }
+    }
+  }
+};
+
+std::string check_params(const ebic_params& p, int32_t ncols) {
+  if (p.population < 1) return "population must be >= 1";
+  if (p.archive_size < 1 || p.archive_size > 4096) return "archive_size must be in [1, 4096]";
+  if (p.min_len < 1) return "min_len must be >= 1";
+  if (p.max_init_len < p.min_len) return "max_init_len must be >= min_len";
+  if (p.max_len < p.max_init_len) return "max_len must be >= max_init_len";
+  if (p.max_len > (uint32_t)EBIC_MAX_CANDIDATE_LEN || (int64_t)p.max_len > ncols)
+    return "max_len must be <= 64 and <= cols";
+  if (p.elite > p.population) return "elite must be <= population";
+  if (p.tournament < 1) return "tournament must be >= 1";
+  if (!(p.p_crossover >= 0.f && p.p_crossover <= 1.f) ||
+      !(p.p_mutation >= 0.f && p.p_mutation <= 1.f))
+    return "probabilities must be in [0, 1]";
+  if (!(p.overlap_threshold >= 0.f)) return "overlap_threshold must be >= 0";
+  if (p.flags & ~EBIC_NEGATIVE_TRENDS) return "unknown flag";
+  return "";
+}
+
+int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebic_result** out) {
+  const uint32_t P = p.population, K = p.archive_size;
+  Ga ga(p, ncols);
+  std::unordered_set<Cand, CandHash> tabu;
+  std::vector<Cand> pop;
+  pop.reserve(P);
+  {
+    std::unordered_set<Cand, CandHash> seen;
+    for (uint32_t i = 0; i < P; ++i) {
+      Cand c = ga.random_candidate();
+      for (int t = 0; t < 32 && seen.count(c); ++t) c = ga.random_candidate();
+      seen.insert(c);
+      pop.push_back(std::move(c));
+    }
+  }
+  std::vector<Member> archive;
+  std::vector<uint16_t> cols;
+  std::vector<uint32_t> offs;
+  std::vector<uint32_t> counts(P), overlaps((size_t)P * K), order(P), rank(P);
+  std::vector<uint64_t> fitness(P);
+  uint64_t evaluated = 0;
+  uint32_t gen = 0;
+  for (; gen < p.generations; ++gen) {
+    cols.clear();
+    offs.assign(1, 0u);
+    for (const Cand& c : pop) {
+      cols.insert(cols.end(), c.begin(), c.end());
+      offs.push_back((uint32_t)cols.size());
+    }
+    int rc = ev.evaluate(cols, offs, P, counts.data(), fitness.data(), overlaps.data());
+    if (rc != EBIC_OK) return rc;
+    evaluated += P;
+    for (const Cand& c : pop) tabu.insert(c);
+    const size_t K_eval = archive.size();  // overlaps is [P][K_eval]
+
+    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+      if (fitness[a] != fitness[b]) return fitness[a] > fitness[b];
+      if (counts[a] != counts[b]) return counts[a] > counts[b];
+      if (pop[a].size() != pop[b].size()) return pop[a].size() > pop[b].size();
+      if (pop[a] != pop[b]) return pop[a] < pop[b];
+      return a < b;
+    });
+    for (uint32_t r = 0; r < P; ++r) rank[order[r]] = r;
+
+    // ---- archive update ----
+    // Offer up to 2K non-archived candidates with rows, best raw quality first. A candidate is
+    // admitted unless a member sharing a column overlaps it by more than the threshold without
+    // being strictly worse; strictly worse members that overlap it that much are replaced.
+    std::unordered_set<Cand, CandHash> in_archive;
+    for (const Member& m : archive) in_archive.insert(m.cols);
+    std::vector<Member> offers;
+    {
+      std::unordered_set<Cand, CandHash> picked;
+      for (uint32_t i = 0; i < P; ++i) {
+        if (counts[i] == 0 || in_archive.count(pop[i]) || picked.count(pop[i])) continue;
+        picked.insert(pop[i]);
+        offers.push_back(Member{pop[i], counts[i], quality(counts[i], pop[i].size()), (int32_t)i});
+      }
+      std::stable_sort(offers.begin(), offers.end(), member_before);
+      if (offers.size() > 2 * (size_t)K) offers.resize(2 * (size_t)K);
+    }
+    std::vector<uint32_t> top;
+    for (const Member& m : offers) top.push_back((uint32_t)m.src);
+    std::vector<uint32_t> pair((size_t)top.size() * top.size());
+    if (!top.empty()) {
+      rc = ev.pair_overlaps(top, pair.data());
+      if (rc != EBIC_OK) return rc;
+    }
+    std::vector<bool> alive(archive.size(), true);
+    std::vector<size_t> admitted;  // positions in `offers`
+    for (size_t t = 0; t < offers.size(); ++t) {
+      const Member& c = offers[t];
+      const uint32_t i = (uint32_t)c.src;
+      const double limit = (double)p.overlap_threshold * (double)c.count;
+      bool ok = true;
+      std::vector<size_t> evict;
+      for (size_t a = 0; a < K_eval && ok; ++a) {
+        if (!alive[a] || !shares_column(c.cols, archive[a].cols)) continue;
+        if ((double)overlaps[(size_t)i * K_eval + a] <= limit) continue;
+        if (c.q > archive[a].q) evict.push_back(a); else ok = false;
+      }
+      for (size_t u : admitted) {  // admitted earlier: at least as good, never replaced here
+        if (!ok) break;
+        if (shares_column(c.cols, offers[u].cols) && (double)pair[t * top.size() + u] > limit)
+          ok = false;
+      }
+      if (!ok) continue;
+      for (size_t a : evict) alive[a] = false;
+      admitted.push_back(t);
+    }
+    std::vector<Member> merged;
+    for (size_t a = 0; a < archive.size(); ++a) {
+      if (!alive[a]) continue;
+      Member m = archive[a];
+      m.src = -(int32_t)a - 1;
+      merged.push_back(m);
+    }
+    for (size_t t : admitted) merged.push_back(offers[t]);
+    std::stable_sort(merged.begin(), merged.end(), member_before);
+    if (merged.size() > K) merged.resize(K);
+    std::vector<int32_t> src;
+    for (const Member& m : merged) src.push_back(m.src);
+    rc = ev.set_archive(src);
+    if (rc != EBIC_OK) return rc;
+    archive = merged;
+
+    if (gen + 1 == p.generations) { ++gen; break; }
+
+    // ---- next population ----
+    std::vector<Cand> next;
+    next.reserve(P);
+    std::unordered_set<Cand, CandHash> in_next;
+    for (uint32_t r = 0; r < p.elite; ++r) {
+      next.push_back(pop[order[r]]);
+      in_next.insert(pop[order[r]]);
+    }
+    auto tournament = [&]() {
+      uint32_t best = ga.rng.below(P);
+      for (uint32_t t = 1; t < p.tournament; ++t) {
+        const uint32_t c = ga.rng.below(P);
+        if (rank[c] < rank[best]) best = c;
+      }
+      return best;
+    };
+    while (next.size() < P) {
+      const uint32_t a = tournament();
+      Cand child = pop[a];
+      if (ga.rng.unit() < p.p_crossover) child = ga.crossover(pop[a], pop[tournament()]);
+      if (ga.rng.unit() < p.p_mutation) ga.mutate(child);
+      for (uint32_t t = 0; t < p.tabu_retries && (tabu.count(child) || in_next.count(child)); ++t)
+        ga.mutate(child);
+      for (int t = 0; t < 32 && (tabu.count(child) || in_next.count(child)); ++t)
+        child = ga.random_candidate();
+      in_next.insert(child);
+      next.push_back(std::move(child));
+    }
+    pop.swap(next);
+  }
+
+  // ---- result ----
+  ebic_result* r = new ebic_result();
+  std::memset(r, 0, sizeof(*r));
+  r->n = (uint32_t)archive.size();
+  r->words = (rows + 31) / 32;
+  r->generations_run = gen;
+  r->candidates_evaluated = evaluated;
+  size_t tot = 0;
+  for (const Member& m : archive) tot += m.cols.size();
+  r->cols = new uint16_t[tot > 0 ? tot : 1];
+  r->offsets = new uint32_t[r->n + 1];
+  r->counts = new uint32_t[r->n > 0 ? r->n : 1];
+  r->quality = new uint64_t[r->n > 0 ? r->n : 1];
+  r->offsets[0] = 0;
+  size_t o = 0;
+  for (uint32_t i = 0; i < r->n; ++i) {
+    std::copy(archive[i].cols.begin(), archive[i].cols.end(), r->cols + o);
+    o += archive[i].cols.size();
+    r->offsets[i + 1] = (uint32_t)o;
+    r->counts[i] = archive[i].count;
+    r->quality[i] = archive[i].q;
+  }
+  if (ev.has_bitmaps()) {
+    r->bitmaps = new uint32_t[(size_t)r->n * (size_t)r->words + 1];
+    int rc = ev.archive_bitmaps(r->bitmaps, r->n);
+    if (rc != EBIC_OK) {
+      ebic_free_result(r);
+      return rc;
+    }
+  }
+  *out = r;
+  return EBIC_OK;
+}
+
+// ---- scoring by caller callbacks ---------------------------------------------------------------
+struct CallbackEvaluator : Evaluator {
+  const ebic_evaluator* cb;
+  explicit CallbackEvaluator(const ebic_evaluator* c) : cb(c) {}
+  int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs, uint32_t n,
+               uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) override {
+    int rc = cb->evaluate(cb->user, cols.data(), offs.data(), n, counts, fitness, overlaps);
+    return rc == 0 ? EBIC_OK : set_last_error(EBIC_ERR_INVALID_ARG, "evaluate callback failed");
+  }
+  int pair_overlaps(const std::vector<uint32_t>& idx, uint32_t* out) override {
+    int rc = cb->pair_overlaps(cb->user, idx.data(), (uint32_t)idx.size(), out);
+    return rc == 0 ? EBIC_OK : set_last_error(EBIC_ERR_INVALID_ARG, "pair_overlaps callback failed");
+  }
+  int set_archive(const std::vector<int32_t>& src) override {
+    int rc = cb->set_archive(cb->user, src.data(), (uint32_t)src.size());
+    return rc == 0 ? EBIC_OK : set_last_error(EBIC_ERR_INVALID_ARG, "set_archive callback failed");
+  }
+};
+
+// ---- scoring on the GPU: device-resident bitmaps and archive ------------------------------------
+#define GA_CUDA(expr)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      (void)cudaGetLastError();                                                          \
+      return set_last_error(e_ == cudaErrorMemoryAllocation ? EBIC_ERR_OOM : EBIC_ERR_CUDA, \
+                            (std::string(#expr) + ": " + cudaGetErrorString(e_)).c_str()); \
+    }                                                                                    \
+  } while (0)
+
+struct GpuEvaluator : Evaluator {
+  const ebic_matrix* m;
+  cudaStream_t s;
+  uint32_t flags, P, K, T, max_len;
+  int64_t W;
+  std::vector<void*> allocs;
+  uint16_t *dcols = nullptr, *acols = nullptr, *pcols = nullptr;
+  uint32_t *doffs = nullptr, *dcounts = nullptr, *dbm = nullptr, *dov = nullptr;
+  uint32_t *aoffs = nullptr, *abm = nullptr, *abm_next = nullptr;
+  uint32_t *poffs = nullptr, *pcounts = nullptr, *pbm = nullptr, *pov = nullptr;
+  uint64_t *dfit = nullptr, *pfit = nullptr;
+  std::vector<uint16_t> pop_cols, arch_cols;
+  std::vector<uint32_t> pop_offs, arch_offs{0}, host_counts;
+  uint32_t n_arch = 0;
+
+  GpuEvaluator(const ebic_matrix* mm, cudaStream_t st, const ebic_params& p, int64_t words)
+      : m(mm), s(st), flags(p.flags), P(p.population), K(p.archive_size),
+        T(2 * p.archive_size), max_len(p.max_len), W(words) {}
+  ~GpuEvaluator() override {
+    cudaStreamSynchronize(s);
+    for (void* a : allocs) cudaFree(a);
+  }
+  template <class X>
+  cudaError_t alloc(X** p, size_t n) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, (n ? n : 1) * sizeof(X));
+    if (e == cudaSuccess) allocs.push_back(v);
+    *p = static_cast<X*>(v);
+    return e;
+  }
+  int init() {
+    GA_CUDA(alloc(&dcols, (size_t)P * max_len));
+    GA_CUDA(alloc(&doffs, (size_t)P + 1));
+    GA_CUDA(alloc(&dcounts, P));
+    GA_CUDA(alloc(&dbm, (size_t)P * W));
+    GA_CUDA(alloc(&dfit, P));
+    GA_CUDA(alloc(&dov, (size_t)P * K));
+    GA_CUDA(alloc(&acols, (size_t)K * max_len));
+    GA_CUDA(alloc(&aoffs, (size_t)K + 1));
+    GA_CUDA(alloc(&abm, (size_t)K * W));
+    GA_CUDA(alloc(&abm_next, (size_t)K * W));
+    GA_CUDA(alloc(&pcols, (size_t)T * max_len));
+    GA_CUDA(alloc(&poffs, (size_t)T + 1));
+    GA_CUDA(alloc(&pcounts, T));
+    GA_CUDA(alloc(&pbm, (size_t)T * W));
+    GA_CUDA(alloc(&pfit, T));
+    GA_CUDA(alloc(&pov, (size_t)T * T));
+    return EBIC_OK;
+  }
+  int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs, uint32_t n,
+               uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) override {
+    pop_cols = cols;
+    pop_offs = offs;
+    GA_CUDA(cudaMemcpyAsync(dcols, cols.data(), cols.size() * 2, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaMemcpyAsync(doffs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, s));
+    int rc = ebic_eval_population(m, dcols, doffs, n, flags, dcounts, dbm, s);
+    if (rc != EBIC_OK) return rc;
+    rc = ebic_fitness(m, dcols, doffs, n, dcounts, dbm, acols, aoffs, abm, n_arch, 0, dfit,
+                      n_arch ? dov : nullptr, s);
+    if (rc != EBIC_OK) return rc;
+    GA_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    if (n_arch)
+      GA_CUDA(cudaMemcpyAsync(overlaps, dov, (size_t)n * n_arch * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaStreamSynchronize(s));
+    host_counts.assign(counts, counts + n);
+    return ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
+  }
+  int pair_overlaps(const std::vector<uint32_t>& idx, uint32_t* out) override {
+    const uint32_t t = (uint32_t)idx.size();
+    std::vector<uint16_t> c;
+    std::vector<uint32_t> o{0}, cn;
+    for (uint32_t k = 0; k < t; ++k) {
+      const uint32_t i = idx[k];
+      c.insert(c.end(), pop_cols.begin() + pop_offs[i], pop_cols.begin() + pop_offs[i + 1]);
+      o.push_back((uint32_t)c.size());
+      cn.push_back(host_counts[i]);
+      GA_CUDA(cudaMemcpyAsync(pbm + (size_t)k * W, dbm + (size_t)i * W, (size_t)W * 4,
+                              cudaMemcpyDeviceToDevice, s));
+    }
+    GA_CUDA(cudaMemcpyAsync(pcols, c.data(), c.size() * 2, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaMemcpyAsync(poffs, o.data(), o.size() * 4, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaMemcpyAsync(pcounts, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
+    int rc = ebic_fitness(m, pcols, poffs, t, pcounts, pbm, pcols, poffs, pbm, t, 0, pfit, pov, s);
+    if (rc != EBIC_OK) return rc;
+    GA_CUDA(cudaMemcpyAsync(out, pov, (size_t)t * t * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaStreamSynchronize(s));
+    return ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
+  }
+  int set_archive(const std::vector<int32_t>& src) override {
+    std::vector<uint16_t> c;
+    std::vector<uint32_t> o{0};
+    for (size_t k = 0; k < src.size(); ++k) {
+      const uint32_t* from;
+      if (src[k] >= 0) {
+        const uint32_t i = (uint32_t)src[k];
+        c.insert(c.end(), pop_cols.begin() + pop_offs[i], pop_cols.begin() + pop_offs[i + 1]);
+        from = dbm + (size_t)i * W;
+      } else {
+        const uint32_t a = (uint32_t)(-src[k] - 1);
+        c.insert(c.end(), arch_cols.begin() + arch_offs[a], arch_cols.begin() + arch_offs[a + 1]);
+        from = abm + (size_t)a * W;
+      }
+      o.push_back((uint32_t)c.size());
+      GA_CUDA(cudaMemcpyAsync(abm_next + k * W, from, (size_t)W * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    std::swap(abm, abm_next);
+    arch_cols = c;
+    arch_offs = o;
+    n_arch = (uint32_t)src.size();
+    if (!c.empty())
+      GA_CUDA(cudaMemcpyAsync(acols, c.data(), c.size() * 2, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaMemcpyAsync(aoffs, o.data(), o.size() * 4, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaStreamSynchronize(s));  // host vectors c, o go out of scope
+    return EBIC_OK;
+  }
+  bool has_bitmaps() const override { return true; }
+  int archive_bitmaps(uint32_t* out, uint32_t k) override {
+    if (k) GA_CUDA(cudaMemcpyAsync(out, abm, (size_t)k * W * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaStreamSynchronize(s));
+    return EBIC_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int ebic_params_default(ebic_params* p) {
+  if (!p) return set_last_error(EBIC_ERR_INVALID_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->population = 1600;
+  p->generations = 100;
+  p->archive_size = 20;
+  p->elite = 16;
+  p->tournament = 4;
+  p->min_len = 2;
+  p->max_init_len = 6;
+  p->max_len = 64;
+  p->p_crossover = 0.5f;
+  p->p_mutation = 0.7f;
+  p->overlap_threshold = 0.5f;
+  p->tabu_retries = 8;
+  p->flags = 0;
+  p->seed = 1807099320ull;
+  return EBIC_OK;
+}
+
+int ebic_run_custom(int64_t rows, int32_t cols, const ebic_params* p, const ebic_evaluator* ev,
+                    ebic_result** out) {
+  if (!p || !ev || !out || !ev->evaluate || !ev->pair_overlaps || !ev->set_archive)
+    return set_last_error(EBIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (rows < 1 || cols < 1 || cols > EBIC_MAX_COLS)
+    return set_last_error(EBIC_ERR_INVALID_ARG, "rows/cols out of range");
+  std::string why = check_params(*p, cols);
+  if (!why.empty()) return set_last_error(EBIC_ERR_INVALID_ARG, why.c_str());
+  try {
+    CallbackEvaluator e(ev);
+    return run_ga(rows, cols, *p, e, out);
+  } catch (const std::bad_alloc&) {
+    return set_last_error(EBIC_ERR_OOM, "host allocation failed");
+  }
+}
+
+int ebic_run(const ebic_matrix* m, const ebic_params* p, void* stream, ebic_result** out) {
+  if (!m || !p || !out) return set_last_error(EBIC_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  MatrixView v;
+  matrix_view(m, &v);
+  std::string why = check_params(*p, v.L.cols);
+  if (!why.empty()) return set_last_error(EBIC_ERR_INVALID_ARG, why.c_str());
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) { (void)cudaGetLastError(); prev = -1; }
+  if (prev != v.device) (void)cudaSetDevice(v.device);
+  int rc;
+  try {
+    GpuEvaluator e(m, static_cast<cudaStream_t>(stream), *p, v.L.words);
+    rc = e.init();
+    if (rc == EBIC_OK) rc = run_ga(v.L.rows, v.L.cols, *p, e, out);
+  } catch (const std::bad_alloc&) {
+    rc = set_last_error(EBIC_ERR_OOM, "host allocation failed");
+  }
+  if (prev >= 0 && prev != v.device) (void)cudaSetDevice(prev);
+  return rc;
+}
+
+int ebic_free_result(ebic_result* r) {
+  if (!r) return EBIC_OK;
+  delete[] r->cols;
+  delete[] r->offsets;
+  delete[] r->counts;
+  delete[] r->quality;
+  delete[] r->bitmaps;
+  delete r;
+  return EBIC_OK;
+}
+
+}  // extern "C"

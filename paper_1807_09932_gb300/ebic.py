@@ -65,6 +65,51 @@ _lib_timing_enable = _sig("ebic_timing_enable", [ctypes.c_int])
 _lib_timing_read = _sig("ebic_timing_read", [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(_I64)])
 _lib_version = _sig("ebic_version", [])
+_lib_selftest = _sig("ebic_selftest_wait_timeout", [ctypes.c_uint64, _P])
+
+
+class EbicParams(ctypes.Structure):
+    _fields_ = [("population", ctypes.c_uint32), ("generations", ctypes.c_uint32),
+                ("archive_size", ctypes.c_uint32), ("elite", ctypes.c_uint32),
+                ("tournament", ctypes.c_uint32), ("min_len", ctypes.c_uint32),
+                ("max_init_len", ctypes.c_uint32), ("max_len", ctypes.c_uint32),
+                ("p_crossover", ctypes.c_float), ("p_mutation", ctypes.c_float),
+                ("overlap_threshold", ctypes.c_float), ("tabu_retries", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class EbicResult(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("cols", ctypes.POINTER(ctypes.c_uint16)),
+                ("offsets", ctypes.POINTER(ctypes.c_uint32)),
+                ("counts", ctypes.POINTER(ctypes.c_uint32)),
+                ("quality", ctypes.POINTER(ctypes.c_uint64)),
+                ("bitmaps", ctypes.POINTER(ctypes.c_uint32)), ("words", ctypes.c_int64),
+                ("generations_run", ctypes.c_uint32), ("candidates_evaluated", ctypes.c_uint64)]
+
+
+EVALUATE_FN = ctypes.CFUNCTYPE(ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint16),
+                               ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.POINTER(ctypes.c_uint32))
+PAIR_FN = ctypes.CFUNCTYPE(ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                           ctypes.POINTER(ctypes.c_uint32))
+SET_ARCHIVE_FN = ctypes.CFUNCTYPE(ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.c_uint32)
+
+
+class EbicEvaluator(ctypes.Structure):
+    _fields_ = [("user", _P), ("evaluate", EVALUATE_FN), ("pair_overlaps", PAIR_FN),
+                ("set_archive", SET_ARCHIVE_FN)]
+
+
+_lib_params_default = _sig("ebic_params_default", [ctypes.POINTER(EbicParams)])
+_lib_run = _sig("ebic_run", [_P, ctypes.POINTER(EbicParams), _P,
+                             ctypes.POINTER(ctypes.POINTER(EbicResult))])
+_lib_run_custom = _sig("ebic_run_custom", [_I64, _I32, ctypes.POINTER(EbicParams),
+                                           ctypes.POINTER(EbicEvaluator),
+                                           ctypes.POINTER(ctypes.POINTER(EbicResult))])
+_lib_free_result = _sig("ebic_free_result", [ctypes.POINTER(EbicResult)])
 
 
 class EbicError(RuntimeError):
@@ -186,6 +231,56 @@ def ebic_timing_read(kind):
     ms, n = ctypes.c_double(), _I64()
     _check(_lib_timing_read(kind, ctypes.byref(ms), ctypes.byref(n)), "ebic_timing_read")
     return ms.value, n.value
+
+
+def ebic_params_default(**overrides):
+    p = EbicParams()
+    _check(_lib_params_default(ctypes.byref(p)), "ebic_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _take_result(rp):
+    r = rp.contents
+    n = r.n
+    offs = np.ctypeslib.as_array(r.offsets, (n + 1,)).copy()
+    out = {"offsets": offs,
+           "cols": np.ctypeslib.as_array(r.cols, (max(int(offs[-1]), 1),))[: int(offs[-1])].copy(),
+           "counts": np.ctypeslib.as_array(r.counts, (max(n, 1),))[:n].copy(),
+           "quality": np.ctypeslib.as_array(r.quality, (max(n, 1),))[:n].copy(),
+           "generations_run": r.generations_run,
+           "candidates_evaluated": r.candidates_evaluated,
+           "bitmaps": None}
+    if bool(r.bitmaps):
+        out["bitmaps"] = np.ctypeslib.as_array(r.bitmaps, (n * r.words + 1,))[: n * r.words] \
+            .reshape(n, r.words).copy()
+    _lib_free_result(rp)
+    out["members"] = [out["cols"][offs[i]:offs[i + 1]].tolist() for i in range(n)]
+    return out
+
+
+def ebic_run(h, params, stream=None):
+    """Run the EBIC generation loop on a loaded matrix; returns the archive as a dict."""
+    rp = ctypes.POINTER(EbicResult)()
+    _check(_lib_run(h, ctypes.byref(params), _stream(stream), ctypes.byref(rp)), "ebic_run")
+    return _take_result(rp)
+
+
+def ebic_run_custom(rows, cols, params, evaluator):
+    """The same loop over an EbicEvaluator of Python callbacks (host buffers)."""
+    rp = ctypes.POINTER(EbicResult)()
+    _check(_lib_run_custom(rows, cols, ctypes.byref(params), ctypes.byref(evaluator),
+                           ctypes.byref(rp)), "ebic_run_custom")
+    return _take_result(rp)
+
+
+def ebic_free_result(rp):
+    _check(_lib_free_result(rp), "ebic_free_result")
+
+
+def ebic_selftest_wait_timeout(timeout_ns, stream=None):
+    return _lib_selftest(timeout_ns, _stream(stream))
 
 
 def ebic_last_error():

@@ -222,6 +222,10 @@ def check_fitness(seed, R=700, C=30, P=60, K=7):
     abm = synth.random_bitmaps(seed + 2, K, R, density=0.4)
     fit, ov = oracle.fitness(R, cols, offs, counts, bm, acols, aoffs, abm)
     arows = [bits_to_rows(abm[a]) for a in range(K)]
+
+    def q(n, L):
+        return n * 2 ** (min(L, 33) - 1)
+
     for i, cand in enumerate(cands):
         rows_i = bits_to_rows(bm[i])
         assert len(rows_i) == counts[i]
@@ -229,9 +233,27 @@ def check_fitness(seed, R=700, C=30, P=60, K=7):
         for a in range(K):
             o = len(rows_i & arows[a])
             assert ov[i, a] == o
-            if set(cand) & set(acands[a]):
+            # a penalises only when it shares a column and is at least as good as the candidate
+            if set(cand) & set(acands[a]) and q(len(arows[a]), len(acands[a])) >= q(
+                    len(rows_i), len(cand)):
                 pen = max(pen, o)
-        assert int(fit[i]) == (int(counts[i]) - pen) * 2 ** (min(len(cand), 33) - 1)
+        assert int(fit[i]) == q(int(counts[i]) - pen, len(cand))
+
+    # a better candidate (superset of an archived bicluster's columns, fewer rows but a higher
+    # quality) is not penalised by it; the archived one is penalised by the better one
+    sub = [list(range(4))]
+    sup = [list(range(6))]
+    Xs = np.tile(np.arange(6, dtype=np.float32), (R, 1))      # every row increasing
+    Xs[: R // 3, 5] = -1.0                                    # a third fail the 6-column chain
+    sc, so = synth.population_from_lists(sub)
+    pc, po = synth.population_from_lists(sup)
+    nsub, bsub = oracle.eval_population(Xs, sc, so)
+    nsup, bsup = oracle.eval_population(Xs, pc, po)
+    assert q(int(nsup[0]), 6) > q(int(nsub[0]), 4)
+    fsup, _ = oracle.fitness(R, pc, po, nsup, bsup, sc, so, bsub)
+    assert int(fsup[0]) == q(int(nsup[0]), 6)
+    fsub, osub = oracle.fitness(R, sc, so, nsub, bsub, pc, po, bsup)
+    assert int(fsub[0]) == q(int(nsub[0]) - int(osub[0, 0]), 4)
 
     # disjoint columns: no penalty whatever the row overlap
     dc, do = synth.population_from_lists([[0, 1, 2]])

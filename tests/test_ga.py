@@ -1,0 +1,134 @@
+"""The host generation loop (ebic_run / ebic_run_custom). The paper does not define EBIC's
+operators, so the loop is pinned for what it promises: determinism from the seed, the archive's
+order and admission rule, exact scores, and agreement of the GPU-scored run with an
+oracle-scored run step for step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09932_gb300 import synth
+
+from ga_oracle import OracleScorer
+
+
+def _ebic():
+    from paper_1807_09932_gb300 import build
+    build.build()
+    from paper_1807_09932_gb300 import ebic
+    return ebic
+
+
+def _small(seed=3):
+    return synth.make_dataset(seed, 700, 24, kind="normal",
+                              planted=[(160, 7, False), (120, 5, True)], nan_frac=0.01)
+
+
+def _params(ebic, **kw):
+    base = dict(population=120, generations=12, archive_size=6, elite=6, tournament=3,
+                max_init_len=5, max_len=12, seed=11)
+    base.update(kw)
+    return ebic.ebic_params_default(**base)
+
+
+def _run_oracle(ebic, ds, params, negative=False):
+    sc = OracleScorer(ds.X, negative=negative)
+    res = ebic.ebic_run_custom(ds.X.shape[0], ds.X.shape[1], params, sc.evaluator)
+    assert sc.error is None, sc.error
+    return res, sc
+
+
+def test_defaults():
+    ebic = _ebic()
+    p = ebic.ebic_params_default()
+    assert (p.population, p.generations, p.archive_size, p.max_len) == (1600, 100, 20, 64)
+
+
+def test_deterministic_and_seed_dependent():
+    ebic = _ebic()
+    ds = _small()
+    a, _ = _run_oracle(ebic, ds, _params(ebic))
+    b, _ = _run_oracle(ebic, ds, _params(ebic))
+    assert a["members"] == b["members"] and np.array_equal(a["counts"], b["counts"])
+    c, _ = _run_oracle(ebic, ds, _params(ebic, seed=12))
+    assert c["members"] != a["members"]
+    assert a["generations_run"] == 12 and a["candidates_evaluated"] == 12 * 120
+
+
+@pytest.mark.parametrize("negative", [False, True])
+def test_archive_invariants(negative):
+    ebic = _ebic()
+    ds = _small()
+    thr = 0.5
+    res, _ = _run_oracle(ebic, ds, _params(ebic, overlap_threshold=thr,
+                                           flags=ebic.EBIC_NEGATIVE_TRENDS if negative else 0),
+                         negative=negative)
+    members = res["members"]
+    assert 1 <= len(members) <= 6
+    assert len({tuple(m) for m in members}) == len(members)
+    cols, offs = synth.population_from_lists(members)
+    cnt, bm = oracle.eval_population(ds.X, cols, offs, negative=negative)
+    assert np.array_equal(cnt, res["counts"])                       # exact scores
+    q = [int(n) << (min(len(m), 33) - 1) for n, m in zip(cnt, members)]
+    assert q == res["quality"].tolist()
+    keys = [(-q[i], -int(cnt[i]), -len(members[i]), members[i]) for i in range(len(members))]
+    assert keys == sorted(keys)                                      # archive order
+    for i in range(len(members)):                                    # admission rule
+        for j in range(i + 1, len(members)):
+            if set(members[i]) & set(members[j]):
+                ov = int(np.sum([bin(int(x)).count("1") for x in (bm[i] & bm[j])]))
+                assert ov <= thr * max(cnt[i], cnt[j]) + 1e-9
+
+
+def test_search_recovers_a_planted_bicluster():
+    ebic = _ebic()
+    ds = synth.make_dataset(21, 800, 20, kind="normal", planted=[(240, 8, False)], nan_frac=0.0)
+    res, _ = _run_oracle(ebic, ds, _params(ebic, population=200, generations=25,
+                                           archive_size=5, max_len=10, seed=5))
+    planted = ds.planted[0]
+    best = res["members"][0]
+    # the best archive member lies inside the planted columns, and its rows cover most of the
+    # planted rows
+    assert len(set(best) & set(planted.cols.tolist())) >= 4, (best, planted.cols)
+    cols, offs = synth.population_from_lists([best])
+    _, bm = oracle.eval_population(ds.X, cols, offs)
+    rows = set(np.nonzero(np.unpackbits(bm[0].view(np.uint8), bitorder="little"))[0].tolist())
+    assert len(rows & set(planted.rows.tolist())) >= 0.9 * len(planted.rows)
+
+
+def test_rejects_bad_params():
+    ebic = _ebic()
+    ds = _small()
+    sc = OracleScorer(ds.X)
+    for bad in (dict(max_len=80), dict(min_len=0), dict(max_init_len=1, min_len=2),
+                dict(elite=500), dict(p_mutation=1.5)):
+        with pytest.raises(ebic.EbicError) as ei:
+            ebic.ebic_run_custom(700, 24, _params(ebic, **bad), sc.evaluator)
+        assert ei.value.code == ebic.EBIC_ERR_INVALID_ARG
+
+
+def test_callback_failure_is_reported():
+    ebic = _ebic()
+    ds = _small()
+    sc = OracleScorer(ds.X)
+    sc.X = None  # the evaluate callback raises -> returns 1
+    with pytest.raises(ebic.EbicError):
+        ebic.ebic_run_custom(700, 24, _params(ebic), sc.evaluator)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("negative", [False, True])
+def test_gpu_run_equals_oracle_run(negative):
+    """The GPU-scored loop and the oracle-scored loop take identical decisions."""
+    ebic = _ebic()
+    ds = _small(seed=8)
+    flags = ebic.EBIC_NEGATIVE_TRENDS if negative else 0
+    params = _params(ebic, flags=flags, generations=10)
+    ref, _ = _run_oracle(ebic, ds, params, negative=negative)
+    with ebic.Matrix(ds.X) as m:
+        got = ebic.ebic_run(m.handle, params)
+    assert got["members"] == ref["members"]
+    assert np.array_equal(got["counts"], ref["counts"])
+    assert np.array_equal(got["quality"], ref["quality"])
+    cols, offs = synth.population_from_lists(got["members"])
+    _, bm = oracle.eval_population(ds.X, cols, offs, negative=negative)
+    assert np.array_equal(got["bitmaps"], bm)

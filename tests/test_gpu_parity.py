@@ -245,3 +245,13 @@ def test_config3_full_size_sampled(ebic):
     ec, eb = oracle.eval_population(X, sc, so)
     assert np.array_equal(got_c[idx], ec)
     assert np.array_equal(got_b[idx], eb)
+
+
+def test_bounded_wait_expires_cleanly_and_context_survives(ebic):
+    """Failure detection on the GPU without a fault: a wait that nothing satisfies expires after
+    its limit, the kernel reports it, and the next evaluation runs normally."""
+    rc = ebic.ebic_selftest_wait_timeout(1_000_000)
+    assert rc == ebic.EBIC_ERR_DEVICE_TIMEOUT
+    assert "expired" in ebic.ebic_last_error()
+    ds, cols, offs = synth.config1()
+    check_eval(ebic, ds.X, cols, offs)

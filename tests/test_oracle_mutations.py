@@ -24,16 +24,22 @@ MUTATIONS = {
     "bit index off by one": ("bm[r >> 5] |= 1u << (r & 31);", "bm[r >> 5] |= 1u << ((r + 1) & 31);"),
     "last row skipped": ("for (int64_t r = 0; r < R; ++r) {\n            int m",
                          "for (int64_t r = 0; r + 1 < R; ++r) {\n            int m"),
-    "penalty without shared columns": ("if (s && o > penalty) penalty = o;",
-                                       "if (o > penalty) penalty = o;"),
-    "penalty summed": ("if (s && o > penalty) penalty = o;", "if (s) penalty += o;"),
+    "penalty without shared columns": ("if (s && at_least_as_good && o > penalty) penalty = o;",
+                                       "if (at_least_as_good && o > penalty) penalty = o;"),
+    "penalty from worse members": ("if (s && at_least_as_good && o > penalty) penalty = o;",
+                                   "if (s && o > penalty) penalty = o;"),
+    "penalty summed": ("if (s && at_least_as_good && o > penalty) penalty = o;",
+                       "if (s && at_least_as_good) penalty += o;"),
+    "domination compared strictly": ("int at_least_as_good = quality(na, La) >= qc;",
+                                     "int at_least_as_good = quality(na, La) > qc;"),
     "weight exponent off by one": ("uint32_t shift = (L < 33 ? L : 33) - 1;",
                                    "uint32_t shift = (L < 33 ? L : 33);"),
     "rank counts duplicates": ("rank += (uint32_t)first;", "rank += 1u;"),
     "rank uses <=": ("if (miss[i] || !(v[i] < v[j])) continue;",
                      "if (miss[i] || !(v[i] <= v[j])) continue;"),
-    "overlap drops last word": ("for (int64_t w = 0; w < W; ++w)\n                o +=",
-                                "for (int64_t w = 0; w + 1 < W; ++w)\n                o +="),
+    "overlap drops last word": ("o += popcount32(bitmaps[p * W + w] & abitmaps[(int64_t)a * W + w]);",
+                                "o += (w + 1 < W) ? popcount32(bitmaps[p * W + w] & "
+                                "abitmaps[(int64_t)a * W + w]) : 0u;"),
 }
 
 CHECKS = [
