@@ -185,6 +185,39 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
 /* The tile height in slabs that the next evaluation will use, and the rows per slab. */
 int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab);
 
+/* ---- batched evaluation: many populations on many matrices in one launch ------------------ */
+/*
+ * One request = one population to score on one loaded matrix, as for ebic_eval_population,
+ * except that every buffer must be device memory of the matrices' (common) device. Candidate lists
+ * are checked on the device; a failed request produces zero counts and no bitmaps, its matrix's
+ * status records EBIC_ERR_INVALID_ARG, and the others are unaffected.
+ * Results are identical to scoring each request alone with ebic_eval_population.
+ */
+typedef struct ebic_eval_request {
+  const ebic_matrix* m;
+  const uint16_t* cols;      /* device CSR columns                                            */
+  const uint32_t* offsets;   /* device CSR offsets [n_cand+1]                                 */
+  uint32_t n_cand;
+  uint32_t flags;            /* EBIC_NEGATIVE_TRENDS or 0                                     */
+  uint32_t* counts;          /* device [n_cand]                                               */
+  uint32_t* bitmaps;         /* device [n_cand][W], or NULL for counts only                   */
+} ebic_eval_request;
+
+/* Score all requests in one persistent launch (plus a check and a plan kernel), asynchronously on
+ * `stream`. Row tiles and candidate chunks of all requests share one dynamic work queue. */
+int ebic_eval_batch(const ebic_eval_request* reqs, uint32_t n_req, void* stream);
+
+/* The same batched launch, captured once in a CUDA graph and replayed. A batch holds device and
+ * pinned host buffers for up to max_requests requests; ebic_batch_run writes the requests into its
+ * pinned block (waiting for the previous replay to finish reading it) and launches the graph on
+ * `stream`. Any composition of up to max_requests requests replays the same graph. */
+typedef struct ebic_batch ebic_batch;
+int ebic_batch_create(uint32_t max_requests, ebic_batch** out);
+int ebic_batch_run(ebic_batch* b, const ebic_eval_request* reqs, uint32_t n_req, void* stream);
+/* Synchronize `stream`; req_status[i] (i < n) receives request i's check bits of the last run. */
+int ebic_batch_status(ebic_batch* b, uint32_t* req_status, uint32_t n, void* stream);
+int ebic_batch_free(ebic_batch* b);
+
 /* ---- the EBIC generation loop (host genetic algorithm over the device evaluator) --------- */
 /*
  * The paper says EBIC uses evolutionary computation over a population of up to 65,535

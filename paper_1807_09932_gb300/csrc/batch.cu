@@ -1,0 +1,680 @@
+// Batched evaluation: many populations on many matrices in one persistent launch.
+//
+// EBIC runs that proceed side by side (many runs, many datasets) each submit one population per
+// generation. Scoring each with its own launch leaves most of the GPU idle for small matrices and
+// pays a launch per population. Here one persistent kernel scores all of them:
+//   * work items are (request, candidate chunk, row tile) triples; a device-side plan kernel turns
+//     each request's candidate count and column total into an item range (prefix sums), so the
+//     sequence of launches needs no host round trip and can be captured in a CUDA graph;
+//   * CTAs take items from one atomic counter (dynamic load balance across uneven candidate
+//     lengths, 2-64, and uneven matrix sizes) and prefetch the next item's row tile with TMA into
+//     the other of two shared-memory stages while they compute the current one;
+//   * every request keeps its own rank layout (8- or 16-bit ranks, VEC, tile height) and
+//     negative-trend option; a switch per item selects the matching instantiation of the same
+//     inner loop as the single-population evaluator, so results are identical to it;
+//   * tensor maps of all matrices sit in a device array.
+// A check kernel first validates every request's candidate list on the device (CSR shape,
+// column range, repeats) and zeroes its counts; a failed request gets no work items.
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ebic.h"
+#include "eval_kernel.cuh"
+
+namespace ebic {
+namespace {
+
+constexpr int kBatchThreads = 512;
+constexpr int kBatchWarps = kBatchThreads / 32;
+
+// layout cases: 0..2 = 8-bit ranks, VEC 4, TS 1/2/4; 3 = 16-bit VEC 4; 4 = VEC 2; 5 = VEC 1
+int layout_case(const Layout& L, int ts) {
+  if (L.width == 8) return ts == 1 ? 0 : ts == 2 ? 1 : 2;
+  return L.vec == 4 ? 3 : L.vec == 2 ? 4 : 5;
+}
+
+struct BatchReq {
+  const uint16_t* cand_cols;
+  const uint32_t* cand_offsets;
+  uint32_t* counts;
+  uint32_t* bitmaps;  // may be null: counts only
+  uint32_t* status;   // the matrix's deferred-status word
+  int64_t slabs, groups, words;
+  uint32_t n_cand;
+  uint32_t cand_base;  // sum of n_cand of the requests before this one
+  int32_t lcase;       // layout case
+  int32_t vec;         // row groups per slab
+  int32_t neg;
+  int32_t ts;
+  int32_t col_box, n_col_boxes;
+  uint32_t stage_bytes;
+  int32_t chunk_cols;
+  uint32_t tmap;       // index into the tensor-map array
+};
+
+struct BatchHeader {
+  uint32_t n_req;
+  uint32_t total_cand;
+  unsigned long long next_item;   // work counter, reset by the plan kernel
+  unsigned long long total_items;
+};
+
+__device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t n, uint32_t cand) {
+  uint32_t lo = 0, hi = n;  // last request with cand_base <= cand
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (reqs[mid].cand_base <= cand) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t find_item(const unsigned long long* start, uint32_t n,
+                                              unsigned long long g) {
+  uint32_t lo = 0, hi = n;  // last request with start <= g
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (start[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Check every candidate of every request (same rules and bounds as the single-population
+// check) and zero the counts. Grid-stride, so the grid does not depend on the batch.
+__global__ void batch_check_kernel(const BatchReq* __restrict__ reqs,
+                                   const BatchHeader* __restrict__ hdr, int32_t* ncols_of,
+                                   uint32_t* __restrict__ req_err) {
+  const uint32_t n_req = hdr->n_req, total = hdr->total_cand;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += gridDim.x * blockDim.x) {
+    const uint32_t r = find_request(reqs, n_req, g);
+    const BatchReq& q = reqs[r];
+    const uint32_t i = g - q.cand_base;
+    q.counts[i] = 0u;
+    const uint32_t* offs = q.cand_offsets;
+    const uint32_t tot = offs[q.n_cand];
+    const uint32_t lo = offs[i], hi = offs[i + 1];
+    bool bad = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > tot;
+    if (!bad) {
+      for (uint32_t j = lo; j < hi; ++j) {
+        const uint16_t c = q.cand_cols[j];
+        bad |= c >= (uint32_t)ncols_of[r];
+        for (uint32_t t = lo; t < j; ++t) bad |= q.cand_cols[t] == c;
+      }
+    }
+    if (bad) {
+      atomicOr(&req_err[r], kErrInvalid);
+      atomicOr(q.status, kErrInvalid);
+    }
+  }
+}
+
+// Item ranges: request r owns items [start[r], start[r+1]) = chunks x row tiles. One thread.
+__global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader* hdr,
+                                  const uint32_t* __restrict__ req_err,
+                                  unsigned long long* __restrict__ start) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  unsigned long long acc = 0;
+  for (uint32_t r = 0; r < hdr->n_req; ++r) {
+    start[r] = acc;
+    const BatchReq& q = reqs[r];
+    if (q.n_cand == 0 || req_err[r] != 0u) continue;
+    const unsigned long long total = q.cand_offsets[q.n_cand];
+    const unsigned long long chunks = (total + q.chunk_cols - 1) / q.chunk_cols;
+    const unsigned long long tiles = (unsigned long long)((q.slabs + q.ts - 1) / q.ts);
+    acc += chunks * tiles;
+  }
+  start[hdr->n_req] = acc;
+  hdr->total_items = acc;
+  hdr->next_item = 0ull;
+}
+
+// One row tile of one request for every candidate of the staged chunk.
+template <int WIDTH, int VEC, int TS, bool NEG>
+__device__ __forceinline__ void batch_tile(const uint8_t* stage, const BatchReq& q,
+                                           const uint16_t* ccols, const uint16_t* coffs,
+                                           uint32_t lo, uint32_t nc, int64_t tile, int lane,
+                                           int warp, const uint32_t (&trot)[5],
+                                           const uint32_t (&tsel)[5]) {
+  constexpr int GT = TS * VEC;
+  constexpr int WPT = GT * Swar<WIDTH>::WPG;
+  const uint32_t col_stride = TS * 128 * VEC;
+  const uint8_t* lane_base = stage + lane * 4 * VEC;
+  const int64_t word0 = tile * WPT;
+  const int64_t g0 = tile * GT;
+  for (uint32_t ci = warp; ci < nc; ci += kBatchWarps) {
+    const int o = coffs[ci];
+    const int L = coffs[ci + 1] - o;
+    uint32_t acc[GT];
+    trend_masks<WIDTH, VEC, TS, NEG>(lane_base, col_stride, ccols + o, L, acc);
+    const uint32_t cand = lo + ci;
+    uint32_t cnt = 0;
+    if (q.bitmaps) {
+      uint32_t* out = q.bitmaps + (size_t)cand * (size_t)q.words;
+#pragma unroll
+      for (int b = 0; b < (GT + WIDTH - 1) / WIDTH; ++b) {
+        const uint32_t w = transpose32(pack_block<WIDTH, GT>(acc, b), trot, tsel);
+        const int g = b * WIDTH + (lane % WIDTH);
+        const int64_t widx = word0 + g * Swar<WIDTH>::WPG + lane / WIDTH;
+        if (g < GT && widx < q.words) {
+          out[widx] = w;
+          cnt += __popc(w);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int g = 0; g < GT; ++g)
+        if (g0 + g < q.groups) cnt += __popc(acc[g] & Swar<WIDTH>::H);
+    }
+    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    if (lane == 0 && cnt) atomicAdd(&q.counts[cand], cnt);
+  }
+}
+
+template <bool NEG>
+__device__ __forceinline__ void batch_tile_case(int lcase, const uint8_t* stage,
+                                                const BatchReq& q, const uint16_t* ccols,
+                                                const uint16_t* coffs, uint32_t lo, uint32_t nc,
+                                                int64_t tile, int lane, int warp,
+                                                const uint32_t (&trot)[5],
+                                                const uint32_t (&tsel)[5]) {
+  switch (lcase) {
+    case 0: batch_tile<8, 4, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    case 1: batch_tile<8, 4, 2, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    case 2: batch_tile<8, 4, 4, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    case 3: batch_tile<16, 4, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    case 4: batch_tile<16, 2, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    default: batch_tile<16, 1, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+  }
+}
+
+// Shared memory: [stage 0][stage 1][chunk columns (chunk_cap + slack)][chunk offsets]
+__global__ void __launch_bounds__(kBatchThreads, 1)
+    batch_eval_kernel(const BatchReq* __restrict__ reqs, const CUtensorMap* __restrict__ tmaps,
+                      BatchHeader* hdr, const unsigned long long* __restrict__ start,
+                      uint32_t stage_cap, int32_t chunk_cap, uint64_t timeout_ns,
+                      uint32_t* err_out) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full_bar[2];
+  __shared__ unsigned long long item_s[2];
+  __shared__ BatchReq q;
+  __shared__ uint32_t cur_r, cur_lo, cur_nc;
+  __shared__ long long cur_k;
+  __shared__ long long it_tile;
+  __shared__ int it_stage;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t trot[5], tsel[5];
+  transpose_consts(lane, trot, tsel);
+  const uint32_t n_req = hdr->n_req;
+  const unsigned long long total = hdr->total_items;
+  uint8_t* const stage0 = smem;
+  uint8_t* const stage1 = smem + stage_cap;
+  uint16_t* const ccols = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)stage_cap);
+  uint16_t* const coffs = ccols + chunk_cap + kChunkSlack;
+
+  auto issue = [&](unsigned long long g, int s) {  // thread 0 only
+    const uint32_t r = find_item(start, n_req, g);
+    const BatchReq& rq = reqs[r];
+    const unsigned long long local = g - start[r];
+    const long long n_tiles = (rq.slabs + rq.ts - 1) / rq.ts;
+    const long long tile = (long long)(local % (unsigned long long)n_tiles);
+    const uint32_t col_stride = (uint32_t)rq.ts * 128u * (uint32_t)rq.vec;
+    uint8_t* dst = s ? stage1 : stage0;
+    dev::acquire_tensormap(&tmaps[rq.tmap]);
+    dev::mbar_arrive_expect_tx(&full_bar[s], rq.stage_bytes);
+    for (int b = 0; b < rq.n_col_boxes; ++b)
+      dev::tma_load_3d(dst + (size_t)b * rq.col_box * col_stride, &tmaps[rq.tmap], &full_bar[s],
+                       0, (int32_t)(tile * rq.ts), b * rq.col_box);
+  };
+
+  if (tid == 0) {
+    dev::mbar_init(&full_bar[0], 1);
+    dev::mbar_init(&full_bar[1], 1);
+    dev::fence_barrier_init();
+    cur_r = 0xFFFFFFFFu;
+    cur_k = -1;
+    for (int s = 0; s < 2; ++s) {
+      const unsigned long long g = atomicAdd(&hdr->next_item, 1ull);
+      item_s[s] = g;
+      if (g < total) issue(g, s);
+    }
+  }
+  __syncthreads();
+
+  bool timed_out = false;
+  int it = 0;
+  for (;; ++it) {
+    const int s = it & 1;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    const unsigned long long g = item_s[s];
+    if (g >= total) break;
+    // thread 0 decides, before the barrier, whether this item needs a new chunk staged, so that
+    // every thread takes the same branch
+    if (tid == 0) {
+      const uint32_t r = find_item(start, n_req, g);
+      const unsigned long long local = g - start[r];
+      const long long n_tiles = (reqs[r].slabs + reqs[r].ts - 1) / reqs[r].ts;
+      const long long k = (long long)(local / (unsigned long long)n_tiles);
+      it_tile = (long long)(local % (unsigned long long)n_tiles);
+      it_stage = (r != cur_r || k != cur_k) ? 1 : 0;
+      if (it_stage) {
+        q = reqs[r];
+        const uint32_t l = lower_bound_u32(q.cand_offsets, q.n_cand, (uint64_t)k * q.chunk_cols);
+        const uint32_t h =
+            lower_bound_u32(q.cand_offsets, q.n_cand, (uint64_t)(k + 1) * q.chunk_cols);
+        cur_lo = l;
+        cur_nc = h - l;
+        cur_r = r;
+        cur_k = k;
+      }
+    }
+    __syncthreads();
+    const long long tile = it_tile;
+    if (it_stage) {  // stage the chunk's candidate lists
+      const uint32_t c0 = q.cand_offsets[cur_lo];
+      const uint32_t span = q.cand_offsets[cur_lo + cur_nc] - c0;
+      for (uint32_t i = tid; i < span; i += kBatchThreads) ccols[i] = q.cand_cols[c0 + i];
+      for (uint32_t i = tid; i <= cur_nc; i += kBatchThreads)
+        coffs[i] = (uint16_t)(q.cand_offsets[cur_lo + i] - c0);
+      __syncthreads();
+    }
+    const bool ok = dev::mbar_wait_bounded(&full_bar[s], parity, timeout_ns);
+    if (!__syncthreads_and(ok)) { timed_out = true; break; }
+    const uint8_t* stage = s ? stage1 : stage0;
+    if (q.neg)
+      batch_tile_case<true>(q.lcase, stage, q, ccols, coffs, cur_lo, cur_nc, tile, lane, warp,
+                            trot, tsel);
+    else
+      batch_tile_case<false>(q.lcase, stage, q, ccols, coffs, cur_lo, cur_nc, tile, lane, warp,
+                             trot, tsel);
+    __syncthreads();  // every warp is done with stage s
+    if (tid == 0) {
+      const unsigned long long gn = atomicAdd(&hdr->next_item, 1ull);
+      item_s[s] = gn;
+      if (gn < total) issue(gn, s);
+    }
+    __syncthreads();
+  }
+  if (timed_out && tid == 0) {
+    atomicOr(err_out, kErrTimeout);
+    atomicOr(q.status, kErrTimeout);
+    // wait, bounded, for the copies still in flight into this CTA's shared memory
+    for (int d = 0; d < 2; ++d) {
+      const int s = (it + d) & 1;
+      if (item_s[s] < total)
+        dev::mbar_wait_bounded(&full_bar[s], (uint32_t)(((it + d) >> 1) & 1), timeout_ns);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace ebic
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+using namespace ebic;
+
+namespace {
+
+struct HostPlan {
+  std::vector<BatchReq> reqs;
+  std::vector<CUtensorMap> tmaps;
+  std::vector<int32_t> ncols;
+  uint32_t total_cand = 0;
+  uint32_t stage_cap = 0;
+  int32_t chunk_cap = 0;
+  int device = -1;
+  int num_sms = 0;
+};
+
+bool is_dev(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
+}
+
+// Host-side checks and per-request plans. fixed_stage_cap > 0 fixes the stage size (graphs).
+int build_plan(const ebic_eval_request* reqs, uint32_t n, uint32_t fixed_stage_cap,
+               HostPlan* hp) {
+  hp->reqs.clear();
+  hp->tmaps.clear();
+  hp->ncols.clear();
+  hp->total_cand = 0;
+  uint64_t total = 0;
+  uint32_t cap = fixed_stage_cap;
+  std::vector<EvalArgs> args(n);
+  std::vector<EvalConfig> cfgs(n);
+  std::vector<const CUtensorMap*> maps(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const ebic_eval_request& r = reqs[i];
+    if (!r.m) return set_last_error(EBIC_ERR_INVALID_ARG, "request has a NULL matrix");
+    MatrixView v;
+    matrix_view(r.m, &v);
+    if (hp->device < 0) {
+      hp->device = v.device;
+      hp->num_sms = v.num_sms;
+    }
+    if (v.device != hp->device)
+      return set_last_error(EBIC_ERR_INVALID_ARG, "all requests must use matrices of one device");
+    if (r.flags & ~EBIC_NEGATIVE_TRENDS) return set_last_error(EBIC_ERR_INVALID_ARG, "unknown flag");
+    if (r.n_cand > 0) {
+      if (!is_dev(r.cols, v.device) || !is_dev(r.offsets, v.device) ||
+          !is_dev(r.counts, v.device) || (r.bitmaps && !is_dev(r.bitmaps, v.device)))
+        return set_last_error(EBIC_ERR_INVALID_ARG,
+                              ("request " + std::to_string(i) +
+                               ": batched requests take device buffers only").c_str());
+    }
+    int rc = matrix_eval_plan(r.m, r.n_cand > 0 ? r.n_cand : 1, 0, &args[i], &cfgs[i], &maps[i]);
+    if (rc != EBIC_OK) return rc;
+    if (!fixed_stage_cap && args[i].stage_bytes > cap) cap = args[i].stage_bytes;
+    if (args[i].stage_bytes > cap)
+      return set_last_error(EBIC_ERR_UNSUPPORTED, "a request's tile exceeds the batch's stage");
+    total += r.n_cand;
+  }
+  if (total > 0xFFFFFFFFull) return set_last_error(EBIC_ERR_UNSUPPORTED, "too many candidates");
+  int64_t cc_cap = (kSmemDynMax - 2 * (int64_t)cap - 2 * (kChunkSlack + 1) - 256) / 4;
+  cc_cap = std::min<int64_t>(cc_cap, kMaxChunkCols) / 64 * 64;
+  if (cc_cap < 64) return set_last_error(EBIC_ERR_UNSUPPORTED, "no shared-memory plan");
+  hp->stage_cap = cap;
+  hp->chunk_cap = (int32_t)cc_cap;
+  uint32_t base = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const ebic_eval_request& r = reqs[i];
+    const EvalArgs& a = args[i];
+    BatchReq q;
+    std::memset(&q, 0, sizeof(q));
+    q.cand_cols = r.cols;
+    q.cand_offsets = r.offsets;
+    q.counts = r.counts;
+    q.bitmaps = r.bitmaps;
+    MatrixView v;
+    matrix_view(r.m, &v);
+    q.status = v.status;
+    q.slabs = a.slabs;
+    q.groups = a.groups;
+    q.words = a.words;
+    q.n_cand = r.n_cand;
+    q.cand_base = base;
+    q.lcase = layout_case(v.L, cfgs[i].ts);
+    q.vec = v.L.vec;
+    q.neg = (r.flags & EBIC_NEGATIVE_TRENDS) ? 1 : 0;
+    q.ts = cfgs[i].ts;
+    q.col_box = a.col_box;
+    q.n_col_boxes = a.n_col_boxes;
+    q.stage_bytes = a.stage_bytes;
+    // chunks: about 2 items per SM over the whole batch is enough with dynamic scheduling
+    q.chunk_cols = std::min<int32_t>(hp->chunk_cap, std::max<int32_t>(64, a.chunk_cols));
+    q.tmap = i;
+    hp->tmaps.push_back(*maps[i]);
+    hp->ncols.push_back(v.L.cols);
+    hp->reqs.push_back(q);
+    base += r.n_cand;
+  }
+  hp->total_cand = base;
+  return EBIC_OK;
+}
+
+int cerr(cudaError_t e, const char* what) {
+  (void)cudaGetLastError();
+  return set_last_error(e == cudaErrorMemoryAllocation ? EBIC_ERR_OOM : EBIC_ERR_CUDA,
+                        (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+}
+
+#define B_CUDA(expr)                               \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cerr(e_, #expr); \
+  } while (0)
+
+// Device-side buffers of one batch (capacity n_max requests).
+struct DeviceBatch {
+  BatchReq* reqs = nullptr;
+  CUtensorMap* tmaps = nullptr;
+  int32_t* ncols = nullptr;
+  uint32_t* req_err = nullptr;
+  unsigned long long* start = nullptr;
+  BatchHeader* hdr = nullptr;
+  uint32_t* err = nullptr;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t batch_bytes(uint32_t n_max) {
+  return align256(sizeof(BatchReq) * n_max) + align256(sizeof(CUtensorMap) * n_max) +
+         align256(4 * (size_t)n_max) + align256(4 * (size_t)n_max) +
+         align256(8 * ((size_t)n_max + 1)) + align256(sizeof(BatchHeader)) + 256;
+}
+
+void carve(uint8_t* base, uint32_t n_max, DeviceBatch* d) {
+  size_t o = 0;
+  d->reqs = reinterpret_cast<BatchReq*>(base + o);
+  o += align256(sizeof(BatchReq) * n_max);
+  d->tmaps = reinterpret_cast<CUtensorMap*>(base + o);
+  o += align256(sizeof(CUtensorMap) * n_max);
+  d->ncols = reinterpret_cast<int32_t*>(base + o);
+  o += align256(4 * (size_t)n_max);
+  d->req_err = reinterpret_cast<uint32_t*>(base + o);
+  o += align256(4 * (size_t)n_max);
+  d->start = reinterpret_cast<unsigned long long*>(base + o);
+  o += align256(8 * ((size_t)n_max + 1));
+  d->hdr = reinterpret_cast<BatchHeader*>(base + o);
+  o += align256(sizeof(BatchHeader));
+  d->err = reinterpret_cast<uint32_t*>(base + o);
+}
+
+int ensure_batch_attr() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(batch_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemDynMax);
+  });
+  if (e != cudaSuccess) return cerr(e, "cudaFuncSetAttribute(batch_eval_kernel)");
+  return EBIC_OK;
+}
+
+// The three launches of a batch (check, plan, evaluate), stream-ordered.
+int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, int num_sms,
+                 cudaStream_t s) {
+  const size_t smem = 2 * (size_t)stage_cap + 2 * ((size_t)chunk_cap + kChunkSlack) +
+                      2 * ((size_t)chunk_cap + 1) + 16;
+  int rc = ensure_batch_attr();
+  if (rc != EBIC_OK) return rc;
+  count_launch();
+  batch_check_kernel<<<4 * num_sms, 256, 0, s>>>(d.reqs, d.hdr, d.ncols, d.req_err);
+  B_CUDA(cudaGetLastError());
+  count_launch();
+  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start);
+  B_CUDA(cudaGetLastError());
+  count_launch();
+  batch_eval_kernel<<<num_sms, kBatchThreads, smem, s>>>(d.reqs, d.tmaps, d.hdr, d.start,
+                                                          stage_cap, chunk_cap, 1000000000ull,
+                                                          d.err);
+  B_CUDA(cudaGetLastError());
+  return EBIC_OK;
+}
+
+void fill_header(const HostPlan& hp, uint32_t n, BatchHeader* h) {
+  std::memset(h, 0, sizeof(*h));
+  h->n_req = n;
+  h->total_cand = hp.total_cand;
+}
+
+}  // namespace
+
+struct ebic_batch {
+  uint32_t n_max = 0;
+  int device = 0;
+  int num_sms = 0;
+  uint8_t* dmem = nullptr;   // device buffers
+  uint8_t* hmem = nullptr;   // pinned mirror of the request/tensor-map/ncols/header part
+  DeviceBatch d, h;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  uint32_t last_n = 0;
+  std::mutex mu;
+};
+
+extern "C" {
+
+int ebic_eval_batch(const ebic_eval_request* reqs, uint32_t n_req, void* stream) {
+  if (n_req == 0) return EBIC_OK;
+  if (!reqs) return set_last_error(EBIC_ERR_INVALID_ARG, "reqs is NULL");
+  HostPlan hp;
+  int rc = build_plan(reqs, n_req, 0, &hp);
+  if (rc != EBIC_OK) return rc;
+  if (hp.total_cand == 0) return EBIC_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) { (void)cudaGetLastError(); prev = -1; }
+  if (prev != hp.device) B_CUDA(cudaSetDevice(hp.device));
+  void* mem = nullptr;
+  B_CUDA(cudaMallocAsync(&mem, batch_bytes(n_req), s));
+  DeviceBatch d;
+  carve(static_cast<uint8_t*>(mem), n_req, &d);
+  BatchHeader h;
+  fill_header(hp, n_req, &h);
+  cudaError_t e = cudaMemcpyAsync(d.reqs, hp.reqs.data(), sizeof(BatchReq) * n_req,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.tmaps, hp.tmaps.data(), sizeof(CUtensorMap) * n_req,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.ncols, hp.ncols.data(), 4 * (size_t)n_req, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.req_err, 0, 4 * (size_t)n_req, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, 4, s);
+  if (e != cudaSuccess) {
+    (void)cudaFreeAsync(mem, s);
+    return cerr(e, "batch set-up");
+  }
+  rc = launch_batch(d, hp.stage_cap, hp.chunk_cap, hp.num_sms, s);
+  cudaError_t f = cudaFreeAsync(mem, s);
+  if (prev >= 0 && prev != hp.device) (void)cudaSetDevice(prev);
+  if (rc != EBIC_OK) return rc;
+  if (f != cudaSuccess) return cerr(f, "cudaFreeAsync");
+  return EBIC_OK;
+}
+
+int ebic_batch_create(uint32_t max_requests, ebic_batch** out) {
+  if (!out || max_requests == 0 || max_requests > 65536)
+    return set_last_error(EBIC_ERR_INVALID_ARG, "max_requests must be in [1, 65536]");
+  *out = nullptr;
+  ebic_batch* b = new ebic_batch();
+  b->n_max = max_requests;
+  auto fail_free = [&](int code) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->dmem) cudaFree(b->dmem);
+    if (b->hmem) cudaFreeHost(b->hmem);
+    delete b;
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  const size_t bytes = batch_bytes(max_requests);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dmem, bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->hmem, bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) return fail_free(cerr(e, "ebic_batch_create"));
+  std::memset(b->hmem, 0, bytes);
+  carve(b->dmem, max_requests, &b->d);
+  carve(b->hmem, max_requests, &b->h);
+  int arc = ensure_batch_attr();  // before the capture: not a stream operation
+  if (arc != EBIC_OK) return fail_free(arc);
+  // capture: copy the descriptor block (pinned -> device), clear the error words, then the
+  // three kernels; the stage size is fixed at the largest tile so any batch composition fits
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail_free(cerr(e, "capture stream"));
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  const size_t desc_bytes = reinterpret_cast<uint8_t*>(b->d.req_err) - b->dmem;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->dmem, b->hmem, desc_bytes, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d.hdr, b->h.hdr, sizeof(BatchHeader), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d.req_err, 0, 4 * (size_t)max_requests, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d.err, 0, 4, cs);
+  int rc = EBIC_OK;
+  if (e == cudaSuccess) {
+    const int64_t cc = std::min<int64_t>(
+        kMaxChunkCols, (kSmemDynMax - 2 * (int64_t)kStageMax - 2 * (kChunkSlack + 1) - 256) / 4);
+    rc = launch_batch(b->d, kStageMax, (int32_t)(cc / 64 * 64), b->num_sms, cs);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess && rc == EBIC_OK) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (rc != EBIC_OK) return fail_free(rc);
+  if (e != cudaSuccess) return fail_free(cerr(e, "batch graph capture"));
+  *out = b;
+  return EBIC_OK;
+}
+
+int ebic_batch_run(ebic_batch* b, const ebic_eval_request* reqs, uint32_t n_req, void* stream) {
+  if (!b) return set_last_error(EBIC_ERR_INVALID_ARG, "batch is NULL");
+  if (n_req > b->n_max) return set_last_error(EBIC_ERR_INVALID_ARG, "more requests than capacity");
+  if (n_req > 0 && !reqs) return set_last_error(EBIC_ERR_INVALID_ARG, "reqs is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  HostPlan hp;
+  if (n_req > 0) {
+    int rc = build_plan(reqs, n_req, kStageMax, &hp);
+    if (rc != EBIC_OK) return rc;
+    if (hp.device != b->device)
+      return set_last_error(EBIC_ERR_INVALID_ARG, "requests on another device than the batch");
+    const int64_t cc = std::min<int64_t>(
+        kMaxChunkCols, (kSmemDynMax - 2 * (int64_t)kStageMax - 2 * (kChunkSlack + 1) - 256) / 4);
+    for (auto& q : hp.reqs) q.chunk_cols = std::min<int32_t>(q.chunk_cols, (int32_t)(cc / 64 * 64));
+  }
+  if (b->pending) B_CUDA(cudaEventSynchronize(b->done));  // the pinned block is read by the graph
+  if (n_req > 0) {
+    std::memcpy(b->h.reqs, hp.reqs.data(), sizeof(BatchReq) * n_req);
+    std::memcpy(b->h.tmaps, hp.tmaps.data(), sizeof(CUtensorMap) * n_req);
+    std::memcpy(b->h.ncols, hp.ncols.data(), 4 * (size_t)n_req);
+  }
+  fill_header(hp, n_req, b->h.hdr);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  B_CUDA(cudaGraphLaunch(b->exec, s));
+  B_CUDA(cudaEventRecord(b->done, s));
+  b->pending = true;
+  b->last_n = n_req;
+  return EBIC_OK;
+}
+
+int ebic_batch_status(ebic_batch* b, uint32_t* req_status, uint32_t n, void* stream) {
+  if (!b || (n > 0 && !req_status)) return set_last_error(EBIC_ERR_INVALID_ARG, "NULL argument");
+  if (n > b->n_max) return set_last_error(EBIC_ERR_INVALID_ARG, "n exceeds capacity");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  B_CUDA(cudaStreamSynchronize(s));
+  uint32_t err = 0;
+  B_CUDA(cudaMemcpy(&err, b->d.err, 4, cudaMemcpyDeviceToHost));
+  if (n) B_CUDA(cudaMemcpy(req_status, b->d.req_err, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  if (err & kErrTimeout)
+    return set_last_error(EBIC_ERR_DEVICE_TIMEOUT, "a bounded device wait expired");
+  for (uint32_t i = 0; i < n; ++i)
+    if (req_status[i]) return set_last_error(EBIC_ERR_INVALID_ARG, "a request failed its check");
+  return EBIC_OK;
+}
+
+int ebic_batch_free(ebic_batch* b) {
+  if (!b) return EBIC_OK;
+  if (b->pending) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->done) cudaEventDestroy(b->done);
+  cudaFree(b->dmem);
+  cudaFreeHost(b->hmem);
+  delete b;
+  return EBIC_OK;
+}
+
+}  // extern "C"

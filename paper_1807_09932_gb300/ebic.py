@@ -103,6 +103,16 @@ class EbicEvaluator(ctypes.Structure):
                 ("set_archive", SET_ARCHIVE_FN)]
 
 
+class EbicEvalRequest(ctypes.Structure):
+    _fields_ = [("m", _P), ("cols", _P), ("offsets", _P), ("n_cand", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("counts", _P), ("bitmaps", _P)]
+
+
+_lib_eval_batch = _sig("ebic_eval_batch", [ctypes.POINTER(EbicEvalRequest), _U32, _P])
+_lib_batch_create = _sig("ebic_batch_create", [_U32, ctypes.POINTER(_P)])
+_lib_batch_run = _sig("ebic_batch_run", [_P, ctypes.POINTER(EbicEvalRequest), _U32, _P])
+_lib_batch_status = _sig("ebic_batch_status", [_P, ctypes.POINTER(ctypes.c_uint32), _U32, _P])
+_lib_batch_free = _sig("ebic_batch_free", [_P])
 _lib_params_default = _sig("ebic_params_default", [ctypes.POINTER(EbicParams)])
 _lib_run = _sig("ebic_run", [_P, ctypes.POINTER(EbicParams), _P,
                              ctypes.POINTER(ctypes.POINTER(EbicResult))])
@@ -231,6 +241,38 @@ def ebic_timing_read(kind):
     ms, n = ctypes.c_double(), _I64()
     _check(_lib_timing_read(kind, ctypes.byref(ms), ctypes.byref(n)), "ebic_timing_read")
     return ms.value, n.value
+
+
+def make_requests(items):
+    """items: (handle, cols, offsets, n_cand, flags, counts, bitmaps) tuples -> ctypes array."""
+    arr = (EbicEvalRequest * max(len(items), 1))()
+    for i, (h, c, o, n, f, cnt, bm) in enumerate(items):
+        arr[i] = EbicEvalRequest(h, _ptr(c), _ptr(o), n, f, _ptr(cnt), _ptr(bm))
+    return arr
+
+
+def ebic_eval_batch(reqs, n_req, stream=None):
+    return _lib_eval_batch(reqs, n_req, _stream(stream))
+
+
+def ebic_batch_create(max_requests):
+    b = _P()
+    _check(_lib_batch_create(max_requests, ctypes.byref(b)), "ebic_batch_create")
+    return b
+
+
+def ebic_batch_run(b, reqs, n_req, stream=None):
+    return _lib_batch_run(b, reqs, n_req, _stream(stream))
+
+
+def ebic_batch_status(b, n, stream=None):
+    out = (ctypes.c_uint32 * max(n, 1))()
+    rc = _lib_batch_status(b, out, n, _stream(stream))
+    return rc, list(out)[:n]
+
+
+def ebic_batch_free(b):
+    _check(_lib_batch_free(b), "ebic_batch_free")
 
 
 def ebic_params_default(**overrides):
