@@ -58,6 +58,12 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="target wall time of the oracle's bounded sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["methylation", "batched", "served"],
+                   default="methylation")
+    p.add_argument("--load", type=float, default=0.7,
+                   help="served: arrival rate as a fraction of the measured capacity")
+    p.add_argument("--runs", type=int, default=32, help="served: concurrent EBIC runs")
+    p.add_argument("--requests", type=int, default=1000, help="served: requests per trace")
     return p.parse_args()
 
 
@@ -204,6 +210,12 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "batched":
+        batched_workload(args)
+        return
+    if args.workload == "served":
+        served_workload(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -420,6 +432,212 @@ def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
                     "frac": (hbm_bytes / t / 1e9) / peaks["hbm_gbs"] if "hbm_gbs" in peaks
                     else None},
             "peak_basis": "64 INT32 lanes/SM/clk x SMs x median SM clock in the timed region"}
+
+
+# ---- config 4: batched vs plain per-population launches ----------------------------------------
+
+def batched_workload(args):
+    """8 datasets (5k-200k rows, 20-500 cols) and 64 populations (200-3,200 candidates of 2-64
+    columns), round-robin over the datasets. One step = all 64 populations scored. Plain: one
+    ebic_eval_population per population. Batched: one ebic_batch_run (CUDA-graph replay of the
+    check, plan and persistent kernels), with tile shapes from the autotuner."""
+    import torch
+
+    from paper_1807_09932_gb300 import autotune, ebic, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    dspecs, pspecs = synth.config4_specs()
+    mats, rows = [], []
+    for d in dspecs:
+        ds = synth.dataset_from_spec(d)
+        mats.append(ebic.Matrix(torch.from_numpy(ds.X).to(dev)))
+        rows.append(d["rows"])
+        del ds
+    pops = []
+    for ps in pspecs:
+        m = mats[ps["dataset"]]
+        c, o = synth.make_population(ps["seed"], ps["n_cand"], m.cols, ps["lmin"],
+                                     min(ps["lmax"], m.cols))
+        n = len(o) - 1
+        pops.append(dict(m=m, n=n, R=m.rows, mean_len=float(np.diff(o).mean()),
+                         dc=torch.from_numpy(c.view(np.int16)).to(dev),
+                         do=torch.from_numpy(o.view(np.int32)).to(dev),
+                         cnt=torch.empty(n, dtype=torch.int32, device=dev),
+                         bm=torch.empty((n, m.words), dtype=torch.int32, device=dev)))
+    cache = autotune.Cache()
+    tuned = {}
+    t_tune = time.perf_counter()
+    for p in pops:  # one tuning per matrix, on its first population
+        if id(p["m"]) in tuned:
+            continue
+        tuned[id(p["m"])] = autotune.tune_matrix(p["m"], p["dc"], p["do"], p["n"], p["mean_len"],
+                                                 p["cnt"], p["bm"], cache=cache, iters=2)
+    t_tune = time.perf_counter() - t_tune
+    evals_per_step = float(sum(p["n"] * p["R"] for p in pops))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def plain_step():
+        for p in pops:
+            rc = ebic.ebic_eval_population(p["m"].handle, p["dc"], p["do"], p["n"], 0, p["cnt"],
+                                           p["bm"], stream.cuda_stream)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_eval_population")
+
+    batch = ebic.ebic_batch_create(len(pops))
+    arr = ebic.make_requests([(p["m"].handle, p["dc"], p["do"], p["n"], 0, p["cnt"], p["bm"])
+                              for p in pops])
+
+    def batched_step():
+        rc = ebic.ebic_batch_run(batch, arr, len(pops), stream.cuda_stream)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_batch_run")
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = []
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+    steps = max(3, min(args.steps, 50))
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = ebic.ebic_launch_count()
+    ms_plain = timed(plain_step, steps)
+    ms_batched = timed(batched_step, steps)
+    launches = ebic.ebic_launch_count() - launches0
+    clk = clocks.stop()
+    rc, st = ebic.ebic_batch_status(batch, len(pops))
+    if rc or any(st):
+        raise SystemExit("batched status error")
+    ebic.ebic_batch_free(batch)
+    line = {"metric": "candidate-row evals/s", "value": evals_per_step / (ms_batched / 1000),
+            "unit": "candidate-row evals/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+            "config": {"workload": "batched: 8 datasets (5k-200k rows x 20-500 cols, N(0,1)/Beta "
+                                   "alternating, planted, 0.5% NaN), 64 populations of 200-3,200 "
+                                   "candidates of 2-64 cols, round-robin; one step = all 64",
+                       "evals_per_step": evals_per_step,
+                       "l2": "flushed between timed steps (512 MB write, outside the events)",
+                       "tiles": {str(i): list(v[:2]) for i, v in enumerate(tuned.values())},
+                       "autotune_s": t_tune},
+            "plain": {"value": evals_per_step / (ms_plain / 1000), "ms_per_step": ms_plain,
+                      "path": "64 x ebic_eval_population, one launch set per population"},
+            "batched_over_plain": ms_plain / ms_batched,
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for m in mats:
+        m.close()
+
+
+# ---- config 5: served (continuous batching) vs plain per-population launches -------------------
+
+def served_workload(args):
+    """32 concurrent EBIC runs on datasets of 10,000-436,444 rows x 20-200 cols, 1,600 candidates
+    per request (2-16 columns), Poisson arrivals at `--load` x the measured batched capacity.
+    Served: the continuous-batching server. Plain: the same arrivals, FIFO, one request at a time
+    through ebic_eval_population + ebic_fitness. Latency = completion - arrival (host clock)."""
+    import torch
+
+    from paper_1807_09932_gb300 import serve, synth
+    torch.cuda.set_device(0)
+    runs = synth.config5_specs(n_runs=args.runs)
+    specs, rows_of = [], {}
+    for i, r in enumerate(runs):
+        ds = synth.dataset_from_spec(r)
+        pool_c, pool_o = synth.make_population(r["seed"] + 1, 40, r["cols"], 2, 6)
+        arch = synth.population_from_lists(
+            [list(pool_c[pool_o[j]:pool_o[j + 1]]) for j in range(20)])
+        specs.append(serve.RunSpec(run_id=i, X=ds.X, max_cand=r["n_cand"], max_len=16,
+                                   archive_cols=arch[0], archive_offsets=arch[1]))
+        rows_of[i] = r["rows"]
+    be = serve.GpuBackend(max_batch=len(specs), max_inflight=2)
+    budget = sum(be.footprint(s) for s in specs) + (1 << 30)
+    srv = serve.Server(be, hbm_budget=budget, max_batch=len(specs), max_inflight=2)
+    for s in specs:
+        srv.add_run(s)
+    for s in specs:
+        s.X = None  # the rank matrices are resident; host copies are not needed any more
+    rng = np.random.default_rng(synth.BASE_SEED + 55)
+    pools = [[synth.make_population(runs[i]["seed"] + 10 + j, runs[i]["n_cand"],
+                                    runs[i]["cols"], 2, 16) for j in range(4)]
+             for i in range(len(specs))]
+
+    def trace(n, rate):
+        t, out = 0.0, []
+        for k in range(n):
+            t += rng.exponential(1.0 / rate) if rate else 0.0
+            run = int(rng.integers(len(specs)))
+            c, o = pools[run][k % 4]
+            out.append(serve.Request(run_id=run, cols=c, offsets=o, t_arrival=t))
+        return out
+
+    mean_evals = float(np.mean([runs[i]["n_cand"] * runs[i]["rows"] for i in range(len(runs))]))
+    plain_stream = torch.cuda.Stream()
+
+    def copy_trace(tr):
+        return [serve.Request(run_id=r.run_id, cols=r.cols, offsets=r.offsets,
+                              t_arrival=r.t_arrival, flags=r.flags) for r in tr]
+
+    def run_served(tr):
+        srv.done.clear()
+        srv.batches = 0
+        return serve.drive(srv, tr, rows_of)
+
+    # warm-up, then capacity: a saturated trace (everything arrives at once) through each path
+    serve.drive(srv, trace(2 * len(specs), 0.0), rows_of)
+    serve.plain_serve(be, trace(len(specs), 0.0), rows_of, plain_stream)
+    sat_trace = trace(4 * len(specs), 0.0)
+    sat_served = run_served(copy_trace(sat_trace))
+    sat_plain = serve.plain_serve(be, copy_trace(sat_trace), rows_of, plain_stream)
+    capacity_rps = sat_served["evals_per_s"] / mean_evals
+    clocks = ClockSampler(0)
+    clocks.start()
+    sweep = []
+    headline = None
+    for load in sorted({0.25, 0.5, args.load, 1.0}):
+        tr = trace(args.requests, load * capacity_rps)
+        sv = run_served(copy_trace(tr))
+        pl = serve.plain_serve(be, copy_trace(tr), rows_of, plain_stream)
+        entry = {"load": load, "rate_rps": load * capacity_rps, "served": sv, "plain": pl}
+        sweep.append(entry)
+        if load == args.load:
+            headline = entry
+    clk = clocks.stop()
+    be.close()
+    served, plain = headline["served"], headline["plain"]
+    line = {"metric": "candidate-row evals/s", "value": served["evals_per_s"],
+            "unit": "candidate-row evals/s", "n_gpus": 1, "steps": served["requests"],
+            "warmup": 3 * len(specs), "ms_per_step": served["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/u16", "data": "synthetic",
+            "config": {"workload": f"served: {len(specs)} EBIC runs on 10,000-436,444 x 20-200 "
+                                   "matrices (N(0,1)/Beta, planted, 0.5% NaN), 1,600 candidates "
+                                   "of 2-16 cols per request, archive of 20 per run, Poisson "
+                                   f"arrivals at {args.load:.2f} x the served capacity",
+                       "arrival_rate_rps": headline["rate_rps"], "capacity_rps": capacity_rps,
+                       "requests_per_trace": args.requests},
+            "served": served, "plain": plain,
+            "saturated": {"served": sat_served, "plain": sat_plain,
+                          "served_over_plain": sat_served["evals_per_s"] / sat_plain["evals_per_s"]},
+            "sweep": sweep, "clocks": clk,
+            "gpu_launches": int(ebic_launches())}
+    print(json.dumps(line), flush=True)
+
+
+def ebic_launches():
+    from paper_1807_09932_gb300 import ebic
+    return ebic.ebic_launch_count()
 
 
 if __name__ == "__main__":

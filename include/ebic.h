@@ -182,6 +182,11 @@ int ebic_matrix_status(ebic_matrix* m, void* stream);
  * EBIC_ERR_UNSUPPORTED. Not thread-safe with concurrent evaluations of the same matrix.
  */
 int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
+/* Candidate columns staged per chunk (the candidate tile: each chunk of the population is
+ * checked against each row tile), or 0 for the built-in choice. Rounded up to a multiple of 64
+ * and capped by the shared memory left after the row-tile stages. Speed only, never results.
+ * Values outside [0, 16384] return EBIC_ERR_INVALID_ARG. */
+int ebic_matrix_set_chunk_cols(ebic_matrix* m, int32_t chunk_cols);
 /* The tile height in slabs that the next evaluation will use, and the rows per slab. */
 int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* rows_per_slab);
 

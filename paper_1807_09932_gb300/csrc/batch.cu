@@ -26,8 +26,13 @@
 namespace ebic {
 namespace {
 
-constexpr int kBatchThreads = 512;
+// 32 warps per CTA: the cases the batch uses (8-bit ranks with tiles of at most 2 slabs, or 1
+// with negative trends; 16-bit ranks with 1 slab) all fit in 64 registers per thread.
+constexpr int kBatchThreads = 1024;
 constexpr int kBatchWarps = kBatchThreads / 32;
+
+// The largest tile height the batch uses for a request (results never depend on the tile).
+int batch_tile_cap(const Layout& L, bool neg) { return L.width == 8 ? (neg ? 1 : 2) : 1; }
 
 // layout cases: 0..2 = 8-bit ranks, VEC 4, TS 1/2/4; 3 = 16-bit VEC 4; 4 = VEC 2; 5 = VEC 1
 int layout_case(const Layout& L, int ts) {
@@ -59,6 +64,7 @@ struct BatchHeader {
   uint32_t total_cand;
   unsigned long long next_item;   // work counter, reset by the plan kernel
   unsigned long long total_items;
+  unsigned long long grab;        // consecutive items taken per grab (set by the plan kernel)
 };
 
 __device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t n, uint32_t cand) {
@@ -113,7 +119,8 @@ __global__ void batch_check_kernel(const BatchReq* __restrict__ reqs,
 // Item ranges: request r owns items [start[r], start[r+1]) = chunks x row tiles. One thread.
 __global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader* hdr,
                                   const uint32_t* __restrict__ req_err,
-                                  unsigned long long* __restrict__ start) {
+                                  unsigned long long* __restrict__ start,
+                                  unsigned long long gridDim_eval) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   unsigned long long acc = 0;
   for (uint32_t r = 0; r < hdr->n_req; ++r) {
@@ -128,6 +135,11 @@ __global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader
   start[hdr->n_req] = acc;
   hdr->total_items = acc;
   hdr->next_item = 0ull;
+  // runs of consecutive items (same candidate chunk, neighbouring row tiles) keep chunk restaging
+  // and item decoding rare; about 8 runs per CTA keep the dynamic balance
+  const unsigned long long runs = 8ull * gridDim_eval;
+  unsigned long long g = (acc + runs - 1) / runs;
+  hdr->grab = g < 1 ? 1 : (g > 64 ? 64 : g);
 }
 
 // One row tile of one request for every candidate of the staged chunk.
@@ -181,8 +193,10 @@ __device__ __forceinline__ void batch_tile_case(int lcase, const uint8_t* stage,
                                                 const uint32_t (&tsel)[5]) {
   switch (lcase) {
     case 0: batch_tile<8, 4, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
-    case 1: batch_tile<8, 4, 2, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
-    case 2: batch_tile<8, 4, 4, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
+    case 1:
+      if constexpr (!NEG)
+        batch_tile<8, 4, 2, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel);
+      break;
     case 3: batch_tile<16, 4, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
     case 4: batch_tile<16, 2, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
     default: batch_tile<16, 1, 1, NEG>(stage, q, ccols, coffs, lo, nc, tile, lane, warp, trot, tsel); break;
@@ -214,10 +228,31 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   uint16_t* const ccols = reinterpret_cast<uint16_t*>(smem + 2 * (size_t)stage_cap);
   uint16_t* const coffs = ccols + chunk_cap + kChunkSlack;
 
+  // thread-0 state: the current run of grabbed items and the request whose range was decoded last
+  unsigned long long run_next = 0, run_end = 0;
+  uint32_t dec_r = 0;
+  unsigned long long dec_lo = 1, dec_hi = 0;
+  auto next_item = [&]() -> unsigned long long {  // thread 0 only
+    if (run_next >= run_end) {
+      const unsigned long long gsz = hdr->grab;
+      run_next = atomicAdd(&hdr->next_item, gsz);
+      run_end = run_next + gsz < total ? run_next + gsz : total;
+      if (run_next >= total) return total;
+    }
+    return run_next++;
+  };
+  auto decode = [&](unsigned long long g) -> uint32_t {  // thread 0 only
+    if (g < dec_lo || g >= dec_hi) {
+      dec_r = find_item(start, n_req, g);
+      dec_lo = start[dec_r];
+      dec_hi = start[dec_r + 1];
+    }
+    return dec_r;
+  };
   auto issue = [&](unsigned long long g, int s) {  // thread 0 only
-    const uint32_t r = find_item(start, n_req, g);
+    const uint32_t r = decode(g);
     const BatchReq& rq = reqs[r];
-    const unsigned long long local = g - start[r];
+    const unsigned long long local = g - dec_lo;
     const long long n_tiles = (rq.slabs + rq.ts - 1) / rq.ts;
     const long long tile = (long long)(local % (unsigned long long)n_tiles);
     const uint32_t col_stride = (uint32_t)rq.ts * 128u * (uint32_t)rq.vec;
@@ -236,7 +271,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     cur_r = 0xFFFFFFFFu;
     cur_k = -1;
     for (int s = 0; s < 2; ++s) {
-      const unsigned long long g = atomicAdd(&hdr->next_item, 1ull);
+      const unsigned long long g = next_item();
       item_s[s] = g;
       if (g < total) issue(g, s);
     }
@@ -253,8 +288,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     // thread 0 decides, before the barrier, whether this item needs a new chunk staged, so that
     // every thread takes the same branch
     if (tid == 0) {
-      const uint32_t r = find_item(start, n_req, g);
-      const unsigned long long local = g - start[r];
+      const uint32_t r = decode(g);
+      const unsigned long long local = g - dec_lo;
       const long long n_tiles = (reqs[r].slabs + reqs[r].ts - 1) / reqs[r].ts;
       const long long k = (long long)(local / (unsigned long long)n_tiles);
       it_tile = (long long)(local % (unsigned long long)n_tiles);
@@ -290,12 +325,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
       batch_tile_case<false>(q.lcase, stage, q, ccols, coffs, cur_lo, cur_nc, tile, lane, warp,
                              trot, tsel);
     __syncthreads();  // every warp is done with stage s
-    if (tid == 0) {
-      const unsigned long long gn = atomicAdd(&hdr->next_item, 1ull);
+    if (tid == 0) {  // item_s[s] is next read two iterations on, after further barriers
+      const unsigned long long gn = next_item();
       item_s[s] = gn;
       if (gn < total) issue(gn, s);
     }
-    __syncthreads();
   }
   if (timed_out && tid == 0) {
     atomicOr(err_out, kErrTimeout);
@@ -370,7 +404,8 @@ int build_plan(const ebic_eval_request* reqs, uint32_t n, uint32_t fixed_stage_c
                               ("request " + std::to_string(i) +
                                ": batched requests take device buffers only").c_str());
     }
-    int rc = matrix_eval_plan(r.m, r.n_cand > 0 ? r.n_cand : 1, 0, &args[i], &cfgs[i], &maps[i]);
+    int rc = matrix_eval_plan(r.m, r.n_cand > 0 ? r.n_cand : 1, 0, &args[i], &cfgs[i], &maps[i],
+                              batch_tile_cap(v.L, (r.flags & EBIC_NEGATIVE_TRENDS) != 0));
     if (rc != EBIC_OK) return rc;
     if (!fixed_stage_cap && args[i].stage_bytes > cap) cap = args[i].stage_bytes;
     if (args[i].stage_bytes > cap)
@@ -490,7 +525,8 @@ int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, in
   batch_check_kernel<<<4 * num_sms, 256, 0, s>>>(d.reqs, d.hdr, d.ncols, d.req_err);
   B_CUDA(cudaGetLastError());
   count_launch();
-  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start);
+  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start,
+                                     (unsigned long long)num_sms);
   B_CUDA(cudaGetLastError());
   count_launch();
   batch_eval_kernel<<<num_sms, kBatchThreads, smem, s>>>(d.reqs, d.tmaps, d.hdr, d.start,

@@ -29,6 +29,7 @@ struct ebic_matrix {
   CUtensorMap tmap[3];         // one per tile height TS = 1, 2, 4
   bool tmap_ok[3] = {false, false, false};
   int tile = 0;                // 0: built-in tile choice; else the TS every evaluation uses
+  int chunk = 0;               // 0: built-in chunk size; else candidate columns per chunk
 };
 
 namespace {
@@ -287,7 +288,7 @@ int default_tile_slabs(const Layout& L) {
 }
 
 bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint, int grid,
-               EvalArgs* a) {
+               EvalArgs* a, int32_t chunk_override) {
   int nb, cb;
   col_boxes(L.cols, &nb, &cb);
   const int64_t col_stride = (int64_t)ts * 128 * L.vec;
@@ -301,6 +302,7 @@ bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint
   const int64_t total = total_cols_hint > 0 ? total_cols_hint : (int64_t)n_cand * 16;
   const int64_t want_chunks = std::max<int64_t>(1, (2 * (int64_t)grid + n_tiles - 1) / n_tiles);
   int64_t cc = (total + want_chunks - 1) / want_chunks;
+  if (chunk_override > 0) cc = chunk_override;
   cc = (cc + 63) / 64 * 64;
   cc = std::max<int64_t>(64, std::min(cc, cc_max));
   a->cols = L.cols;
@@ -324,12 +326,13 @@ void matrix_view(const ebic_matrix* m, MatrixView* v) {
 }
 
 int matrix_eval_plan(const ebic_matrix* cm, uint32_t n_cand, int64_t total_cols_hint,
-                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap) {
+                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap, int ts_cap) {
   ebic_matrix* m = const_cast<ebic_matrix*>(cm);
   const Layout& L = m->L;
   int ts = m->tile ? m->tile : default_tile_slabs(L);
   while (ts > 1 && ts > L.slabs) ts >>= 1;
-  if (!plan_eval(L, ts, n_cand, total_cols_hint, m->num_sms, a))
+  while (ts_cap > 0 && ts > ts_cap) ts >>= 1;
+  if (!plan_eval(L, ts, n_cand, total_cols_hint, m->num_sms, a, m->chunk))
     return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
   int rc = get_tmap(m, ts, a->col_box, tmap);
   if (rc != EBIC_OK) return rc;
@@ -505,7 +508,7 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
   int ts = m->tile ? m->tile : default_tile_slabs(L);
   while (ts > 1 && ts > L.slabs) ts >>= 1;
   EvalArgs a;
-  if (!plan_eval(L, ts, n_cand, total_hint, m->num_sms, &a))
+  if (!plan_eval(L, ts, n_cand, total_hint, m->num_sms, &a, m->chunk))
     return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
   const CUtensorMap* tmap = nullptr;
   int rc = get_tmap(m, ts, a.col_box, &tmap);
@@ -749,6 +752,14 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs) {
       return fail(EBIC_ERR_UNSUPPORTED, "tile does not fit in shared memory for this matrix");
   }
   m->tile = tile_slabs;
+  return EBIC_OK;
+}
+
+int ebic_matrix_set_chunk_cols(ebic_matrix* m, int32_t chunk_cols) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (chunk_cols < 0 || chunk_cols > kMaxChunkCols)
+    return fail(EBIC_ERR_INVALID_ARG, "chunk_cols must be in [0, 16384]");
+  m->chunk = chunk_cols;
   return EBIC_OK;
 }
 

@@ -110,7 +110,7 @@ struct EvalConfig {
 // Tile choice and shared-memory plan for a matrix layout (host).
 int default_tile_slabs(const Layout& L);
 bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint, int grid,
-               EvalArgs* a);
+               EvalArgs* a, int32_t chunk_override = 0);
 
 cudaError_t launch_eval(const EvalConfig& cfg, const CUtensorMap* tmap, const EvalArgs& a,
                         cudaStream_t s);
@@ -149,7 +149,7 @@ void matrix_view(const ebic_matrix* m, MatrixView* v);
 // Tile choice, launch plan and tensor map for evaluating n_cand candidates on m (the same choice
 // ebic_eval_population makes). Returns EBIC_OK or an error code with the last-error message set.
 int matrix_eval_plan(const ebic_matrix* m, uint32_t n_cand, int64_t total_cols_hint,
-                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap);
+                     EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap, int ts_cap = 0);
 // Record the calling thread's last-error message and return `code`.
 int set_last_error(int code, const char* msg);
 // Host-side check of a CSR candidate list; empty string when valid.

@@ -59,6 +59,7 @@ _lib_fitness = _sig("ebic_fitness", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32,
 _lib_status = _sig("ebic_matrix_status", [_P, _P])
 _lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
 _lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
+_lib_set_chunk = _sig("ebic_matrix_set_chunk_cols", [_P, _I32])
 _lib_last_error = _sig("ebic_last_error", [], ctypes.c_char_p)
 _lib_launch_count = _sig("ebic_launch_count", [], ctypes.c_int64)
 _lib_timing_enable = _sig("ebic_timing_enable", [ctypes.c_int])
@@ -219,6 +220,10 @@ def ebic_matrix_set_tile(h, tile_slabs):
     _check(_lib_set_tile(h, tile_slabs), "ebic_matrix_set_tile")
 
 
+def ebic_matrix_set_chunk_cols(h, chunk_cols):
+    _check(_lib_set_chunk(h, chunk_cols), "ebic_matrix_set_chunk_cols")
+
+
 def ebic_matrix_get_tile(h):
     t, r = _I32(), _I32()
     _check(_lib_get_tile(h, ctypes.byref(t), ctypes.byref(r)), "ebic_matrix_get_tile")
@@ -375,6 +380,9 @@ class Matrix:
 
     def set_tile(self, tile_slabs):
         ebic_matrix_set_tile(self.handle, tile_slabs)
+
+    def set_chunk_cols(self, chunk_cols):
+        ebic_matrix_set_chunk_cols(self.handle, chunk_cols)
 
     def status(self, stream=None):
         return ebic_matrix_status(self.handle, stream)

@@ -1,0 +1,364 @@
+"""Continuous-batching server for population-evaluation requests from many concurrent EBIC runs.
+
+Each EBIC run owns one matrix and an elite archive. It sends one request per generation (its
+population) and waits for that request's counts and fitness before it breeds the next one.
+The server:
+  * admits runs by device-memory footprint (rank matrix + population, bitmap and archive
+    buffers). A run that does not fit waits until a finished run frees its memory;
+  * keeps every admitted run's rank matrix and archive resident on the device;
+  * batches the requests that have arrived into one launch. It keeps up to `max_inflight`
+    batches on the GPU (one stream each), so a request that arrives while others run is
+    launched as soon as a slot frees. Its upload overlaps the running batch, and its kernels
+    start as the running batch drains;
+  * records per-request latency (completion minus arrival, host clock), p50/p99 and
+    throughput in candidate-row evals/s.
+
+The device work goes through a backend: ``GpuBackend`` (the C ABI: ebic_batch_run in a CUDA
+graph, then ebic_fitness per request against its run's resident archive) or, in tests, a fake
+one. ``plain_serve`` is the comparison point: the same arrivals served one request at a time
+with the per-population calls (ebic_eval_population + ebic_fitness), in arrival order.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    run_id: int
+    cols: np.ndarray          # uint16 CSR columns
+    offsets: np.ndarray       # uint32 CSR offsets
+    t_arrival: float
+    flags: int = 0
+    rid: int = -1
+    t_launch: float = float("nan")
+    t_done: float = float("nan")
+    counts: np.ndarray | None = None
+    fitness: np.ndarray | None = None
+
+    @property
+    def n_cand(self):
+        return len(self.offsets) - 1
+
+    @property
+    def latency(self):
+        return self.t_done - self.t_arrival
+
+
+@dataclasses.dataclass
+class RunSpec:
+    run_id: int
+    X: np.ndarray             # float32 [rows, cols]
+    max_cand: int
+    max_len: int = 64
+    exclude_missing: bool = True
+    archive_cols: np.ndarray | None = None      # CSR of the initial archive (may be empty)
+    archive_offsets: np.ndarray | None = None
+
+
+def percentile(values, q):
+    if not values:
+        return float("nan")
+    v = sorted(values)
+    k = (len(v) - 1) * q / 100.0
+    lo = int(np.floor(k))
+    hi = min(lo + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+class Server:
+    def __init__(self, backend, hbm_budget, max_batch=64, max_inflight=2):
+        self.be = backend
+        self.budget = hbm_budget
+        self.used = 0
+        self.max_batch = max_batch
+        self.max_inflight = max_inflight
+        self.open = {}                      # run_id -> footprint
+        self.waiting_runs = collections.deque()
+        self.queue = collections.deque()    # arrived requests, FIFO
+        self.busy_runs = set()              # runs with a request in flight
+        self.inflight = []                  # (token, [requests])
+        self.done = []
+        self._next_rid = 0
+        self.batches = 0
+
+    # ---- runs ---------------------------------------------------------------------------------
+    def add_run(self, spec: RunSpec):
+        need = self.be.footprint(spec)
+        if need > self.budget:
+            raise ValueError(f"run {spec.run_id} needs {need} bytes, more than the budget")
+        if self.used + need <= self.budget and not self.waiting_runs:
+            self._open(spec, need)
+            return True
+        self.waiting_runs.append((spec, need))
+        return False
+
+    def _open(self, spec, need):
+        self.be.open_run(spec)
+        self.open[spec.run_id] = need
+        self.used += need
+
+    def finish_run(self, run_id):
+        if run_id in self.busy_runs:
+            raise RuntimeError("run has a request in flight")
+        need = self.open.pop(run_id)
+        self.be.close_run(run_id)
+        self.used -= need
+        while self.waiting_runs and self.used + self.waiting_runs[0][1] <= self.budget:
+            spec, n = self.waiting_runs.popleft()
+            self._open(spec, n)
+
+    def is_open(self, run_id):
+        return run_id in self.open
+
+    # ---- requests -----------------------------------------------------------------------------
+    def submit(self, req: Request):
+        req.rid = self._next_rid
+        self._next_rid += 1
+        self.queue.append(req)
+        return req.rid
+
+    def pump(self):
+        """Collect finished batches, then launch the waiting requests if a slot is free.
+        Returns the requests completed in this call."""
+        finished = []
+        still = []
+        for token, reqs in self.inflight:
+            if self.be.done(token):
+                self.be.collect(token, reqs)
+                t = self.be.now()
+                for r in reqs:
+                    r.t_done = t
+                    self.busy_runs.discard(r.run_id)
+                finished.extend(reqs)
+            else:
+                still.append((token, reqs))
+        self.inflight = still
+        self.done.extend(finished)
+        while len(self.inflight) < self.max_inflight and self.queue:
+            batch, rest = [], collections.deque()
+            seen = set()
+            while self.queue and len(batch) < self.max_batch:
+                r = self.queue.popleft()
+                if (r.run_id in self.open and r.run_id not in self.busy_runs
+                        and r.run_id not in seen):
+                    batch.append(r)
+                    seen.add(r.run_id)
+                else:
+                    rest.append(r)
+            rest.extend(self.queue)
+            self.queue = rest
+            if not batch:
+                break
+            t = self.be.now()
+            for r in batch:
+                r.t_launch = t
+                self.busy_runs.add(r.run_id)
+            self.inflight.append((self.be.launch(batch), batch))
+            self.batches += 1
+        return finished
+
+    def idle(self):
+        return not self.queue and not self.inflight
+
+    # ---- statistics ---------------------------------------------------------------------------
+    def stats(self, t0, t1, rows_of):
+        lat = [r.latency for r in self.done]
+        evals = sum(r.n_cand * rows_of[r.run_id] for r in self.done)
+        return {"requests": len(self.done), "batches": self.batches,
+                "p50_ms": 1000 * percentile(lat, 50), "p99_ms": 1000 * percentile(lat, 99),
+                "mean_ms": 1000 * (sum(lat) / len(lat)) if lat else float("nan"),
+                "evals_per_s": evals / (t1 - t0) if t1 > t0 else float("nan"),
+                "wall_s": t1 - t0}
+
+
+def drive(server, arrivals, rows_of, on_done=None, clock=None, spin=None):
+    """Open-loop driver: submit each request when its arrival time has passed, pump until all
+    are done. ``arrivals`` is a list of Requests sorted by t_arrival (relative seconds).
+    Returns the server's stats over the whole run."""
+    be = server.be
+    clock = clock or be.now
+    t0 = clock()
+    for r in arrivals:
+        r.t_arrival += t0
+    i = 0
+    while i < len(arrivals) or not server.idle():
+        now = clock()
+        while i < len(arrivals) and arrivals[i].t_arrival <= now:
+            server.submit(arrivals[i])
+            i += 1
+        for r in server.pump():
+            if on_done:
+                on_done(r)
+        if spin:
+            spin(arrivals[i].t_arrival if i < len(arrivals) else None)
+    return server.stats(t0, clock(), rows_of)
+
+
+# ---- GPU backend ------------------------------------------------------------------------------
+
+class GpuBackend:
+    """Resident rank matrices, per-run device buffers and archives; batched graph launches."""
+
+    def __init__(self, max_batch=64, max_inflight=2, device=0):
+        import torch
+
+        from . import ebic
+        self.torch = torch
+        self.ebic = ebic
+        self.dev = torch.device("cuda", device)
+        self.runs = {}
+        self.slots = [dict(stream=torch.cuda.Stream(self.dev), batch=ebic.ebic_batch_create(max_batch),
+                           busy=False) for _ in range(max_inflight)]
+
+    def close(self):
+        for s in self.slots:
+            s["stream"].synchronize()
+            self.ebic.ebic_batch_free(s["batch"])
+        self.slots = []
+        for rid in list(self.runs):
+            self.close_run(rid)
+
+    @staticmethod
+    def footprint(spec: RunSpec):
+        R, C = spec.X.shape
+        W = (R + 31) // 32
+        rank_bytes = R * C * (1 if C <= 127 else 2) * 1.02 + 4096
+        k = 0 if spec.archive_offsets is None else len(spec.archive_offsets) - 1
+        per_run = (spec.max_cand * (spec.max_len * 2 + 4 + 4 + 8 + W * 4)
+                   + k * (W * 4 + 64 * 2 + 4) + 4096)
+        return int(rank_bytes + per_run)
+
+    def now(self):
+        return time.perf_counter()
+
+    def open_run(self, spec: RunSpec):
+        torch = self.torch
+        m = self.ebic.Matrix(spec.X, exclude_missing=spec.exclude_missing)
+        W = m.words
+        P = spec.max_cand
+        run = dict(m=m, P=P, W=W, rows=spec.X.shape[0],
+                   dcols=torch.empty(P * spec.max_len, dtype=torch.int16, device=self.dev),
+                   doffs=torch.empty(P + 1, dtype=torch.int32, device=self.dev),
+                   counts=torch.empty(P, dtype=torch.int32, device=self.dev),
+                   bitmaps=torch.empty((P, W), dtype=torch.int32, device=self.dev),
+                   fit=torch.empty(P, dtype=torch.int64, device=self.dev),
+                   hcols=torch.empty(P * spec.max_len, dtype=torch.int16).pin_memory(),
+                   hoffs=torch.empty(P + 1, dtype=torch.int32).pin_memory(),
+                   hcounts=torch.empty(P, dtype=torch.int32).pin_memory(),
+                   hfit=torch.empty(P, dtype=torch.int64).pin_memory())
+        # resident archive: its members scored once on this matrix
+        if spec.archive_offsets is not None and len(spec.archive_offsets) > 1:
+            ac, ao = spec.archive_cols, spec.archive_offsets
+            _, abm = self.ebic.eval_population(m, ac, ao)
+            run["acols"] = torch.from_numpy(np.ascontiguousarray(ac).view(np.int16)).to(self.dev)
+            run["aoffs"] = torch.from_numpy(np.ascontiguousarray(ao).view(np.int32)).to(self.dev)
+            run["abm"] = torch.from_numpy(abm.view(np.int32)).to(self.dev)
+            run["K"] = len(ao) - 1
+        else:
+            run["acols"] = torch.zeros(1, dtype=torch.int16, device=self.dev)
+            run["aoffs"] = torch.zeros(1, dtype=torch.int32, device=self.dev)
+            run["abm"] = torch.zeros((1, W), dtype=torch.int32, device=self.dev)
+            run["K"] = 0
+        self.runs[spec.run_id] = run
+
+    def close_run(self, run_id):
+        run = self.runs.pop(run_id)
+        self.torch.cuda.synchronize(self.dev)
+        run["m"].close()
+
+    def launch(self, reqs):
+        torch, ebic = self.torch, self.ebic
+        slot = next(s for s in self.slots if not s["busy"])
+        slot["busy"] = True
+        st = slot["stream"]
+        items = []
+        with torch.cuda.stream(st):
+            for r in reqs:
+                run = self.runs[r.run_id]
+                n, tot = r.n_cand, int(r.offsets[-1])
+                run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
+                run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
+                run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
+                run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
+                items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+                              run["counts"], run["bitmaps"]))
+            arr = ebic.make_requests(items)
+            rc = ebic.ebic_batch_run(slot["batch"], arr, len(items), st.cuda_stream)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_batch_run")
+            for r in reqs:
+                run = self.runs[r.run_id]
+                n = r.n_cand
+                rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n,
+                                       run["counts"], run["bitmaps"], run["acols"],
+                                       run["aoffs"], run["abm"], run["K"], 0, run["fit"], None,
+                                       st.cuda_stream)
+                if rc:
+                    raise ebic.EbicError(rc, "ebic_fitness")
+                run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
+                run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return dict(slot=slot, event=ev)
+
+    def done(self, token):
+        return token["event"].query()
+
+    def collect(self, token, reqs):
+        token["event"].synchronize()
+        token["slot"]["busy"] = False
+        for r in reqs:
+            run = self.runs[r.run_id]
+            n = r.n_cand
+            r.counts = run["hcounts"][:n].numpy().view(np.uint32).copy()
+            r.fitness = run["hfit"][:n].numpy().view(np.uint64).copy()
+
+    # the comparison point: one request at a time, per-population calls
+    def plain(self, r, stream):
+        torch, ebic = self.torch, self.ebic
+        run = self.runs[r.run_id]
+        n, tot = r.n_cand, int(r.offsets[-1])
+        with torch.cuda.stream(stream):
+            run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
+            run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
+            run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
+            run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
+            rc = ebic.ebic_eval_population(run["m"].handle, run["dcols"], run["doffs"], n,
+                                           r.flags, run["counts"], run["bitmaps"],
+                                           stream.cuda_stream)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_eval_population")
+            rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n, run["counts"],
+                                   run["bitmaps"], run["acols"], run["aoffs"], run["abm"],
+                                   run["K"], 0, run["fit"], None, stream.cuda_stream)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_fitness")
+            run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
+            run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
+        stream.synchronize()
+        r.counts = run["hcounts"][:n].numpy().view(np.uint32).copy()
+        r.fitness = run["hfit"][:n].numpy().view(np.uint64).copy()
+
+
+def plain_serve(backend, arrivals, rows_of, stream):
+    """The comparison point: FIFO, one request at a time through the per-population calls."""
+    t0 = backend.now()
+    for r in arrivals:
+        r.t_arrival += t0
+    for r in arrivals:
+        while backend.now() < r.t_arrival:
+            pass
+        r.t_launch = backend.now()
+        backend.plain(r, stream)
+        r.t_done = backend.now()
+    t1 = backend.now()
+    lat = [r.latency for r in arrivals]
+    evals = sum(r.n_cand * rows_of[r.run_id] for r in arrivals)
+    return {"requests": len(arrivals), "p50_ms": 1000 * percentile(lat, 50),
+            "p99_ms": 1000 * percentile(lat, 99), "mean_ms": 1000 * sum(lat) / len(lat),
+            "evals_per_s": evals / (t1 - t0), "wall_s": t1 - t0}

@@ -1,0 +1,135 @@
+"""Serving loop: admission by device-memory footprint, continuous batching, one request in
+flight per run, latency accounting (host-only with a fake backend and clock); on the GPU every
+served result equals the same request scored alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_09932_gb300 import serve, synth
+
+from fake_backend import FakeBackend, FakeClock
+
+
+def _spec(i, rows=300, cols=12, max_cand=50):
+    ds = synth.make_dataset(500 + i, rows, cols, planted=[(60, 5, False)], nan_frac=0.01)
+    ac, ao = synth.population_from_lists([[0, 1], [2, 3, 4]])
+    return serve.RunSpec(run_id=i, X=ds.X, max_cand=max_cand, max_len=cols,
+                         archive_cols=ac, archive_offsets=ao)
+
+
+def _req(run_id, t, seed, n=20, cols=12):
+    c, o = synth.make_population(seed, n, cols, 2, 6)
+    return serve.Request(run_id=run_id, cols=c, offsets=o, t_arrival=t)
+
+
+def _drive_fake(srv, clock, be, arrivals, rows_of):
+    def spin(next_arrival):
+        nxt = be.next_event(srv.inflight)
+        cands = [t for t in (nxt, next_arrival) if t is not None]
+        if cands:
+            clock.t = max(clock.t, min(cands))
+    return serve.drive(srv, arrivals, rows_of, spin=spin)
+
+
+def test_percentile_matches_numpy():
+    v = list(np.random.default_rng(0).random(101))
+    for q in (0, 50, 90, 99, 100):
+        assert abs(serve.percentile(v, q) - np.percentile(v, q)) < 1e-12
+
+
+def test_admission_by_footprint():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    specs = [_spec(i) for i in range(3)]
+    need = be.footprint(specs[0])
+    srv = serve.Server(be, hbm_budget=2 * need + 10)
+    assert srv.add_run(specs[0]) and srv.add_run(specs[1])
+    assert not srv.add_run(specs[2])          # waits for memory
+    assert not srv.is_open(2) and srv.used == 2 * need
+    srv.finish_run(0)                         # frees a run's memory -> the waiting run opens
+    assert srv.is_open(2) and srv.used == 2 * need
+    with pytest.raises(ValueError):
+        serve.Server(be, hbm_budget=need - 1).add_run(specs[0])
+
+
+def test_continuous_batching_and_latency_accounting():
+    clock = FakeClock()
+    be = FakeBackend(clock, fixed=1.0, per_eval=0.0)   # every batch takes 1 fake second
+    srv = serve.Server(be, hbm_budget=1 << 40, max_batch=3, max_inflight=1)
+    for i in range(5):
+        srv.add_run(_spec(i))
+    # five requests at t=0, one more at t=0.5 (arrives while the first batch runs)
+    arr = [_req(i, 0.0, 10 + i) for i in range(5)] + [_req(0, 0.5, 99)]
+    rows = {i: 300 for i in range(5)}
+    st = _drive_fake(srv, clock, be, arr, rows)
+    assert st["requests"] == 6
+    # batch 1: runs 0,1,2 (max_batch 3); batch 2: runs 3,4 and run 0's second request, which
+    # arrived during batch 1 and could only go once run 0's first request had finished
+    assert be.launched == [[0, 1, 2], [3, 4, 5]]
+    lat = sorted(round(r.latency, 9) for r in srv.done)
+    assert lat == [1.0, 1.0, 1.0, 1.5, 2.0, 2.0]
+    assert st["p50_ms"] == pytest.approx(1250.0)
+
+
+def test_one_request_in_flight_per_run_and_results_exact():
+    clock = FakeClock()
+    be = FakeBackend(clock, fixed=0.1, per_eval=1e-8)
+    srv = serve.Server(be, hbm_budget=1 << 40, max_batch=8, max_inflight=2)
+    specs = [_spec(i) for i in range(3)]
+    for s in specs:
+        srv.add_run(s)
+    arr = [_req(i % 3, 0.01 * i, 40 + i) for i in range(12)]
+    st = _drive_fake(srv, clock, be, arr, {i: 300 for i in range(3)})
+    assert st["requests"] == 12
+    for batch in be.launched:  # never two requests of one run in a batch
+        runs = [arr[rid].run_id for rid in batch]
+        assert len(runs) == len(set(runs))
+    for r in srv.done:
+        X = specs[r.run_id].X
+        c, _ = oracle.eval_population(X, r.cols, r.offsets)
+        assert np.array_equal(r.counts, c)
+        assert r.t_done >= r.t_launch >= r.t_arrival
+
+
+@pytest.mark.gpu
+def test_served_results_equal_alone():
+    import torch
+    from paper_1807_09932_gb300 import ebic
+    be = serve.GpuBackend(max_batch=16, max_inflight=2)
+    try:
+        srv = serve.Server(be, hbm_budget=8 << 30, max_batch=16, max_inflight=2)
+        specs = []
+        for i in range(6):
+            R, C = (3000 + 977 * i, [30, 64, 127, 150, 300, 40][i])
+            ds = synth.make_dataset(700 + i, R, C, planted=synth.planted_specs_for(700 + i, R, C),
+                                    nan_frac=0.01)
+            pool_c, pool_o = synth.make_population(800 + i, 200, C, 2, 8)
+            cnt, _ = oracle.eval_population(ds.X, pool_c, pool_o)
+            top = np.argsort(-cnt.astype(np.int64), kind="stable")[:5]
+            ac, ao = synth.population_from_lists(
+                [list(pool_c[pool_o[j]:pool_o[j + 1]]) for j in top])
+            specs.append(serve.RunSpec(run_id=i, X=ds.X, max_cand=400, max_len=min(C, 64),
+                                       archive_cols=ac, archive_offsets=ao))
+            srv.add_run(specs[-1])
+        arr = []
+        for k in range(30):
+            i = k % 6
+            C = specs[i].X.shape[1]
+            c, o = synth.make_population(900 + k, int(50 + 10 * k), C, 2, min(C, 64))
+            arr.append(serve.Request(run_id=i, cols=c, offsets=o, t_arrival=0.0005 * k,
+                                     flags=ebic.EBIC_NEGATIVE_TRENDS if k % 4 == 3 else 0))
+        st = serve.drive(srv, arr, {s.run_id: s.X.shape[0] for s in specs})
+        assert st["requests"] == 30
+        for r in srv.done:
+            s = specs[r.run_id]
+            m = be.runs[r.run_id]["m"]
+            c, b = ebic.eval_population(m, r.cols, r.offsets, negative=bool(r.flags))
+            _, abm = ebic.eval_population(m, s.archive_cols, s.archive_offsets)
+            f, _ = ebic.fitness(m, r.cols, r.offsets, c, b, s.archive_cols, s.archive_offsets,
+                                abm)
+            assert np.array_equal(r.counts, c)
+            assert np.array_equal(r.fitness, f)
+            ec, eb = oracle.eval_population(s.X, r.cols, r.offsets, negative=bool(r.flags))
+            assert np.array_equal(r.counts, ec)
+    finally:
+        be.close()
