@@ -39,7 +39,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = ("methylation-shaped: float32 436,444 x 64, Beta(0.5,0.5) background, 10 planted trend "
             "biclusters (5,000-50,000 rows x 5-16 cols), 0.5% NaN, missing-value exclusion on; "
-            "population 1,600 candidates of 2-16 cols; elite archive of 20")
+            "population 1,600 candidates of 2-16 cols; elite archive of 20 (the 10 planted "
+            "biclusters + the 10 best-quality candidates of a separate 1,600-candidate pool)")
 N_POPS = 4          # distinct seeded populations, cycled over the steps
 ARCHIVE = 20
 FLUSH_BYTES = 512 << 20
@@ -72,6 +73,11 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def synth_planted(ds):
+    from paper_1807_09932_gb300 import synth
+    return synth.population_from_lists([list(p.cols) for p in ds.planted])
 
 
 def make_workload():
@@ -170,7 +176,9 @@ def reference_arm(args):
     # archive: the 20 best candidates of a separate population, by the oracle itself
     ac, ao = arch_pool
     cnt, bm = oracle.eval_population(X, ac, ao, exclude_missing=True)
-    arch = _archive_from(ac, ao, cnt, bm)
+    pc, po = synth_planted(ds)
+    _, pbm = oracle.eval_population(X, pc, po, exclude_missing=True)
+    arch = _archive_from(ds, ac, ao, cnt, bm, pbm)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     n, threads, run = oracle_sample(ds, pops, arch, min(per_step, args.cpu_seconds))
     for _ in range(args.warmup):
@@ -195,13 +203,19 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def _archive_from(cols, offs, counts, bitmaps, k=ARCHIVE):
-    """The k candidates with the most rows (ties by index): a stand-in elite archive."""
+def _archive_from(ds, cols, offs, counts, bitmaps, planted_bitmaps, k=ARCHIVE):
+    """A stand-in elite archive, as a converged EBIC run holds: the planted biclusters (their
+    column orders) and the best remaining slots filled with the highest-quality candidates
+    (rows << (min(L,33)-1), ties by index) of a separate random pool."""
     from paper_1807_09932_gb300 import synth
-    order = np.lexsort((np.arange(len(counts)), -counts.astype(np.int64)))[:k]
-    acand = [list(cols[offs[i]:offs[i + 1]]) for i in order]
+    planted = [list(p.cols) for p in ds.planted][:k]
+    L = np.diff(offs).astype(np.int64)
+    q = counts.astype(np.int64) << (np.minimum(L, 33) - 1)
+    order = np.lexsort((np.arange(len(counts)), -q))[: k - len(planted)]
+    acand = planted + [list(cols[offs[i]:offs[i + 1]]) for i in order]
     acols, aoffs = synth.population_from_lists(acand)
-    return acols, aoffs, np.ascontiguousarray(bitmaps[order])
+    abm = np.concatenate([planted_bitmaps[: len(planted)], bitmaps[order]], axis=0)
+    return acols, aoffs, np.ascontiguousarray(abm)
 
 
 # ---- our arm -------------------------------------------------------------------------------------
@@ -250,7 +264,9 @@ def main():
     # elite archive: the 20 best of a separate population, evaluated on the GPU
     ac, ao = arch_pool
     acnt, abm = ebic.eval_population(m, ac, ao)
-    acols, aoffs, abm = _archive_from(ac, ao, acnt, abm)
+    pc, po = synth_planted(ds)
+    _, pbm = ebic.eval_population(m, pc, po)
+    acols, aoffs, abm = _archive_from(ds, ac, ao, acnt, abm, pbm)
     dacols, daoffs, dabm = d(acols), d(aoffs), d(abm)
     K = len(aoffs) - 1
 
@@ -401,37 +417,58 @@ def main():
     m.close()
 
 
-def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
-    """The evaluator against its binding on-chip roof.
+def eval_traffic():
+    """DRAM bytes per evaluator launch from the committed ncu capture, if the kernel source is
+    still the one that was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "eval_population_traffic.json")
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_per_launch"]
 
-    Algorithmic work per launch: every candidate column is one packed-field compare per row,
-    i.e. sum_c L_c * R field compares, done 32/rank_bits rows per 32-bit ALU lane-op; and the
-    same sum_c L_c * R * (rank_bits/8) bytes read from shared memory. Peaks: 64 INT32 ALU lanes
-    and 128 B of shared-memory bandwidth per SM per clock, times the SM count and the median SM
-    clock measured during the timed region (the recipe's unit counts; the HBM figure is the
-    measured copy bandwidth).
+
+def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
+    """The evaluator against the roof that binds it.
+
+    Algorithmic work per launch (one population): every candidate column must be read for every
+    row, sum_c L_c * R ranks of rank_bits/8 bytes each, out of shared memory (the row tile is
+    staged there by TMA); and each is one packed-field compare, 32/rank_bits rows per 32-bit
+    lane-op. Peaks from the recipe's unit counts and the median SM clock sampled during the
+    timed region: shared memory 128 B/clk/SM, INT32 ALU 64 lanes/clk/SM. The shared-memory time
+    is the larger of the two minimum times, so it is the binding roof ("bound"); the ALU and HBM
+    roofs are reported beside it. HBM: rank matrix + bitmaps against the measured copy
+    bandwidth (MEASURED_PEAKS.json).
     """
     sum_l = float(np.mean([int(o[-1]) for _, o in pops]))
     bytes_per_rank = m.rank_bits / 8
     fields_per_word = 32 // m.rank_bits
     clock_hz = (clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0) * 1e6
     t = launch_ms / 1000.0
-    lane_ops = sum_l * R / fields_per_word          # compares, 32-bit lane ops
-    alu_peak = 64 * sms * clock_hz                   # lane ops / s
     smem_bytes = sum_l * R * bytes_per_rank
     smem_peak = 128 * sms * clock_hz
+    lane_ops = sum_l * R / fields_per_word
+    alu_peak = 64 * sms * clock_hz
     hbm_bytes = m.cols * R * bytes_per_rank + 1600 * m.words * 4
-    return {"bound": "alu", "achieved": lane_ops / t / 1e9, "peak": alu_peak / 1e9,
-            "unit": "Gop/s", "frac": (lane_ops / t) / alu_peak, "traffic": None,
+    return {"bound": "smem", "achieved": smem_bytes / t / 1e9, "peak": smem_peak / 1e9,
+            "unit": "GB/s", "frac": (smem_bytes / t) / smem_peak, "traffic": eval_traffic(),
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                            "(profiles/eval_population_traffic.json); null if the kernel source "
+                            "changed since that capture",
             "kernel": "eval_population_kernel", "launch_ms": launch_ms,
-            "algorithmic_ops_per_launch": lane_ops,
-            "smem": {"achieved_gbs": smem_bytes / t / 1e9, "peak_gbs": smem_peak / 1e9,
-                     "frac": smem_bytes / t / smem_peak},
+            "algorithmic_bytes_per_launch": smem_bytes,
+            "peak_basis": "shared memory 128 B/clk/SM x SMs x median SM clock in the timed region",
+            "alu": {"achieved_gops": lane_ops / t / 1e9, "peak_gops": alu_peak / 1e9,
+                    "frac": (lane_ops / t) / alu_peak,
+                    "basis": "one 32-bit compare per column per 32/rank_bits rows; 64 INT32 lanes/clk/SM"},
             "hbm": {"algorithmic_bytes": hbm_bytes, "achieved_gbs": hbm_bytes / t / 1e9,
                     "peak_gbs": peaks.get("hbm_gbs"),
                     "frac": (hbm_bytes / t / 1e9) / peaks["hbm_gbs"] if "hbm_gbs" in peaks
-                    else None},
-            "peak_basis": "64 INT32 lanes/SM/clk x SMs x median SM clock in the timed region"}
+                    else None, "basis": "rank matrix + bitmaps vs MEASURED_PEAKS.json hbm_gbs"}}
 
 
 # ---- config 4: batched vs plain per-population launches ----------------------------------------

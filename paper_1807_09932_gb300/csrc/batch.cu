@@ -177,7 +177,7 @@ __device__ __forceinline__ void batch_tile(const uint8_t* stage, const BatchReq&
     } else {
 #pragma unroll
       for (int g = 0; g < GT; ++g)
-        if (g0 + g < q.groups) cnt += __popc(acc[g] & Swar<WIDTH>::H);
+        if (g0 + g < q.groups) cnt += __popc(acc[g]);
     }
     cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
     if (lane == 0 && cnt) atomicAdd(&q.counts[cand], cnt);

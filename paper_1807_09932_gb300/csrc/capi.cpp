@@ -268,7 +268,6 @@ Layout make_layout(int64_t rows, int32_t cols) {
   const int64_t g = (rows + L.rows_per_group - 1) / L.rows_per_group;
   L.slabs = (g + L.vec - 1) / L.vec;
   L.groups = L.slabs * L.vec;
-  L.sentinel = L.width == 8 ? 0x7Fu : 0x7FFFu;
   return L;
 }
 
@@ -474,8 +473,8 @@ int ebic_matrix_ranks(const ebic_matrix* m, uint16_t* out, void* stream) {
     const int64_t lane = rr & 31, k = rr >> 5, q = g / L.vec, j = g % L.vec;
     for (int32_t c = 0; c < L.cols; ++c) {
       const size_t w = (((size_t)c * L.slabs + q) * 32 + lane) * L.vec + j;
-      const uint32_t v = (raw[w] >> (L.width * k)) & mask;
-      out[r * L.cols + c] = v == L.sentinel ? 0xFFFFu : (uint16_t)v;
+      const uint32_t v = (raw[w] >> (L.width * k)) & mask;  // code 0 = missing, else rank + 1
+      out[r * L.cols + c] = v == 0 ? 0xFFFFu : (uint16_t)(v - 1);
     }
   }
   return EBIC_OK;

@@ -9,10 +9,9 @@
 //   so that one 16-byte load per lane (VEC = 4) fetches four groups of one column, and a 3-D
 //   TMA box {32*VEC words, TS slabs, columns} lands in shared memory column-major with the TS
 //   slabs of one column contiguous.
-//   Rows past the end (padding of the last slab) hold the sentinel in every column.
-//   The sentinel S = 2^(WIDTH-1) - 1 (0x7F or 0x7FFF) marks a missing value; every real rank is
-//   at most cols - 1 <= S - 1, so the top bit of every field is always 0, which the SWAR
-//   compare in the evaluator relies on.
+//   Stored codes: 0 marks a missing value (and every padding row past the end); a real value is
+//   stored as its dense rank + 1, in 1..cols. Since cols <= 127 (8-bit) or <= 32767 (16-bit), the
+//   top bit of every field is always 0, which the SWAR compare in the evaluator relies on.
 #pragma once
 
 #include <cstddef>
@@ -45,7 +44,6 @@ struct Layout {
   int64_t groups = 0;        // ceil(rows / rows_per_group), padded up to a whole slab
   int64_t slabs = 0;         // Q
   int64_t words = 0;         // W = ceil(rows / 32)
-  uint32_t sentinel = 0x7F;
   size_t rank_words() const { return (size_t)cols * (size_t)slabs * 32u * (size_t)vec; }
   int64_t rows_per_slab() const { return (int64_t)rows_per_group * vec; }
   int64_t words_per_slab() const { return (int64_t)words_per_group * vec; }

@@ -18,10 +18,10 @@
 //     (b | H) - a == b + H - a has no borrow between fields and its top field bit is set
 //     exactly when b >= a (H = the top bit of every field). AND-ing these words along the
 //     chain leaves the top bit of a field set iff that row is non-decreasing along the order;
-//   * exclusion by sentinel: a missing value has the largest code S. A non-decreasing chain that
-//     contains S ends in S, a non-increasing one starts with S, so requiring
-//     last <= S-1 (increasing) and S-1 >= first (decreasing) removes exactly the rows with a
-//     missing value among the candidate's columns; padded rows hold S and never match;
+//   * exclusion by code: a missing value has code 0, below every real rank (1..C). A
+//     non-decreasing chain that contains a 0 starts with it, a non-increasing one ends with it,
+//     so requiring first >= 1 (increasing) and last >= 1 (decreasing) removes exactly the rows
+//     with a missing value among the candidate's columns; padded rows hold 0 and never match;
 //   * bitmap words without ballots: each lane gathers the match bits of up to 8 (16) groups into
 //     one word, and a 5-stage shuffle butterfly transposes the warp's 32x32 bit matrix, so that
 //     every lane holds one LSB-first bitmap word; the words of a tile go to HBM as one coalesced
@@ -38,15 +38,15 @@ template <int WIDTH>
 struct Swar;
 template <>
 struct Swar<8> {
-  static constexpr uint32_t H = 0x80808080u;       // top bit of each 8-bit field
-  static constexpr uint32_t SP_H = 0xFEFEFEFEu;    // (S-1) + H per field, S = 0x7F
-  static constexpr int WPG = 4;                    // bitmap words per 128-row group
+  static constexpr uint32_t H = 0x80808080u;    // top bit of each 8-bit field
+  static constexpr uint32_t LB = 0x7F7F7F7Fu;   // H - 1 per field: top bit of v + LB <=> v >= 1
+  static constexpr int WPG = 4;                 // bitmap words per 128-row group
 };
 template <>
 struct Swar<16> {
   static constexpr uint32_t H = 0x80008000u;
-  static constexpr uint32_t SP_H = 0xFFFEFFFEu;    // (S-1) + H per field, S = 0x7FFF
-  static constexpr int WPG = 2;                    // bitmap words per 64-row group
+  static constexpr uint32_t LB = 0x7FFF7FFFu;
+  static constexpr int WPG = 2;                 // bitmap words per 64-row group
 };
 
 template <int VEC>
@@ -69,35 +69,61 @@ __device__ __forceinline__ void load_col(const uint8_t* colbase, uint32_t (&v)[T
   for (int s = 0; s < TS; ++s) load_vec<VEC>(colbase + s * 128 * VEC, v + s * VEC);
 }
 
-// Trend accumulators of one candidate for the lane's rows of the tile: on return, the top bit of
-// each field of acc[g] is set iff that row follows the candidate (increasing, or decreasing when
-// NEG); the other bits are don't-care. The chain is walked two columns per iteration so that
-// each pair of compares costs two 3-input adds and one 3-input AND per word.
+// Trend accumulators of one candidate for the lane's rows of the tile: on return acc[g] holds,
+// in the top bit of each field (and nowhere else), whether that row follows the candidate
+// (increasing, or also decreasing when NEG).
+// Codes: a missing value is 0 and real ranks are 1..C, so 0 is below every real rank. A
+// non-decreasing chain that contains a 0 must start with it, and a non-increasing one must end
+// with it; requiring first >= 1 (resp. last >= 1) excludes exactly the rows with a missing value
+// among the candidate's columns. The increasing test starts from that bound (no extra step at
+// the end), and the chain is walked four columns per iteration: a compare costs one 3-input add,
+// and every two compares one 3-input AND.
 template <int WIDTH, int VEC, int TS, bool NEG>
 __device__ __forceinline__ void trend_masks(const uint8_t* lane_base, uint32_t col_stride,
                                             const uint16_t* ccols, int L,
                                             uint32_t (&acc)[TS * VEC]) {
   constexpr int GT = TS * VEC;
   constexpr uint32_t H = Swar<WIDTH>::H;
-  constexpr uint32_t SP_H = Swar<WIDTH>::SP_H;
+  constexpr uint32_t LB = Swar<WIDTH>::LB;
   uint32_t a[GT], accd[GT];
   load_col<VEC, TS>(lane_base + (uint32_t)ccols[0] * col_stride, a);
 #pragma unroll
   for (int g = 0; g < GT; ++g) {
-    acc[g] = 0xFFFFFFFFu;
-    if (NEG) accd[g] = SP_H - a[g];  // S-1 >= first: no missing value at the chain's head
+    acc[g] = a[g] + LB;  // first >= 1: no missing value at the head of an increasing chain
+    if (NEG) accd[g] = 0xFFFFFFFFu;
   }
   int i = 1;
-  // column indices of the next pair are read one iteration ahead (the chunk buffer has slack
-  // past its last column, so reading two entries beyond a candidate stays inside it)
-  uint32_t nb = ccols[1], nc = ccols[2];
+  // column indices are read one step ahead (the chunk buffer has slack past its last column,
+  // so reading a few entries beyond a candidate stays inside it)
+  uint32_t n0 = ccols[1], n1 = ccols[2];
+  if constexpr (!NEG && GT <= 8) {
+    uint32_t n2 = ccols[3], n3 = ccols[4];
+#pragma unroll 1
+    for (; i + 3 < L; i += 4) {
+      uint32_t b[GT], c[GT], d[GT], e[GT];
+      load_col<VEC, TS>(lane_base + n0 * col_stride, b);
+      load_col<VEC, TS>(lane_base + n1 * col_stride, c);
+      load_col<VEC, TS>(lane_base + n2 * col_stride, d);
+      load_col<VEC, TS>(lane_base + n3 * col_stride, e);
+      n0 = ccols[i + 4];
+      n1 = ccols[i + 5];
+      n2 = ccols[i + 6];
+      n3 = ccols[i + 7];
+#pragma unroll
+      for (int g = 0; g < GT; ++g) {
+        const uint32_t t = acc[g] & (b[g] + H - a[g]) & (c[g] + H - b[g]);
+        acc[g] = t & (d[g] + H - c[g]) & (e[g] + H - d[g]);  // a <= b <= c <= d <= e
+        a[g] = e[g];
+      }
+    }
+  }
 #pragma unroll 1
   for (; i + 1 < L; i += 2) {
     uint32_t b[GT], c[GT];
-    load_col<VEC, TS>(lane_base + nb * col_stride, b);
-    load_col<VEC, TS>(lane_base + nc * col_stride, c);
-    nb = ccols[i + 2];
-    nc = ccols[i + 3];
+    load_col<VEC, TS>(lane_base + n0 * col_stride, b);
+    load_col<VEC, TS>(lane_base + n1 * col_stride, c);
+    n0 = ccols[i + 2];
+    n1 = ccols[i + 3];
 #pragma unroll
     for (int g = 0; g < GT; ++g) {
       acc[g] = acc[g] & (b[g] + H - a[g]) & (c[g] + H - b[g]);            // a <= b <= c
@@ -107,7 +133,7 @@ __device__ __forceinline__ void trend_masks(const uint8_t* lane_base, uint32_t c
   }
   if (i < L) {
     uint32_t b[GT];
-    load_col<VEC, TS>(lane_base + nb * col_stride, b);
+    load_col<VEC, TS>(lane_base + n0 * col_stride, b);
 #pragma unroll
     for (int g = 0; g < GT; ++g) {
       acc[g] &= b[g] + H - a[g];
@@ -117,21 +143,30 @@ __device__ __forceinline__ void trend_masks(const uint8_t* lane_base, uint32_t c
   }
 #pragma unroll
   for (int g = 0; g < GT; ++g) {
-    acc[g] &= SP_H - a[g];  // last <= S-1: no missing value at the chain's tail
-    if (NEG) acc[g] |= accd[g];
+    if (NEG) acc[g] |= accd[g] & (a[g] + LB);  // last >= 1 for the decreasing chain
+    acc[g] &= H;
   }
 }
 
 // Gather the match bits of up to WIDTH groups into one word per lane: bit (k*WIDTH + gl) is the
 // top bit of field k of acc[b*WIDTH + gl], i.e. row (group b*WIDTH+gl, sub-row k, this lane).
+// acc holds only top-of-field bits, so shifting group gl's bits right by (WIDTH-1-gl) puts them
+// at distinct positions; the shift is done as the high half of a multiply-add on the FMA pipe,
+// which also accumulates (the bit sets are disjoint, so the sum is their union).
 template <int WIDTH, int GT>
 __device__ __forceinline__ uint32_t pack_block(const uint32_t (&acc)[GT], int b) {
-  constexpr uint32_t LOWF = WIDTH == 8 ? 0x01010101u : 0x00010001u;  // bit 0 of every field
   uint32_t x = 0;
 #pragma unroll
   for (int gl = 0; gl < WIDTH; ++gl) {
     const int g = b * WIDTH + gl;
-    if (g < GT) x |= (acc[g] >> (WIDTH - 1 - gl)) & (LOWF << gl);
+    if (g < GT) {
+      if (gl == WIDTH - 1) {
+        x |= acc[g];
+      } else {
+        const uint32_t mul = 1u << (32 - (WIDTH - 1 - gl));  // hi(acc * 2^(32-s)) = acc >> s
+        asm("mad.hi.u32 %0, %1, %2, %0;" : "+r"(x) : "r"(acc[g]), "r"(mul));
+      }
+    }
   }
   return x;
 }
@@ -290,7 +325,7 @@ __global__ void __launch_bounds__(eval_threads<TS * VEC, NEG>(), 1)
       } else {
 #pragma unroll
         for (int g = 0; g < GT; ++g)
-          if (g0 + g < a.groups) cnt += __popc(acc[g] & Swar<WIDTH>::H);
+          if (g0 + g < a.groups) cnt += __popc(acc[g]);
       }
       cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
       if (lane == 0 && cnt) atomicAdd(&a.counts[cand], cnt);

@@ -51,6 +51,31 @@ __global__ void prepare_kernel(PrepareArgs a) {
   }
 }
 
+// Carry-save adder: a + b + c = 2 * carry + sum, bit by bit (two 3-input logic ops).
+__device__ __forceinline__ void csa(uint32_t& carry, uint32_t& sum, uint32_t a, uint32_t b,
+                                    uint32_t c) {
+  sum = a ^ b ^ c;
+  carry = (a & b) | (c & (a ^ b));
+}
+
+// Total population count of 8 words with a carry-save tree (Harley and Seal): the words are
+// summed bit-parallel into ones/twos/fours/eights, and only those four are popcounted, so the
+// popcount pipe does 4 operations instead of 8 and the ALU pipe absorbs the rest.
+__device__ __forceinline__ uint32_t popc8(const uint32_t (&w)[8]) {
+  uint32_t t1, t2, t3, o1, o2, ones, f1, tw1;
+  csa(t1, o1, w[0], w[1], w[2]);
+  csa(t2, o2, o1, w[3], w[4]);
+  csa(t3, ones, o2, w[5], w[6]);
+  const uint32_t t4 = ones & w[7];
+  ones ^= w[7];
+  csa(f1, tw1, t1, t2, t3);
+  const uint32_t f2 = tw1 & t4;
+  const uint32_t twos = tw1 ^ t4;
+  const uint32_t eights = f1 & f2;
+  const uint32_t fours = f1 ^ f2;
+  return __popc(ones) + 2u * __popc(twos) + 4u * __popc(fours) + 8u * __popc(eights);
+}
+
 constexpr int kOverlapWarps = 8;
 constexpr int kOvCPW = 4;                          // candidates per warp (register blocking)
 constexpr int kOvCands = kOverlapWarps * kOvCPW;   // candidates per block
@@ -105,12 +130,16 @@ __global__ void __launch_bounds__(kOverlapWarps * 32)
           cw[c][t] = (c0 + c < n_cand && w < W) ? __ldg(bitmaps + (size_t)(c0 + c) * W + w) : 0u;
         }
       for (int a = 0; a < na; ++a) {
-        uint32_t p[kOvCPW] = {};
+        uint32_t x[kOvNPL];
 #pragma unroll
-        for (int t = 0; t < kOvNPL; ++t) {
-          const uint32_t x = arch_s[a][lane + 32 * t];
+        for (int t = 0; t < kOvNPL; ++t) x[t] = arch_s[a][lane + 32 * t];
+        uint32_t p[kOvCPW];
 #pragma unroll
-          for (int c = 0; c < kOvCPW; ++c) p[c] += __popc(cw[c][t] & x);
+        for (int c = 0; c < kOvCPW; ++c) {
+          uint32_t w[kOvNPL];
+#pragma unroll
+          for (int t = 0; t < kOvNPL; ++t) w[t] = cw[c][t] & x[t];
+          p[c] = popc8(w);
         }
 #pragma unroll
         for (int c = 0; c < kOvCPW; ++c) {

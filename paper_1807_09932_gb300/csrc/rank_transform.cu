@@ -4,8 +4,9 @@
 // (arXiv 1807.09932, Methods, "Handling missing values": the "greater or equal" relation between
 // the values in the candidate's columns). A per-row dense rank, rank(x) = number of distinct
 // non-missing values of the row strictly below x, keeps that relation exactly:
-// x <= y  <=>  rank(x) <= rank(y). Missing values (NaN, exclusion on) get the sentinel S, larger
-// than every rank; with exclusion off NaN is first replaced by the fill value.
+// x <= y  <=>  rank(x) <= rank(y). Stored codes are rank + 1 (1..C); missing values (NaN,
+// exclusion on) and padding rows get code 0, below every real code; with exclusion off NaN is
+// first replaced by the fill value.
 //
 // Float order without float compares: the IEEE bit pattern is mapped to an unsigned key that
 // orders like the value (-0 folded onto +0, negatives bit-inverted, positives given the top bit),
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(512) rank_transform_kernel(const float* __rest
                                                             int64_t Q, int N, int nwarps) {
   constexpr int RPG = WIDTH == 8 ? 128 : 64;  // rows per group
   constexpr int RPS = RPG * VEC;              // rows per slab
-  constexpr uint32_t S = WIDTH == 8 ? 0x7Fu : 0x7FFFu;
+  constexpr uint32_t MISSING = 0u;  // code of a missing value and of padding rows
   constexpr int TROW = 32 * VEC + 1;          // padded words per column in the tile
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
@@ -59,10 +60,11 @@ __global__ void __launch_bounds__(512) rank_transform_kernel(const float* __rest
     const int j = rho / RPG, rr = rho % RPG, l = rr & 31, k = rr >> 5;
     uint8_t* cell0 = reinterpret_cast<uint8_t*>(tile) + ((size_t)l * VEC + j) * 4 +
                      (WIDTH == 8 ? k : 2 * k);
-    if (r >= R) {  // padding rows hold the sentinel in every column
+    if (r >= R) {  // padding rows hold the missing code in every column
       for (int c = lane; c < C; c += 32) {
         uint8_t* cell = cell0 + (size_t)c * TROW * 4;
-        if (WIDTH == 8) *cell = (uint8_t)S; else *reinterpret_cast<uint16_t*>(cell) = (uint16_t)S;
+        if (WIDTH == 8) *cell = (uint8_t)MISSING;
+        else *reinterpret_cast<uint16_t*>(cell) = (uint16_t)MISSING;
       }
       continue;
     }
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(512) rank_transform_kernel(const float* __rest
       const bool fresh = key != kMissingKey && (p == 0 || (uint32_t)(buf[p - 1] >> 32) != key);
       run += fresh;
       if (c < (uint32_t)C) {
-        const uint32_t rank = key == kMissingKey ? S : run - 1;
+        const uint32_t rank = key == kMissingKey ? MISSING : run;  // 1-based dense rank
         uint8_t* cell = cell0 + (size_t)c * TROW * 4;
         if (WIDTH == 8) *cell = (uint8_t)rank;
         else *reinterpret_cast<uint16_t*>(cell) = (uint16_t)rank;
