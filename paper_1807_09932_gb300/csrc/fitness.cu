@@ -13,6 +13,8 @@
 // The overlap pass reads every candidate bitmap from HBM once, against archive words staged in
 // shared memory; the finalize pass builds the candidate's column set as a shared-memory bitset and
 // tests each archive member's columns against it.
+#include <algorithm>
+
 #include "ebic_internal.h"
 
 namespace ebic {
