@@ -63,6 +63,8 @@ extern "C" {
 /* Negative trends: a row that is non-increasing along the candidate's order also matches. A row
  * that is both non-decreasing and non-increasing (constant) is counted once. */
 #define EBIC_NEGATIVE_TRENDS 0x1u
+/* Evaluate with the rank-code evaluator even when the matrix has a pair table (speed only). */
+#define EBIC_EVAL_DIRECT 0x2u
 
 /* Largest supported column count of this build. Rows are limited to 2^31 - 1, the paper's
  * per-GPU row limit (Methods, "Support for Big Data"). */
@@ -182,6 +184,23 @@ int ebic_matrix_status(ebic_matrix* m, void* stream);
  * EBIC_ERR_UNSUPPORTED. Not thread-safe with concurrent evaluations of the same matrix.
  */
 int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
+/*
+ * Pair table: an exact alternative encoding of the same rule, for populations scored many times
+ * on one matrix. For every ordered column pair (a, b) the table holds the bitmap of rows where a
+ * is not missing and b's value is >= a's; the diagonal holds "a not missing". A candidate's
+ * bitmap is then the AND of its consecutive pairs' rows (the reversed pairs for decreasing
+ * trends), one 32-bit AND per 32 rows per column, instead of a compare per row per column.
+ * The table takes cols * cols * W * 4 bytes of device memory and is built once, by the
+ * evaluator itself (on the population of all pairs), so results never change.
+ *   ebic_matrix_build_pairs: build it if it needs at most max_bytes (else EBIC_ERR_UNSUPPORTED);
+ *                            *bytes (may be NULL) receives the size. Synchronous.
+ *   ebic_matrix_drop_pairs:  free it.
+ * While a matrix has a table, ebic_eval_population uses it unless EBIC_EVAL_DIRECT is given.
+ * ebic_eval_population_noalloc and the batched calls always use the rank-code evaluator.
+ */
+int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, uint64_t* bytes);
+int ebic_matrix_drop_pairs(ebic_matrix* m);
+
 /* Candidate columns staged per chunk (the candidate tile: each chunk of the population is
  * checked against each row tile), or 0 for the built-in choice. Rounded up to a multiple of 64
  * and capped by the shared memory left after the row-tile stages. Speed only, never results.
@@ -306,7 +325,8 @@ int64_t ebic_launch_count(void);
 #define EBIC_TIMING_EVALUATE       2  /* the population evaluator */
 #define EBIC_TIMING_OVERLAP        3  /* bitmap overlaps against the archive */
 #define EBIC_TIMING_FITNESS        4  /* penalised fitness */
-#define EBIC_TIMING_KINDS          5
+#define EBIC_TIMING_PAIR_EVALUATE  5  /* the pair-table evaluator */
+#define EBIC_TIMING_KINDS          6
 /* Enable (1) or disable (0) recording. Either way, the events recorded so far are dropped. */
 int ebic_timing_enable(int on);
 /* Wait for the recorded events of `kind` and return their summed duration and count. */

@@ -30,6 +30,8 @@ struct ebic_matrix {
   bool tmap_ok[3] = {false, false, false};
   int tile = 0;                // 0: built-in tile choice; else the TS every evaluation uses
   int chunk = 0;               // 0: built-in chunk size; else candidate columns per chunk
+  uint32_t* pairs = nullptr;   // pair table [cols*cols][W] or null
+  size_t pair_bytes = 0;
 };
 
 namespace {
@@ -441,6 +443,7 @@ int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uin
 int ebic_free_matrix(ebic_matrix* m) {
   if (!m) return EBIC_OK;
   DeviceGuard g(m->device);
+  if (m->pairs) cudaFree(m->pairs);
   cudaError_t e1 = cudaFree(m->ranks);
   cudaError_t e2 = cudaFree(m->status);
   delete m;
@@ -485,7 +488,8 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
                          void* stream) {
   ebic_matrix* m = const_cast<ebic_matrix*>(cm);
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
-  if (flags & ~EBIC_NEGATIVE_TRENDS) return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
+  if (flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_EVAL_DIRECT))
+    return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
   if (n_cand == 0) return EBIC_OK;
   if (!cols || !offsets || !counts) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard g(m->device);
@@ -554,6 +558,12 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
     pa.status = m->status;
     EBIC_CUDA(launch_prepare(pa, s));
   }
+  if (m->pairs && !(flags & EBIC_EVAL_DIRECT)) {
+    Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
+    EBIC_CUDA(launch_pair_eval(m->pairs, L.cols, L.words, dcols, doffs, n_cand,
+                               (flags & EBIC_NEGATIVE_TRENDS) != 0, dcounts, dbitmaps, err,
+                               m->num_sms, s));
+  } else {
   a.n_cand = n_cand;
   a.cand_cols = dcols;
   a.cand_offsets = doffs;
@@ -572,6 +582,7 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
   {
     Timed t(EBIC_TIMING_EVALUATE, s);
     EBIC_CUDA(launch_eval(cfg, tmap, a, s));
+  }
   }
 
   if (counts_host || bitmaps_host) {
@@ -751,6 +762,60 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs) {
       return fail(EBIC_ERR_UNSUPPORTED, "tile does not fit in shared memory for this matrix");
   }
   m->tile = tile_slabs;
+  return EBIC_OK;
+}
+
+int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, uint64_t* bytes) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  const Layout& L = m->L;
+  const uint64_t need = (uint64_t)L.cols * (uint64_t)L.cols * (uint64_t)L.words * 4ull;
+  if (bytes) *bytes = need;
+  if (need > max_bytes)
+    return fail(EBIC_ERR_UNSUPPORTED, "the pair table needs " + std::to_string(need) +
+                                          " bytes, more than max_bytes");
+  DeviceGuard g(m->device);
+  if (m->pairs) return EBIC_OK;
+  // the population of all ordered pairs (a, b), a != b, and of all singles (a), in table order
+  const uint32_t C = (uint32_t)L.cols, n = C * C;
+  std::vector<uint16_t> cols;
+  std::vector<uint32_t> offs(1, 0u);
+  cols.reserve((size_t)2 * n);
+  for (uint32_t a = 0; a < C; ++a)
+    for (uint32_t b = 0; b < C; ++b) {
+      cols.push_back((uint16_t)a);
+      if (b != a) cols.push_back((uint16_t)b);
+      offs.push_back((uint32_t)cols.size());
+    }
+  uint32_t* table = nullptr;
+  uint32_t* counts = nullptr;
+  cudaError_t e = cudaMalloc(&table, need);
+  if (e == cudaSuccess) e = cudaMalloc(&counts, (size_t)n * 4);
+  if (e != cudaSuccess) {
+    if (table) cudaFree(table);
+    return cuda_fail(e, "pair table allocation");
+  }
+  int rc = ebic_eval_population(m, cols.data(), offs.data(), n, EBIC_EVAL_DIRECT, counts, table,
+                                stream);
+  cudaError_t e2 = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  cudaFree(counts);
+  if (rc == EBIC_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "pair table build");
+  if (rc != EBIC_OK) {
+    cudaFree(table);
+    return rc;
+  }
+  m->pairs = table;
+  m->pair_bytes = need;
+  return EBIC_OK;
+}
+
+int ebic_matrix_drop_pairs(ebic_matrix* m) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (m->pairs) {
+    DeviceGuard g(m->device);
+    EBIC_CUDA(cudaFree(m->pairs));
+    m->pairs = nullptr;
+    m->pair_bytes = 0;
+  }
   return EBIC_OK;
 }
 

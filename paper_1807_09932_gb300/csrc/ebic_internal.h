@@ -118,6 +118,12 @@ cudaError_t launch_eval_w16v4(const EvalConfig&, const CUtensorMap*, const EvalA
 cudaError_t launch_eval_w16v2(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 
+// ---- pair-table evaluation -----------------------------------------------------------------
+cudaError_t launch_pair_eval(const uint32_t* table, int32_t C, int64_t W, const uint16_t* cols,
+                             const uint32_t* offsets, uint32_t n_cand, bool negative,
+                             uint32_t* counts, uint32_t* bitmaps, const uint32_t* err,
+                             int num_sms, cudaStream_t s);
+
 // ---- fitness -------------------------------------------------------------------------------
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,
                            uint32_t n_arch, int64_t words, uint32_t* overlaps,

@@ -27,6 +27,7 @@ EBIC_ERR_UNSUPPORTED = -5
 EBIC_ERR_NO_DEVICE = -6
 EBIC_EXCLUDE_MISSING = 0x1
 EBIC_NEGATIVE_TRENDS = 0x1
+EBIC_EVAL_DIRECT = 0x2
 EBIC_MAX_COLS = 832
 EBIC_MAX_CANDIDATE_LEN = 64
 
@@ -60,6 +61,9 @@ _lib_status = _sig("ebic_matrix_status", [_P, _P])
 _lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
 _lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
 _lib_set_chunk = _sig("ebic_matrix_set_chunk_cols", [_P, _I32])
+_lib_build_pairs = _sig("ebic_matrix_build_pairs", [_P, ctypes.c_uint64, _P,
+                                                    ctypes.POINTER(ctypes.c_uint64)])
+_lib_drop_pairs = _sig("ebic_matrix_drop_pairs", [_P])
 _lib_last_error = _sig("ebic_last_error", [], ctypes.c_char_p)
 _lib_launch_count = _sig("ebic_launch_count", [], ctypes.c_int64)
 _lib_timing_enable = _sig("ebic_timing_enable", [ctypes.c_int])
@@ -224,6 +228,18 @@ def ebic_matrix_set_chunk_cols(h, chunk_cols):
     _check(_lib_set_chunk(h, chunk_cols), "ebic_matrix_set_chunk_cols")
 
 
+def ebic_matrix_build_pairs(h, max_bytes, stream=None):
+    """Build the matrix's pair table if it fits max_bytes; returns its size in bytes."""
+    n = ctypes.c_uint64()
+    _check(_lib_build_pairs(h, max_bytes, _stream(stream), ctypes.byref(n)),
+           "ebic_matrix_build_pairs")
+    return n.value
+
+
+def ebic_matrix_drop_pairs(h):
+    _check(_lib_drop_pairs(h), "ebic_matrix_drop_pairs")
+
+
 def ebic_matrix_get_tile(h):
     t, r = _I32(), _I32()
     _check(_lib_get_tile(h, ctypes.byref(t), ctypes.byref(r)), "ebic_matrix_get_tile")
@@ -231,7 +247,8 @@ def ebic_matrix_get_tile(h):
 
 
 EBIC_TIMING_RANK_TRANSFORM, EBIC_TIMING_PREPARE, EBIC_TIMING_EVALUATE = 0, 1, 2
-EBIC_TIMING_OVERLAP, EBIC_TIMING_FITNESS, EBIC_TIMING_KINDS = 3, 4, 5
+EBIC_TIMING_OVERLAP, EBIC_TIMING_FITNESS, EBIC_TIMING_PAIR_EVALUATE = 3, 4, 5
+EBIC_TIMING_KINDS = 6
 
 
 def ebic_launch_count():
@@ -381,6 +398,12 @@ class Matrix:
     def set_tile(self, tile_slabs):
         ebic_matrix_set_tile(self.handle, tile_slabs)
 
+    def build_pairs(self, max_bytes=1 << 34, stream=None):
+        return ebic_matrix_build_pairs(self.handle, max_bytes, stream)
+
+    def drop_pairs(self):
+        ebic_matrix_drop_pairs(self.handle)
+
     def set_chunk_cols(self, chunk_cols):
         ebic_matrix_set_chunk_cols(self.handle, chunk_cols)
 
@@ -389,7 +412,7 @@ class Matrix:
 
 
 def eval_population(m: Matrix, cols, offsets, *, negative=False, want_bitmaps=True, counts=None,
-                    bitmaps=None, stream=None):
+                    bitmaps=None, stream=None, direct=False):
     """Counts and bitmaps. Host numpy inputs give host numpy outputs unless buffers are given."""
     n = len(offsets) - 1
     if counts is None:
@@ -398,8 +421,8 @@ def eval_population(m: Matrix, cols, offsets, *, negative=False, want_bitmaps=Tr
         bitmaps = np.zeros((n, m.words), dtype=np.uint32)
     if not want_bitmaps:
         bitmaps = None
-    rc = ebic_eval_population(m.handle, cols, offsets, n,
-                              EBIC_NEGATIVE_TRENDS if negative else 0, counts, bitmaps, stream)
+    flags = (EBIC_NEGATIVE_TRENDS if negative else 0) | (EBIC_EVAL_DIRECT if direct else 0)
+    rc = ebic_eval_population(m.handle, cols, offsets, n, flags, counts, bitmaps, stream)
     _check(rc, "ebic_eval_population")
     return counts, bitmaps
 
