@@ -131,22 +131,32 @@ __global__ void __launch_bounds__(kOverlapWarps * 32)
           const int64_t w = ws + lane + 32 * t;
           cw[c][t] = (c0 + c < n_cand && w < W) ? __ldg(bitmaps + (size_t)(c0 + c) * W + w) : 0u;
         }
-      for (int a = 0; a < na; ++a) {
-        uint32_t x[kOvNPL];
+      // a candidate whose 256 words here are all zero contributes nothing to any overlap: long
+      // chains match few rows, so most of their sub-segments are skipped (warp-uniform flags)
+      bool nz[kOvCPW];
+      bool any = false;
 #pragma unroll
-        for (int t = 0; t < kOvNPL; ++t) x[t] = arch_s[a][lane + 32 * t];
-        uint32_t p[kOvCPW];
+      for (int c = 0; c < kOvCPW; ++c) {
+        uint32_t o = 0;
 #pragma unroll
-        for (int c = 0; c < kOvCPW; ++c) {
-          uint32_t w[kOvNPL];
+        for (int t = 0; t < kOvNPL; ++t) o |= cw[c][t];
+        nz[c] = __any_sync(0xFFFFFFFFu, o != 0u);
+        any |= nz[c];
+      }
+      if (any) {
+        for (int a = 0; a < na; ++a) {
+          uint32_t x[kOvNPL];
 #pragma unroll
-          for (int t = 0; t < kOvNPL; ++t) w[t] = cw[c][t] & x[t];
-          p[c] = popc8(w);
-        }
+          for (int t = 0; t < kOvNPL; ++t) x[t] = arch_s[a][lane + 32 * t];
 #pragma unroll
-        for (int c = 0; c < kOvCPW; ++c) {
-          const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, p[c]);
-          if (lane == 0) part_s[warp * kOvCPW + c][a] += v;
+          for (int c = 0; c < kOvCPW; ++c) {
+            if (!nz[c]) continue;
+            uint32_t w[kOvNPL];
+#pragma unroll
+            for (int t = 0; t < kOvNPL; ++t) w[t] = cw[c][t] & x[t];
+            const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, popc8(w));
+            if (lane == 0) part_s[warp * kOvCPW + c][a] += v;
+          }
         }
       }
     }
