@@ -61,6 +61,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-pairs", action="store_true",
                    help="score with the rank-code evaluator instead of the pair table")
+    p.add_argument("--unfused", action="store_true",
+                   help="time ebic_eval_population + ebic_fitness instead of ebic_eval_fitness")
     p.add_argument("--pair-budget", type=int, default=8 << 30,
                    help="largest pair table to build, bytes")
     p.add_argument("--workload", choices=["methylation", "batched", "served"],
@@ -291,13 +293,19 @@ def main():
 
     def step(i):
         dc, do, n = dpops[i % N_POPS]
-        rc = ebic.ebic_eval_population(h, dc, do, n, 0, counts, bitmaps, sp)
+        if args.unfused:
+            rc = ebic.ebic_eval_population(h, dc, do, n, 0, counts, bitmaps, sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_eval_population")
+            rc = ebic.ebic_fitness(h, dc, do, n, counts, bitmaps, dacols, daoffs, dabm, K, 0,
+                                   fit, None, sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_fitness")
+            return
+        rc = ebic.ebic_eval_fitness(h, dc, do, n, 0, dacols, daoffs, dabm, K, counts, None, fit,
+                                    None, sp)
         if rc:
-            raise ebic.EbicError(rc, "ebic_eval_population")
-        rc = ebic.ebic_fitness(h, dc, do, n, counts, bitmaps, dacols, daoffs, dabm, K, 0, fit,
-                               None, sp)
-        if rc:
-            raise ebic.EbicError(rc, "ebic_fitness")
+            raise ebic.EbicError(rc, "ebic_eval_fitness")
 
     for i in range(args.warmup):
         step(i)
@@ -358,13 +366,19 @@ def main():
 
         def e2e_step(i):
             hc, ho, n = hpops[i % N_POPS]
-            rc = ebic.ebic_eval_population(h, hc, ho, n, 0, counts, bitmaps, sp)
+            if args.unfused:
+                rc = ebic.ebic_eval_population(h, hc, ho, n, 0, counts, bitmaps, sp)
+                if rc:
+                    raise ebic.EbicError(rc, "ebic_eval_population")
+                rc = ebic.ebic_fitness(h, hc, ho, n, counts, bitmaps, dacols, daoffs, dabm, K,
+                                       0, hfit, None, sp)   # host output: synchronizes
+                if rc:
+                    raise ebic.EbicError(rc, "ebic_fitness")
+                return
+            rc = ebic.ebic_eval_fitness(h, hc, ho, n, 0, dacols, daoffs, dabm, K, counts, None,
+                                        hfit, None, sp)   # host output: synchronizes
             if rc:
-                raise ebic.EbicError(rc, "ebic_eval_population")
-            rc = ebic.ebic_fitness(h, hc, ho, n, counts, bitmaps, dacols, daoffs, dabm, K, 0,
-                                   hfit, None, sp)   # host output: synchronizes
-            if rc:
-                raise ebic.EbicError(rc, "ebic_fitness")
+                raise ebic.EbicError(rc, "ebic_eval_fitness")
 
         for i in range(3):
             e2e_step(i)
@@ -383,17 +397,22 @@ def main():
         e2e = {"value": float(P) * R * args.e2e_steps * ws / et,
                "unit": "candidate-row evals/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * et / args.e2e_steps,
-               "path": "ebic_eval_population + ebic_fitness, population in pinned host memory, "
-                       "fitness read back to pinned host memory"}
+               "path": ("ebic_eval_population + ebic_fitness" if args.unfused
+                        else "ebic_eval_fitness") +
+                       ", population in pinned host memory, fitness read back to pinned host "
+                       "memory"}
 
     # ---- roofline of the dominant kernel (the evaluator) ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     eval_launch_ms = eval_ms / max(eval_n, 1)
-    kernels = {"overlap": roofline_overlap(pops, K, m, ov_ms / max(ov_n, 1), sms, clk)}
+    kernels = {}
+    if ov_n:
+        kernels["overlap"] = roofline_overlap(pops, K, m, ov_ms / ov_n, sms, clk)
     if pev_n:
-        kernels["pair_evaluate"] = roofline_pairs(pops, R, m, pev_ms / pev_n, clk, peaks)
+        kernels["pair_evaluate"] = roofline_pairs(pops, R, m, pev_ms / pev_n, clk, peaks,
+                                                  not args.unfused, K)
     if eval_n:
         kernels["evaluate"] = roofline_eval(pops, R, m, eval_launch_ms, sms, clk, peaks)
     dominant = max(kernels, key=lambda k: kernels[k]["launch_ms"])
@@ -408,6 +427,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": R, "cols": C, "population": P,
                        "archive": K, "populations_cycled": N_POPS,
+                       "step": ("ebic_eval_population + ebic_fitness" if args.unfused
+                                else "ebic_eval_fitness (evaluation and archive overlaps fused)"),
                        "l2": "flushed between timed steps (512 MB write, outside the events)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "rank_bits": m.rank_bits, "tile": list(m.tile)},
@@ -454,11 +475,13 @@ def eval_traffic():
     return rec["dram_bytes_per_launch"]
 
 
-def roofline_pairs(pops, R, m, launch_ms, clk, peaks):
+def roofline_pairs(pops, R, m, launch_ms, clk, peaks, fused, K):
     """The pair-table evaluator: an HBM stream. Algorithmic bytes per launch: the table rows the
-    population needs (distinct consecutive column pairs; each read once) plus the bitmaps it
-    writes and its counts, against the measured HBM copy bandwidth."""
+    population needs (distinct consecutive column pairs, rows of W rounded up to 128 words;
+    each read once) and its counts, plus the bitmaps it writes (unfused) or the padded archive
+    rows it reads (fused), against the measured HBM copy bandwidth."""
     W = m.words
+    Wt = (W + 127) // 128 * 128
     per = []
     for c, o in pops:
         pairs = set()
@@ -468,13 +491,15 @@ def roofline_pairs(pops, R, m, launch_ms, clk, peaks):
                 pairs.add((int(seq[0]), int(seq[0])))
             for a, b in zip(seq[:-1], seq[1:]):
                 pairs.add((int(a), int(b)))
-        per.append(len(pairs) * W * 4 + (len(o) - 1) * (W * 4 + 4))
+        extra = K * Wt * 4 if fused else (len(o) - 1) * W * 4
+        per.append(len(pairs) * Wt * 4 + (len(o) - 1) * 4 + extra)
     hbm_bytes = float(np.mean(per))
     t = launch_ms / 1000.0
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": hbm_bytes / t / 1e9, "peak": peak, "unit": "GB/s",
             "frac": (hbm_bytes / t / 1e9) / peak, "traffic": None,
-            "kernel": "pair_eval_kernel", "launch_ms": launch_ms,
+            "kernel": "pair_eval_kernel" + (" (fused overlaps)" if fused else ""),
+            "launch_ms": launch_ms,
             "algorithmic_bytes_per_launch": hbm_bytes,
             "peak_basis": "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)"
                           if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}

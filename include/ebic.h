@@ -169,6 +169,31 @@ int ebic_fitness(const ebic_matrix* m, const uint16_t* cols, const uint32_t* off
                  uint64_t* fitness, uint32_t* overlaps, void* stream);
 
 /*
+ * One generation's scoring in one call: ebic_eval_population followed by ebic_fitness, with
+ * the same results (arXiv 1807.09932, Methods: the population is evaluated by counting rows,
+ * "Handling missing values"; the fitness as defined for ebic_fitness above).
+ *   cols, offsets, n_cand, flags   the population and flags, as for ebic_eval_population
+ *   arch_cols, arch_offsets, arch_bitmaps, n_arch   the archive, as for ebic_fitness
+ *   counts     out: uint32[n_cand] matched rows
+ *   bitmaps    out: uint32[n_cand][W] row bitmaps, or NULL when the caller needs none
+ *   fitness    out: uint64[n_cand]
+ *   overlaps   out: uint32[n_cand][n_arch], or NULL. When NULL, the overlap of a candidate with
+ *              a member that shares no column with it is not computed (it cannot change F_c).
+ * When the matrix has a pair table, EBIC_EVAL_DIRECT is not given and n_arch <= 64, the call
+ * runs as one preparation launch, one pass that evaluates the population and ANDs its words
+ * with the archive's while they are in registers (the bitmaps never round-trip through device
+ * memory), and one finalize launch. Otherwise it makes the two calls in sequence (with the
+ * bitmaps in stream-ordered scratch when `bitmaps` is NULL). Buffers may be host or device memory
+ * as for the two calls; a candidate list keeps its columns and offsets in the same memory.
+ * Errors as for the two calls.
+ */
+int ebic_eval_fitness(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                      uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                      const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                      uint32_t n_arch, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
+                      uint32_t* overlaps, void* stream);
+
+/*
  * Synchronize `stream` and return the deferred device status of `m`, then clear it. That
  * status is EBIC_OK, EBIC_ERR_INVALID_ARG (a device-resident candidate list failed the device
  * check) or EBIC_ERR_DEVICE_TIMEOUT (a bounded wait in a kernel expired). The status is shared by
@@ -190,12 +215,14 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
  * is not missing and b's value is >= a's; the diagonal holds "a not missing". A candidate's
  * bitmap is then the AND of its consecutive pairs' rows (the reversed pairs for decreasing
  * trends), one 32-bit AND per 32 rows per column, instead of a compare per row per column.
- * The table takes cols * cols * W * 4 bytes of device memory and is built once, by the
- * evaluator itself (on the population of all pairs), so results never change.
+ * The table takes cols * cols * W' * 4 bytes of device memory, W' = W rounded up to a multiple
+ * of 128 (its rows are padded with zero words), and is built once, by the evaluator itself (on
+ * the population of all pairs), so results never change.
  *   ebic_matrix_build_pairs: build it if it needs at most max_bytes (else EBIC_ERR_UNSUPPORTED);
  *                            *bytes (may be NULL) receives the size. Synchronous.
  *   ebic_matrix_drop_pairs:  free it.
- * While a matrix has a table, ebic_eval_population uses it unless EBIC_EVAL_DIRECT is given.
+ * While a matrix has a table, ebic_eval_population and ebic_eval_fitness use it unless
+ * EBIC_EVAL_DIRECT is given.
  * ebic_eval_population_noalloc and the batched calls always use the rank-code evaluator.
  */
 int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, uint64_t* bytes);

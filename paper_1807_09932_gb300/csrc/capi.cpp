@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -30,7 +31,8 @@ struct ebic_matrix {
   bool tmap_ok[3] = {false, false, false};
   int tile = 0;                // 0: built-in tile choice; else the TS every evaluation uses
   int chunk = 0;               // 0: built-in chunk size; else candidate columns per chunk
-  uint32_t* pairs = nullptr;   // pair table [cols*cols][W] or null
+  uint32_t* pairs = nullptr;   // pair table [cols*cols][pair_stride], padding zero, or null
+  uint32_t pair_stride = 0;
   size_t pair_bytes = 0;
 };
 
@@ -310,6 +312,7 @@ bool plan_eval(const Layout& L, int ts, uint32_t n_cand, int64_t total_cols_hint
   a->slabs = L.slabs;
   a->groups = L.groups;
   a->words = L.words;
+  a->bitmap_stride = L.words;
   a->chunk_cols = (int32_t)cc;
   a->col_box = cb;
   a->n_col_boxes = nb;
@@ -365,6 +368,135 @@ cudaError_t launch_eval(const EvalConfig& cfg, const CUtensorMap* tmap, const Ev
 }
 
 }  // namespace ebic
+
+// ebic_eval_population with the candidates' bitmaps `bitmap_stride` words apart (the pair table
+// is built through this with its padded stride).
+static int eval_population_impl(ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                         uint32_t n_cand, uint32_t flags, uint32_t* counts, uint32_t* bitmaps,
+                         int64_t bitmap_stride, void* stream) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_EVAL_DIRECT))
+    return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
+  if (n_cand == 0) return EBIC_OK;
+  if (!cols || !offsets || !counts) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(m->device);
+  const int dev = m->device;
+  const Layout& L = m->L;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
+                        (const void*)bitmaps})
+    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+
+  const bool host_lists = !on_device(cols, dev) && !on_device(offsets, dev);
+  int64_t total_hint = 0;
+  if (host_lists) {
+    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+    total_hint = offsets[n_cand];
+  }
+
+  int ts = m->tile ? m->tile : default_tile_slabs(L);
+  while (ts > 1 && ts > L.slabs) ts >>= 1;
+  EvalArgs a;
+  if (!plan_eval(L, ts, n_cand, total_hint, m->num_sms, &a, m->chunk))
+    return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
+  const CUtensorMap* tmap = nullptr;
+  int rc = get_tmap(m, ts, a.col_box, &tmap);
+  if (rc != EBIC_OK) return rc;
+
+  Scratch sc(s);
+  uint32_t* err = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
+  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  const uint16_t* dcols = nullptr;
+  const uint32_t* doffs = nullptr;
+  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
+  // the column count is only known from the offsets; device lists are read by the kernels
+  const size_t ncols_total = host_lists ? offsets[n_cand] : 0;
+  if (on_device(cols, dev)) {
+    dcols = cols;
+  } else {
+    size_t n = ncols_total;
+    if (!host_lists) {  // host columns with device offsets: fetch the total first
+      uint32_t t = 0;
+      EBIC_CUDA(cudaMemcpyAsync(&t, offsets + n_cand, 4, cudaMemcpyDeviceToHost, s));
+      EBIC_CUDA(cudaStreamSynchronize(s));
+      n = t;
+    }
+    EBIC_CUDA(to_device(cols, n, dev, sc, &dcols));
+  }
+  bool counts_host = false, bitmaps_host = false;
+  uint32_t* dcounts = nullptr;
+  uint32_t* dbitmaps = nullptr;
+  EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
+  if (bitmaps)
+    EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * bitmap_stride, dev, sc, &dbitmaps,
+                         &bitmaps_host));
+
+  {
+    Timed t(EBIC_TIMING_PREPARE, s);
+    PrepareArgs pa;
+    pa.cols[0] = dcols;
+    pa.offsets[0] = doffs;
+    pa.n[0] = host_lists ? 0 : n_cand;  // host lists were checked on the host
+    pa.ncols = L.cols;
+    pa.zero = dcounts;
+    pa.n_zero = n_cand;
+    pa.err = err;
+    pa.status = m->status;
+    EBIC_CUDA(launch_prepare(pa, s));
+  }
+  if (m->pairs && !(flags & EBIC_EVAL_DIRECT) && bitmap_stride == L.words) {
+    Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
+    PairArgs p;
+    p.table = m->pairs;
+    p.stride = m->pair_stride;
+    p.C = L.cols;
+    p.W = L.words;
+    p.cols = dcols;
+    p.offsets = doffs;
+    p.n_cand = n_cand;
+    p.counts = dcounts;
+    p.bitmaps = dbitmaps;
+    p.err = err;
+    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms, s));
+  } else {
+  a.n_cand = n_cand;
+  a.cand_cols = dcols;
+  a.cand_offsets = doffs;
+  a.counts = dcounts;
+  a.bitmaps = dbitmaps;
+  a.bitmap_stride = bitmap_stride;
+  a.err = err;
+  a.err_out = err;
+  a.status = m->status;
+  EvalConfig cfg;
+  cfg.width = L.width;
+  cfg.vec = L.vec;
+  cfg.ts = ts;
+  cfg.negative = (flags & EBIC_NEGATIVE_TRENDS) != 0;
+  cfg.bitmaps = dbitmaps != nullptr;
+  cfg.grid = m->num_sms;
+  {
+    Timed t(EBIC_TIMING_EVALUATE, s);
+    EBIC_CUDA(launch_eval(cfg, tmap, a, s));
+  }
+  }
+
+  if (counts_host || bitmaps_host) {
+    if (counts_host)
+      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
+    if (bitmaps_host)
+      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbitmaps, (size_t)n_cand * bitmap_stride * 4,
+                                cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_eval_population");
+  }
+  return EBIC_OK;
+}
+
 
 extern "C" {
 
@@ -488,115 +620,8 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
                          void* stream) {
   ebic_matrix* m = const_cast<ebic_matrix*>(cm);
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
-  if (flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_EVAL_DIRECT))
-    return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
-  if (n_cand == 0) return EBIC_OK;
-  if (!cols || !offsets || !counts) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
-  DeviceGuard g(m->device);
-  const int dev = m->device;
-  const Layout& L = m->L;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
-                        (const void*)bitmaps})
-    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
-
-  const bool host_lists = !on_device(cols, dev) && !on_device(offsets, dev);
-  int64_t total_hint = 0;
-  if (host_lists) {
-    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
-    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
-    total_hint = offsets[n_cand];
-  }
-
-  int ts = m->tile ? m->tile : default_tile_slabs(L);
-  while (ts > 1 && ts > L.slabs) ts >>= 1;
-  EvalArgs a;
-  if (!plan_eval(L, ts, n_cand, total_hint, m->num_sms, &a, m->chunk))
-    return fail(EBIC_ERR_UNSUPPORTED, "no shared-memory plan for this matrix shape");
-  const CUtensorMap* tmap = nullptr;
-  int rc = get_tmap(m, ts, a.col_box, &tmap);
-  if (rc != EBIC_OK) return rc;
-
-  Scratch sc(s);
-  uint32_t* err = nullptr;
-  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
-  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-  const uint16_t* dcols = nullptr;
-  const uint32_t* doffs = nullptr;
-  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
-  // the column count is only known from the offsets; device lists are read by the kernels
-  const size_t ncols_total = host_lists ? offsets[n_cand] : 0;
-  if (on_device(cols, dev)) {
-    dcols = cols;
-  } else {
-    size_t n = ncols_total;
-    if (!host_lists) {  // host columns with device offsets: fetch the total first
-      uint32_t t = 0;
-      EBIC_CUDA(cudaMemcpyAsync(&t, offsets + n_cand, 4, cudaMemcpyDeviceToHost, s));
-      EBIC_CUDA(cudaStreamSynchronize(s));
-      n = t;
-    }
-    EBIC_CUDA(to_device(cols, n, dev, sc, &dcols));
-  }
-  bool counts_host = false, bitmaps_host = false;
-  uint32_t* dcounts = nullptr;
-  uint32_t* dbitmaps = nullptr;
-  EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
-  if (bitmaps)
-    EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbitmaps, &bitmaps_host));
-
-  {
-    Timed t(EBIC_TIMING_PREPARE, s);
-    PrepareArgs pa;
-    pa.cols[0] = dcols;
-    pa.offsets[0] = doffs;
-    pa.n[0] = host_lists ? 0 : n_cand;  // host lists were checked on the host
-    pa.ncols = L.cols;
-    pa.zero = dcounts;
-    pa.n_zero = n_cand;
-    pa.err = err;
-    pa.status = m->status;
-    EBIC_CUDA(launch_prepare(pa, s));
-  }
-  if (m->pairs && !(flags & EBIC_EVAL_DIRECT)) {
-    Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
-    EBIC_CUDA(launch_pair_eval(m->pairs, L.cols, L.words, dcols, doffs, n_cand,
-                               (flags & EBIC_NEGATIVE_TRENDS) != 0, dcounts, dbitmaps, err,
-                               m->num_sms, s));
-  } else {
-  a.n_cand = n_cand;
-  a.cand_cols = dcols;
-  a.cand_offsets = doffs;
-  a.counts = dcounts;
-  a.bitmaps = dbitmaps;
-  a.err = err;
-  a.err_out = err;
-  a.status = m->status;
-  EvalConfig cfg;
-  cfg.width = L.width;
-  cfg.vec = L.vec;
-  cfg.ts = ts;
-  cfg.negative = (flags & EBIC_NEGATIVE_TRENDS) != 0;
-  cfg.bitmaps = dbitmaps != nullptr;
-  cfg.grid = m->num_sms;
-  {
-    Timed t(EBIC_TIMING_EVALUATE, s);
-    EBIC_CUDA(launch_eval(cfg, tmap, a, s));
-  }
-  }
-
-  if (counts_host || bitmaps_host) {
-    if (counts_host)
-      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
-    if (bitmaps_host)
-      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbitmaps, (size_t)n_cand * L.words * 4,
-                                cudaMemcpyDeviceToHost, s));
-    uint32_t bits = 0;
-    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
-    EBIC_CUDA(cudaStreamSynchronize(s));
-    return status_code(bits, "ebic_eval_population");
-  }
-  return EBIC_OK;
+  return eval_population_impl(m, cols, offsets, n_cand, flags, counts, bitmaps, m->L.words,
+                              stream);
 }
 
 int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
@@ -707,6 +732,153 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
   return EBIC_OK;
 }
 
+int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                      uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                      const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                      uint32_t n_arch, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
+                      uint32_t* overlaps, void* stream) {
+  ebic_matrix* m = const_cast<ebic_matrix*>(cm);
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_EVAL_DIRECT))
+    return fail(EBIC_ERR_INVALID_ARG, "unknown eval flag");
+  if (n_cand == 0) return EBIC_OK;
+  if (!cols || !offsets || !counts || !fitness) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  if (n_arch > 0 && (!arch_cols || !arch_offsets || !arch_bitmaps))
+    return fail(EBIC_ERR_INVALID_ARG, "NULL archive argument");
+  DeviceGuard g(m->device);
+  const int dev = m->device;
+  const Layout& L = m->L;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
+                        (const void*)bitmaps, (const void*)arch_cols, (const void*)arch_offsets,
+                        (const void*)arch_bitmaps, (const void*)fitness, (const void*)overlaps})
+    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+
+  const bool fused = m->pairs && !(flags & EBIC_EVAL_DIRECT) && n_arch <= (uint32_t)kPairMaxArch;
+  if (!fused) {
+    // the two calls in sequence; the bitmaps go through scratch when the caller wants none
+    Scratch sc(s);
+    uint32_t* bm = bitmaps;
+    if (!bm) EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&bm), (size_t)n_cand * L.words * 4));
+    int rc = ebic_eval_population(m, cols, offsets, n_cand, flags, counts, bm, stream);
+    if (rc != EBIC_OK) return rc;
+    return ebic_fitness(m, cols, offsets, n_cand, counts, bm, arch_cols, arch_offsets,
+                        arch_bitmaps, n_arch, 0, fitness, overlaps, stream);
+  }
+
+  const bool host_c = !on_device(cols, dev) && !on_device(offsets, dev);
+  if (host_c) {
+    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+  }
+  const bool host_a = n_arch == 0 || (!on_device(arch_cols, dev) && !on_device(arch_offsets, dev));
+  if (n_arch > 0 && host_a) {
+    std::string why = check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
+  }
+  if ((!host_c && (!on_device(cols, dev) || !on_device(offsets, dev))) ||
+      (n_arch > 0 && !host_a && (!on_device(arch_cols, dev) || !on_device(arch_offsets, dev))))
+    return fail(EBIC_ERR_INVALID_ARG,
+                "a candidate list must have its columns and offsets in the same memory");
+
+  Scratch sc(s);
+  uint32_t* err = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
+  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  const uint16_t *dcols = nullptr, *dacols = nullptr;
+  const uint32_t *doffs = nullptr, *daoffs = nullptr, *dabm = nullptr;
+  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
+  EBIC_CUDA(to_device(cols, host_c ? (size_t)offsets[n_cand] : 0, dev, sc, &dcols));
+  if (n_arch > 0) {
+    EBIC_CUDA(to_device(arch_offsets, (size_t)n_arch + 1, dev, sc, &daoffs));
+    EBIC_CUDA(to_device(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, dev, sc, &dacols));
+    EBIC_CUDA(to_device(arch_bitmaps, (size_t)n_arch * L.words, dev, sc, &dabm));
+  }
+  bool counts_host = false, bm_host = false, fit_host = false, ov_host = false;
+  uint32_t *dcounts = nullptr, *dbm = nullptr, *dov = nullptr, *dpad = nullptr,
+           *darch_counts = nullptr;
+  uint64_t *dfit = nullptr, *dshare = nullptr;
+  const size_t n_ov = (size_t)n_cand * n_arch;
+  const uint32_t stride = m->pair_stride;
+  EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
+  if (bitmaps)
+    EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm, &bm_host));
+  EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
+  if (n_arch > 0) {
+    if (overlaps) {
+      EBIC_CUDA(out_buffer(overlaps, n_ov, dev, sc, &dov, &ov_host));
+    } else {
+      EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), n_ov * sizeof(uint32_t)));
+    }
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dpad), (size_t)n_arch * stride * 4));
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&darch_counts), (size_t)n_arch * 4));
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dshare), (size_t)n_cand * 8));
+  }
+  {
+    Timed t(EBIC_TIMING_PREPARE, s);
+    FusedPrepareArgs pa;
+    pa.cols = dcols;
+    pa.offsets = doffs;
+    pa.n_cand = n_cand;
+    pa.acols = dacols;
+    pa.aoffsets = daoffs;
+    pa.n_arch = n_arch;
+    pa.check_arch = !host_a;
+    pa.ncols = L.cols;
+    pa.W = L.words;
+    pa.stride = stride;
+    pa.arch_src = dabm;
+    pa.arch_pad = dpad;
+    pa.counts = dcounts;
+    pa.overlaps = dov;
+    pa.arch_counts = darch_counts;
+    pa.share = dshare;
+    pa.err = err;
+    pa.status = m->status;
+    EBIC_CUDA(launch_fused_prepare(pa, m->num_sms, s));
+  }
+  {
+    Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
+    PairArgs p;
+    p.table = m->pairs;
+    p.stride = stride;
+    p.C = L.cols;
+    p.W = L.words;
+    p.cols = dcols;
+    p.offsets = doffs;
+    p.n_cand = n_cand;
+    p.counts = dcounts;
+    p.bitmaps = dbm;
+    p.arch = n_arch > 0 ? dpad : nullptr;
+    p.n_arch = n_arch;
+    p.score = overlaps ? nullptr : dshare;  // all members only when the caller reads them
+    p.overlaps = dov;
+    p.arch_counts = darch_counts;
+    p.err = err;
+    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms, s));
+  }
+  {
+    Timed t(EBIC_TIMING_FITNESS, s);
+    EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, darch_counts,
+                                    dshare, dfit, err, s));
+  }
+  if (counts_host || bm_host || fit_host || ov_host) {
+    if (counts_host)
+      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
+    if (bm_host)
+      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbm, (size_t)n_cand * L.words * 4,
+                                cudaMemcpyDeviceToHost, s));
+    if (fit_host)
+      EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
+    if (ov_host) EBIC_CUDA(cudaMemcpyAsync(overlaps, dov, n_ov * 4, cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_eval_fitness");
+  }
+  return EBIC_OK;
+}
+
 int ebic_matrix_status(ebic_matrix* m, void* stream) {
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
   DeviceGuard g(m->device);
@@ -768,11 +940,13 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs) {
 int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, uint64_t* bytes) {
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
   const Layout& L = m->L;
-  const uint64_t need = (uint64_t)L.cols * (uint64_t)L.cols * (uint64_t)L.words * 4ull;
+  const int64_t stride = pair_stride(L.words);
+  const uint64_t need = (uint64_t)L.cols * (uint64_t)L.cols * (uint64_t)stride * 4ull;
   if (bytes) *bytes = need;
   if (need > max_bytes)
     return fail(EBIC_ERR_UNSUPPORTED, "the pair table needs " + std::to_string(need) +
                                           " bytes, more than max_bytes");
+  if (stride > INT32_MAX) return fail(EBIC_ERR_UNSUPPORTED, "too many rows for a pair table");
   DeviceGuard g(m->device);
   if (m->pairs) return EBIC_OK;
   // the population of all ordered pairs (a, b), a != b, and of all singles (a), in table order
@@ -786,17 +960,20 @@ int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, ui
       if (b != a) cols.push_back((uint16_t)b);
       offs.push_back((uint32_t)cols.size());
     }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t* table = nullptr;
   uint32_t* counts = nullptr;
   cudaError_t e = cudaMalloc(&table, need);
   if (e == cudaSuccess) e = cudaMalloc(&counts, (size_t)n * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(table, 0, need, s);  // the rows' padding words
   if (e != cudaSuccess) {
     if (table) cudaFree(table);
+    if (counts) cudaFree(counts);
     return cuda_fail(e, "pair table allocation");
   }
-  int rc = ebic_eval_population(m, cols.data(), offs.data(), n, EBIC_EVAL_DIRECT, counts, table,
-                                stream);
-  cudaError_t e2 = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  int rc = eval_population_impl(m, cols.data(), offs.data(), n, EBIC_EVAL_DIRECT, counts, table,
+                                stride, stream);
+  cudaError_t e2 = cudaStreamSynchronize(s);
   cudaFree(counts);
   if (rc == EBIC_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "pair table build");
   if (rc != EBIC_OK) {
@@ -804,6 +981,7 @@ int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, ui
     return rc;
   }
   m->pairs = table;
+  m->pair_stride = (uint32_t)stride;
   m->pair_bytes = need;
   return EBIC_OK;
 }
@@ -814,6 +992,7 @@ int ebic_matrix_drop_pairs(ebic_matrix* m) {
     DeviceGuard g(m->device);
     EBIC_CUDA(cudaFree(m->pairs));
     m->pairs = nullptr;
+    m->pair_stride = 0;
     m->pair_bytes = 0;
   }
   return EBIC_OK;

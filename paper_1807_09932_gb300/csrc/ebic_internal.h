@@ -87,7 +87,8 @@ struct EvalArgs {
   const uint16_t* cand_cols = nullptr;     // device CSR
   const uint32_t* cand_offsets = nullptr;  // device CSR
   uint32_t* counts = nullptr;              // device, zeroed before the launch
-  uint32_t* bitmaps = nullptr;             // device [n_cand][W] or null
+  uint32_t* bitmaps = nullptr;             // device [n_cand][bitmap_stride] or null
+  int64_t bitmap_stride = 0;               // words between candidates' bitmaps (>= W)
   int32_t chunk_cols = 0;    // CC: candidate columns staged per chunk
   int32_t col_box = 0;       // columns per TMA box
   int32_t n_col_boxes = 0;
@@ -118,11 +119,65 @@ cudaError_t launch_eval_w16v4(const EvalConfig&, const CUtensorMap*, const EvalA
 cudaError_t launch_eval_w16v2(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 
-// ---- pair-table evaluation -----------------------------------------------------------------
-cudaError_t launch_pair_eval(const uint32_t* table, int32_t C, int64_t W, const uint16_t* cols,
-                             const uint32_t* offsets, uint32_t n_cand, bool negative,
-                             uint32_t* counts, uint32_t* bitmaps, const uint32_t* err,
-                             int num_sms, cudaStream_t s);
+// ---- pair-table evaluation (optionally with the archive overlaps fused in) -----------------
+constexpr int kPairRangeWords = 128;  // table and padded archive row strides are multiples
+constexpr int kPairMaxArch = 64;      // archive members the fused overlap pass takes
+// Row stride (words) of the pair table and of padded archive bitmaps for W-word bitmaps.
+inline int64_t pair_stride(int64_t words) {
+  return (words + kPairRangeWords - 1) / kPairRangeWords * kPairRangeWords;
+}
+struct PairArgs {
+  const uint32_t* table = nullptr;   // [C*C][stride], padding words zero
+  uint32_t stride = 0;               // row stride of table and arch (words)
+  int32_t C = 0;                     // matrix columns
+  int64_t W = 0;                     // words per bitmap
+  const uint16_t* cols = nullptr;    // device CSR candidate list (checked)
+  const uint32_t* offsets = nullptr;
+  uint32_t n_cand = 0;
+  uint32_t* counts = nullptr;        // [n_cand], zeroed before the launch
+  uint32_t* bitmaps = nullptr;       // [n_cand][W] or null
+  // fused overlaps: null arch = evaluation only
+  const uint32_t* arch = nullptr;    // [n_arch][stride], padding words zero
+  uint32_t n_arch = 0;               // <= kPairMaxArch
+  const uint64_t* score = nullptr;   // per candidate: members whose overlap is needed; null: all
+  uint32_t* overlaps = nullptr;      // [n_cand][n_arch], zeroed before the launch
+  uint32_t* arch_counts = nullptr;   // [n_arch], zeroed before the launch
+  const uint32_t* err = nullptr;     // non-zero: do nothing
+};
+cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStream_t s);
+
+// Preparation of the fused pass, one launch: checks the candidate list and (check_arch) the
+// archive list, zeroes counts, overlaps and archive counts, writes for every candidate the mask
+// of archive members sharing a column with it, and copies the archive bitmaps (row stride W)
+// into rows of `stride` words with zero padding. A failed check ORs kErrInvalid into *err and
+// *status.
+struct FusedPrepareArgs {
+  const uint16_t* cols = nullptr;
+  const uint32_t* offsets = nullptr;
+  uint32_t n_cand = 0;
+  const uint16_t* acols = nullptr;
+  const uint32_t* aoffsets = nullptr;
+  uint32_t n_arch = 0;               // <= kPairMaxArch
+  bool check_arch = true;
+  int32_t ncols = 0;
+  int64_t W = 0;
+  uint32_t stride = 0;
+  const uint32_t* arch_src = nullptr;  // [n_arch][W]
+  uint32_t* arch_pad = nullptr;        // [n_arch][stride]
+  uint32_t* counts = nullptr;
+  uint32_t* overlaps = nullptr;
+  uint32_t* arch_counts = nullptr;
+  uint64_t* share = nullptr;
+  uint32_t* err = nullptr;
+  uint32_t* status = nullptr;
+};
+cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStream_t s);
+// F_c from counts, overlaps and the share masks of the fused preparation.
+cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
+                                  const uint32_t* arch_offsets, uint32_t n_arch,
+                                  const uint32_t* overlaps, const uint32_t* arch_counts,
+                                  const uint64_t* share, uint64_t* fitness, const uint32_t* err,
+                                  cudaStream_t s);
 
 // ---- fitness -------------------------------------------------------------------------------
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(eval_threads<TS * VEC, NEG>(), 1)
       uint32_t cnt = 0;
       if constexpr (BITMAPS) {
         // lane j of transpose block b ends up with bitmap word (b*WIDTH + j%WIDTH)*WPG + j/WIDTH
-        uint32_t* out = a.bitmaps + (size_t)cand * (size_t)a.words;
+        uint32_t* out = a.bitmaps + (size_t)cand * (size_t)a.bitmap_stride;
 #pragma unroll
         for (int b = 0; b < (GT + WIDTH - 1) / WIDTH; ++b) {
           const uint32_t w = transpose32(pack_block<WIDTH, GT>(acc, b), trot, tsel);

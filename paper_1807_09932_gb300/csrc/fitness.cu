@@ -20,37 +20,155 @@
 namespace ebic {
 namespace {
 
-// Device-side check of up to two CSR candidate lists, and zeroing of one output, in one launch.
-// Thread i checks candidate i of each list: offsets[0] == 0, 1 <= L <= 64, the candidate ends
-// at or before offsets[n] (so its columns lie inside cols[0 .. offsets[n]), the caller's
-// buffer), and its columns are < ncols and distinct. Reads stay in bounds whatever the other
-// candidates' offsets are.
-__global__ void prepare_kernel(PrepareArgs a) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (a.zero && i < a.n_zero) a.zero[i] = 0u;
-  if (a.zero2 && i < a.n_zero2) a.zero2[i] = 0u;
+constexpr int kSetWords = (kMaxCols + 31) / 32;  // a column set as a bitset
+constexpr int kPrepWarps = 8;
+
+// Warp-cooperative check of candidate i of a CSR list of n: offsets[0] == 0, 1 <= L <= 64, the
+// candidate ends at or before offsets[n] (so its columns lie inside cols[0 .. offsets[n]), the
+// caller's buffer), its columns are < ncols and distinct. Columns are read only when the offsets
+// pass, so reads stay in bounds whatever the other candidates' offsets are. Leaves the
+// candidate's column set in `set` (the warp's own shared-memory bitset; empty when the offsets
+// fail). Returns true on every lane when the candidate is invalid.
+__device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
+                                     const uint32_t* __restrict__ offs, uint32_t n, uint32_t i,
+                                     int32_t ncols, uint32_t* set, int lane) {
+  const uint32_t total = offs[n];
+  const uint32_t lo = offs[i], hi = offs[i + 1];
+  const bool bad = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
+  const int nw = (ncols + 31) / 32;
+  for (int w = lane; w < nw; w += 32) set[w] = 0u;
+  __syncwarp();
+  bool b = false;
+  if (!bad) {
+    for (uint32_t j = lo + lane; j < hi; j += 32) {
+      const uint32_t c = cols[j];
+      if (c >= (uint32_t)ncols) {
+        b = true;
+        continue;
+      }
+      const uint32_t bit = 1u << (c & 31u);
+      b |= (atomicOr(&set[c >> 5], bit) & bit) != 0u;  // seen before: a repeated column
+    }
+  }
+  __syncwarp();
+  return __any_sync(0xFFFFFFFFu, bad || b);
+}
+
+__device__ __forceinline__ void report_invalid(bool bad, uint32_t* err, uint32_t* status) {
+  if (bad) {
+    atomicOr(err, kErrInvalid);
+    if (status) atomicOr(status, kErrInvalid);
+  }
+}
+
+// Device-side check of up to two CSR candidate lists (a warp per candidate) and zeroing of up to
+// two outputs, in one launch.
+__global__ void __launch_bounds__(kPrepWarps * 32) prepare_kernel(PrepareArgs a) {
+  __shared__ uint32_t sets[kPrepWarps][kSetWords];
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+  if (a.zero)
+    for (size_t i = tid; i < a.n_zero; i += nthreads) a.zero[i] = 0u;
+  if (a.zero2)
+    for (size_t i = tid; i < a.n_zero2; i += nthreads) a.zero2[i] = 0u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t gw = blockIdx.x * kPrepWarps + warp, nwarps = gridDim.x * kPrepWarps;
   bool bad = false;
 #pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    if (i >= a.n[l]) continue;
-    const uint32_t* offs = a.offsets[l];
-    const uint32_t total = offs[a.n[l]];
-    const uint32_t lo = offs[i], hi = offs[i + 1];
-    bool b = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
-    if (!b) {
-      const uint16_t* cols = a.cols[l];
-      for (uint32_t j = lo; j < hi; ++j) {
-        const uint16_t c = cols[j];
-        b |= c >= (uint32_t)a.ncols;
-        for (uint32_t t = lo; t < j; ++t) b |= cols[t] == c;
-      }
+  for (int l = 0; l < 2; ++l)
+    for (uint32_t i = gw; i < a.n[l]; i += nwarps)
+      bad |= check_candidate_warp(a.cols[l], a.offsets[l], a.n[l], i, a.ncols, sets[warp], lane);
+  if (lane == 0) report_invalid(bad, a.err, a.status);
+}
+
+// Preparation of the fused evaluation + overlap pass (see launch_fused_prepare).
+__global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPrepareArgs a) {
+  __shared__ uint32_t msets[kPairMaxArch][kSetWords];  // archive members' column sets
+  __shared__ uint32_t sets[kPrepWarps][kSetWords];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+  const uint32_t gw = blockIdx.x * kPrepWarps + warp, nwarps = gridDim.x * kPrepWarps;
+  const int nw = (a.ncols + 31) / 32;
+  const uint32_t na = a.n_arch;
+
+  // archive padded copy and zeroed archive counts
+  const size_t n_pad = (size_t)na * a.stride;
+  for (size_t i = tid; i < n_pad; i += nthreads) {
+    const size_t m = i / a.stride, w = i - m * a.stride;
+    a.arch_pad[i] = w < (size_t)a.W ? a.arch_src[m * (size_t)a.W + w] : 0u;
+  }
+  for (size_t i = tid; i < na; i += nthreads) a.arch_counts[i] = 0u;
+
+  // every block builds the members' column sets; a member whose offsets fail contributes none
+  // (the list is rejected below, and the pass that follows then does nothing)
+  for (int i = threadIdx.x; i < (int)na * kSetWords; i += blockDim.x) (&msets[0][0])[i] = 0u;
+  __syncthreads();
+  const uint32_t atotal = na ? a.aoffsets[na] : 0u;
+  for (uint32_t m = warp; m < na; m += kPrepWarps) {
+    const uint32_t lo = a.aoffsets[m], hi = a.aoffsets[m + 1];
+    if ((m == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > atotal) continue;
+    for (uint32_t j = lo + lane; j < hi; j += 32) {
+      const uint32_t c = a.acols[j];
+      if (c < (uint32_t)a.ncols) atomicOr(&msets[m][c >> 5], 1u << (c & 31u));
     }
-    bad |= b;
   }
-  if (bad) {
-    atomicOr(a.err, kErrInvalid);
-    if (a.status) atomicOr(a.status, kErrInvalid);
+  __syncthreads();
+
+  bool bad = false;
+  for (uint32_t i = gw; i < a.n_cand; i += nwarps) {
+    bad |= check_candidate_warp(a.cols, a.offsets, a.n_cand, i, a.ncols, sets[warp], lane);
+    uint32_t s0 = 0u, s1 = 0u;
+    for (int w = 0; w < nw; ++w) {
+      const uint32_t cw = sets[warp][w];
+      if ((uint32_t)lane < na) s0 |= cw & msets[lane][w];
+      if ((uint32_t)lane + 32u < na) s1 |= cw & msets[lane + 32][w];
+    }
+    const uint32_t lo_mask = __ballot_sync(0xFFFFFFFFu, s0 != 0u);
+    const uint32_t hi_mask = __ballot_sync(0xFFFFFFFFu, s1 != 0u);
+    if (lane == 0) {
+      if (a.share) a.share[i] = ((uint64_t)hi_mask << 32) | lo_mask;
+      a.counts[i] = 0u;
+    }
+    for (uint32_t m = lane; m < na; m += 32) a.overlaps[(size_t)i * na + m] = 0u;
+    __syncwarp();  // the set is rebuilt for the next candidate
   }
+  if (a.check_arch)
+    for (uint32_t i = gw; i < na; i += nwarps)
+      bad |= check_candidate_warp(a.acols, a.aoffsets, na, i, a.ncols, sets[warp], lane);
+  if (lane == 0) report_invalid(bad, a.err, a.status);
+}
+
+// F_c for the fused pass: a warp per candidate, a lane per archive member; the share masks of the
+// preparation stand for the column-set test.
+__global__ void __launch_bounds__(kPrepWarps * 32)
+    fused_finalize_kernel(const uint32_t* __restrict__ offsets, uint32_t n_cand,
+                          const uint32_t* __restrict__ counts,
+                          const uint32_t* __restrict__ aoffsets, uint32_t n_arch,
+                          const uint32_t* __restrict__ overlaps,
+                          const uint32_t* __restrict__ arch_counts,
+                          const uint64_t* __restrict__ share, uint64_t* __restrict__ fitness,
+                          const uint32_t* err) {
+  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t c = blockIdx.x * kPrepWarps + warp;
+  if (c >= n_cand) return;
+  const uint32_t L = offsets[c + 1] - offsets[c];
+  const uint32_t n = counts[c];
+  const uint32_t shift = (L < 33u ? L : 33u) - 1u;
+  const uint64_t qc = (uint64_t)n << shift;
+  const uint64_t sh = n_arch ? share[c] : 0ull;
+  uint32_t best = 0;
+  for (uint32_t m = lane; m < n_arch; m += 32) {
+    if (!((sh >> m) & 1ull)) continue;  // shares no column with the candidate
+    const uint32_t al = aoffsets[m + 1] - aoffsets[m];
+    const uint64_t qa = (uint64_t)arch_counts[m] << ((al < 33u ? al : 33u) - 1u);
+    if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
+    const uint32_t ov = overlaps[(size_t)c * n_arch + m];
+    best = ov > best ? ov : best;
+  }
+  best = __reduce_max_sync(0xFFFFFFFFu, best);
+  if (lane == 0) fitness[c] = (uint64_t)(n - best) << shift;
 }
 
 // Carry-save adder: a + b + c = 2 * carry + sum, bit by bit (two 3-input logic ops).
@@ -222,12 +340,40 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
 }  // namespace
 
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
-  size_t work = a.n_zero > a.n_zero2 ? a.n_zero : a.n_zero2;
-  for (int l = 0; l < 2; ++l) work = a.n[l] > work ? a.n[l] : work;
-  if (work == 0) return cudaSuccess;
-  const int T = 256;
+  size_t warps = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
+  const size_t zero = a.n_zero > a.n_zero2 ? a.n_zero : a.n_zero2;
+  size_t blocks = (warps + kPrepWarps - 1) / kPrepWarps;
+  const size_t zb = (zero + kPrepWarps * 32 * 4 - 1) / (kPrepWarps * 32 * 4);
+  blocks = blocks > zb ? blocks : zb;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks > 4096) blocks = 4096;  // grid-stride beyond
   count_launch();
-  prepare_kernel<<<(unsigned)((work + T - 1) / T), T, 0, s>>>(a);
+  prepare_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStream_t s) {
+  if (a.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
+  size_t blocks = (a.n_cand + kPrepWarps - 1) / kPrepWarps;
+  const size_t cb = ((size_t)a.n_arch * a.stride + kPrepWarps * 32 * 8 - 1) / (kPrepWarps * 32 * 8);
+  blocks = blocks > cb ? blocks : cb;
+  const size_t cap = (size_t)(num_sms > 0 ? num_sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  count_launch();
+  fused_prepare_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
+                                  const uint32_t* arch_offsets, uint32_t n_arch,
+                                  const uint32_t* overlaps, const uint32_t* arch_counts,
+                                  const uint64_t* share, uint64_t* fitness, const uint32_t* err,
+                                  cudaStream_t s) {
+  if (n_cand == 0) return cudaSuccess;
+  count_launch();
+  fused_finalize_kernel<<<(n_cand + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(
+      offsets, n_cand, counts, arch_offsets, n_arch, overlaps, arch_counts, share, fitness, err);
   return cudaGetLastError();
 }
 

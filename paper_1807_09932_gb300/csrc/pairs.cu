@@ -1,4 +1,5 @@
-// Pair-table evaluation: an exact alternative encoding of the same trend rule.
+// Pair-table evaluation: an exact alternative encoding of the same trend rule, with the archive
+// overlaps of the fitness optionally computed in the same pass.
 //
 // For a loaded matrix, the pair table holds one row bitmap per ordered column pair (a, b):
 //   T[a*C + b] = rows where a is not missing and code[b] >= code[a]   (a != b)
@@ -14,13 +15,27 @@
 //   L = 1:      T[c_1*C + c_1]
 // so a candidate costs one 32-bit AND per 32 rows per column, streamed from the table.
 //
-// Work order: items are (range of 4 row tiles of 32 words, group of 32 candidates), taken
+// Table rows are stored with a stride of ceil(W / 128) * 128 words whose padding words are zero,
+// so a lane reads four consecutive words with one 16-byte load and never tests a bound: a padding
+// word ANDs to zero and counts nothing.
+//
+// Work order: items are (range of 128 words = 4,096 rows, group of 32 candidates), taken
 // round-robin by a persistent grid in range-major order, so all CTAs work on the same few row
 // ranges at a time and the table rows of those ranges stay in L2 while every candidate reads
 // them; each table word comes from HBM about once per evaluation. Each warp takes one candidate
 // of its item: it reads the column list once (a lane per column), turns it into the table rows
 // of the consecutive pairs (a lane per pair), and walks the chain four pairs at a time, each
-// step issuing 16 independent 128-byte loads (one per pair and tile; 32 with negative trends).
+// step issuing four independent 512-byte warp loads (eight with negative trends).
+//
+// Fused overlaps (the fitness's o(c, a) = popcount(M_c & M_a), Methods, "Handling missing
+// values" and the archive rule of the fitness): the warp that has just built a candidate's words
+// of a range ANDs them with the archive members' words of the same range (archive rows padded to
+// the same stride) and adds the popcounts, so candidate bitmaps never go through HBM. Ranges
+// where the candidate matches no row are skipped, and so are archive members that the caller
+// does not need (those sharing no column with the candidate cannot penalise it). When the
+// candidate's non-zero words in the range number 32 or fewer (long chains match few rows), they
+// are first compacted to one per lane, so each member costs one gathered word and one popcount
+// per lane instead of four.
 #include "ebic_internal.h"
 
 namespace ebic {
@@ -28,116 +43,197 @@ namespace {
 
 constexpr int kPairThreads = 1024;
 constexpr int kPairWarps = kPairThreads / 32;
+constexpr int kRangeWords = kPairRangeWords;  // words per item: four per lane
 
-constexpr int kPairTiles = 4;  // 32-word row tiles per item (4,096 rows)
+__device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
 
-template <bool NEG, bool BITMAPS>
-__global__ void __launch_bounds__(kPairThreads, 1)
-    pair_eval_kernel(const uint32_t* __restrict__ table, int32_t C, int64_t W,
-                     const uint16_t* __restrict__ cols, const uint32_t* __restrict__ offsets,
-                     uint32_t n_cand, uint32_t* __restrict__ counts,
-                     uint32_t* __restrict__ bitmaps, const uint32_t* err) {
-  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;  // invalid input
+__device__ __forceinline__ uint32_t popc4(uint4 v) {
+  // carry-save: popc(a) + popc(b) + popc(c) = popc(a ^ b ^ c) + 2 popc(maj(a, b, c))
+  const uint32_t s = v.x ^ v.y ^ v.z;
+  const uint32_t c = (v.x & v.y) | (v.z & (v.x ^ v.y));
+  return __popc(s) + 2u * __popc(c) + __popc(v.w);
+}
+
+// The candidate's bitmap words 4*lane .. 4*lane+3 of the range whose first table word is `base`
+// (table + range*128): AND of its consecutive pairs' table rows, OR the reversed pairs' AND
+// with negative trends.
+template <bool NEG>
+__device__ __forceinline__ uint4 pair_chain(const PairArgs& p, uint32_t cand,
+                                            const uint32_t* base, int lane) {
+  const uint32_t o = p.offsets[cand];
+  const int L = (int)(p.offsets[cand + 1] - o);
+  const uint32_t C = (uint32_t)p.C;
+  // lane i holds column i and 32 + i, then the table rows of its consecutive pairs:
+  // fwd(i) = c_i*C + c_{i+1} (increasing), bwd(i) = c_{i+1}*C + c_i (decreasing)
+  const uint32_t c_lo = lane < L ? p.cols[o + lane] : 0u;
+  const uint32_t c_hi = lane + 32 < L ? p.cols[o + 32 + lane] : 0u;
+  const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
+  const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
+  const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
+  const uint32_t next_lo = lane == 31 ? h0 : n_lo;  // c_{i+1} for i = lane
+  const uint32_t fwd_lo = L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo;
+  const uint32_t fwd_hi = c_hi * C + n_hi;
+  const uint32_t bwd_lo = next_lo * C + c_lo, bwd_hi = n_hi * C + c_hi;
+  const int n_terms = L == 1 ? 1 : L - 1;
+  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  uint4 x = ones, y = ones;
+  for (int i0 = 0; i0 < n_terms; i0 += 4) {
+    uint4 v[4], u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k;
+      v[k] = u[k] = ones;
+      if (i < n_terms) {  // warp-uniform
+        const uint32_t pf = __shfl_sync(0xFFFFFFFFu, i < 32 ? fwd_lo : fwd_hi, i & 31);
+        v[k] = __ldg(reinterpret_cast<const uint4*>(base + (uint64_t)pf * p.stride));
+        if (NEG && L > 1) {
+          const uint32_t pb = __shfl_sync(0xFFFFFFFFu, i < 32 ? bwd_lo : bwd_hi, i & 31);
+          u[k] = __ldg(reinterpret_cast<const uint4*>(base + (uint64_t)pb * p.stride));
+        }
+      }
+    }
+    x = and4(x, and4(and4(v[0], v[1]), and4(v[2], v[3])));
+    if (NEG) y = and4(y, and4(and4(u[0], u[1]), and4(u[2], u[3])));
+  }
+  if (NEG && L > 1) x = make_uint4(x.x | y.x, x.y | y.y, x.z | y.z, x.w | y.w);
+  return x;
+}
+
+template <bool NEG, bool BITMAPS, bool OVERLAP>
+__global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairArgs p) {
+  // per warp: its 128 words for the coalesced bitmap store, or its compacted non-zero words
+  __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
+  if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) return;  // invalid input
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t span = 32 * kPairTiles;  // words per item
-  const int64_t n_ranges = (W + span - 1) / span;
-  const int64_t n_groups = (n_cand + kPairWarps - 1) / kPairWarps;
+  const int64_t n_ranges = (p.W + kRangeWords - 1) / kRangeWords;
+  const int64_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
   const int64_t n_items = n_ranges * n_groups;
+  const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
+  const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int64_t range = it / n_groups, grp = it - range * n_groups;
+    const uint64_t rword = (uint64_t)range * kRangeWords;  // first word of the range
+    if (OVERLAP && grp == 0) {  // the archive members' own row counts, once per range
+      for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
+        const uint4 av = __ldg(reinterpret_cast<const uint4*>(
+            p.arch + (uint64_t)a * p.stride + rword + 4 * lane));
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, popc4(av));
+        if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
+      }
+    }
     const uint32_t cand = (uint32_t)(grp * kPairWarps + warp);
-    if (cand >= n_cand) continue;  // warp-uniform
-    const uint32_t o = offsets[cand];
-    const int L = (int)(offsets[cand + 1] - o);
-    // lane i holds column i and 32 + i, then the table rows of its consecutive pairs:
-    // fwd(i) = c_i*C + c_{i+1} (increasing), bwd(i) = c_{i+1}*C + c_i (decreasing)
-    const uint32_t c_lo = lane < L ? cols[o + lane] : 0u;
-    const uint32_t c_hi = lane + 32 < L ? cols[o + 32 + lane] : 0u;
-    const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
-    const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
-    const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
-    const uint32_t next_lo = lane == 31 ? h0 : n_lo;   // c_{i+1} for i = lane
-    const uint32_t fwd_lo = L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo;
-    const uint32_t fwd_hi = c_hi * C + n_hi;
-    const uint32_t bwd_lo = next_lo * C + c_lo, bwd_hi = n_hi * C + c_hi;
-    const int n_terms = L == 1 ? 1 : L - 1;
-    const int64_t w0 = range * span + lane;
-    uint32_t x[kPairTiles], y[kPairTiles];
+    if (cand >= p.n_cand) continue;  // warp-uniform
+    const uint4 x = pair_chain<NEG>(p, cand, p.table + rword + 4 * lane, lane);
+    const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, popc4(x));
+    if (lane == 0 && cnt) atomicAdd(&p.counts[cand], cnt);
+    if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
+      uint32_t* st = stage[warp];
+      *reinterpret_cast<uint4*>(st + 4 * lane) = x;
+      __syncwarp();
+      uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
 #pragma unroll
-    for (int j = 0; j < kPairTiles; ++j) x[j] = y[j] = 0xFFFFFFFFu;
-    for (int i0 = 0; i0 < n_terms; i0 += 4) {
-      uint32_t v[4][kPairTiles], u[4][kPairTiles];
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t w = rword + 32 * j + lane;
+        if (w < (uint64_t)p.W) out[w] = st[32 * j + lane];
+      }
+      __syncwarp();
+    }
+    if constexpr (OVERLAP) {
+      if (cnt == 0) continue;  // warp-uniform: nothing of this range overlaps anything
+      uint64_t members = p.score ? p.score[cand] & all_members : all_members;
+      if (members == 0) continue;
+      uint32_t* ov = p.overlaps + (uint64_t)cand * n_arch;
+      const uint32_t* abase = p.arch + rword;
+      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, x.x != 0u);
+      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, x.y != 0u);
+      const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, x.z != 0u);
+      const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, x.w != 0u);
+      const int n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
+      const int nz = n0 + n1 + n2 + __popc(b3);
+      if (nz <= 32) {
+        // compact the non-zero words: lane i takes the i-th one (value and word offset)
+        uint32_t* sv = stage[warp];
+        uint32_t* si = stage[warp] + 32;
+        const uint32_t lt = (1u << lane) - 1u;
+        if (x.x) { const int q = __popc(b0 & lt); sv[q] = x.x; si[q] = 4 * lane; }
+        if (x.y) { const int q = n0 + __popc(b1 & lt); sv[q] = x.y; si[q] = 4 * lane + 1; }
+        if (x.z) { const int q = n0 + n1 + __popc(b2 & lt); sv[q] = x.z; si[q] = 4 * lane + 2; }
+        if (x.w) {
+          const int q = n0 + n1 + n2 + __popc(b3 & lt);
+          sv[q] = x.w;
+          si[q] = 4 * lane + 3;
+        }
+        __syncwarp();
+        const uint32_t mv = lane < nz ? sv[lane] : 0u;
+        const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
+        __syncwarp();
+        while (members) {  // four members per round, their loads in flight together
+          int a[4];
+          uint32_t v[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int i = i0 + k;
+          for (int k = 0; k < 4; ++k) {
+            a[k] = members ? __ffsll((long long)members) - 1 : -1;
+            members &= members - 1ull;
+          }
 #pragma unroll
-        for (int j = 0; j < kPairTiles; ++j) v[k][j] = u[k][j] = 0xFFFFFFFFu;
-        if (i < n_terms) {  // warp-uniform
-          const uint32_t pf = i < 32 ? __shfl_sync(0xFFFFFFFFu, fwd_lo, i)
-                                     : __shfl_sync(0xFFFFFFFFu, fwd_hi, i - 32);
-          const uint32_t* rf = table + (size_t)pf * W;
-          uint32_t pb = 0;
-          if (NEG && L > 1)
-            pb = i < 32 ? __shfl_sync(0xFFFFFFFFu, bwd_lo, i)
-                        : __shfl_sync(0xFFFFFFFFu, bwd_hi, i - 32);
-          const uint32_t* rb = table + (size_t)pb * W;
+          for (int k = 0; k < 4; ++k)
+            v[k] = a[k] >= 0 ? __ldg(ab + (uint64_t)a[k] * p.stride) : 0u;
 #pragma unroll
-          for (int j = 0; j < kPairTiles; ++j) {
-            const int64_t w = w0 + 32 * j;
-            if (w < W) {
-              v[k][j] = __ldg(rf + w);
-              if (NEG && L > 1) u[k][j] = __ldg(rb + w);
-            }
+          for (int k = 0; k < 4; ++k) {
+            if (a[k] < 0) break;
+            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & v[k]));
+            if (lane == 0 && r) atomicAdd(&ov[a[k]], r);
+          }
+        }
+      } else {
+        const uint32_t* ab = abase + 4 * lane;
+        while (members) {
+          int a[4];
+          uint4 v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            a[k] = members ? __ffsll((long long)members) - 1 : -1;
+            members &= members - 1ull;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            v[k] = a[k] >= 0
+                       ? __ldg(reinterpret_cast<const uint4*>(ab + (uint64_t)a[k] * p.stride))
+                       : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (a[k] < 0) break;
+            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, popc4(and4(x, v[k])));
+            if (lane == 0 && r) atomicAdd(&ov[a[k]], r);
           }
         }
       }
-#pragma unroll
-      for (int j = 0; j < kPairTiles; ++j) {
-        x[j] &= (v[0][j] & v[1][j]) & (v[2][j] & v[3][j]);
-        if (NEG) y[j] &= (u[0][j] & u[1][j]) & (u[2][j] & u[3][j]);
-      }
     }
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int j = 0; j < kPairTiles; ++j) {
-      const int64_t w = w0 + 32 * j;
-      uint32_t r = x[j];
-      if (NEG && L > 1) r |= y[j];
-      if (w < W) {
-        if (BITMAPS) bitmaps[(size_t)cand * W + w] = r;
-        cnt += __popc(r);
-      }
-    }
-    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    if (lane == 0 && cnt) atomicAdd(&counts[cand], cnt);
   }
+}
+
+template <bool NEG, bool BITMAPS>
+cudaError_t launch_variant(const PairArgs& p, int grid, cudaStream_t s) {
+  if (p.arch)
+    pair_eval_kernel<NEG, BITMAPS, true><<<grid, kPairThreads, 0, s>>>(p);
+  else
+    pair_eval_kernel<NEG, BITMAPS, false><<<grid, kPairThreads, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_pair_eval(const uint32_t* table, int32_t C, int64_t W, const uint16_t* cols,
-                             const uint32_t* offsets, uint32_t n_cand, bool negative,
-                             uint32_t* counts, uint32_t* bitmaps, const uint32_t* err,
-                             int num_sms, cudaStream_t s) {
-  if (n_cand == 0) return cudaSuccess;
-  const int grid = num_sms;
+cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStream_t s) {
+  if (p.n_cand == 0) return cudaSuccess;
+  if (p.arch && p.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
+  if (p.stride % kRangeWords != 0 || (int64_t)p.stride < p.W) return cudaErrorInvalidValue;
   count_launch();
-  if (negative) {
-    if (bitmaps)
-      pair_eval_kernel<true, true><<<grid, kPairThreads, 0, s>>>(table, C, W, cols, offsets,
-                                                                  n_cand, counts, bitmaps, err);
-    else
-      pair_eval_kernel<true, false><<<grid, kPairThreads, 0, s>>>(table, C, W, cols, offsets,
-                                                                   n_cand, counts, bitmaps, err);
-  } else {
-    if (bitmaps)
-      pair_eval_kernel<false, true><<<grid, kPairThreads, 0, s>>>(table, C, W, cols, offsets,
-                                                                   n_cand, counts, bitmaps, err);
-    else
-      pair_eval_kernel<false, false><<<grid, kPairThreads, 0, s>>>(table, C, W, cols, offsets,
-                                                                    n_cand, counts, bitmaps, err);
-  }
-  return cudaGetLastError();
+  const bool bm = p.bitmaps != nullptr;
+  if (negative)
+    return bm ? launch_variant<true, true>(p, grid, s) : launch_variant<true, false>(p, grid, s);
+  return bm ? launch_variant<false, true>(p, grid, s) : launch_variant<false, false>(p, grid, s);
 }
 
 }  // namespace ebic

@@ -57,6 +57,8 @@ _lib_eval = _sig("ebic_eval_population", [_P, _P, _P, _U32, _U32, _P, _P, _P])
 _lib_eval_noalloc = _sig("ebic_eval_population_noalloc", [_P, _P, _P, _U32, _U32, _P, _P, _P])
 _lib_fitness = _sig("ebic_fitness", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32, _U32, _P, _P,
                                      _P])
+_lib_eval_fitness = _sig("ebic_eval_fitness", [_P, _P, _P, _U32, _U32, _P, _P, _P, _U32, _P,
+                                               _P, _P, _P, _P])
 _lib_status = _sig("ebic_matrix_status", [_P, _P])
 _lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
 _lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
@@ -214,6 +216,13 @@ def ebic_fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offs
     return _lib_fitness(h, _ptr(cols), _ptr(offsets), n_cand, _ptr(counts), _ptr(bitmaps),
                         _ptr(arch_cols), _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, flags,
                         _ptr(fitness), _ptr(overlaps), _stream(stream))
+
+
+def ebic_eval_fitness(h, cols, offsets, n_cand, flags, arch_cols, arch_offsets, arch_bitmaps,
+                      n_arch, counts, bitmaps, fitness, overlaps, stream=None):
+    return _lib_eval_fitness(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(arch_cols),
+                             _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, _ptr(counts),
+                             _ptr(bitmaps), _ptr(fitness), _ptr(overlaps), _stream(stream))
 
 
 def ebic_matrix_status(h, stream=None):
@@ -440,3 +449,21 @@ def fitness(m: Matrix, cols, offsets, counts, bitmaps, arch_cols, arch_offsets, 
                       stream)
     _check(rc, "ebic_fitness")
     return fitness_out, overlaps
+
+
+def eval_fitness(m: Matrix, cols, offsets, arch_cols, arch_offsets, arch_bitmaps, *,
+                 negative=False, direct=False, want_bitmaps=False, want_overlaps=False,
+                 stream=None):
+    """One generation's scoring (ebic_eval_fitness): counts, bitmaps or None, fitness, overlaps
+    or None, as host numpy arrays."""
+    n = len(offsets) - 1
+    k = len(arch_offsets) - 1
+    counts = np.zeros(n, dtype=np.uint32)
+    bitmaps = np.zeros((n, m.words), dtype=np.uint32) if want_bitmaps else None
+    fit = np.zeros(n, dtype=np.uint64)
+    overlaps = np.zeros((n, k), dtype=np.uint32) if want_overlaps and k else None
+    flags = (EBIC_NEGATIVE_TRENDS if negative else 0) | (EBIC_EVAL_DIRECT if direct else 0)
+    rc = ebic_eval_fitness(m.handle, cols, offsets, n, flags, arch_cols, arch_offsets,
+                           arch_bitmaps, k, counts, bitmaps, fit, overlaps, stream)
+    _check(rc, "ebic_eval_fitness")
+    return counts, bitmaps, fit, overlaps
