@@ -794,23 +794,20 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(to_device(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, dev, sc, &dacols));
     EBIC_CUDA(to_device(arch_bitmaps, (size_t)n_arch * L.words, dev, sc, &dabm));
   }
-  bool counts_host = false, bm_host = false, fit_host = false, ov_host = false;
+  bool counts_host = false, bm_host = false, fit_host = false;
   uint32_t *dcounts = nullptr, *dbm = nullptr, *dov = nullptr, *dpad = nullptr,
            *darch_counts = nullptr;
   uint64_t *dfit = nullptr, *dshare = nullptr;
-  const size_t n_ov = (size_t)n_cand * n_arch;
+  // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
+  const uint32_t ov_stride = (n_arch + 1u) & ~1u;
   const uint32_t stride = m->pair_stride;
   EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
   if (bitmaps)
     EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm, &bm_host));
   EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
   if (n_arch > 0) {
-    if (overlaps) {
-      EBIC_CUDA(out_buffer(overlaps, n_ov, dev, sc, &dov, &ov_host));
-    } else {
-      EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), n_ov * sizeof(uint32_t)));
-    }
-    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dpad), (size_t)n_arch * stride * 4));
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), (size_t)n_cand * ov_stride * 4));
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dpad), (size_t)ov_stride * stride * 4));
     EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&darch_counts), (size_t)n_arch * 4));
     EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dshare), (size_t)n_cand * 8));
   }
@@ -831,6 +828,7 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     pa.arch_pad = dpad;
     pa.counts = dcounts;
     pa.overlaps = dov;
+    pa.ov_stride = ov_stride;
     pa.arch_counts = darch_counts;
     pa.share = dshare;
     pa.err = err;
@@ -853,15 +851,21 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.n_arch = n_arch;
     p.score = overlaps ? nullptr : dshare;  // all members only when the caller reads them
     p.overlaps = dov;
+    p.ov_stride = ov_stride;
     p.arch_counts = darch_counts;
     p.err = err;
     EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms, s));
   }
   {
     Timed t(EBIC_TIMING_FITNESS, s);
-    EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, darch_counts,
-                                    dshare, dfit, err, s));
+    EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, ov_stride,
+                                    darch_counts, dshare, dfit, err, s));
   }
+  const bool ov_host = overlaps && n_arch > 0 && !on_device(overlaps, dev);
+  if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout
+    EBIC_CUDA(cudaMemcpy2DAsync(overlaps, (size_t)n_arch * 4, dov, (size_t)ov_stride * 4,
+                                (size_t)n_arch * 4, n_cand,
+                                ov_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   if (counts_host || bm_host || fit_host || ov_host) {
     if (counts_host)
       EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
@@ -870,7 +874,6 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
                                 cudaMemcpyDeviceToHost, s));
     if (fit_host)
       EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
-    if (ov_host) EBIC_CUDA(cudaMemcpyAsync(overlaps, dov, n_ov * 4, cudaMemcpyDeviceToHost, s));
     uint32_t bits = 0;
     EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
     EBIC_CUDA(cudaStreamSynchronize(s));
@@ -946,7 +949,8 @@ int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, ui
   if (need > max_bytes)
     return fail(EBIC_ERR_UNSUPPORTED, "the pair table needs " + std::to_string(need) +
                                           " bytes, more than max_bytes");
-  if (stride > INT32_MAX) return fail(EBIC_ERR_UNSUPPORTED, "too many rows for a pair table");
+  if (need / 4ull > 0xFFFFFFFFull)  // table rows are addressed with 32-bit word offsets
+    return fail(EBIC_ERR_UNSUPPORTED, "the pair table would exceed 2^32 words");
   DeviceGuard g(m->device);
   if (m->pairs) return EBIC_OK;
   // the population of all ordered pairs (a, b), a != b, and of all singles (a), in table order

@@ -137,10 +137,11 @@ struct PairArgs {
   uint32_t* counts = nullptr;        // [n_cand], zeroed before the launch
   uint32_t* bitmaps = nullptr;       // [n_cand][W] or null
   // fused overlaps: null arch = evaluation only
-  const uint32_t* arch = nullptr;    // [n_arch][stride], padding words zero
+  const uint32_t* arch = nullptr;    // [n_arch rounded up to even][stride], padding words zero
   uint32_t n_arch = 0;               // <= kPairMaxArch
   const uint64_t* score = nullptr;   // per candidate: members whose overlap is needed; null: all
-  uint32_t* overlaps = nullptr;      // [n_cand][n_arch], zeroed before the launch
+  uint32_t* overlaps = nullptr;      // [n_cand][ov_stride], zeroed before the launch
+  uint32_t ov_stride = 0;            // n_arch rounded up to even (pairs of counters, 8-byte aligned)
   uint32_t* arch_counts = nullptr;   // [n_arch], zeroed before the launch
   const uint32_t* err = nullptr;     // non-zero: do nothing
 };
@@ -163,9 +164,10 @@ struct FusedPrepareArgs {
   int64_t W = 0;
   uint32_t stride = 0;
   const uint32_t* arch_src = nullptr;  // [n_arch][W]
-  uint32_t* arch_pad = nullptr;        // [n_arch][stride]
+  uint32_t* arch_pad = nullptr;        // [n_arch rounded up to even][stride]
   uint32_t* counts = nullptr;
-  uint32_t* overlaps = nullptr;
+  uint32_t* overlaps = nullptr;        // [n_cand][ov_stride]
+  uint32_t ov_stride = 0;
   uint32_t* arch_counts = nullptr;
   uint64_t* share = nullptr;
   uint32_t* err = nullptr;
@@ -175,9 +177,9 @@ cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStr
 // F_c from counts, overlaps and the share masks of the fused preparation.
 cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
                                   const uint32_t* arch_offsets, uint32_t n_arch,
-                                  const uint32_t* overlaps, const uint32_t* arch_counts,
-                                  const uint64_t* share, uint64_t* fitness, const uint32_t* err,
-                                  cudaStream_t s);
+                                  const uint32_t* overlaps, uint32_t ov_stride,
+                                  const uint32_t* arch_counts, const uint64_t* share,
+                                  uint64_t* fitness, const uint32_t* err, cudaStream_t s);
 
 // ---- fitness -------------------------------------------------------------------------------
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,

@@ -93,10 +93,10 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
   const uint32_t na = a.n_arch;
 
   // archive padded copy and zeroed archive counts
-  const size_t n_pad = (size_t)na * a.stride;
+  const size_t n_pad = (size_t)((na + 1u) & ~1u) * a.stride;  // an even number of rows
   for (size_t i = tid; i < n_pad; i += nthreads) {
     const size_t m = i / a.stride, w = i - m * a.stride;
-    a.arch_pad[i] = w < (size_t)a.W ? a.arch_src[m * (size_t)a.W + w] : 0u;
+    a.arch_pad[i] = m < na && w < (size_t)a.W ? a.arch_src[m * (size_t)a.W + w] : 0u;
   }
   for (size_t i = tid; i < na; i += nthreads) a.arch_counts[i] = 0u;
 
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
       if (a.share) a.share[i] = ((uint64_t)hi_mask << 32) | lo_mask;
       a.counts[i] = 0u;
     }
-    for (uint32_t m = lane; m < na; m += 32) a.overlaps[(size_t)i * na + m] = 0u;
+    for (uint32_t m = lane; m < a.ov_stride; m += 32) a.overlaps[(size_t)i * a.ov_stride + m] = 0u;
     __syncwarp();  // the set is rebuilt for the next candidate
   }
   if (a.check_arch)
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     fused_finalize_kernel(const uint32_t* __restrict__ offsets, uint32_t n_cand,
                           const uint32_t* __restrict__ counts,
                           const uint32_t* __restrict__ aoffsets, uint32_t n_arch,
-                          const uint32_t* __restrict__ overlaps,
+                          const uint32_t* __restrict__ overlaps, uint32_t ov_stride,
                           const uint32_t* __restrict__ arch_counts,
                           const uint64_t* __restrict__ share, uint64_t* __restrict__ fitness,
                           const uint32_t* err) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
     const uint32_t al = aoffsets[m + 1] - aoffsets[m];
     const uint64_t qa = (uint64_t)arch_counts[m] << ((al < 33u ? al : 33u) - 1u);
     if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
-    const uint32_t ov = overlaps[(size_t)c * n_arch + m];
+    const uint32_t ov = overlaps[(size_t)c * ov_stride + m];
     best = ov > best ? ov : best;
   }
   best = __reduce_max_sync(0xFFFFFFFFu, best);
@@ -355,7 +355,8 @@ cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
 cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStream_t s) {
   if (a.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
   size_t blocks = (a.n_cand + kPrepWarps - 1) / kPrepWarps;
-  const size_t cb = ((size_t)a.n_arch * a.stride + kPrepWarps * 32 * 8 - 1) / (kPrepWarps * 32 * 8);
+  const size_t cb = ((size_t)(a.n_arch + 1) * a.stride + kPrepWarps * 32 * 8 - 1) /
+                    (kPrepWarps * 32 * 8);
   blocks = blocks > cb ? blocks : cb;
   const size_t cap = (size_t)(num_sms > 0 ? num_sms : 1) * 8;
   if (blocks > cap) blocks = cap;
@@ -367,13 +368,14 @@ cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStr
 
 cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
                                   const uint32_t* arch_offsets, uint32_t n_arch,
-                                  const uint32_t* overlaps, const uint32_t* arch_counts,
-                                  const uint64_t* share, uint64_t* fitness, const uint32_t* err,
-                                  cudaStream_t s) {
+                                  const uint32_t* overlaps, uint32_t ov_stride,
+                                  const uint32_t* arch_counts, const uint64_t* share,
+                                  uint64_t* fitness, const uint32_t* err, cudaStream_t s) {
   if (n_cand == 0) return cudaSuccess;
   count_launch();
   fused_finalize_kernel<<<(n_cand + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(
-      offsets, n_cand, counts, arch_offsets, n_arch, overlaps, arch_counts, share, fitness, err);
+      offsets, n_cand, counts, arch_offsets, n_arch, overlaps, ov_stride, arch_counts, share,
+      fitness, err);
   return cudaGetLastError();
 }
 

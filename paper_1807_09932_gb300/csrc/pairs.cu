@@ -58,47 +58,67 @@ __device__ __forceinline__ uint32_t popc4(uint4 v) {
 
 // The candidate's bitmap words 4*lane .. 4*lane+3 of the range whose first table word is `base`
 // (table + range*128): AND of its consecutive pairs' table rows, OR the reversed pairs' AND
-// with negative trends.
+// with negative trends. The walk stops early once every word of the warp is zero (long chains
+// match no row of most ranges).
 template <bool NEG>
 __device__ __forceinline__ uint4 pair_chain(const PairArgs& p, uint32_t cand,
                                             const uint32_t* base, int lane) {
   const uint32_t o = p.offsets[cand];
   const int L = (int)(p.offsets[cand + 1] - o);
-  const uint32_t C = (uint32_t)p.C;
-  // lane i holds column i and 32 + i, then the table rows of its consecutive pairs:
-  // fwd(i) = c_i*C + c_{i+1} (increasing), bwd(i) = c_{i+1}*C + c_i (decreasing)
+  const uint32_t C = (uint32_t)p.C, S = p.stride;
+  // lane i holds column i and 32 + i, then the table-row offsets (words) of its consecutive
+  // pairs: fwd(i) = (c_i*C + c_{i+1}) * S (increasing), bwd(i) = (c_{i+1}*C + c_i) * S
   const uint32_t c_lo = lane < L ? p.cols[o + lane] : 0u;
   const uint32_t c_hi = lane + 32 < L ? p.cols[o + 32 + lane] : 0u;
   const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
   const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
   const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
   const uint32_t next_lo = lane == 31 ? h0 : n_lo;  // c_{i+1} for i = lane
-  const uint32_t fwd_lo = L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo;
-  const uint32_t fwd_hi = c_hi * C + n_hi;
-  const uint32_t bwd_lo = next_lo * C + c_lo, bwd_hi = n_hi * C + c_hi;
+  const uint32_t fwd_lo = (L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo) * S;
+  const uint32_t fwd_hi = (c_hi * C + n_hi) * S;
+  const uint32_t bwd_lo = (next_lo * C + c_lo) * S, bwd_hi = (n_hi * C + c_hi) * S;
   const int n_terms = L == 1 ? 1 : L - 1;
+  const bool two = NEG && L > 1;  // warp-uniform
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
   uint4 x = ones, y = ones;
-  for (int i0 = 0; i0 < n_terms; i0 += 4) {
-    uint4 v[4], u[4];
+  // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
+  auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
+    for (int i0 = t0; i0 < t1; i0 += 4) {
+      uint4 v[4], u[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = i0 + k;
-      v[k] = u[k] = ones;
-      if (i < n_terms) {  // warp-uniform
-        const uint32_t pf = __shfl_sync(0xFFFFFFFFu, i < 32 ? fwd_lo : fwd_hi, i & 31);
-        v[k] = __ldg(reinterpret_cast<const uint4*>(base + (uint64_t)pf * p.stride));
-        if (NEG && L > 1) {
-          const uint32_t pb = __shfl_sync(0xFFFFFFFFu, i < 32 ? bwd_lo : bwd_hi, i & 31);
-          u[k] = __ldg(reinterpret_cast<const uint4*>(base + (uint64_t)pb * p.stride));
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k;
+        v[k] = u[k] = ones;
+        if (i < t1) {  // warp-uniform
+          v[k] = __ldg(reinterpret_cast<const uint4*>(
+              base + __shfl_sync(0xFFFFFFFFu, offf, i & 31)));
+          if (two)
+            u[k] = __ldg(reinterpret_cast<const uint4*>(
+                base + __shfl_sync(0xFFFFFFFFu, offb, i & 31)));
         }
       }
+      x = and4(x, and4(and4(v[0], v[1]), and4(v[2], v[3])));
+      uint32_t any = x.x | x.y | x.z | x.w;
+      if (NEG) {
+        y = and4(y, and4(and4(u[0], u[1]), and4(u[2], u[3])));
+        if (two) any |= y.x | y.y | y.z | y.w;
+      }
+      if (!__any_sync(0xFFFFFFFFu, any != 0u)) return false;  // all zero from here on
     }
-    x = and4(x, and4(and4(v[0], v[1]), and4(v[2], v[3])));
-    if (NEG) y = and4(y, and4(and4(u[0], u[1]), and4(u[2], u[3])));
-  }
-  if (NEG && L > 1) x = make_uint4(x.x | y.x, x.y | y.y, x.z | y.z, x.w | y.w);
+    return true;
+  };
+  if (walk(fwd_lo, bwd_lo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
+    walk(fwd_hi, bwd_hi, 32, n_terms);
+  if (two) x = make_uint4(x.x | y.x, x.y | y.y, x.z | y.z, x.w | y.w);
   return x;
+}
+
+// Adds a packed pair of warp sums (member 2k in the low 16 bits, 2k+1 in the high 16 bits) to
+// the two adjacent 32-bit overlap counters of the pair with one 64-bit atomic (no carry crosses
+// from the low counter: each total is at most the row count, below 2^32).
+__device__ __forceinline__ void add_pair(unsigned long long* ov2, int k, uint32_t r, int lane) {
+  if (lane == 0 && r)
+    atomicAdd(&ov2[k], (unsigned long long)(r & 0xFFFFu) | ((unsigned long long)(r >> 16) << 32));
 }
 
 template <bool NEG, bool BITMAPS, bool OVERLAP>
@@ -107,13 +127,17 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
   if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) return;  // invalid input
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n_ranges = (p.W + kRangeWords - 1) / kRangeWords;
-  const int64_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
-  const int64_t n_items = n_ranges * n_groups;
+  const uint32_t n_ranges = (uint32_t)((p.W + kRangeWords - 1) / kRangeWords);
+  const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
+  const uint64_t n_items = (uint64_t)n_ranges * n_groups;
   const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
+  const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
-  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int64_t range = it / n_groups, grp = it - range * n_groups;
+  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division
+  const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
+  uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
+  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, range += d_range, grp += d_grp,
+                range += grp >= n_groups ? 1u : 0u, grp -= grp >= n_groups ? n_groups : 0u) {
     const uint64_t rword = (uint64_t)range * kRangeWords;  // first word of the range
     if (OVERLAP && grp == 0) {  // the archive members' own row counts, once per range
       for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
@@ -123,7 +147,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
         if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
       }
     }
-    const uint32_t cand = (uint32_t)(grp * kPairWarps + warp);
+    const uint32_t cand = grp * kPairWarps + warp;
     if (cand >= p.n_cand) continue;  // warp-uniform
     const uint4 x = pair_chain<NEG>(p, cand, p.table + rword + 4 * lane, lane);
     const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, popc4(x));
@@ -142,10 +166,12 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
     }
     if constexpr (OVERLAP) {
       if (cnt == 0) continue;  // warp-uniform: nothing of this range overlaps anything
-      uint64_t members = p.score ? p.score[cand] & all_members : all_members;
+      const uint64_t members = p.score ? p.score[cand] & all_members : all_members;
       if (members == 0) continue;
-      uint32_t* ov = p.overlaps + (uint64_t)cand * n_arch;
+      unsigned long long* ov2 =
+          reinterpret_cast<unsigned long long*>(p.overlaps + (uint64_t)cand * p.ov_stride);
       const uint32_t* abase = p.arch + rword;
+      const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
       const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, x.x != 0u);
       const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, x.y != 0u);
       const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, x.z != 0u);
@@ -166,48 +192,40 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
           si[q] = 4 * lane + 3;
         }
         __syncwarp();
-        const uint32_t mv = lane < nz ? sv[lane] : 0u;
-        const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
-        __syncwarp();
-        while (members) {  // four members per round, their loads in flight together
-          int a[4];
-          uint32_t v[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            a[k] = members ? __ffsll((long long)members) - 1 : -1;
-            members &= members - 1ull;
+        if (nz <= 16) {
+          // each half-warp holds the same (up to) 16 words; the low half takes member 2k and
+          // the high half member 2k+1 of each pair, one word and one popcount per lane
+          const int src = lane & 15;
+          const uint32_t mv = src < nz ? sv[src] : 0u;
+          const uint32_t* ab = abase + (src < nz ? si[src] : 0u) + (lane >= 16 ? p.stride : 0u);
+          const int sh = lane >= 16 ? 16 : 0;
+          __syncwarp();
+          for (int k = 0; k < n_pairs; ++k, ab += S2) {
+            if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
+            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & __ldg(ab)) << sh);
+            add_pair(ov2, k, r, lane);
           }
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            v[k] = a[k] >= 0 ? __ldg(ab + (uint64_t)a[k] * p.stride) : 0u;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (a[k] < 0) break;
-            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & v[k]));
-            if (lane == 0 && r) atomicAdd(&ov[a[k]], r);
+        } else {
+          const uint32_t mv = lane < nz ? sv[lane] : 0u;
+          const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
+          __syncwarp();
+          for (int k = 0; k < n_pairs; ++k, ab += S2) {
+            if (((members >> (2 * k)) & 3ull) == 0) continue;
+            const uint32_t w0 = __ldg(ab), w1 = __ldg(ab + p.stride);
+            const uint32_t r =
+                __reduce_add_sync(0xFFFFFFFFu, __popc(mv & w0) + (__popc(mv & w1) << 16));
+            add_pair(ov2, k, r, lane);
           }
         }
       } else {
         const uint32_t* ab = abase + 4 * lane;
-        while (members) {
-          int a[4];
-          uint4 v[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            a[k] = members ? __ffsll((long long)members) - 1 : -1;
-            members &= members - 1ull;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            v[k] = a[k] >= 0
-                       ? __ldg(reinterpret_cast<const uint4*>(ab + (uint64_t)a[k] * p.stride))
-                       : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (a[k] < 0) break;
-            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, popc4(and4(x, v[k])));
-            if (lane == 0 && r) atomicAdd(&ov[a[k]], r);
-          }
+        for (int k = 0; k < n_pairs; ++k, ab += S2) {
+          if (((members >> (2 * k)) & 3ull) == 0) continue;
+          const uint4 w0 = __ldg(reinterpret_cast<const uint4*>(ab));
+          const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(ab + p.stride));
+          const uint32_t r = __reduce_add_sync(
+              0xFFFFFFFFu, popc4(and4(x, w0)) + (popc4(and4(x, w1)) << 16));
+          add_pair(ov2, k, r, lane);
         }
       }
     }
@@ -229,6 +247,8 @@ cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStr
   if (p.n_cand == 0) return cudaSuccess;
   if (p.arch && p.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
   if (p.stride % kRangeWords != 0 || (int64_t)p.stride < p.W) return cudaErrorInvalidValue;
+  if ((uint64_t)p.C * (uint64_t)p.C * p.stride > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  if (p.arch && (p.ov_stride % 2 != 0 || p.ov_stride < p.n_arch)) return cudaErrorInvalidValue;
   count_launch();
   const bool bm = p.bitmaps != nullptr;
   if (negative)
