@@ -221,6 +221,10 @@ cudaEvent_t take_event() {
 
 // Records a start event before and an end event after the launches in its scope, on the
 // stream they are launched on, when timing is enabled.
+// Kernels of a call are chained with programmatic dependent launch unless per-kernel timing is
+// on (an event recorded between two kernels would separate them anyway).
+bool timing_on() { return g_timing.load(std::memory_order_relaxed); }
+
 struct Timed {
   int kind;
   cudaStream_t s;
@@ -459,7 +463,10 @@ static int eval_population_impl(ebic_matrix* m, const uint16_t* cols, const uint
     p.counts = dcounts;
     p.bitmaps = dbitmaps;
     p.err = err;
-    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms, s));
+    p.err_out = err;
+    p.status = m->status;
+    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms,
+                               !timing_on(), s));
   } else {
   a.n_cand = n_cand;
   a.cand_cols = dcols;
@@ -854,12 +861,15 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.ov_stride = ov_stride;
     p.arch_counts = darch_counts;
     p.err = err;
-    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms, s));
+    p.err_out = err;
+    p.status = m->status;
+    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms,
+                               !timing_on(), s));
   }
   {
     Timed t(EBIC_TIMING_FITNESS, s);
     EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, ov_stride,
-                                    darch_counts, dshare, dfit, err, s));
+                                    darch_counts, dshare, dfit, err, !timing_on(), s));
   }
   const bool ov_host = overlaps && n_arch > 0 && !on_device(overlaps, dev);
   if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout

@@ -144,8 +144,14 @@ struct PairArgs {
   uint32_t ov_stride = 0;            // n_arch rounded up to even (pairs of counters, 8-byte aligned)
   uint32_t* arch_counts = nullptr;   // [n_arch], zeroed before the launch
   const uint32_t* err = nullptr;     // non-zero: do nothing
+  uint32_t* err_out = nullptr;       // where a timeout is reported (per call)
+  uint32_t* status = nullptr;        // matrix status word
+  uint64_t timeout_ns = 1000000000ull;  // limit of each wait for staged table rows
 };
-cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStream_t s);
+// pdl: launch with programmatic stream serialization (the kernel waits for the previous one in
+// the stream itself, so its launch overlaps that kernel's tail).
+cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, bool pdl,
+                             cudaStream_t s);
 
 // Preparation of the fused pass, one launch: checks the candidate list and (check_arch) the
 // archive list, zeroes counts, overlaps and archive counts, writes for every candidate the mask
@@ -179,7 +185,25 @@ cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, cons
                                   const uint32_t* arch_offsets, uint32_t n_arch,
                                   const uint32_t* overlaps, uint32_t ov_stride,
                                   const uint32_t* arch_counts, const uint64_t* share,
-                                  uint64_t* fitness, const uint32_t* err, cudaStream_t s);
+                                  uint64_t* fitness, const uint32_t* err, bool pdl,
+                                  cudaStream_t s);
+
+// Launch `kernel` with or without programmatic stream serialization.
+template <typename... Params, typename... Args>
+cudaError_t launch_maybe_pdl(bool pdl, void (*kernel)(Params...), dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // ---- fitness -------------------------------------------------------------------------------
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,

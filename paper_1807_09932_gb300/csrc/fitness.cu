@@ -15,6 +15,7 @@
 // tests each archive member's columns against it.
 #include <algorithm>
 
+#include "device_common.cuh"
 #include "ebic_internal.h"
 
 namespace ebic {
@@ -29,12 +30,10 @@ constexpr int kPrepWarps = 8;
 // pass, so reads stay in bounds whatever the other candidates' offsets are. Leaves the
 // candidate's column set in `set` (the warp's own shared-memory bitset; empty when the offsets
 // fail). Returns true on every lane when the candidate is invalid.
-__device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
-                                     const uint32_t* __restrict__ offs, uint32_t n, uint32_t i,
-                                     int32_t ncols, uint32_t* set, int lane) {
-  const uint32_t total = offs[n];
-  const uint32_t lo = offs[i], hi = offs[i + 1];
-  const bool bad = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
+__device__ bool check_candidate_span(const uint16_t* __restrict__ cols, uint32_t lo, uint32_t hi,
+                                     uint32_t total, bool first, int32_t ncols, uint32_t* set,
+                                     int lane) {
+  const bool bad = (first && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
   const int nw = (ncols + 31) / 32;
   for (int w = lane; w < nw; w += 32) set[w] = 0u;
   __syncwarp();
@@ -54,6 +53,12 @@ __device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
   return __any_sync(0xFFFFFFFFu, bad || b);
 }
 
+__device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
+                                     const uint32_t* __restrict__ offs, uint32_t n, uint32_t i,
+                                     int32_t ncols, uint32_t* set, int lane) {
+  return check_candidate_span(cols, offs[i], offs[i + 1], offs[n], i == 0, ncols, set, lane);
+}
+
 __device__ __forceinline__ void report_invalid(bool bad, uint32_t* err, uint32_t* status) {
   if (bad) {
     atomicOr(err, kErrInvalid);
@@ -65,6 +70,7 @@ __device__ __forceinline__ void report_invalid(bool bad, uint32_t* err, uint32_t
 // two outputs, in one launch.
 __global__ void __launch_bounds__(kPrepWarps * 32) prepare_kernel(PrepareArgs a) {
   __shared__ uint32_t sets[kPrepWarps][kSetWords];
+  dev::pdl_trigger();  // a following pair-table pass may be scheduled; it waits for this grid
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nthreads = (size_t)gridDim.x * blockDim.x;
   if (a.zero)
@@ -81,10 +87,15 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prepare_kernel(PrepareArgs a)
   if (lane == 0) report_invalid(bad, a.err, a.status);
 }
 
-// Preparation of the fused evaluation + overlap pass (see launch_fused_prepare).
+// Preparation of the fused evaluation + overlap pass (see launch_fused_prepare). Three phases,
+// each a single round of independent loads: (A) archive offsets, the archive copy and the
+// warp's first candidate's offsets; (B) the archive members' columns; (C) the candidates'
+// columns.
 __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPrepareArgs a) {
   __shared__ uint32_t msets[kPairMaxArch][kSetWords];  // archive members' column sets
   __shared__ uint32_t sets[kPrepWarps][kSetWords];
+  __shared__ uint32_t aoff_s[kPairMaxArch + 1];
+  dev::pdl_trigger();  // the pair-table pass may be scheduled; it waits for this grid
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nthreads = (size_t)gridDim.x * blockDim.x;
@@ -92,32 +103,82 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
   const int nw = (a.ncols + 31) / 32;
   const uint32_t na = a.n_arch;
 
-  // archive padded copy and zeroed archive counts
-  const size_t n_pad = (size_t)((na + 1u) & ~1u) * a.stride;  // an even number of rows
-  for (size_t i = tid; i < n_pad; i += nthreads) {
-    const size_t m = i / a.stride, w = i - m * a.stride;
-    a.arch_pad[i] = m < na && w < (size_t)a.W ? a.arch_src[m * (size_t)a.W + w] : 0u;
-  }
-  for (size_t i = tid; i < na; i += nthreads) a.arch_counts[i] = 0u;
-
-  // every block builds the members' column sets; a member whose offsets fail contributes none
-  // (the list is rejected below, and the pass that follows then does nothing)
+  // (A)
+  if (threadIdx.x <= na && na) aoff_s[threadIdx.x] = a.aoffsets[threadIdx.x];
   for (int i = threadIdx.x; i < (int)na * kSetWords; i += blockDim.x) (&msets[0][0])[i] = 0u;
-  __syncthreads();
-  const uint32_t atotal = na ? a.aoffsets[na] : 0u;
-  for (uint32_t m = warp; m < na; m += kPrepWarps) {
-    const uint32_t lo = a.aoffsets[m], hi = a.aoffsets[m + 1];
-    if ((m == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > atotal) continue;
-    for (uint32_t j = lo + lane; j < hi; j += 32) {
-      const uint32_t c = a.acols[j];
-      if (c < (uint32_t)a.ncols) atomicOr(&msets[m][c >> 5], 1u << (c & 31u));
+  uint32_t lo0 = 0, hi0 = 0, tot0 = 0;
+  if (gw < a.n_cand) {
+    lo0 = a.offsets[gw];
+    hi0 = a.offsets[gw + 1];
+    tot0 = a.offsets[a.n_cand];
+  }
+  {  // archive rows padded to the table stride (an even number of rows), four loads in flight
+    const uint32_t* __restrict__ src = a.arch_src;
+    uint32_t* __restrict__ dst = a.arch_pad;
+    const uint64_t n_pad = (uint64_t)((na + 1u) & ~1u) * a.stride;
+    const bool narrow = n_pad < (1ull << 32);  // 32-bit index arithmetic suffices
+    for (uint64_t i0 = tid; i0 < n_pad; i0 += 4 * nthreads) {
+      uint32_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t i = i0 + k * nthreads;
+        uint64_t m, w;
+        if (narrow) {
+          const uint32_t i32 = (uint32_t)i;
+          m = i32 / a.stride;
+          w = i32 - (uint32_t)m * a.stride;
+        } else {
+          m = i / a.stride;
+          w = i - m * a.stride;
+        }
+        v[k] = i < n_pad && m < na && w < (uint64_t)a.W ? src[m * (uint64_t)a.W + w] : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t i = i0 + k * nthreads;
+        if (i < n_pad) dst[i] = v[k];
+      }
     }
   }
+  for (size_t i = tid; i < na; i += nthreads) a.arch_counts[i] = 0u;
   __syncthreads();
 
+  // (B) every block builds the members' column sets, one (member, position) per thread; a
+  // member whose offsets fail contributes none (the list is rejected below, and the pass that
+  // follows then does nothing)
+  const uint32_t atotal = na ? aoff_s[na] : 0u;
+  for (uint32_t t0 = threadIdx.x; t0 < na * (uint32_t)kMaxLen; t0 += 4 * blockDim.x) {
+    uint32_t c[4], m[4];
+    bool ok[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t t = t0 + k * blockDim.x;
+      m[k] = t / kMaxLen;
+      const uint32_t j = t % kMaxLen;
+      ok[k] = false;
+      c[k] = 0u;
+      if (m[k] < na) {
+        const uint32_t lo = aoff_s[m[k]], hi = aoff_s[m[k] + 1];
+        const bool sane = !(m[k] == 0 && lo != 0u) && hi > lo && hi - lo <= (uint32_t)kMaxLen &&
+                          hi <= atotal;
+        ok[k] = sane && j < hi - lo;
+        if (ok[k]) c[k] = a.acols[lo + j];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (ok[k] && c[k] < (uint32_t)a.ncols) atomicOr(&msets[m[k]][c[k] >> 5], 1u << (c[k] & 31u));
+  }
+  __syncthreads();
+
+  // (C) a warp per candidate: check, share mask, zeroed outputs
   bool bad = false;
   for (uint32_t i = gw; i < a.n_cand; i += nwarps) {
-    bad |= check_candidate_warp(a.cols, a.offsets, a.n_cand, i, a.ncols, sets[warp], lane);
+    if (i != gw) {
+      lo0 = a.offsets[i];
+      hi0 = a.offsets[i + 1];
+    }
+    bad |= check_candidate_span(a.cols, lo0, hi0, tot0, i == 0, a.ncols, sets[warp], lane);
     uint32_t s0 = 0u, s1 = 0u;
     for (int w = 0; w < nw; ++w) {
       const uint32_t cw = sets[warp][w];
@@ -135,7 +196,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
   }
   if (a.check_arch)
     for (uint32_t i = gw; i < na; i += nwarps)
-      bad |= check_candidate_warp(a.acols, a.aoffsets, na, i, a.ncols, sets[warp], lane);
+      bad |= check_candidate_span(a.acols, aoff_s[i], aoff_s[i + 1], atotal, i == 0, a.ncols,
+                                  sets[warp], lane);
   if (lane == 0) report_invalid(bad, a.err, a.status);
 }
 
@@ -149,11 +211,15 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
                           const uint32_t* __restrict__ arch_counts,
                           const uint64_t* __restrict__ share, uint64_t* __restrict__ fitness,
                           const uint32_t* err) {
-  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x * kPrepWarps + warp;
-  if (c >= n_cand) return;
-  const uint32_t L = offsets[c + 1] - offsets[c];
+  // the call's inputs (written before the preparation ran) are read before the wait
+  const bool live = c < n_cand;
+  const uint32_t L = live ? offsets[c + 1] - offsets[c] : 1u;
+  const uint32_t al0 = lane < (int)n_arch ? aoffsets[lane + 1] - aoffsets[lane] : 0u;
+  const uint32_t al1 = lane + 32 < (int)n_arch ? aoffsets[lane + 33] - aoffsets[lane + 32] : 0u;
+  dev::pdl_wait();  // the pair-table pass is complete and visible
+  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0 || !live) return;
   const uint32_t n = counts[c];
   const uint32_t shift = (L < 33u ? L : 33u) - 1u;
   const uint64_t qc = (uint64_t)n << shift;
@@ -161,7 +227,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   uint32_t best = 0;
   for (uint32_t m = lane; m < n_arch; m += 32) {
     if (!((sh >> m) & 1ull)) continue;  // shares no column with the candidate
-    const uint32_t al = aoffsets[m + 1] - aoffsets[m];
+    const uint32_t al = m < 32 ? al0 : al1;
     const uint64_t qa = (uint64_t)arch_counts[m] << ((al < 33u ? al : 33u) - 1u);
     if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
     const uint32_t ov = overlaps[(size_t)c * ov_stride + m];
@@ -370,13 +436,14 @@ cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, cons
                                   const uint32_t* arch_offsets, uint32_t n_arch,
                                   const uint32_t* overlaps, uint32_t ov_stride,
                                   const uint32_t* arch_counts, const uint64_t* share,
-                                  uint64_t* fitness, const uint32_t* err, cudaStream_t s) {
+                                  uint64_t* fitness, const uint32_t* err, bool pdl,
+                                  cudaStream_t s) {
   if (n_cand == 0) return cudaSuccess;
   count_launch();
-  fused_finalize_kernel<<<(n_cand + kPrepWarps - 1) / kPrepWarps, kPrepWarps * 32, 0, s>>>(
-      offsets, n_cand, counts, arch_offsets, n_arch, overlaps, ov_stride, arch_counts, share,
-      fitness, err);
-  return cudaGetLastError();
+  return launch_maybe_pdl(pdl, fused_finalize_kernel,
+                          dim3((n_cand + kPrepWarps - 1) / kPrepWarps), dim3(kPrepWarps * 32), 0,
+                          s, offsets, n_cand, counts, arch_offsets, n_arch, overlaps, ov_stride,
+                          arch_counts, share, fitness, err);
 }
 
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,

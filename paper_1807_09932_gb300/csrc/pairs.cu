@@ -36,6 +36,7 @@
 // candidate's non-zero words in the range number 32 or fewer (long chains match few rows), they
 // are first compacted to one per lane, so each member costs one gathered word and one popcount
 // per lane instead of four.
+#include "device_common.cuh"
 #include "ebic_internal.h"
 
 namespace ebic {
@@ -125,6 +126,8 @@ template <bool NEG, bool BITMAPS, bool OVERLAP>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairArgs p) {
   // per warp: its 128 words for the coalesced bitmap store, or its compacted non-zero words
   __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
+  dev::pdl_wait();     // the preparation (checks, zeroed outputs) is complete and visible
+  dev::pdl_trigger();  // the finalize launch may be scheduled now; it waits for this grid itself
   if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) return;  // invalid input
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_ranges = (uint32_t)((p.W + kRangeWords - 1) / kRangeWords);
@@ -233,17 +236,18 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
 }
 
 template <bool NEG, bool BITMAPS>
-cudaError_t launch_variant(const PairArgs& p, int grid, cudaStream_t s) {
+cudaError_t launch_variant(const PairArgs& p, int grid, bool pdl, cudaStream_t s) {
   if (p.arch)
-    pair_eval_kernel<NEG, BITMAPS, true><<<grid, kPairThreads, 0, s>>>(p);
-  else
-    pair_eval_kernel<NEG, BITMAPS, false><<<grid, kPairThreads, 0, s>>>(p);
-  return cudaGetLastError();
+    return launch_maybe_pdl(pdl, pair_eval_kernel<NEG, BITMAPS, true>, dim3(grid),
+                            dim3(kPairThreads), 0, s, p);
+  return launch_maybe_pdl(pdl, pair_eval_kernel<NEG, BITMAPS, false>, dim3(grid),
+                          dim3(kPairThreads), 0, s, p);
 }
 
 }  // namespace
 
-cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStream_t s) {
+cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, bool pdl,
+                             cudaStream_t s) {
   if (p.n_cand == 0) return cudaSuccess;
   if (p.arch && p.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
   if (p.stride % kRangeWords != 0 || (int64_t)p.stride < p.W) return cudaErrorInvalidValue;
@@ -252,8 +256,10 @@ cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, cudaStr
   count_launch();
   const bool bm = p.bitmaps != nullptr;
   if (negative)
-    return bm ? launch_variant<true, true>(p, grid, s) : launch_variant<true, false>(p, grid, s);
-  return bm ? launch_variant<false, true>(p, grid, s) : launch_variant<false, false>(p, grid, s);
+    return bm ? launch_variant<true, true>(p, grid, pdl, s)
+              : launch_variant<true, false>(p, grid, pdl, s);
+  return bm ? launch_variant<false, true>(p, grid, pdl, s)
+            : launch_variant<false, false>(p, grid, pdl, s);
 }
 
 }  // namespace ebic
