@@ -15,36 +15,40 @@
 //   L = 1:      T[c_1*C + c_1]
 // so a candidate costs one 32-bit AND per 32 rows per column, streamed from the table.
 //
-// Table rows are stored with a stride of ceil(W / 128) * 128 words whose padding words are zero,
-// so a lane reads four consecutive words with one 16-byte load and never tests a bound: a padding
-// word ANDs to zero and counts nothing.
+// Table rows are stored with a stride of ceil(W / 256) * 256 words whose padding words are zero,
+// so a lane reads four consecutive words of each 128-word half of an item with one 16-byte load
+// and never tests a bound: a padding word ANDs to zero and counts nothing.
 //
-// Work order: items are (range of 128 words = 4,096 rows, group of 32 candidates), taken
+// Work order: items are (range of 256 words = 8,192 rows, group of 24 candidates), taken
 // round-robin by a persistent grid in range-major order, so all CTAs work on the same few row
 // ranges at a time and the table rows of those ranges stay in L2 while every candidate reads
 // them; each table word comes from HBM about once per evaluation. Each warp takes one candidate
 // of its item: it reads the column list once (a lane per column), turns it into the table rows
-// of the consecutive pairs (a lane per pair), and walks the chain four pairs at a time, each
-// step issuing four independent 512-byte warp loads (eight with negative trends).
+// of the consecutive pairs (a lane per pair), and walks the chain four pairs at a time, each step
+// keeping eight 512-byte warp loads in flight (four pairs x two halves; with negative trends two
+// pairs, both orders). A half stops loading once all its words are zero and the walk stops when
+// both are: long chains match no row of most ranges.
 //
 // Fused overlaps (the fitness's o(c, a) = popcount(M_c & M_a), Methods, "Handling missing
 // values" and the archive rule of the fitness): the warp that has just built a candidate's words
-// of a range ANDs them with the archive members' words of the same range (archive rows padded to
-// the same stride) and adds the popcounts, so candidate bitmaps never go through HBM. Ranges
+// of a half ANDs them with the archive members' words of the same rows (archive rows padded to
+// the same stride) and adds the popcounts, so candidate bitmaps never go through HBM. Halves
 // where the candidate matches no row are skipped, and so are archive members that the caller
-// does not need (those sharing no column with the candidate cannot penalise it). When the
-// candidate's non-zero words in the range number 32 or fewer (long chains match few rows), they
-// are first compacted to one per lane, so each member costs one gathered word and one popcount
-// per lane instead of four.
+// does not need (those sharing no column with the candidate cannot penalise it). By the number
+// of non-zero words in the half: up to 12 are walked by a lane per member (no reductions); up
+// to 32 are compacted to one per lane and members go two per warp reduction; denser halves
+// take the wanted members two at a time over all words.
 #include "device_common.cuh"
 #include "ebic_internal.h"
 
 namespace ebic {
 namespace {
 
-constexpr int kPairThreads = 1024;
+constexpr int kPairThreads = 768;
 constexpr int kPairWarps = kPairThreads / 32;
-constexpr int kRangeWords = kPairRangeWords;  // words per item: four per lane
+constexpr int kItemWords = kPairRangeWords;  // words per item: two halves of four per lane
+constexpr int kRangeWords = kItemWords / 2;  // words per half (4,096 rows)
+constexpr int kFewWords = 12;  // at most this many non-zero words: a lane per archive member
 
 __device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
   return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
@@ -57,13 +61,15 @@ __device__ __forceinline__ uint32_t popc4(uint4 v) {
   return __popc(s) + 2u * __popc(c) + __popc(v.w);
 }
 
-// The candidate's bitmap words 4*lane .. 4*lane+3 of the range whose first table word is `base`
-// (table + range*128): AND of its consecutive pairs' table rows, OR the reversed pairs' AND
-// with negative trends. The walk stops early once every word of the warp is zero (long chains
-// match no row of most ranges).
+// The candidate's bitmap words 4*lane .. 4*lane+3 of the two halves of the item whose first
+// table word is `base` (table + item*256; the second half 128 words on): AND of its consecutive
+// pairs' table rows, OR the reversed pairs' AND with negative trends. Each step keeps the rows
+// of several terms of both halves in flight; a half stops loading once every word of it in the
+// warp is zero, and the walk stops when both are (long chains match no row of most ranges).
 template <bool NEG>
-__device__ __forceinline__ uint4 pair_chain(const PairArgs& p, uint32_t cand,
-                                            const uint32_t* base, int lane) {
+__device__ __forceinline__ void pair_chain(const PairArgs& p, uint32_t cand,
+                                           const uint32_t* base, int lane, uint4 (&out)[2]) {
+  constexpr int kStep = NEG ? 2 : 4;  // terms per step (each one or two rows per half)
   const uint32_t o = p.offsets[cand];
   const int L = (int)(p.offsets[cand + 1] - o);
   const uint32_t C = (uint32_t)p.C, S = p.stride;
@@ -81,37 +87,69 @@ __device__ __forceinline__ uint4 pair_chain(const PairArgs& p, uint32_t cand,
   const int n_terms = L == 1 ? 1 : L - 1;
   const bool two = NEG && L > 1;  // warp-uniform
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
-  uint4 x = ones, y = ones;
+  uint4 x0 = ones, x1 = ones, y0 = ones, y1 = ones;
+  bool live0 = true, live1 = true;  // warp-uniform: the half still has a non-zero word
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
   auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
-    for (int i0 = t0; i0 < t1; i0 += 4) {
-      uint4 v[4], u[4];
+    for (int i0 = t0; i0 < t1; i0 += kStep) {
+      uint4 v0[kStep], v1[kStep], u0[kStep], u1[kStep];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < kStep; ++k) {
         const int i = i0 + k;
-        v[k] = u[k] = ones;
+        v0[k] = v1[k] = u0[k] = u1[k] = ones;
         if (i < t1) {  // warp-uniform
-          v[k] = __ldg(reinterpret_cast<const uint4*>(
-              base + __shfl_sync(0xFFFFFFFFu, offf, i & 31)));
-          if (two)
-            u[k] = __ldg(reinterpret_cast<const uint4*>(
-                base + __shfl_sync(0xFFFFFFFFu, offb, i & 31)));
+          const uint32_t* rf = base + __shfl_sync(0xFFFFFFFFu, offf, i & 31);
+          if (live0) v0[k] = __ldg(reinterpret_cast<const uint4*>(rf));
+          if (live1) v1[k] = __ldg(reinterpret_cast<const uint4*>(rf + kRangeWords));
+          if (two) {
+            const uint32_t* rb = base + __shfl_sync(0xFFFFFFFFu, offb, i & 31);
+            if (live0) u0[k] = __ldg(reinterpret_cast<const uint4*>(rb));
+            if (live1) u1[k] = __ldg(reinterpret_cast<const uint4*>(rb + kRangeWords));
+          }
         }
       }
-      x = and4(x, and4(and4(v[0], v[1]), and4(v[2], v[3])));
-      uint32_t any = x.x | x.y | x.z | x.w;
-      if (NEG) {
-        y = and4(y, and4(and4(u[0], u[1]), and4(u[2], u[3])));
-        if (two) any |= y.x | y.y | y.z | y.w;
+#pragma unroll
+      for (int k = 0; k < kStep; ++k) {
+        x0 = and4(x0, v0[k]);
+        x1 = and4(x1, v1[k]);
       }
-      if (!__any_sync(0xFFFFFFFFu, any != 0u)) return false;  // all zero from here on
+      uint32_t any0 = x0.x | x0.y | x0.z | x0.w, any1 = x1.x | x1.y | x1.z | x1.w;
+      if (NEG) {
+#pragma unroll
+        for (int k = 0; k < kStep; ++k) {
+          y0 = and4(y0, u0[k]);
+          y1 = and4(y1, u1[k]);
+        }
+        if (two) {
+          any0 |= y0.x | y0.y | y0.z | y0.w;
+          any1 |= y1.x | y1.y | y1.z | y1.w;
+        }
+      }
+      live0 = __any_sync(0xFFFFFFFFu, any0 != 0u);
+      live1 = __any_sync(0xFFFFFFFFu, any1 != 0u);
+      if (!live0 && !live1) return false;  // all zero from here on
     }
     return true;
   };
   if (walk(fwd_lo, bwd_lo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
     walk(fwd_hi, bwd_hi, 32, n_terms);
-  if (two) x = make_uint4(x.x | y.x, x.y | y.y, x.z | y.z, x.w | y.w);
-  return x;
+  if (two) {
+    x0 = make_uint4(x0.x | y0.x, x0.y | y0.y, x0.z | y0.z, x0.w | y0.w);
+    x1 = make_uint4(x1.x | y1.x, x1.y | y1.y, x1.z | y1.z, x1.w | y1.w);
+  }
+  // a half that went all-zero stays zero (its remaining terms were not loaded)
+  out[0] = live0 ? x0 : make_uint4(0u, 0u, 0u, 0u);
+  out[1] = live1 ? x1 : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// An archive row segment: re-read by every warp of the CTA that scores a candidate of the same
+// range, so it is kept in L1 in preference to the streamed table rows.
+__device__ __forceinline__ uint4 ld_arch4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::evict_last.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
 }
 
 // Adds a packed pair of warp sums (member 2k in the low 16 bits, 2k+1 in the high 16 bits) to
@@ -122,116 +160,159 @@ __device__ __forceinline__ void add_pair(unsigned long long* ov2, int k, uint32_
     atomicAdd(&ov2[k], (unsigned long long)(r & 0xFFFFu) | ((unsigned long long)(r >> 16) << 32));
 }
 
+// Bitmap words and archive overlaps of candidate `cand` for the 128-word half at `rword`, from
+// its words x (lane holds words 4*lane .. 4*lane+3) and their warp total cnt.
+template <bool BITMAPS, bool OVERLAP>
+__device__ __forceinline__ void half_epilogue(const PairArgs& p, uint32_t cand, uint64_t rword,
+                                              uint4 x, uint32_t cnt, uint32_t* st, int lane,
+                                              uint32_t n_arch, int n_pairs,
+                                              uint64_t all_members) {
+  if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
+    *reinterpret_cast<uint4*>(st + 4 * lane) = x;
+    __syncwarp();
+    uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t w = rword + 32 * j + lane;
+      if (w < (uint64_t)p.W) out[w] = st[32 * j + lane];
+    }
+    __syncwarp();
+  }
+  if constexpr (OVERLAP) {
+    if (cnt == 0) return;  // warp-uniform: nothing of this range overlaps anything
+    const uint64_t members = p.score ? p.score[cand] & all_members : all_members;
+    if (members == 0) return;
+    unsigned long long* ov2 =
+        reinterpret_cast<unsigned long long*>(p.overlaps + (uint64_t)cand * p.ov_stride);
+    const uint32_t* abase = p.arch + rword;
+    const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
+    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, x.x != 0u);
+    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, x.y != 0u);
+    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, x.z != 0u);
+    const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, x.w != 0u);
+    const int n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
+    const int nz = n0 + n1 + n2 + __popc(b3);
+    if (nz <= 32) {
+      // compact the non-zero words: lane i takes the i-th one (value and word offset)
+      uint32_t* sv = st;
+      uint32_t* si = st + 32;
+      const uint32_t lt = (1u << lane) - 1u;
+      if (x.x) { const int q = __popc(b0 & lt); sv[q] = x.x; si[q] = 4 * lane; }
+      if (x.y) { const int q = n0 + __popc(b1 & lt); sv[q] = x.y; si[q] = 4 * lane + 1; }
+      if (x.z) { const int q = n0 + n1 + __popc(b2 & lt); sv[q] = x.z; si[q] = 4 * lane + 2; }
+      if (x.w) {
+        const int q = n0 + n1 + n2 + __popc(b3 & lt);
+        sv[q] = x.w;
+        si[q] = 4 * lane + 3;
+      }
+      __syncwarp();
+      if (nz <= kFewWords) {
+        // few non-zero words: a lane per archive member (two for members 32..63) walks them
+        // all, gathering its member's word at each; no warp reduction, one atomic per member
+        const bool a0 = (members >> lane) & 1ull;
+        const bool a1 = lane + 32 < 64 && ((members >> (lane + 32)) & 1ull);
+        const uint32_t* ar0 = abase + (uint64_t)lane * p.stride;
+        const uint32_t* ar1 = abase + (uint64_t)(lane + 32) * p.stride;
+        uint32_t o0 = 0, o1 = 0;
+#pragma unroll 4
+        for (int i = 0; i < nz; ++i) {
+          const uint32_t v = sv[i], w = si[i];
+          if (a0) o0 += __popc(v & __ldg(ar0 + w));
+          if (a1) o1 += __popc(v & __ldg(ar1 + w));
+        }
+        __syncwarp();
+        uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
+        if (o0) atomicAdd(&ov[lane], o0);
+        if (o1) atomicAdd(&ov[lane + 32], o1);
+      } else if (nz <= 16) {
+        // each half-warp holds the same (up to) 16 words; the low half takes member 2k and
+        // the high half member 2k+1 of each pair, one word and one popcount per lane
+        const int src = lane & 15;
+        const uint32_t mv = src < nz ? sv[src] : 0u;
+        const uint32_t* ab = abase + (src < nz ? si[src] : 0u) + (lane >= 16 ? p.stride : 0u);
+        const int sh = lane >= 16 ? 16 : 0;
+        __syncwarp();
+        for (int k = 0; k < n_pairs; ++k, ab += S2) {
+          if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
+          const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & __ldg(ab)) << sh);
+          add_pair(ov2, k, r, lane);
+        }
+      } else {
+        const uint32_t mv = lane < nz ? sv[lane] : 0u;
+        const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
+        __syncwarp();
+        for (int k = 0; k < n_pairs; ++k, ab += S2) {
+          if (((members >> (2 * k)) & 3ull) == 0) continue;
+          const uint32_t w0 = __ldg(ab), w1 = __ldg(ab + p.stride);
+          const uint32_t r =
+              __reduce_add_sync(0xFFFFFFFFu, __popc(mv & w0) + (__popc(mv & w1) << 16));
+          add_pair(ov2, k, r, lane);
+        }
+      }
+    } else {
+      // dense: the wanted members two at a time (no unwanted partner), one packed reduction
+      // (each sum <= 4,096), lanes 0 and 1 add the two totals
+      const uint32_t* ab = abase + 4 * lane;
+      uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
+      uint64_t mm = members;
+      while (mm) {  // warp-uniform
+        const int ma = __ffsll((long long)mm) - 1;
+        mm &= mm - 1ull;
+        const int mb = mm ? __ffsll((long long)mm) - 1 : ma;
+        const bool has_b = mm != 0ull;
+        mm &= mm - 1ull;
+        const uint4 wa = ld_arch4(ab + (uint64_t)ma * p.stride);
+        const uint4 wb = ld_arch4(ab + (uint64_t)mb * p.stride);
+        const uint32_t r = __reduce_add_sync(
+            0xFFFFFFFFu, popc4(and4(x, wa)) + (has_b ? popc4(and4(x, wb)) << 16 : 0u));
+        const uint32_t v = lane == 0 ? (r & 0xFFFFu) : (r >> 16);
+        if (lane < 2 && v) atomicAdd(&ov[lane == 0 ? ma : mb], v);
+      }
+    }
+  }
+}
+
 template <bool NEG, bool BITMAPS, bool OVERLAP>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairArgs p) {
-  // per warp: its 128 words for the coalesced bitmap store, or its compacted non-zero words
+  // per warp: 128 words for the coalesced bitmap store, or its compacted non-zero words
   __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
   dev::pdl_wait();     // the preparation (checks, zeroed outputs) is complete and visible
   dev::pdl_trigger();  // the finalize launch may be scheduled now; it waits for this grid itself
   if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) return;  // invalid input
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t n_ranges = (uint32_t)((p.W + kRangeWords - 1) / kRangeWords);
+  const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
   const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
   const uint64_t n_items = (uint64_t)n_ranges * n_groups;
   const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
   const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
+  uint32_t* st = stage[warp];
   // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division
   const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
   uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, range += d_range, grp += d_grp,
                 range += grp >= n_groups ? 1u : 0u, grp -= grp >= n_groups ? n_groups : 0u) {
-    const uint64_t rword = (uint64_t)range * kRangeWords;  // first word of the range
+    const uint64_t rword = (uint64_t)range * kItemWords;  // first word of the item
     if (OVERLAP && grp == 0) {  // the archive members' own row counts, once per range
       for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
-        const uint4 av = __ldg(reinterpret_cast<const uint4*>(
-            p.arch + (uint64_t)a * p.stride + rword + 4 * lane));
-        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, popc4(av));
+        const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
+        const uint4 a0 = __ldg(reinterpret_cast<const uint4*>(ar));
+        const uint4 a1 = __ldg(reinterpret_cast<const uint4*>(ar + kRangeWords));
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, popc4(a0) + popc4(a1));
         if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
       }
     }
     const uint32_t cand = grp * kPairWarps + warp;
     if (cand >= p.n_cand) continue;  // warp-uniform
-    const uint4 x = pair_chain<NEG>(p, cand, p.table + rword + 4 * lane, lane);
-    const uint32_t cnt = __reduce_add_sync(0xFFFFFFFFu, popc4(x));
-    if (lane == 0 && cnt) atomicAdd(&p.counts[cand], cnt);
-    if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
-      uint32_t* st = stage[warp];
-      *reinterpret_cast<uint4*>(st + 4 * lane) = x;
-      __syncwarp();
-      uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint64_t w = rword + 32 * j + lane;
-        if (w < (uint64_t)p.W) out[w] = st[32 * j + lane];
-      }
-      __syncwarp();
-    }
-    if constexpr (OVERLAP) {
-      if (cnt == 0) continue;  // warp-uniform: nothing of this range overlaps anything
-      const uint64_t members = p.score ? p.score[cand] & all_members : all_members;
-      if (members == 0) continue;
-      unsigned long long* ov2 =
-          reinterpret_cast<unsigned long long*>(p.overlaps + (uint64_t)cand * p.ov_stride);
-      const uint32_t* abase = p.arch + rword;
-      const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
-      const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, x.x != 0u);
-      const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, x.y != 0u);
-      const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, x.z != 0u);
-      const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, x.w != 0u);
-      const int n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
-      const int nz = n0 + n1 + n2 + __popc(b3);
-      if (nz <= 32) {
-        // compact the non-zero words: lane i takes the i-th one (value and word offset)
-        uint32_t* sv = stage[warp];
-        uint32_t* si = stage[warp] + 32;
-        const uint32_t lt = (1u << lane) - 1u;
-        if (x.x) { const int q = __popc(b0 & lt); sv[q] = x.x; si[q] = 4 * lane; }
-        if (x.y) { const int q = n0 + __popc(b1 & lt); sv[q] = x.y; si[q] = 4 * lane + 1; }
-        if (x.z) { const int q = n0 + n1 + __popc(b2 & lt); sv[q] = x.z; si[q] = 4 * lane + 2; }
-        if (x.w) {
-          const int q = n0 + n1 + n2 + __popc(b3 & lt);
-          sv[q] = x.w;
-          si[q] = 4 * lane + 3;
-        }
-        __syncwarp();
-        if (nz <= 16) {
-          // each half-warp holds the same (up to) 16 words; the low half takes member 2k and
-          // the high half member 2k+1 of each pair, one word and one popcount per lane
-          const int src = lane & 15;
-          const uint32_t mv = src < nz ? sv[src] : 0u;
-          const uint32_t* ab = abase + (src < nz ? si[src] : 0u) + (lane >= 16 ? p.stride : 0u);
-          const int sh = lane >= 16 ? 16 : 0;
-          __syncwarp();
-          for (int k = 0; k < n_pairs; ++k, ab += S2) {
-            if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
-            const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & __ldg(ab)) << sh);
-            add_pair(ov2, k, r, lane);
-          }
-        } else {
-          const uint32_t mv = lane < nz ? sv[lane] : 0u;
-          const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
-          __syncwarp();
-          for (int k = 0; k < n_pairs; ++k, ab += S2) {
-            if (((members >> (2 * k)) & 3ull) == 0) continue;
-            const uint32_t w0 = __ldg(ab), w1 = __ldg(ab + p.stride);
-            const uint32_t r =
-                __reduce_add_sync(0xFFFFFFFFu, __popc(mv & w0) + (__popc(mv & w1) << 16));
-            add_pair(ov2, k, r, lane);
-          }
-        }
-      } else {
-        const uint32_t* ab = abase + 4 * lane;
-        for (int k = 0; k < n_pairs; ++k, ab += S2) {
-          if (((members >> (2 * k)) & 3ull) == 0) continue;
-          const uint4 w0 = __ldg(reinterpret_cast<const uint4*>(ab));
-          const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(ab + p.stride));
-          const uint32_t r = __reduce_add_sync(
-              0xFFFFFFFFu, popc4(and4(x, w0)) + (popc4(and4(x, w1)) << 16));
-          add_pair(ov2, k, r, lane);
-        }
-      }
-    }
+    uint4 x[2];
+    pair_chain<NEG>(p, cand, p.table + rword + 4 * lane, lane, x);
+    const uint32_t c0 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[0]));
+    const uint32_t c1 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[1]));
+    if (lane == 0 && c0 + c1) atomicAdd(&p.counts[cand], c0 + c1);
+    half_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x[0], c0, st, lane, n_arch, n_pairs,
+                                    all_members);
+    half_epilogue<BITMAPS, OVERLAP>(p, cand, rword + kRangeWords, x[1], c1, st, lane, n_arch,
+                                    n_pairs, all_members);
   }
 }
 
@@ -250,7 +331,7 @@ cudaError_t launch_pair_eval(const PairArgs& p, bool negative, int grid, bool pd
                              cudaStream_t s) {
   if (p.n_cand == 0) return cudaSuccess;
   if (p.arch && p.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
-  if (p.stride % kRangeWords != 0 || (int64_t)p.stride < p.W) return cudaErrorInvalidValue;
+  if (p.stride % kItemWords != 0 || (int64_t)p.stride < p.W) return cudaErrorInvalidValue;
   if ((uint64_t)p.C * (uint64_t)p.C * p.stride > 0xFFFFFFFFull) return cudaErrorInvalidValue;
   if (p.arch && (p.ov_stride % 2 != 0 || p.ov_stride < p.n_arch)) return cudaErrorInvalidValue;
   count_launch();
