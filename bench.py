@@ -475,11 +475,11 @@ def main():
     m.close()
 
 
-def eval_traffic():
-    """DRAM bytes per evaluator launch from the committed ncu capture, if the kernel source is
-    still the one that was captured."""
+def traffic_record(name):
+    """DRAM bytes per launch of a kernel from a committed ncu capture
+    (profiles/<name>_traffic.json), if the kernel source is still the one that was captured."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "eval_population_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     try:
         rec = json.load(open(path))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
@@ -511,8 +511,12 @@ def roofline_pairs(pops, R, m, launch_ms, clk, peaks, fused, K):
     hbm_bytes = float(np.mean(per))
     t = launch_ms / 1000.0
     peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = traffic_record("pair_eval_fused") if fused else None
     return {"bound": "hbm", "achieved": hbm_bytes / t / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": (hbm_bytes / t / 1e9) / peak, "traffic": None,
+            "frac": (hbm_bytes / t / 1e9) / peak, "traffic": traffic,
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                            "(profiles/pair_eval_fused_traffic.json); null if the kernel source "
+                            "changed since that capture",
             "kernel": "pair_eval_kernel" + (" (fused overlaps)" if fused else ""),
             "launch_ms": launch_ms,
             "algorithmic_bytes_per_launch": hbm_bytes,
@@ -564,7 +568,8 @@ def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
     alu_peak = 64 * sms * clock_hz
     hbm_bytes = m.cols * R * bytes_per_rank + 1600 * m.words * 4
     return {"bound": "smem", "achieved": smem_bytes / t / 1e9, "peak": smem_peak / 1e9,
-            "unit": "GB/s", "frac": (smem_bytes / t) / smem_peak, "traffic": eval_traffic(),
+            "unit": "GB/s", "frac": (smem_bytes / t) / smem_peak,
+            "traffic": traffic_record("eval_population"),
             "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
                             "(profiles/eval_population_traffic.json); null if the kernel source "
                             "changed since that capture",
