@@ -437,6 +437,12 @@ static int eval_population_impl(ebic_matrix* m, const uint16_t* cols, const uint
     EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * bitmap_stride, dev, sc, &dbitmaps,
                          &bitmaps_host));
 
+  const bool use_pairs = m->pairs && !(flags & EBIC_EVAL_DIRECT) && bitmap_stride == L.words;
+  const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
+  uint32_t* dterms = nullptr;  // the pair-table term lists, built by the preparation kernel
+  if (use_pairs)
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dterms),
+                       (size_t)n_cand * term_slots(neg) * sizeof(uint32_t)));
   {
     Timed t(EBIC_TIMING_PREPARE, s);
     PrepareArgs pa;
@@ -448,25 +454,28 @@ static int eval_population_impl(ebic_matrix* m, const uint16_t* cols, const uint
     pa.n_zero = n_cand;
     pa.err = err;
     pa.status = m->status;
+    pa.terms = dterms;
+    pa.n_terms_cand = use_pairs ? n_cand : 0;
+    pa.pair_cols = L.cols;
+    pa.pair_stride = m->pair_stride;
+    pa.negative = neg;
     EBIC_CUDA(launch_prepare(pa, s));
   }
-  if (m->pairs && !(flags & EBIC_EVAL_DIRECT) && bitmap_stride == L.words) {
+  if (use_pairs) {
     Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
     PairArgs p;
     p.table = m->pairs;
     p.stride = m->pair_stride;
     p.C = L.cols;
     p.W = L.words;
-    p.cols = dcols;
-    p.offsets = doffs;
+    p.terms = dterms;
     p.n_cand = n_cand;
     p.counts = dcounts;
     p.bitmaps = dbitmaps;
     p.err = err;
     p.err_out = err;
     p.status = m->status;
-    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms,
-                               !timing_on(), s));
+    EBIC_CUDA(launch_pair_eval(p, neg, m->num_sms, !timing_on(), s));
   } else {
   a.n_cand = n_cand;
   a.cand_cols = dcols;
@@ -818,6 +827,10 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&darch_counts), (size_t)n_arch * 4));
     EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dshare), (size_t)n_cand * 8));
   }
+  const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
+  uint32_t* dterms = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dterms),
+                     (size_t)n_cand * term_slots(neg) * sizeof(uint32_t)));
   {
     Timed t(EBIC_TIMING_PREPARE, s);
     FusedPrepareArgs pa;
@@ -838,6 +851,8 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     pa.ov_stride = ov_stride;
     pa.arch_counts = darch_counts;
     pa.share = dshare;
+    pa.terms = dterms;
+    pa.negative = neg;
     pa.err = err;
     pa.status = m->status;
     EBIC_CUDA(launch_fused_prepare(pa, m->num_sms, s));
@@ -849,8 +864,7 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.stride = stride;
     p.C = L.cols;
     p.W = L.words;
-    p.cols = dcols;
-    p.offsets = doffs;
+    p.terms = dterms;
     p.n_cand = n_cand;
     p.counts = dcounts;
     p.bitmaps = dbm;
@@ -863,8 +877,7 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.err = err;
     p.err_out = err;
     p.status = m->status;
-    EBIC_CUDA(launch_pair_eval(p, (flags & EBIC_NEGATIVE_TRENDS) != 0, m->num_sms,
-                               !timing_on(), s));
+    EBIC_CUDA(launch_pair_eval(p, neg, m->num_sms, !timing_on(), s));
   }
   {
     Timed t(EBIC_TIMING_FITNESS, s);

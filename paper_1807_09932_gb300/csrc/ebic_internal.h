@@ -74,6 +74,12 @@ struct PrepareArgs {
   size_t n_zero2 = 0;
   uint32_t* err = nullptr;
   uint32_t* status = nullptr;
+  // pair-table term lists of list 0 (see kTermSlots), built when terms is not null
+  uint32_t* terms = nullptr;
+  uint32_t n_terms_cand = 0;  // candidates of list 0 to build them for
+  int32_t pair_cols = 0;      // C of the pair table
+  uint32_t pair_stride = 0;   // its row stride (words)
+  bool negative = false;
 };
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s);
 
@@ -126,13 +132,20 @@ constexpr int kPairMaxArch = 64;      // archive members the fused overlap pass 
 inline int64_t pair_stride(int64_t words) {
   return (words + kPairRangeWords - 1) / kPairRangeWords * kPairRangeWords;
 }
+// A candidate's term list, written by the preparation kernels: [kTermSlots] uint32 words per
+// candidate, slot t < L-1 the table-row offset (words) of its consecutive pair t (the diagonal
+// row for L = 1), slot 63 the length L; with negative trends slots 64 + t hold the reversed
+// pairs' rows. Unused slots are 0.
+constexpr int kTermSlots = 64;
+__host__ __device__ inline int term_slots(bool negative) {
+  return negative ? 2 * kTermSlots : kTermSlots;
+}
 struct PairArgs {
   const uint32_t* table = nullptr;   // [C*C][stride], padding words zero
   uint32_t stride = 0;               // row stride of table and arch (words)
   int32_t C = 0;                     // matrix columns
   int64_t W = 0;                     // words per bitmap
-  const uint16_t* cols = nullptr;    // device CSR candidate list (checked)
-  const uint32_t* offsets = nullptr;
+  const uint32_t* terms = nullptr;   // [n_cand][term_slots(negative)] term lists
   uint32_t n_cand = 0;
   uint32_t* counts = nullptr;        // [n_cand], zeroed before the launch
   uint32_t* bitmaps = nullptr;       // [n_cand][W] or null
@@ -176,6 +189,8 @@ struct FusedPrepareArgs {
   uint32_t ov_stride = 0;
   uint32_t* arch_counts = nullptr;
   uint64_t* share = nullptr;
+  uint32_t* terms = nullptr;           // [n_cand][term_slots(negative)]
+  bool negative = false;
   uint32_t* err = nullptr;
   uint32_t* status = nullptr;
 };

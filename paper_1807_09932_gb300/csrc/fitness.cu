@@ -59,6 +59,34 @@ __device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
   return check_candidate_span(cols, offs[i], offs[i + 1], offs[n], i == 0, ncols, set, lane);
 }
 
+// The term list of one candidate (see kTermSlots), a warp per candidate. Its offsets must have
+// passed the check (lo < hi <= lo + 64, inside the caller's columns); a column >= C makes a
+// garbage offset, but the call is then rejected and no later kernel reads the list.
+__device__ void build_terms_warp(const uint16_t* __restrict__ cols, uint32_t lo, uint32_t hi,
+                                 uint32_t C, uint32_t S, bool negative, uint32_t* out,
+                                 int lane) {
+  const int L = (int)(hi - lo);
+  const uint32_t c_lo = lane < L ? cols[lo + lane] : 0u;
+  const uint32_t c_hi = lane + 32 < L ? cols[lo + 32 + lane] : 0u;
+  const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
+  const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
+  const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
+  const uint32_t next_lo = lane == 31 ? h0 : n_lo;  // c_{i+1} for i = lane
+  const int n_terms = L == 1 ? 1 : L - 1;
+  const bool t_lo = lane < n_terms, t_hi = lane + 32 < n_terms;
+  out[lane] = t_lo ? (L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo) * S : 0u;
+  out[32 + lane] = lane == 31 ? (uint32_t)L : (t_hi ? (c_hi * C + n_hi) * S : 0u);
+  if (negative) {
+    out[64 + lane] = t_lo && L > 1 ? (next_lo * C + c_lo) * S : 0u;
+    out[96 + lane] = t_hi ? (n_hi * C + c_hi) * S : 0u;
+  }
+}
+
+__device__ __forceinline__ bool offsets_sane(uint32_t lo, uint32_t hi, uint32_t total,
+                                             bool first) {
+  return !(first && lo != 0u) && hi > lo && hi - lo <= (uint32_t)kMaxLen && hi <= total;
+}
+
 __device__ __forceinline__ void report_invalid(bool bad, uint32_t* err, uint32_t* status) {
   if (bad) {
     atomicOr(err, kErrInvalid);
@@ -84,6 +112,16 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prepare_kernel(PrepareArgs a)
   for (int l = 0; l < 2; ++l)
     for (uint32_t i = gw; i < a.n[l]; i += nwarps)
       bad |= check_candidate_warp(a.cols[l], a.offsets[l], a.n[l], i, a.ncols, sets[warp], lane);
+  if (a.terms) {
+    const uint32_t total = a.offsets[0][a.n_terms_cand];
+    const int slots = term_slots(a.negative);
+    for (uint32_t i = gw; i < a.n_terms_cand; i += nwarps) {
+      const uint32_t lo = a.offsets[0][i], hi = a.offsets[0][i + 1];
+      if (offsets_sane(lo, hi, total, i == 0))
+        build_terms_warp(a.cols[0], lo, hi, (uint32_t)a.pair_cols, a.pair_stride, a.negative,
+                         a.terms + (size_t)i * slots, lane);
+    }
+  }
   if (lane == 0) report_invalid(bad, a.err, a.status);
 }
 
@@ -179,6 +217,9 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
       hi0 = a.offsets[i + 1];
     }
     bad |= check_candidate_span(a.cols, lo0, hi0, tot0, i == 0, a.ncols, sets[warp], lane);
+    if (offsets_sane(lo0, hi0, tot0, i == 0))
+      build_terms_warp(a.cols, lo0, hi0, (uint32_t)a.ncols, a.stride, a.negative,
+                       a.terms + (size_t)i * term_slots(a.negative), lane);
     uint32_t s0 = 0u, s1 = 0u;
     for (int w = 0; w < nw; ++w) {
       const uint32_t cw = sets[warp][w];
@@ -407,6 +448,7 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
 
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
   size_t warps = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
+  if (a.terms && a.n_terms_cand > warps) warps = a.n_terms_cand;
   const size_t zero = a.n_zero > a.n_zero2 ? a.n_zero : a.n_zero2;
   size_t blocks = (warps + kPrepWarps - 1) / kPrepWarps;
   const size_t zb = (zero + kPrepWarps * 32 * 4 - 1) / (kPrepWarps * 32 * 4);

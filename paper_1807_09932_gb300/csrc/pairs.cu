@@ -66,24 +66,34 @@ __device__ __forceinline__ uint32_t popc4(uint4 v) {
 // pairs' table rows, OR the reversed pairs' AND with negative trends. Each step keeps the rows
 // of several terms of both halves in flight; a half stops loading once every word of it in the
 // warp is zero, and the walk stops when both are (long chains match no row of most ranges).
+// One candidate's term list as the warp holds it: lane i has the row offsets of terms i and
+// 32 + i (forward; reversed in blo/bhi), lane 31's hi word is the length L.
+struct Terms {
+  uint32_t lo = 0, hi = 0, blo = 0, bhi = 0;
+};
+
 template <bool NEG>
-__device__ __forceinline__ void pair_chain(const PairArgs& p, uint32_t cand,
-                                           const uint32_t* base, int lane, uint4 (&out)[2]) {
+__device__ __forceinline__ void load_terms(const PairArgs& p, uint32_t cand, int lane,
+                                           Terms& t) {
+  const uint32_t* tp = p.terms + (uint64_t)cand * (NEG ? 2 * kTermSlots : kTermSlots);
+  t.lo = __ldg(tp + lane);
+  t.hi = __ldg(tp + 32 + lane);
+  if (NEG) {
+    t.blo = __ldg(tp + 64 + lane);
+    t.bhi = __ldg(tp + 96 + lane);
+  }
+}
+
+// The candidate's bitmap words 4*lane .. 4*lane+3 of the two halves of the item whose first
+// table word is `base` (table + item*256; the second half 128 words on): AND of its consecutive
+// pairs' table rows, OR the reversed pairs' AND with negative trends. Each step keeps the rows
+// of several terms of both halves in flight; a half stops loading once every word of it in the
+// warp is zero, and the walk stops when both are (long chains match no row of most ranges).
+template <bool NEG>
+__device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base, int lane,
+                                           uint4 (&out)[2]) {
   constexpr int kStep = NEG ? 2 : 4;  // terms per step (each one or two rows per half)
-  const uint32_t o = p.offsets[cand];
-  const int L = (int)(p.offsets[cand + 1] - o);
-  const uint32_t C = (uint32_t)p.C, S = p.stride;
-  // lane i holds column i and 32 + i, then the table-row offsets (words) of its consecutive
-  // pairs: fwd(i) = (c_i*C + c_{i+1}) * S (increasing), bwd(i) = (c_{i+1}*C + c_i) * S
-  const uint32_t c_lo = lane < L ? p.cols[o + lane] : 0u;
-  const uint32_t c_hi = lane + 32 < L ? p.cols[o + 32 + lane] : 0u;
-  const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
-  const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
-  const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
-  const uint32_t next_lo = lane == 31 ? h0 : n_lo;  // c_{i+1} for i = lane
-  const uint32_t fwd_lo = (L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo) * S;
-  const uint32_t fwd_hi = (c_hi * C + n_hi) * S;
-  const uint32_t bwd_lo = (next_lo * C + c_lo) * S, bwd_hi = (n_hi * C + c_hi) * S;
+  const int L = (int)__shfl_sync(0xFFFFFFFFu, t.hi, 31);
   const int n_terms = L == 1 ? 1 : L - 1;
   const bool two = NEG && L > 1;  // warp-uniform
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -131,8 +141,8 @@ __device__ __forceinline__ void pair_chain(const PairArgs& p, uint32_t cand,
     }
     return true;
   };
-  if (walk(fwd_lo, bwd_lo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
-    walk(fwd_hi, bwd_hi, 32, n_terms);
+  if (walk(t.lo, t.blo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
+    walk(t.hi, t.bhi, 32, n_terms);
   if (two) {
     x0 = make_uint4(x0.x | y0.x, x0.y | y0.y, x0.z | y0.z, x0.w | y0.w);
     x1 = make_uint4(x1.x | y1.x, x1.y | y1.y, x1.z | y1.z, x1.w | y1.w);
@@ -287,13 +297,29 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
   uint32_t* st = stage[warp];
-  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division
+  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
+  // the term list of the warp's next item is loaded while the current one is walked
   const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
+  uint64_t it = blockIdx.x;
   uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x, range += d_range, grp += d_grp,
-                range += grp >= n_groups ? 1u : 0u, grp -= grp >= n_groups ? n_groups : 0u) {
+  Terms next;
+  if (it < n_items && grp * kPairWarps + warp < p.n_cand)
+    load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
+  while (it < n_items) {
     const uint64_t rword = (uint64_t)range * kItemWords;  // first word of the item
-    if (OVERLAP && grp == 0) {  // the archive members' own row counts, once per range
+    const uint32_t cand = grp * kPairWarps + warp;
+    const uint32_t cur_grp = grp;
+    const Terms t = next;
+    it += gridDim.x;
+    range += d_range;
+    grp += d_grp;
+    if (grp >= n_groups) {
+      grp -= n_groups;
+      ++range;
+    }
+    if (it < n_items && grp * kPairWarps + warp < p.n_cand)
+      load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
+    if (OVERLAP && cur_grp == 0) {  // the archive members' own row counts, once per range
       for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
         const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
         const uint4 a0 = __ldg(reinterpret_cast<const uint4*>(ar));
@@ -302,10 +328,9 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
         if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
       }
     }
-    const uint32_t cand = grp * kPairWarps + warp;
     if (cand >= p.n_cand) continue;  // warp-uniform
     uint4 x[2];
-    pair_chain<NEG>(p, cand, p.table + rword + 4 * lane, lane, x);
+    pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
     const uint32_t c0 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[0]));
     const uint32_t c1 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[1]));
     if (lane == 0 && c0 + c1) atomicAdd(&p.counts[cand], c0 + c1);
