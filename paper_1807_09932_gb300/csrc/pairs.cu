@@ -170,57 +170,64 @@ __device__ __forceinline__ void add_pair(unsigned long long* ov2, int k, uint32_
     atomicAdd(&ov2[k], (unsigned long long)(r & 0xFFFFu) | ((unsigned long long)(r >> 16) << 32));
 }
 
-// Bitmap words and archive overlaps of candidate `cand` for the 128-word half at `rword`, from
-// its words x (lane holds words 4*lane .. 4*lane+3) and their warp total cnt.
+// Bitmap words and archive overlaps of candidate `cand` for the 256-word item at `rword`, from
+// its words x (lane holds words 4*lane .. 4*lane+3 of the first half in x[0] and 128 + the same
+// of the second half in x[1]) and their warp total cnt.
 template <bool BITMAPS, bool OVERLAP>
-__device__ __forceinline__ void half_epilogue(const PairArgs& p, uint32_t cand, uint64_t rword,
-                                              uint4 x, uint32_t cnt, uint32_t* st, int lane,
-                                              uint32_t n_arch, int n_pairs,
+__device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, uint64_t rword,
+                                              const uint4 (&x)[2], uint32_t cnt, uint32_t* st,
+                                              int lane, uint32_t n_arch, int n_pairs,
                                               uint64_t all_members) {
   if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
-    *reinterpret_cast<uint4*>(st + 4 * lane) = x;
-    __syncwarp();
     uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint64_t w = rword + 32 * j + lane;
-      if (w < (uint64_t)p.W) out[w] = st[32 * j + lane];
+    for (int h = 0; h < 2; ++h) {
+      *reinterpret_cast<uint4*>(st + 4 * lane) = x[h];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t w = rword + kRangeWords * h + 32 * j + lane;
+        if (w < (uint64_t)p.W) out[w] = st[32 * j + lane];
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
   if constexpr (OVERLAP) {
-    if (cnt == 0) return;  // warp-uniform: nothing of this range overlaps anything
+    if (cnt == 0) return;  // warp-uniform: nothing of this item overlaps anything
     const uint64_t members = p.score ? p.score[cand] & all_members : all_members;
     if (members == 0) return;
-    unsigned long long* ov2 =
-        reinterpret_cast<unsigned long long*>(p.overlaps + (uint64_t)cand * p.ov_stride);
     const uint32_t* abase = p.arch + rword;
-    const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
-    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, x.x != 0u);
-    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, x.y != 0u);
-    const uint32_t b2 = __ballot_sync(0xFFFFFFFFu, x.z != 0u);
-    const uint32_t b3 = __ballot_sync(0xFFFFFFFFu, x.w != 0u);
-    const int n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
-    const int nz = n0 + n1 + n2 + __popc(b3);
+    uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
+    // the lane's eight words and where they sit in the item
+    const uint32_t xw[8] = {x[0].x, x[0].y, x[0].z, x[0].w, x[1].x, x[1].y, x[1].z, x[1].w};
+    uint32_t bal[8];
+    int nz = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      bal[j] = __ballot_sync(0xFFFFFFFFu, xw[j] != 0u);
+      nz += __popc(bal[j]);
+    }
     if (nz <= 32) {
       // compact the non-zero words: lane i takes the i-th one (value and word offset)
       uint32_t* sv = st;
       uint32_t* si = st + 32;
       const uint32_t lt = (1u << lane) - 1u;
-      if (x.x) { const int q = __popc(b0 & lt); sv[q] = x.x; si[q] = 4 * lane; }
-      if (x.y) { const int q = n0 + __popc(b1 & lt); sv[q] = x.y; si[q] = 4 * lane + 1; }
-      if (x.z) { const int q = n0 + n1 + __popc(b2 & lt); sv[q] = x.z; si[q] = 4 * lane + 2; }
-      if (x.w) {
-        const int q = n0 + n1 + n2 + __popc(b3 & lt);
-        sv[q] = x.w;
-        si[q] = 4 * lane + 3;
+      int base = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (xw[j]) {
+          const int q = base + __popc(bal[j] & lt);
+          sv[q] = xw[j];
+          si[q] = (j < 4 ? 0u : (uint32_t)kRangeWords) + 4u * lane + (j & 3);
+        }
+        base += __popc(bal[j]);
       }
       __syncwarp();
       if (nz <= kFewWords) {
         // few non-zero words: a lane per archive member (two for members 32..63) walks them
         // all, gathering its member's word at each; no warp reduction, one atomic per member
         const bool a0 = (members >> lane) & 1ull;
-        const bool a1 = lane + 32 < 64 && ((members >> (lane + 32)) & 1ull);
+        const bool a1 = (members >> (lane + 32)) & 1ull;
         const uint32_t* ar0 = abase + (uint64_t)lane * p.stride;
         const uint32_t* ar1 = abase + (uint64_t)(lane + 32) * p.stride;
         uint32_t o0 = 0, o1 = 0;
@@ -231,28 +238,18 @@ __device__ __forceinline__ void half_epilogue(const PairArgs& p, uint32_t cand, 
           if (a1) o1 += __popc(v & __ldg(ar1 + w));
         }
         __syncwarp();
-        uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
         if (o0) atomicAdd(&ov[lane], o0);
         if (o1) atomicAdd(&ov[lane + 32], o1);
-      } else if (nz <= 16) {
-        // each half-warp holds the same (up to) 16 words; the low half takes member 2k and
-        // the high half member 2k+1 of each pair, one word and one popcount per lane
-        const int src = lane & 15;
-        const uint32_t mv = src < nz ? sv[src] : 0u;
-        const uint32_t* ab = abase + (src < nz ? si[src] : 0u) + (lane >= 16 ? p.stride : 0u);
-        const int sh = lane >= 16 ? 16 : 0;
-        __syncwarp();
-        for (int k = 0; k < n_pairs; ++k, ab += S2) {
-          if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
-          const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, __popc(mv & __ldg(ab)) << sh);
-          add_pair(ov2, k, r, lane);
-        }
       } else {
+        // a word per lane, two members per warp reduction (sums <= 1,024), one 64-bit atomic
+        // per member pair
+        unsigned long long* ov2 = reinterpret_cast<unsigned long long*>(ov);
+        const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
         const uint32_t mv = lane < nz ? sv[lane] : 0u;
         const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
         __syncwarp();
         for (int k = 0; k < n_pairs; ++k, ab += S2) {
-          if (((members >> (2 * k)) & 3ull) == 0) continue;
+          if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
           const uint32_t w0 = __ldg(ab), w1 = __ldg(ab + p.stride);
           const uint32_t r =
               __reduce_add_sync(0xFFFFFFFFu, __popc(mv & w0) + (__popc(mv & w1) << 16));
@@ -261,9 +258,8 @@ __device__ __forceinline__ void half_epilogue(const PairArgs& p, uint32_t cand, 
       }
     } else {
       // dense: the wanted members two at a time (no unwanted partner), one packed reduction
-      // (each sum <= 4,096), lanes 0 and 1 add the two totals
+      // (each sum <= 8,192), lanes 0 and 1 add the two totals
       const uint32_t* ab = abase + 4 * lane;
-      uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
       uint64_t mm = members;
       while (mm) {  // warp-uniform
         const int ma = __ffsll((long long)mm) - 1;
@@ -271,10 +267,13 @@ __device__ __forceinline__ void half_epilogue(const PairArgs& p, uint32_t cand, 
         const int mb = mm ? __ffsll((long long)mm) - 1 : ma;
         const bool has_b = mm != 0ull;
         mm &= mm - 1ull;
-        const uint4 wa = ld_arch4(ab + (uint64_t)ma * p.stride);
-        const uint4 wb = ld_arch4(ab + (uint64_t)mb * p.stride);
-        const uint32_t r = __reduce_add_sync(
-            0xFFFFFFFFu, popc4(and4(x, wa)) + (has_b ? popc4(and4(x, wb)) << 16 : 0u));
+        const uint32_t* pa = ab + (uint64_t)ma * p.stride;
+        const uint32_t* pb = ab + (uint64_t)mb * p.stride;
+        const uint4 wa0 = ld_arch4(pa), wa1 = ld_arch4(pa + kRangeWords);
+        const uint4 wb0 = ld_arch4(pb), wb1 = ld_arch4(pb + kRangeWords);
+        const uint32_t sa = popc4(and4(x[0], wa0)) + popc4(and4(x[1], wa1));
+        const uint32_t sb = has_b ? popc4(and4(x[0], wb0)) + popc4(and4(x[1], wb1)) : 0u;
+        const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, sa + (sb << 16));
         const uint32_t v = lane == 0 ? (r & 0xFFFFu) : (r >> 16);
         if (lane < 2 && v) atomicAdd(&ov[lane == 0 ? ma : mb], v);
       }
@@ -331,13 +330,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
     if (cand >= p.n_cand) continue;  // warp-uniform
     uint4 x[2];
     pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
-    const uint32_t c0 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[0]));
-    const uint32_t c1 = __reduce_add_sync(0xFFFFFFFFu, popc4(x[1]));
-    if (lane == 0 && c0 + c1) atomicAdd(&p.counts[cand], c0 + c1);
-    half_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x[0], c0, st, lane, n_arch, n_pairs,
+    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, popc4(x[0]) + popc4(x[1]));
+    if (lane == 0 && c) atomicAdd(&p.counts[cand], c);
+    item_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x, c, st, lane, n_arch, n_pairs,
                                     all_members);
-    half_epilogue<BITMAPS, OVERLAP>(p, cand, rword + kRangeWords, x[1], c1, st, lane, n_arch,
-                                    n_pairs, all_members);
   }
 }
 
