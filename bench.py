@@ -496,7 +496,7 @@ def roofline_pairs(pops, R, m, launch_ms, clk, peaks, fused, K):
     each read once) and its counts, plus the bitmaps it writes (unfused) or the padded archive
     rows it reads (fused), against the measured HBM copy bandwidth."""
     W = m.words
-    Wt = (W + 255) // 256 * 256
+    Wt = (W + 511) // 512 * 512
     per = []
     for c, o in pops:
         pairs = set()

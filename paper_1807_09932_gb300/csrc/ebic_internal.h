@@ -126,7 +126,7 @@ cudaError_t launch_eval_w16v2(const EvalConfig&, const CUtensorMap*, const EvalA
 cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 
 // ---- pair-table evaluation (optionally with the archive overlaps fused in) -----------------
-constexpr int kPairRangeWords = 256;  // table and padded archive row strides are multiples
+constexpr int kPairRangeWords = 512;  // table and padded archive row strides are multiples
 constexpr int kPairMaxArch = 64;      // archive members the fused overlap pass takes
 // Row stride (words) of the pair table and of padded archive bitmaps for W-word bitmaps.
 inline int64_t pair_stride(int64_t words) {

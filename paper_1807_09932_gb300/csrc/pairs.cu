@@ -15,28 +15,30 @@
 //   L = 1:      T[c_1*C + c_1]
 // so a candidate costs one 32-bit AND per 32 rows per column, streamed from the table.
 //
-// Table rows are stored with a stride of ceil(W / 256) * 256 words whose padding words are zero,
-// so a lane reads four consecutive words of each 128-word half of an item with one 16-byte load
+// Table rows are stored with a stride of ceil(W / 512) * 512 words whose padding words are zero,
+// so a lane reads four consecutive words of each 128-word part of an item with one 16-byte load
 // and never tests a bound: a padding word ANDs to zero and counts nothing.
 //
-// Work order: items are (range of 256 words = 8,192 rows, group of 24 candidates), taken
+// Work order: items are (range of 512 words = 16,384 rows, group of 24 candidates), taken
 // round-robin by a persistent grid in range-major order, so all CTAs work on the same few row
 // ranges at a time and the table rows of those ranges stay in L2 while every candidate reads
 // them; each table word comes from HBM about once per evaluation. Each warp takes one candidate
-// of its item: it reads the column list once (a lane per column), turns it into the table rows
-// of the consecutive pairs (a lane per pair), and walks the chain four pairs at a time, each step
-// keeping eight 512-byte warp loads in flight (four pairs x two halves; with negative trends two
-// pairs, both orders). A half stops loading once all its words are zero and the walk stops when
-// both are: long chains match no row of most ranges.
+// of its item. The preparation kernel has already turned the candidate into its term list (the
+// table-row offsets of its consecutive pairs), which the warp loads while it walks its previous
+// item. The chain goes two pairs per step, each step keeping eight 512-byte warp loads in flight
+// (two pairs x four parts; with negative trends one pair, both orders). A part stops loading
+// once all its words are zero and the walk stops when all are: long chains match no row of
+// most ranges. Larger items amortise the per-item work (the term list, the reductions and
+// atomics of the epilogue) over more rows.
 //
 // Fused overlaps (the fitness's o(c, a) = popcount(M_c & M_a), Methods, "Handling missing
 // values" and the archive rule of the fitness): the warp that has just built a candidate's words
-// of a half ANDs them with the archive members' words of the same rows (archive rows padded to
-// the same stride) and adds the popcounts, so candidate bitmaps never go through HBM. Halves
+// of an item ANDs them with the archive members' words of the same rows (archive rows padded to
+// the same stride) and adds the popcounts, so candidate bitmaps never go through HBM. Items
 // where the candidate matches no row are skipped, and so are archive members that the caller
 // does not need (those sharing no column with the candidate cannot penalise it). By the number
-// of non-zero words in the half: up to 12 are walked by a lane per member (no reductions); up
-// to 32 are compacted to one per lane and members go two per warp reduction; denser halves
+// of non-zero words in the item: up to 12 are walked by a lane per member (no reductions); up
+// to 32 are compacted to one per lane and members go two per warp reduction; denser items
 // take the wanted members two at a time over all words.
 #include "device_common.cuh"
 #include "ebic_internal.h"
@@ -46,8 +48,11 @@ namespace {
 
 constexpr int kPairThreads = 768;
 constexpr int kPairWarps = kPairThreads / 32;
-constexpr int kItemWords = kPairRangeWords;  // words per item: two halves of four per lane
-constexpr int kRangeWords = kItemWords / 2;  // words per half (4,096 rows)
+constexpr int kParts = 4;        // 128-word parts per item (four words per lane each)
+constexpr int kStepTerms = 2;    // terms per chain step (one with negative trends)
+constexpr int kRangeWords = 128;             // words per part (4,096 rows)
+constexpr int kItemWords = kParts * kRangeWords;
+static_assert(kPairRangeWords % kItemWords == 0, "table stride must hold whole items");
 constexpr int kFewWords = 12;  // at most this many non-zero words: a lane per archive member
 
 __device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
@@ -61,11 +66,6 @@ __device__ __forceinline__ uint32_t popc4(uint4 v) {
   return __popc(s) + 2u * __popc(c) + __popc(v.w);
 }
 
-// The candidate's bitmap words 4*lane .. 4*lane+3 of the two halves of the item whose first
-// table word is `base` (table + item*256; the second half 128 words on): AND of its consecutive
-// pairs' table rows, OR the reversed pairs' AND with negative trends. Each step keeps the rows
-// of several terms of both halves in flight; a half stops loading once every word of it in the
-// warp is zero, and the walk stops when both are (long chains match no row of most ranges).
 // One candidate's term list as the warp holds it: lane i has the row offsets of terms i and
 // 32 + i (forward; reversed in blo/bhi), lane 31's hi word is the length L.
 struct Terms {
@@ -84,72 +84,75 @@ __device__ __forceinline__ void load_terms(const PairArgs& p, uint32_t cand, int
   }
 }
 
-// The candidate's bitmap words 4*lane .. 4*lane+3 of the two halves of the item whose first
-// table word is `base` (table + item*256; the second half 128 words on): AND of its consecutive
-// pairs' table rows, OR the reversed pairs' AND with negative trends. Each step keeps the rows
-// of several terms of both halves in flight; a half stops loading once every word of it in the
-// warp is zero, and the walk stops when both are (long chains match no row of most ranges).
+// The candidate's bitmap words 4*lane .. 4*lane+3 of each 128-word part of the item whose first
+// table word is `base` (table + item*kItemWords): AND of its consecutive pairs' table rows, OR
+// the reversed pairs' AND with negative trends. Each step keeps the rows of several terms of
+// every part in flight; a part stops loading once every word of it in the warp is zero, and the
+// walk stops when all are (long chains match no row of most ranges).
 template <bool NEG>
 __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base, int lane,
-                                           uint4 (&out)[2]) {
-  constexpr int kStep = NEG ? 2 : 4;  // terms per step (each one or two rows per half)
+                                           uint4 (&out)[kParts]) {
+  constexpr int kStep = NEG ? kStepTerms / 2 : kStepTerms;
   const int L = (int)__shfl_sync(0xFFFFFFFFu, t.hi, 31);
   const int n_terms = L == 1 ? 1 : L - 1;
   const bool two = NEG && L > 1;  // warp-uniform
   const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
-  uint4 x0 = ones, x1 = ones, y0 = ones, y1 = ones;
-  bool live0 = true, live1 = true;  // warp-uniform: the half still has a non-zero word
+  uint4 x[kParts], y[kParts];
+  bool live[kParts];  // warp-uniform: the part still has a non-zero word
+#pragma unroll
+  for (int q = 0; q < kParts; ++q) {
+    x[q] = y[q] = ones;
+    live[q] = true;
+  }
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
   auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
     for (int i0 = t0; i0 < t1; i0 += kStep) {
-      uint4 v0[kStep], v1[kStep], u0[kStep], u1[kStep];
+      uint4 v[kStep][kParts], u[kStep][kParts];
 #pragma unroll
       for (int k = 0; k < kStep; ++k) {
         const int i = i0 + k;
-        v0[k] = v1[k] = u0[k] = u1[k] = ones;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q) v[k][q] = u[k][q] = ones;
         if (i < t1) {  // warp-uniform
           const uint32_t* rf = base + __shfl_sync(0xFFFFFFFFu, offf, i & 31);
-          if (live0) v0[k] = __ldg(reinterpret_cast<const uint4*>(rf));
-          if (live1) v1[k] = __ldg(reinterpret_cast<const uint4*>(rf + kRangeWords));
+#pragma unroll
+          for (int q = 0; q < kParts; ++q)
+            if (live[q]) v[k][q] = __ldg(reinterpret_cast<const uint4*>(rf + q * kRangeWords));
           if (two) {
             const uint32_t* rb = base + __shfl_sync(0xFFFFFFFFu, offb, i & 31);
-            if (live0) u0[k] = __ldg(reinterpret_cast<const uint4*>(rb));
-            if (live1) u1[k] = __ldg(reinterpret_cast<const uint4*>(rb + kRangeWords));
+#pragma unroll
+            for (int q = 0; q < kParts; ++q)
+              if (live[q]) u[k][q] = __ldg(reinterpret_cast<const uint4*>(rb + q * kRangeWords));
           }
         }
       }
+      bool any_live = false;
 #pragma unroll
-      for (int k = 0; k < kStep; ++k) {
-        x0 = and4(x0, v0[k]);
-        x1 = and4(x1, v1[k]);
-      }
-      uint32_t any0 = x0.x | x0.y | x0.z | x0.w, any1 = x1.x | x1.y | x1.z | x1.w;
-      if (NEG) {
+      for (int q = 0; q < kParts; ++q) {
 #pragma unroll
-        for (int k = 0; k < kStep; ++k) {
-          y0 = and4(y0, u0[k]);
-          y1 = and4(y1, u1[k]);
+        for (int k = 0; k < kStep; ++k) x[q] = and4(x[q], v[k][q]);
+        uint32_t any = x[q].x | x[q].y | x[q].z | x[q].w;
+        if (NEG) {
+#pragma unroll
+          for (int k = 0; k < kStep; ++k) y[q] = and4(y[q], u[k][q]);
+          if (two) any |= y[q].x | y[q].y | y[q].z | y[q].w;
         }
-        if (two) {
-          any0 |= y0.x | y0.y | y0.z | y0.w;
-          any1 |= y1.x | y1.y | y1.z | y1.w;
-        }
+        live[q] = __any_sync(0xFFFFFFFFu, any != 0u);
+        any_live |= live[q];
       }
-      live0 = __any_sync(0xFFFFFFFFu, any0 != 0u);
-      live1 = __any_sync(0xFFFFFFFFu, any1 != 0u);
-      if (!live0 && !live1) return false;  // all zero from here on
+      if (!any_live) return false;  // all zero from here on
     }
     return true;
   };
   if (walk(t.lo, t.blo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
     walk(t.hi, t.bhi, 32, n_terms);
-  if (two) {
-    x0 = make_uint4(x0.x | y0.x, x0.y | y0.y, x0.z | y0.z, x0.w | y0.w);
-    x1 = make_uint4(x1.x | y1.x, x1.y | y1.y, x1.z | y1.z, x1.w | y1.w);
+#pragma unroll
+  for (int q = 0; q < kParts; ++q) {
+    if (two) x[q] = make_uint4(x[q].x | y[q].x, x[q].y | y[q].y, x[q].z | y[q].z,
+                               x[q].w | y[q].w);
+    // a part that went all-zero stays zero (its remaining terms were not loaded)
+    out[q] = live[q] ? x[q] : make_uint4(0u, 0u, 0u, 0u);
   }
-  // a half that went all-zero stays zero (its remaining terms were not loaded)
-  out[0] = live0 ? x0 : make_uint4(0u, 0u, 0u, 0u);
-  out[1] = live1 ? x1 : make_uint4(0u, 0u, 0u, 0u);
 }
 
 // An archive row segment: re-read by every warp of the CTA that scores a candidate of the same
@@ -170,18 +173,18 @@ __device__ __forceinline__ void add_pair(unsigned long long* ov2, int k, uint32_
     atomicAdd(&ov2[k], (unsigned long long)(r & 0xFFFFu) | ((unsigned long long)(r >> 16) << 32));
 }
 
-// Bitmap words and archive overlaps of candidate `cand` for the 256-word item at `rword`, from
-// its words x (lane holds words 4*lane .. 4*lane+3 of the first half in x[0] and 128 + the same
-// of the second half in x[1]) and their warp total cnt.
+// Bitmap words and archive overlaps of candidate `cand` for the item at `rword`, from its words
+// x (lane holds words 4*lane .. 4*lane+3 of part q, i.e. item words 128q + 4*lane + j, in x[q])
+// and their warp total cnt.
 template <bool BITMAPS, bool OVERLAP>
 __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, uint64_t rword,
-                                              const uint4 (&x)[2], uint32_t cnt, uint32_t* st,
+                                              const uint4 (&x)[kParts], uint32_t cnt, uint32_t* st,
                                               int lane, uint32_t n_arch, int n_pairs,
                                               uint64_t all_members) {
   if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
     uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kParts; ++h) {
       *reinterpret_cast<uint4*>(st + 4 * lane) = x[h];
       __syncwarp();
 #pragma unroll
@@ -199,11 +202,18 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
     const uint32_t* abase = p.arch + rword;
     uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
     // the lane's eight words and where they sit in the item
-    const uint32_t xw[8] = {x[0].x, x[0].y, x[0].z, x[0].w, x[1].x, x[1].y, x[1].z, x[1].w};
-    uint32_t bal[8];
+    uint32_t xw[4 * kParts];
+#pragma unroll
+    for (int q = 0; q < kParts; ++q) {
+      xw[4 * q] = x[q].x;
+      xw[4 * q + 1] = x[q].y;
+      xw[4 * q + 2] = x[q].z;
+      xw[4 * q + 3] = x[q].w;
+    }
+    uint32_t bal[4 * kParts];
     int nz = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4 * kParts; ++j) {
       bal[j] = __ballot_sync(0xFFFFFFFFu, xw[j] != 0u);
       nz += __popc(bal[j]);
     }
@@ -214,11 +224,11 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
       const uint32_t lt = (1u << lane) - 1u;
       int base = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 4 * kParts; ++j) {
         if (xw[j]) {
           const int q = base + __popc(bal[j] & lt);
           sv[q] = xw[j];
-          si[q] = (j < 4 ? 0u : (uint32_t)kRangeWords) + 4u * lane + (j & 3);
+          si[q] = (uint32_t)(kRangeWords * (j / 4)) + 4u * lane + (j & 3);
         }
         base += __popc(bal[j]);
       }
@@ -258,7 +268,7 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
       }
     } else {
       // dense: the wanted members two at a time (no unwanted partner), one packed reduction
-      // (each sum <= 8,192), lanes 0 and 1 add the two totals
+      // (each sum <= 128 * 4 * kParts * 32 / 4 < 2^16), lanes 0 and 1 add the two totals
       const uint32_t* ab = abase + 4 * lane;
       uint64_t mm = members;
       while (mm) {  // warp-uniform
@@ -269,10 +279,13 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
         mm &= mm - 1ull;
         const uint32_t* pa = ab + (uint64_t)ma * p.stride;
         const uint32_t* pb = ab + (uint64_t)mb * p.stride;
-        const uint4 wa0 = ld_arch4(pa), wa1 = ld_arch4(pa + kRangeWords);
-        const uint4 wb0 = ld_arch4(pb), wb1 = ld_arch4(pb + kRangeWords);
-        const uint32_t sa = popc4(and4(x[0], wa0)) + popc4(and4(x[1], wa1));
-        const uint32_t sb = has_b ? popc4(and4(x[0], wb0)) + popc4(and4(x[1], wb1)) : 0u;
+        uint32_t sa = 0, sb = 0;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q) {
+          sa += popc4(and4(x[q], ld_arch4(pa + q * kRangeWords)));
+          sb += popc4(and4(x[q], ld_arch4(pb + q * kRangeWords)));
+        }
+        if (!has_b) sb = 0u;
         const uint32_t r = __reduce_add_sync(0xFFFFFFFFu, sa + (sb << 16));
         const uint32_t v = lane == 0 ? (r & 0xFFFFu) : (r >> 16);
         if (lane < 2 && v) atomicAdd(&ov[lane == 0 ? ma : mb], v);
@@ -321,16 +334,21 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
     if (OVERLAP && cur_grp == 0) {  // the archive members' own row counts, once per range
       for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
         const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
-        const uint4 a0 = __ldg(reinterpret_cast<const uint4*>(ar));
-        const uint4 a1 = __ldg(reinterpret_cast<const uint4*>(ar + kRangeWords));
-        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, popc4(a0) + popc4(a1));
+        uint32_t pa = 0;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q)
+          pa += popc4(__ldg(reinterpret_cast<const uint4*>(ar + q * kRangeWords)));
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, pa);
         if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
       }
     }
     if (cand >= p.n_cand) continue;  // warp-uniform
-    uint4 x[2];
+    uint4 x[kParts];
     pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
-    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, popc4(x[0]) + popc4(x[1]));
+    uint32_t pc = 0;
+#pragma unroll
+    for (int q = 0; q < kParts; ++q) pc += popc4(x[q]);
+    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
     if (lane == 0 && c) atomicAdd(&p.counts[cand], c);
     item_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x, c, st, lane, n_arch, n_pairs,
                                     all_members);
