@@ -798,9 +798,6 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
                 "a candidate list must have its columns and offsets in the same memory");
 
   Scratch sc(s);
-  uint32_t* err = nullptr;
-  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
-  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
   const uint16_t *dcols = nullptr, *dacols = nullptr;
   const uint32_t *doffs = nullptr, *daoffs = nullptr, *dabm = nullptr;
   EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
@@ -811,26 +808,42 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(to_device(arch_bitmaps, (size_t)n_arch * L.words, dev, sc, &dabm));
   }
   bool counts_host = false, bm_host = false, fit_host = false;
-  uint32_t *dcounts = nullptr, *dbm = nullptr, *dov = nullptr, *dpad = nullptr,
-           *darch_counts = nullptr;
-  uint64_t *dfit = nullptr, *dshare = nullptr;
-  // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
-  const uint32_t ov_stride = (n_arch + 1u) & ~1u;
-  const uint32_t stride = m->pair_stride;
+  uint32_t *dcounts = nullptr, *dbm = nullptr;
+  uint64_t* dfit = nullptr;
   EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
   if (bitmaps)
     EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm, &bm_host));
   EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
-  if (n_arch > 0) {
-    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dov), (size_t)n_cand * ov_stride * 4));
-    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dpad), (size_t)ov_stride * stride * 4));
-    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&darch_counts), (size_t)n_arch * 4));
-    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dshare), (size_t)n_cand * 8));
-  }
+
+  // the call's working buffers, carved from one stream-ordered allocation; none needs zeroing
+  // before the preparation kernel (it writes every word the later kernels read)
   const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
-  uint32_t* dterms = nullptr;
-  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dterms),
-                     (size_t)n_cand * term_slots(neg) * sizeof(uint32_t)));
+  // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
+  const uint32_t ov_stride = (n_arch + 1u) & ~1u;
+  const uint32_t stride = m->pair_stride;
+  const uint32_t prep_blocks = fused_prepare_blocks(n_cand, n_arch, stride, m->num_sms);
+  size_t total = 0;
+  auto carve = [&total](size_t bytes) {
+    const size_t off = total;
+    total += (bytes + 255) & ~(size_t)255;
+    return off;
+  };
+  const size_t o_err = carve(sizeof(uint32_t));
+  const size_t o_flags = carve((size_t)prep_blocks * 4);
+  const size_t o_terms = carve((size_t)n_cand * term_slots(neg) * 4);
+  const size_t o_ov = carve(n_arch ? (size_t)n_cand * ov_stride * 4 : 0);
+  const size_t o_pad = carve(n_arch ? (size_t)ov_stride * stride * 4 : 0);
+  const size_t o_acnt = carve((size_t)n_arch * 4);
+  const size_t o_share = carve(n_arch ? (size_t)n_cand * 8 : 0);
+  char* work = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&work), total));
+  uint32_t* err = reinterpret_cast<uint32_t*>(work + o_err);
+  uint32_t* dflags = reinterpret_cast<uint32_t*>(work + o_flags);
+  uint32_t* dterms = reinterpret_cast<uint32_t*>(work + o_terms);
+  uint32_t* dov = n_arch ? reinterpret_cast<uint32_t*>(work + o_ov) : nullptr;
+  uint32_t* dpad = n_arch ? reinterpret_cast<uint32_t*>(work + o_pad) : nullptr;
+  uint32_t* darch_counts = n_arch ? reinterpret_cast<uint32_t*>(work + o_acnt) : nullptr;
+  uint64_t* dshare = n_arch ? reinterpret_cast<uint64_t*>(work + o_share) : nullptr;
   {
     Timed t(EBIC_TIMING_PREPARE, s);
     FusedPrepareArgs pa;
@@ -853,9 +866,9 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     pa.share = dshare;
     pa.terms = dterms;
     pa.negative = neg;
-    pa.err = err;
+    pa.flags = dflags;
     pa.status = m->status;
-    EBIC_CUDA(launch_fused_prepare(pa, m->num_sms, s));
+    EBIC_CUDA(launch_fused_prepare(pa, prep_blocks, s));
   }
   {
     Timed t(EBIC_TIMING_PAIR_EVALUATE, s);
@@ -874,8 +887,9 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.overlaps = dov;
     p.ov_stride = ov_stride;
     p.arch_counts = darch_counts;
-    p.err = err;
-    p.err_out = err;
+    p.flags = dflags;
+    p.n_flags = prep_blocks;
+    p.err_out = err;  // CTA 0 stores the OR of the flags here for the finalize and the host
     p.status = m->status;
     EBIC_CUDA(launch_pair_eval(p, neg, m->num_sms, !timing_on(), s));
   }

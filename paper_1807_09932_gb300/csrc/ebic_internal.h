@@ -156,8 +156,10 @@ struct PairArgs {
   uint32_t* overlaps = nullptr;      // [n_cand][ov_stride], zeroed before the launch
   uint32_t ov_stride = 0;            // n_arch rounded up to even (pairs of counters, 8-byte aligned)
   uint32_t* arch_counts = nullptr;   // [n_arch], zeroed before the launch
-  const uint32_t* err = nullptr;     // non-zero: do nothing
-  uint32_t* err_out = nullptr;       // where a timeout is reported (per call)
+  const uint32_t* err = nullptr;     // non-zero: do nothing (when flags is null)
+  const uint32_t* flags = nullptr;   // else: the preparation's block flags; any non-zero: do
+  uint32_t n_flags = 0;              // nothing, and CTA 0 stores their OR in *err_out
+  uint32_t* err_out = nullptr;       // the call's error word
   uint32_t* status = nullptr;        // matrix status word
   uint64_t timeout_ns = 1000000000ull;  // limit of each wait for staged table rows
 };
@@ -191,10 +193,12 @@ struct FusedPrepareArgs {
   uint64_t* share = nullptr;
   uint32_t* terms = nullptr;           // [n_cand][term_slots(negative)]
   bool negative = false;
-  uint32_t* err = nullptr;
+  uint32_t* flags = nullptr;           // [blocks]: each block stores kErrInvalid or 0
   uint32_t* status = nullptr;
 };
-cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStream_t s);
+// Blocks of the fused preparation launch (and so the number of its flags).
+uint32_t fused_prepare_blocks(uint32_t n_cand, uint32_t n_arch, uint32_t stride, int num_sms);
+cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, uint32_t blocks, cudaStream_t s);
 // F_c from counts, overlaps and the share masks of the fused preparation.
 cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
                                   const uint32_t* arch_offsets, uint32_t n_arch,

@@ -239,7 +239,12 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
     for (uint32_t i = gw; i < na; i += nwarps)
       bad |= check_candidate_span(a.acols, aoff_s[i], aoff_s[i + 1], atotal, i == 0, a.ncols,
                                   sets[warp], lane);
-  if (lane == 0) report_invalid(bad, a.err, a.status);
+  // the block's verdict, stored (not accumulated) in its own flag: nothing needs zeroing first
+  const bool block_bad = __syncthreads_or(bad) != 0;
+  if (threadIdx.x == 0) {
+    a.flags[blockIdx.x] = block_bad ? kErrInvalid : 0u;
+    if (block_bad && a.status) atomicOr(a.status, kErrInvalid);
+  }
 }
 
 // F_c for the fused pass: a warp per candidate, a lane per archive member; the share masks of the
@@ -460,17 +465,21 @@ cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, int num_sms, cudaStream_t s) {
-  if (a.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
-  size_t blocks = (a.n_cand + kPrepWarps - 1) / kPrepWarps;
-  const size_t cb = ((size_t)(a.n_arch + 1) * a.stride + kPrepWarps * 32 * 8 - 1) /
+uint32_t fused_prepare_blocks(uint32_t n_cand, uint32_t n_arch, uint32_t stride, int num_sms) {
+  size_t blocks = (n_cand + kPrepWarps - 1) / kPrepWarps;
+  const size_t cb = ((size_t)(n_arch + 1) * stride + kPrepWarps * 32 * 8 - 1) /
                     (kPrepWarps * 32 * 8);
   blocks = blocks > cb ? blocks : cb;
   const size_t cap = (size_t)(num_sms > 0 ? num_sms : 1) * 8;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
+  return (uint32_t)blocks;
+}
+
+cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, uint32_t blocks, cudaStream_t s) {
+  if (a.n_arch > (uint32_t)kPairMaxArch) return cudaErrorInvalidValue;
   count_launch();
-  fused_prepare_kernel<<<(unsigned)blocks, kPrepWarps * 32, 0, s>>>(a);
+  fused_prepare_kernel<<<blocks, kPrepWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -300,8 +300,16 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
   dev::pdl_wait();     // the preparation (checks, zeroed outputs) is complete and visible
   dev::pdl_trigger();  // the finalize launch may be scheduled now; it waits for this grid itself
-  if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) return;  // invalid input
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (p.flags) {  // the preparation's per-block verdicts; CTA 0 records the call's error word
+    uint32_t f = 0;
+    for (uint32_t i = lane; i < p.n_flags; i += 32) f |= p.flags[i];
+    f = __reduce_or_sync(0xFFFFFFFFu, f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.err_out = f;
+    if (f) return;  // invalid input
+  } else if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) {
+    return;  // invalid input
+  }
   const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
   const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
   const uint64_t n_items = (uint64_t)n_ranges * n_groups;
