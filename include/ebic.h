@@ -280,8 +280,9 @@ int ebic_batch_free(ebic_batch* b);
  * n << (min(L,33)-1). A candidate enters the archive unless a member sharing a column overlaps
  * it by more than overlap_threshold x its row count without being strictly worse; strictly worse
  * members it overlaps that much are replaced by it.
- * Each generation the population is scored with ebic_eval_population and ebic_fitness against
- * the current archive (device-resident rank matrix, bitmaps and archive).
+ * Each generation the population is scored with ebic_eval_fitness against the current archive
+ * (device-resident rank matrix, bitmaps and archive); when the matrix has a pair table
+ * (ebic_matrix_build_pairs) that is one fused pass. Results do not depend on the table.
  */
 typedef struct ebic_params {
   uint32_t population;       /* candidates per generation (default 1600)                      */

@@ -445,10 +445,11 @@ struct GpuEvaluator : Evaluator {
     pop_offs = offs;
     GA_CUDA(cudaMemcpyAsync(dcols, cols.data(), cols.size() * 2, cudaMemcpyHostToDevice, s));
     GA_CUDA(cudaMemcpyAsync(doffs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, s));
-    int rc = ebic_eval_population(m, dcols, doffs, n, flags, dcounts, dbm, s);
-    if (rc != EBIC_OK) return rc;
-    rc = ebic_fitness(m, dcols, doffs, n, dcounts, dbm, acols, aoffs, abm, n_arch, 0, dfit,
-                      n_arch ? dov : nullptr, s);
+    // one generation's scoring in one call: with a pair table on the matrix, the evaluation and
+    // the archive overlaps run as one pass (the bitmaps are still written: the archive update
+    // needs the offered candidates' rows)
+    int rc = ebic_eval_fitness(m, dcols, doffs, n, flags, acols, aoffs, abm, n_arch, dcounts, dbm,
+                               dfit, n_arch ? dov : nullptr, s);
     if (rc != EBIC_OK) return rc;
     GA_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
     GA_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n * 8, cudaMemcpyDeviceToHost, s));

@@ -116,15 +116,19 @@ def test_callback_failure_is_reported():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("negative", [False, True])
-def test_gpu_run_equals_oracle_run(negative):
-    """The GPU-scored loop and the oracle-scored loop take identical decisions."""
+def test_gpu_run_equals_oracle_run(negative, pairs):
+    """The GPU-scored loop and the oracle-scored loop take identical decisions, with the
+    rank-code evaluator and with the fused pair-table pass."""
     ebic = _ebic()
     ds = _small(seed=8)
     flags = ebic.EBIC_NEGATIVE_TRENDS if negative else 0
     params = _params(ebic, flags=flags, generations=10)
     ref, _ = _run_oracle(ebic, ds, params, negative=negative)
     with ebic.Matrix(ds.X) as m:
+        if pairs:
+            m.build_pairs()
         got = ebic.ebic_run(m.handle, params)
     assert got["members"] == ref["members"]
     assert np.array_equal(got["counts"], ref["counts"])
