@@ -342,6 +342,49 @@ int ebic_run_custom(int64_t rows, int32_t cols, const ebic_params* p, const ebic
 
 int ebic_free_result(ebic_result* r);
 
+/* ---- text input and bicluster output ---------------------------------------------------- */
+/*
+ * A matrix read from a delimited text file (arXiv 1807.09932, Methods, "Different input file
+ * formats support"): values separated by commas, tabs or semicolons; a header row of column
+ * names and a first column of row names are optional; with both, the upper-left (corner) field
+ * may be absent (R's write.table layout). Quotes around names are dropped.
+ *   values      [rows][cols] row-major float32; missing values are NaN
+ *   row_names   [rows] NUL-terminated strings, or NULL when the file has no row names
+ *   col_names   [cols], or NULL when the file has no header row
+ */
+typedef struct ebic_text_matrix {
+  float* values;
+  int64_t rows;
+  int32_t cols;
+  char** row_names;
+  char** col_names;
+} ebic_text_matrix;
+
+/*
+ * Read `path`. delimiter: ',', '\t', ';' or 0 to take the one most frequent in the first line.
+ * missing: a marker of missing values (Methods, "Handling missing values": "replaced with a
+ * predefined value (e.g. 0 or 999)"), compared as a number when it parses as one, else as text;
+ * or NULL. Empty fields and NA / NaN are missing too. Missing cells are NaN, so the evaluator's
+ * EBIC_EXCLUDE_MISSING applies to them. A header row is recognised by a field that is neither a
+ * number nor missing; a row-name column likewise in the first data row. Returns
+ * EBIC_ERR_INVALID_ARG (message with the line and column) for a row with another number of
+ * fields or a cell that is not a number. *out is freed with ebic_free_text_matrix.
+ */
+int ebic_read_matrix_text(const char* path, char delimiter, const char* missing,
+                          ebic_text_matrix** out);
+int ebic_free_text_matrix(ebic_text_matrix* m);
+
+/*
+ * Write the archive of an ebic_run result (Methods, "Compatibility with R and Bioconductor")
+ * in the layout of the biclust package's bicluster result files: a title line, then for each
+ * member a line "rows cols", a line of its row names and a line of its column names (in the
+ * member's column order), separated by spaces. Names come from `names` (the matrix the run was
+ * on, as read by ebic_read_matrix_text) or, where it has none or names is NULL, are 1-based
+ * indices. The result must carry bitmaps (ebic_run's does).
+ */
+int ebic_write_biclusters(const char* path, const char* title, const ebic_result* r,
+                          const ebic_text_matrix* names);
+
 /* ---- diagnostics ----------------------------------------------------------------------- */
 /* Kernels launched by this library in this process so far (every launch is counted). */
 int64_t ebic_launch_count(void);

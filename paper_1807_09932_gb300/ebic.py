@@ -95,6 +95,12 @@ class EbicResult(ctypes.Structure):
                 ("generations_run", ctypes.c_uint32), ("candidates_evaluated", ctypes.c_uint64)]
 
 
+class EbicTextMatrix(ctypes.Structure):
+    _fields_ = [("values", ctypes.POINTER(ctypes.c_float)), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int32), ("row_names", ctypes.POINTER(ctypes.c_char_p)),
+                ("col_names", ctypes.POINTER(ctypes.c_char_p))]
+
+
 EVALUATE_FN = ctypes.CFUNCTYPE(ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint16),
                                ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
                                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
@@ -127,6 +133,12 @@ _lib_run_custom = _sig("ebic_run_custom", [_I64, _I32, ctypes.POINTER(EbicParams
                                            ctypes.POINTER(EbicEvaluator),
                                            ctypes.POINTER(ctypes.POINTER(EbicResult))])
 _lib_free_result = _sig("ebic_free_result", [ctypes.POINTER(EbicResult)])
+_lib_read_text = _sig("ebic_read_matrix_text", [ctypes.c_char_p, ctypes.c_char, ctypes.c_char_p,
+                                                ctypes.POINTER(ctypes.POINTER(EbicTextMatrix))])
+_lib_free_text = _sig("ebic_free_text_matrix", [ctypes.POINTER(EbicTextMatrix)])
+_lib_write_bic = _sig("ebic_write_biclusters", [ctypes.c_char_p, ctypes.c_char_p,
+                                                ctypes.POINTER(EbicResult),
+                                                ctypes.POINTER(EbicTextMatrix)])
 
 
 class EbicError(RuntimeError):
@@ -467,3 +479,87 @@ def eval_fitness(m: Matrix, cols, offsets, arch_cols, arch_offsets, arch_bitmaps
                            arch_bitmaps, k, counts, bitmaps, fit, overlaps, stream)
     _check(rc, "ebic_eval_fitness")
     return counts, bitmaps, fit, overlaps
+
+
+# ---- text input and bicluster output ------------------------------------------------------------
+
+def ebic_read_matrix_text(path, delimiter, missing, out):
+    """out: a ctypes.POINTER(EbicTextMatrix) receiving the matrix (see TextMatrix)."""
+    return _lib_read_text(path, delimiter, missing, ctypes.byref(out))
+
+
+def ebic_free_text_matrix(m):
+    return _lib_free_text(m)
+
+
+def ebic_write_biclusters(path, title, result, names):
+    """result: an EbicResult (by pointer or byref); names: a POINTER(EbicTextMatrix) or None."""
+    return _lib_write_bic(path, title, result, names)
+
+
+class TextMatrix:
+    """A matrix read by ebic_read_matrix_text: values (float32 numpy [rows][cols], NaN where
+    missing), row_names and col_names (lists of str, or None). Keep it open while writing results
+    with its names; close() (or a with-block) frees the library's copy."""
+
+    def __init__(self, path, delimiter=None, missing=None):
+        self._p = None
+        d = b"\0" if delimiter is None else str(delimiter).encode()
+        if len(d) != 1:
+            raise ValueError("delimiter must be one character")
+        self._p = ctypes.POINTER(EbicTextMatrix)()
+        _check(_lib_read_text(os.fsencode(path), d,
+                              None if missing is None else str(missing).encode(),
+                              ctypes.byref(self._p)), "ebic_read_matrix_text")
+        t = self._p.contents
+        self.rows, self.cols = int(t.rows), int(t.cols)
+        self.values = np.ctypeslib.as_array(t.values, (self.rows * self.cols,)) \
+            .reshape(self.rows, self.cols).copy()
+        self.row_names = [t.row_names[i].decode() for i in range(self.rows)] \
+            if bool(t.row_names) else None
+        self.col_names = [t.col_names[i].decode() for i in range(self.cols)] \
+            if bool(t.col_names) else None
+
+    def close(self):
+        if getattr(self, "_p", None):
+            _lib_free_text(self._p)
+            self._p = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()
+
+
+def read_matrix_text(path, delimiter=None, missing=None):
+    """(values, row_names, col_names) of a delimited text matrix; see ebic_read_matrix_text."""
+    with TextMatrix(path, delimiter, missing) as t:
+        return t.values, t.row_names, t.col_names
+
+
+def write_biclusters(path, result, rows, names=None, title="EBIC"):
+    """Write an ebic_run result dict (members, counts, bitmaps) in the biclust result-file
+    layout; `rows` is the matrix's row count, `names` an open TextMatrix or None."""
+    n = len(result["members"])
+    W = words(rows)
+    cols = np.ascontiguousarray(result["cols"], dtype=np.uint16) if n else np.zeros(1, np.uint16)
+    offs = np.ascontiguousarray(result["offsets"], dtype=np.uint32)
+    counts = np.ascontiguousarray(result["counts"], dtype=np.uint32) if n else np.zeros(1, np.uint32)
+    qual = np.ascontiguousarray(result["quality"], dtype=np.uint64) if n else np.zeros(1, np.uint64)
+    bm = np.ascontiguousarray(result["bitmaps"], dtype=np.uint32).reshape(-1) if n \
+        else np.zeros(1, np.uint32)
+    r = EbicResult()
+    r.n = n
+    r.cols = cols.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))
+    r.offsets = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    r.counts = counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    r.quality = qual.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    r.bitmaps = bm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    r.words = W
+    nm = names._p if names is not None else None
+    _check(_lib_write_bic(os.fsencode(path), title.encode(), ctypes.byref(r), nm),
+           "ebic_write_biclusters")
