@@ -22,6 +22,7 @@
 
 #include "ebic.h"
 #include "eval_kernel.cuh"
+#include "pair_chain.cuh"
 
 namespace ebic {
 namespace {
@@ -57,6 +58,9 @@ struct BatchReq {
   uint32_t stage_bytes;
   int32_t chunk_cols;
   uint32_t tmap;       // index into the tensor-map array
+  const uint32_t* pairs;  // the matrix's pair table: the request runs on the batched pair pass
+  uint32_t pair_stride;
+  int32_t pair_cols;
 };
 
 struct BatchHeader {
@@ -117,16 +121,32 @@ __global__ void batch_check_kernel(const BatchReq* __restrict__ reqs,
 }
 
 // Item ranges: request r owns items [start[r], start[r+1]) = chunks x row tiles. One thread.
+// Requests on matrices with a pair table get no items here: they own items of the batched pair
+// pass instead, [pstart[k][r], pstart[k][r+1]) for k = their negative-trend flag, one item per
+// (range of pairdev::kItemWords words, group of pairdev::kPairWarps candidates).
 __global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader* hdr,
                                   const uint32_t* __restrict__ req_err,
                                   unsigned long long* __restrict__ start,
-                                  unsigned long long gridDim_eval) {
+                                  unsigned long long* __restrict__ pstart,
+                                  uint32_t n_max, unsigned long long gridDim_eval) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  unsigned long long pacc[2] = {0ull, 0ull};
+  for (uint32_t r = 0; r < hdr->n_req; ++r) {
+    pstart[r] = pacc[0];
+    pstart[n_max + 1 + r] = pacc[1];
+    const BatchReq& q = reqs[r];
+    if (q.pairs == nullptr || q.n_cand == 0 || req_err[r] != 0u) continue;
+    const unsigned long long ranges = (q.words + pairdev::kItemWords - 1) / pairdev::kItemWords;
+    const unsigned long long groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
+    pacc[q.neg ? 1 : 0] += ranges * groups;
+  }
+  pstart[hdr->n_req] = pacc[0];
+  pstart[n_max + 1 + hdr->n_req] = pacc[1];
   unsigned long long acc = 0;
   for (uint32_t r = 0; r < hdr->n_req; ++r) {
     start[r] = acc;
     const BatchReq& q = reqs[r];
-    if (q.n_cand == 0 || req_err[r] != 0u) continue;
+    if (q.n_cand == 0 || req_err[r] != 0u || q.pairs != nullptr) continue;
     const unsigned long long total = q.cand_offsets[q.n_cand];
     const unsigned long long chunks = (total + q.chunk_cols - 1) / q.chunk_cols;
     const unsigned long long tiles = (unsigned long long)((q.slabs + q.ts - 1) / q.ts);
@@ -343,6 +363,48 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
+// The batched pair-table pass: every request whose matrix has a pair table and whose negative-
+// trend flag is NEG, its items (range of kItemWords words, group of kPairWarps candidates) laid
+// end to end in request order and taken round-robin by a persistent grid, so the CTAs walk each
+// request's ranges in order and its table rows stay in L2 while its candidates read them. The
+// chain and epilogue are the single-population pass's (pair_chain.cuh); the term list is
+// computed in registers from the checked candidate list.
+template <bool NEG>
+__global__ void __launch_bounds__(pairdev::kPairThreads, 1)
+    batch_pair_kernel(const BatchReq* __restrict__ reqs, const BatchHeader* __restrict__ hdr,
+                      const unsigned long long* __restrict__ pstart) {
+  __shared__ __align__(16) uint32_t stage[pairdev::kPairWarps][pairdev::kRangeWords];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t n_req = hdr->n_req;
+  const unsigned long long total = pstart[n_req];
+  for (unsigned long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const uint32_t r = find_item(pstart, n_req, it);
+    const BatchReq& q = reqs[r];
+    const unsigned long long local = it - pstart[r];
+    const uint32_t n_groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
+    const uint64_t range = local / n_groups, grp = local - range * n_groups;
+    const uint32_t cand = (uint32_t)grp * pairdev::kPairWarps + warp;
+    if (cand >= q.n_cand) continue;  // warp-uniform
+    const uint64_t rword = range * pairdev::kItemWords;
+    pairdev::Terms t;
+    pairdev::terms_from_list<NEG>(q.cand_cols, q.cand_offsets, cand, (uint32_t)q.pair_cols,
+                                  q.pair_stride, lane, t);
+    uint4 x[pairdev::kParts];
+    pairdev::pair_chain<NEG>(t, q.pairs + rword + 4 * lane, lane, x);
+    uint32_t pc = 0;
+#pragma unroll
+    for (int k = 0; k < pairdev::kParts; ++k) pc += pairdev::popc4(x[k]);
+    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
+    if (lane == 0 && c) atomicAdd(&q.counts[cand], c);
+    if (q.bitmaps) {  // warp-uniform
+      PairArgs pa;
+      pa.bitmaps = q.bitmaps;
+      pa.W = q.words;
+      pairdev::item_epilogue<true, false>(pa, cand, rword, x, c, stage[warp], lane, 0u, 0, 0ull);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace ebic
 
@@ -446,6 +508,9 @@ int build_plan(const ebic_eval_request* reqs, uint32_t n, uint32_t fixed_stage_c
     // chunks: about 2 items per SM over the whole batch is enough with dynamic scheduling
     q.chunk_cols = std::min<int32_t>(hp->chunk_cap, std::max<int32_t>(64, a.chunk_cols));
     q.tmap = i;
+    q.pairs = v.pairs;
+    q.pair_stride = v.pair_stride;
+    q.pair_cols = v.L.cols;
     hp->tmaps.push_back(*maps[i]);
     hp->ncols.push_back(v.L.cols);
     hp->reqs.push_back(q);
@@ -474,8 +539,10 @@ struct DeviceBatch {
   int32_t* ncols = nullptr;
   uint32_t* req_err = nullptr;
   unsigned long long* start = nullptr;
+  unsigned long long* pstart = nullptr;  // [2][n_max + 1]: the pair pass's item starts
   BatchHeader* hdr = nullptr;
   uint32_t* err = nullptr;
+  uint32_t n_max = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -483,7 +550,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 size_t batch_bytes(uint32_t n_max) {
   return align256(sizeof(BatchReq) * n_max) + align256(sizeof(CUtensorMap) * n_max) +
          align256(4 * (size_t)n_max) + align256(4 * (size_t)n_max) +
-         align256(8 * ((size_t)n_max + 1)) + align256(sizeof(BatchHeader)) + 256;
+         align256(8 * ((size_t)n_max + 1)) + align256(16 * ((size_t)n_max + 1)) +
+         align256(sizeof(BatchHeader)) + 256;
 }
 
 void carve(uint8_t* base, uint32_t n_max, DeviceBatch* d) {
@@ -498,9 +566,12 @@ void carve(uint8_t* base, uint32_t n_max, DeviceBatch* d) {
   o += align256(4 * (size_t)n_max);
   d->start = reinterpret_cast<unsigned long long*>(base + o);
   o += align256(8 * ((size_t)n_max + 1));
+  d->pstart = reinterpret_cast<unsigned long long*>(base + o);
+  o += align256(16 * ((size_t)n_max + 1));
   d->hdr = reinterpret_cast<BatchHeader*>(base + o);
   o += align256(sizeof(BatchHeader));
   d->err = reinterpret_cast<uint32_t*>(base + o);
+  d->n_max = n_max;
 }
 
 int ensure_batch_attr() {
@@ -514,7 +585,8 @@ int ensure_batch_attr() {
   return EBIC_OK;
 }
 
-// The three launches of a batch (check, plan, evaluate), stream-ordered.
+// The launches of a batch (check, plan, the rank-code pass, the two pair-table passes),
+// stream-ordered.
 int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, int num_sms,
                  cudaStream_t s) {
   const size_t smem = 2 * (size_t)stage_cap + 2 * ((size_t)chunk_cap + kChunkSlack) +
@@ -525,13 +597,21 @@ int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, in
   batch_check_kernel<<<4 * num_sms, 256, 0, s>>>(d.reqs, d.hdr, d.ncols, d.req_err);
   B_CUDA(cudaGetLastError());
   count_launch();
-  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start,
+  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start, d.pstart, d.n_max,
                                      (unsigned long long)num_sms);
   B_CUDA(cudaGetLastError());
   count_launch();
   batch_eval_kernel<<<num_sms, kBatchThreads, smem, s>>>(d.reqs, d.tmaps, d.hdr, d.start,
                                                           stage_cap, chunk_cap, 1000000000ull,
                                                           d.err);
+  B_CUDA(cudaGetLastError());
+  // the requests on matrices with a pair table (none: both grids exit at once)
+  count_launch();
+  batch_pair_kernel<false><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr, d.pstart);
+  B_CUDA(cudaGetLastError());
+  count_launch();
+  batch_pair_kernel<true><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
+                                                                    d.pstart + d.n_max + 1);
   B_CUDA(cudaGetLastError());
   return EBIC_OK;
 }

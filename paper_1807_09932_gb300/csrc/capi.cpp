@@ -331,6 +331,8 @@ void matrix_view(const ebic_matrix* m, MatrixView* v) {
   v->L = m->L;
   v->status = m->status;
   v->num_sms = m->num_sms;
+  v->pairs = m->pairs;
+  v->pair_stride = m->pair_stride;
 }
 
 int matrix_eval_plan(const ebic_matrix* cm, uint32_t n_cand, int64_t total_cols_hint,

@@ -247,6 +247,8 @@ struct MatrixView {
   Layout L;
   uint32_t* status = nullptr;
   int num_sms = 0;
+  const uint32_t* pairs = nullptr;  // the matrix's pair table, or null
+  uint32_t pair_stride = 0;
 };
 // Read-only view of a matrix handle's shape and device words.
 void matrix_view(const ebic_matrix* m, MatrixView* v);

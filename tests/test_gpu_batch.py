@@ -140,3 +140,63 @@ def test_bad_request_fails_alone(ebic):
         ebic.ebic_batch_free(b)
         for _, m in mats:
             m.status()
+
+
+def _with_pairs(ebic, mats, which):
+    for i, (_, m) in enumerate(mats):
+        if which(i):
+            m.build_pairs()
+
+
+def _check_against_direct(ebic, reqs):
+    """The rank-code evaluator, whatever the matrix holds."""
+    for r in reqs:
+        c, b = ebic.eval_population(r["m"], r["cols"], r["offs"], negative=bool(r["flags"]),
+                                    want_bitmaps=r["bitmaps"] is not None, direct=True)
+        assert np.array_equal(r["counts"].cpu().numpy().view(np.uint32), c)
+        if r["bitmaps"] is not None:
+            assert np.array_equal(r["bitmaps"].cpu().numpy().view(np.uint32), b)
+
+
+def test_batch_with_pair_tables(ebic):
+    """Requests on matrices with a pair table run on the batched pair pass, the others on the
+    rank-code pass, in one batch; both give the rank-code evaluator's bytes and the oracle's."""
+    import torch
+    mats = _matrices(ebic)
+    _with_pairs(ebic, mats, lambda i: i % 2 == 0)
+    reqs = _requests(ebic, mats, 32, seed=11)
+    arr = ebic.make_requests(_items(reqs))
+    assert ebic.ebic_eval_batch(arr, len(reqs)) == ebic.EBIC_OK, ebic.ebic_last_error()
+    torch.cuda.synchronize()
+    for _, m in mats:
+        assert m.status() == ebic.EBIC_OK
+    _check_against_direct(ebic, reqs)
+    for r in reqs[:8]:
+        c, _ = oracle.eval_population(r["ds"].X, r["cols"], r["offs"], negative=bool(r["flags"]))
+        assert np.array_equal(r["counts"].cpu().numpy().view(np.uint32), c)
+    # the captured graph, with compositions of pair and rank-code requests
+    b = ebic.ebic_batch_create(64)
+    try:
+        for seed, n_pop in ((12, 40), (13, 3), (14, 64)):
+            reqs = _requests(ebic, mats, n_pop, seed=seed)
+            arr = ebic.make_requests(_items(reqs))
+            assert ebic.ebic_batch_run(b, arr, len(reqs)) == ebic.EBIC_OK, ebic.ebic_last_error()
+            rc, st = ebic.ebic_batch_status(b, len(reqs))
+            assert rc == ebic.EBIC_OK and not any(st)
+            _check_against_direct(ebic, reqs)
+        # a bad request on a matrix with a table fails alone
+        reqs = _requests(ebic, mats, 6, seed=15)
+        bad = reqs[0]  # mats[0] has a table
+        cols = bad["cols"].copy()
+        cols[0] = bad["ds"].X.shape[1]
+        bad["dcols"] = _dev(cols)
+        arr = ebic.make_requests(_items(reqs))
+        assert ebic.ebic_batch_run(b, arr, len(reqs)) == ebic.EBIC_OK
+        rc, st = ebic.ebic_batch_status(b, len(reqs))
+        assert rc == ebic.EBIC_ERR_INVALID_ARG
+        assert st[0] != 0 and all(s == 0 for i, s in enumerate(st) if i != 0)
+        assert bad["m"].status() == ebic.EBIC_ERR_INVALID_ARG
+        assert int(bad["counts"].abs().sum()) == 0
+        _check_against_direct(ebic, reqs[1:])
+    finally:
+        ebic.ebic_batch_free(b)
