@@ -630,6 +630,14 @@ def batched_workload(args):
         tuned[id(p["m"])] = autotune.tune_matrix(p["m"], p["dc"], p["do"], p["n"], p["mean_len"],
                                                  p["cnt"], p["bm"], cache=cache, iters=2)
     t_tune = time.perf_counter() - t_tune
+    # pair tables (once per matrix; 3.8 GB for these eight): both arms then use them, the plain
+    # one through ebic_eval_population and the batched one through its pair-table pass
+    pair_bytes, t_pairs = 0, 0.0
+    if not args.no_pairs:
+        t0 = time.perf_counter()
+        for m in mats:
+            pair_bytes += m.build_pairs(max_bytes=args.pair_budget)
+        t_pairs = time.perf_counter() - t0
     evals_per_step = float(sum(p["n"] * p["R"] for p in pops))
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -675,6 +683,14 @@ def batched_workload(args):
     rc, st = ebic.ebic_batch_status(batch, len(pops))
     if rc or any(st):
         raise SystemExit("batched status error")
+    rank_code = None
+    if pair_bytes:  # context: the same batch on the rank-code pass (tables dropped)
+        for m in mats:
+            m.drop_pairs()
+        ms_rank = timed(batched_step, steps)
+        ms_rank_plain = timed(plain_step, steps)
+        rank_code = {"batched_ms_per_step": ms_rank, "plain_ms_per_step": ms_rank_plain,
+                     "batched_value": evals_per_step / (ms_rank / 1000)}
     ebic.ebic_batch_free(batch)
     line = {"metric": "candidate-row evals/s", "value": evals_per_step / (ms_batched / 1000),
             "unit": "candidate-row evals/s", "n_gpus": 1, "steps": steps,
@@ -686,10 +702,13 @@ def batched_workload(args):
                        "evals_per_step": evals_per_step,
                        "l2": "flushed between timed steps (512 MB write, outside the events)",
                        "tiles": {str(i): list(v[:2]) for i, v in enumerate(tuned.values())},
-                       "autotune_s": t_tune},
+                       "autotune_s": t_tune,
+                       "pair_tables": {"bytes": pair_bytes, "build_s": t_pairs}},
             "plain": {"value": evals_per_step / (ms_plain / 1000), "ms_per_step": ms_plain,
-                      "path": "64 x ebic_eval_population, one launch set per population"},
+                      "path": "64 x ebic_eval_population, one launch set per population"
+                              + (" (pair tables)" if pair_bytes else "")},
             "batched_over_plain": ms_plain / ms_batched,
+            "rank_code_pass": rank_code,
             "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(line), flush=True)
     for m in mats:
