@@ -736,7 +736,8 @@ def served_workload(args):
         specs.append(serve.RunSpec(run_id=i, X=ds.X, max_cand=r["n_cand"], max_len=16,
                                    archive_cols=arch[0], archive_offsets=arch[1]))
         rows_of[i] = r["rows"]
-    be = serve.GpuBackend(max_batch=len(specs), max_inflight=2)
+    be = serve.GpuBackend(max_batch=len(specs), max_inflight=2,
+                          pair_budget=0 if args.no_pairs else args.pair_budget)
     budget = sum(be.footprint(s) for s in specs) + (1 << 30)
     srv = serve.Server(be, hbm_budget=budget, max_batch=len(specs), max_inflight=2)
     for s in specs:

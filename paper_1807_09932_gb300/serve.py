@@ -204,12 +204,15 @@ def drive(server, arrivals, rows_of, on_done=None, clock=None, spin=None):
 class GpuBackend:
     """Resident rank matrices, per-run device buffers and archives; batched graph launches."""
 
-    def __init__(self, max_batch=64, max_inflight=2, device=0):
+    def __init__(self, max_batch=64, max_inflight=2, device=0, pair_budget=0):
+        """pair_budget: a run whose matrix's pair table takes at most this many bytes gets one
+        when it opens (its requests then run on the pair-table passes); 0: none."""
         import torch
 
         from . import ebic
         self.torch = torch
         self.ebic = ebic
+        self.pair_budget = int(pair_budget)
         self.dev = torch.device("cuda", device)
         self.runs = {}
         self.slots = [dict(stream=torch.cuda.Stream(self.dev), batch=ebic.ebic_batch_create(max_batch),
@@ -224,10 +227,19 @@ class GpuBackend:
             self.close_run(rid)
 
     @staticmethod
-    def footprint(spec: RunSpec):
+    def pair_bytes(spec: RunSpec):
+        """Device bytes of the run matrix's pair table (C*C rows of W rounded up to 512 words)."""
+        R, C = spec.X.shape
+        W = (R + 31) // 32
+        return C * C * ((W + 511) // 512 * 512) * 4
+
+    def footprint(self, spec: RunSpec):
         R, C = spec.X.shape
         W = (R + 31) // 32
         rank_bytes = R * C * (1 if C <= 127 else 2) * 1.02 + 4096
+        pb = self.pair_bytes(spec)
+        if 0 < pb <= self.pair_budget:
+            rank_bytes += pb
         k = 0 if spec.archive_offsets is None else len(spec.archive_offsets) - 1
         per_run = (spec.max_cand * (spec.max_len * 2 + 4 + 4 + 8 + W * 4)
                    + k * (W * 4 + 64 * 2 + 4) + 4096)
@@ -239,6 +251,8 @@ class GpuBackend:
     def open_run(self, spec: RunSpec):
         torch = self.torch
         m = self.ebic.Matrix(spec.X, exclude_missing=spec.exclude_missing)
+        if 0 < self.pair_bytes(spec) <= self.pair_budget:
+            m.build_pairs(max_bytes=self.pair_budget)
         W = m.words
         P = spec.max_cand
         run = dict(m=m, P=P, W=W, rows=spec.X.shape[0],
