@@ -482,15 +482,19 @@ def main():
 
 def traffic_record(name):
     """DRAM bytes per launch of a kernel from a committed ncu capture
-    (profiles/<name>_traffic.json), if the kernel source is still the one that was captured."""
+    (profiles/<name>_traffic.json), if the kernel's sources are still the ones that were captured
+    (SHA-256 over the listed files, concatenated in order)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        sources = rec.get("sources") or [rec["source"]]
+        h = hashlib.sha256()
+        for src in sources:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
     except (OSError, ValueError, KeyError):
         return None
-    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+    if h.hexdigest() != rec.get("source_sha256"):
         return None
     return rec["dram_bytes_per_launch"]
 
