@@ -235,6 +235,11 @@ cudaError_t launch_fitness_finalize(const uint16_t* cols, const uint32_t* offset
                                     const uint32_t* overlaps, const uint32_t* arch_counts,
                                     uint64_t* fitness, const uint32_t* err, cudaStream_t s);
 
+// Row gather for the host GA: dst row k = a's row idx[k] when idx[k] >= 0, else b's row
+// -idx[k]-1 (rows of W words; idx in device memory). One launch instead of a copy per row.
+cudaError_t launch_gather_rows(const uint32_t* a, const uint32_t* b, const int32_t* idx,
+                               uint32_t n, int64_t W, uint32_t* dst, cudaStream_t s);
+
 // ---- host helpers shared by the C-ABI translation units ------------------------------------
 }  // namespace ebic
 

@@ -449,7 +449,30 @@ __global__ void __launch_bounds__(kFinalizeWarps * 32)
   }
 }
 
+__global__ void gather_rows_kernel(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                                   const int32_t* __restrict__ idx, uint32_t n, int64_t W,
+                                   uint32_t* __restrict__ dst) {
+  const uint64_t total = (uint64_t)n * (uint64_t)W;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = i / (uint64_t)W, w = i - k * (uint64_t)W;
+    const int32_t r = idx[k];
+    dst[i] = r >= 0 ? a[(uint64_t)r * W + w] : b[(uint64_t)(-r - 1) * W + w];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_rows(const uint32_t* a, const uint32_t* b, const int32_t* idx,
+                               uint32_t n, int64_t W, uint32_t* dst, cudaStream_t s) {
+  if (n == 0 || W == 0) return cudaSuccess;
+  const uint64_t total = (uint64_t)n * (uint64_t)W;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  gather_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, b, idx, n, W, dst);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
   size_t warps = a.n[0] > a.n[1] ? a.n[0] : a.n[1];

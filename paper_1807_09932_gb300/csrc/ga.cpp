@@ -25,7 +25,6 @@
 #include <cstring>
 #include <memory>
 #include <string>
-#include <unordered_set>
 #include <vector>
 
 #include "ebic.h"
@@ -55,6 +54,65 @@ struct CandHash {
     for (uint16_t x : c) { h ^= x; h *= 1099511628211ull; }
     return (size_t)(h ^ c.size());
   }
+};
+
+// An exact set of column sequences without an allocation per entry: the sequences sit in one
+// arena, found by open addressing (linear probing) on their FNV-1a hash; clear() keeps the
+// capacity for the next generation.
+class CandSet {
+ public:
+  void clear() {
+    std::fill(slots_.begin(), slots_.end(), 0u);
+    arena_.clear();
+    ent_.clear();
+  }
+  size_t count(const Cand& c) const { return find(c, CandHash()(c)) ? 1 : 0; }
+  bool insert(const Cand& c) {
+    const uint64_t h = CandHash()(c);
+    if (find(c, h)) return false;
+    if ((ent_.size() + 1) * 2 > slots_.size()) grow();
+    ent_.push_back(Ent{(uint32_t)arena_.size(), (uint32_t)c.size(), h});
+    arena_.insert(arena_.end(), c.begin(), c.end());
+    place((uint32_t)ent_.size(), h);
+    return true;
+  }
+
+ private:
+  struct Ent {
+    uint32_t off, len;
+    uint64_t h;
+  };
+  static size_t slot_of(uint64_t h) {  // spread the hash's bits before masking
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    return (size_t)h;
+  }
+  bool find(const Cand& c, uint64_t h) const {
+    if (slots_.empty()) return false;
+    const size_t mask = slots_.size() - 1;
+    for (size_t i = slot_of(h) & mask;; i = (i + 1) & mask) {
+      const uint32_t s = slots_[i];
+      if (s == 0) return false;
+      const Ent& e = ent_[s - 1];
+      if (e.h == h && e.len == c.size() &&
+          std::equal(c.begin(), c.end(), arena_.begin() + e.off))
+        return true;
+    }
+  }
+  void place(uint32_t entry_plus_one, uint64_t h) {
+    const size_t mask = slots_.size() - 1;
+    size_t i = slot_of(h) & mask;
+    while (slots_[i] != 0) i = (i + 1) & mask;
+    slots_[i] = entry_plus_one;
+  }
+  void grow() {
+    slots_.assign(slots_.empty() ? 4096 : slots_.size() * 2, 0u);
+    for (size_t k = 0; k < ent_.size(); ++k) place((uint32_t)k + 1, ent_[k].h);
+  }
+  std::vector<uint16_t> arena_;
+  std::vector<Ent> ent_;
+  std::vector<uint32_t> slots_;  // entry index + 1, 0 = empty
 };
 
 uint64_t quality(uint32_t n, size_t L) { return (uint64_t)n << ((L < 33 ? L : 33) - 1); }
@@ -189,11 +247,11 @@ std::string check_params(const ebic_params& p, int32_t ncols) {
 int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebic_result** out) {
   const uint32_t P = p.population, K = p.archive_size;
   Ga ga(p, ncols);
-  std::unordered_set<Cand, CandHash> tabu;
+  CandSet tabu, in_archive, picked, in_next;
   std::vector<Cand> pop;
   pop.reserve(P);
   {
-    std::unordered_set<Cand, CandHash> seen;
+    CandSet seen;
     for (uint32_t i = 0; i < P; ++i) {
       Cand c = ga.random_candidate();
       for (int t = 0; t < 32 && seen.count(c); ++t) c = ga.random_candidate();
@@ -205,7 +263,7 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
   std::vector<uint16_t> cols;
   std::vector<uint32_t> offs;
   std::vector<uint32_t> counts(P), overlaps((size_t)P * K), order(P), rank(P);
-  std::vector<uint64_t> fitness(P);
+  std::vector<uint64_t> fitness(P), head4(P);
   uint64_t evaluated = 0;
   uint32_t gen = 0;
   for (; gen < p.generations; ++gen) {
@@ -221,12 +279,24 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     for (const Cand& c : pop) tabu.insert(c);
     const size_t K_eval = archive.size();  // overlaps is [P][K_eval]
 
-    for (uint32_t i = 0; i < P; ++i) order[i] = i;
+    // lexicographic order of equal-length sequences: their first four columns packed high to low
+    // decide most comparisons; the rest of the sequence breaks the remaining ties
+    for (uint32_t i = 0; i < P; ++i) {
+      order[i] = i;
+      uint64_t k = 0;
+      for (size_t j = 0; j < 4; ++j) k = (k << 16) | (j < pop[i].size() ? pop[i][j] : 0u);
+      head4[i] = k;
+    }
     std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
       if (fitness[a] != fitness[b]) return fitness[a] > fitness[b];
       if (counts[a] != counts[b]) return counts[a] > counts[b];
       if (pop[a].size() != pop[b].size()) return pop[a].size() > pop[b].size();
-      if (pop[a] != pop[b]) return pop[a] < pop[b];
+      if (head4[a] != head4[b]) return head4[a] < head4[b];
+      if (pop[a].size() > 4) {
+        const auto ta = pop[a].begin() + 4, tb = pop[b].begin() + 4;
+        if (!std::equal(ta, pop[a].end(), tb))
+          return std::lexicographical_compare(ta, pop[a].end(), tb, pop[b].end());
+      }
       return a < b;
     });
     for (uint32_t r = 0; r < P; ++r) rank[order[r]] = r;
@@ -235,11 +305,11 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     // Offer up to 2K non-archived candidates with rows, best raw quality first. A candidate is
     // admitted unless a member sharing a column overlaps it by more than the threshold without
     // being strictly worse; strictly worse members that overlap it that much are replaced.
-    std::unordered_set<Cand, CandHash> in_archive;
+    in_archive.clear();
     for (const Member& m : archive) in_archive.insert(m.cols);
     std::vector<Member> offers;
     {
-      std::unordered_set<Cand, CandHash> picked;
+      picked.clear();
       for (uint32_t i = 0; i < P; ++i) {
         if (counts[i] == 0 || in_archive.count(pop[i]) || picked.count(pop[i])) continue;
         picked.insert(pop[i]);
@@ -298,7 +368,7 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     // ---- next population ----
     std::vector<Cand> next;
     next.reserve(P);
-    std::unordered_set<Cand, CandHash> in_next;
+    in_next.clear();
     for (uint32_t r = 0; r < p.elite; ++r) {
       next.push_back(pop[order[r]]);
       in_next.insert(pop[order[r]]);
@@ -401,6 +471,8 @@ struct GpuEvaluator : Evaluator {
   uint32_t *aoffs = nullptr, *abm = nullptr, *abm_next = nullptr;
   uint32_t *poffs = nullptr, *pcounts = nullptr, *pbm = nullptr, *pov = nullptr;
   uint64_t *dfit = nullptr, *pfit = nullptr;
+  int32_t* didx = nullptr;  // rows to gather (population index, or -(archive index + 1))
+  std::vector<int32_t> hidx;
   std::vector<uint16_t> pop_cols, arch_cols;
   std::vector<uint32_t> pop_offs, arch_offs{0}, host_counts;
   uint32_t n_arch = 0;
@@ -437,6 +509,7 @@ struct GpuEvaluator : Evaluator {
     GA_CUDA(alloc(&pbm, (size_t)T * W));
     GA_CUDA(alloc(&pfit, T));
     GA_CUDA(alloc(&pov, (size_t)T * T));
+    GA_CUDA(alloc(&didx, (size_t)std::max(T, K)));
     return EBIC_OK;
   }
   int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs, uint32_t n,
@@ -463,39 +536,44 @@ struct GpuEvaluator : Evaluator {
     const uint32_t t = (uint32_t)idx.size();
     std::vector<uint16_t> c;
     std::vector<uint32_t> o{0}, cn;
+    hidx.assign(idx.begin(), idx.end());
     for (uint32_t k = 0; k < t; ++k) {
       const uint32_t i = idx[k];
       c.insert(c.end(), pop_cols.begin() + pop_offs[i], pop_cols.begin() + pop_offs[i + 1]);
       o.push_back((uint32_t)c.size());
       cn.push_back(host_counts[i]);
-      GA_CUDA(cudaMemcpyAsync(pbm + (size_t)k * W, dbm + (size_t)i * W, (size_t)W * 4,
-                              cudaMemcpyDeviceToDevice, s));
     }
+    // pageable-source copies return once the source is staged, so the vectors may go
+    GA_CUDA(cudaMemcpyAsync(didx, hidx.data(), (size_t)t * 4, cudaMemcpyHostToDevice, s));
+    GA_CUDA(launch_gather_rows(dbm, dbm, didx, t, W, pbm, s));
     GA_CUDA(cudaMemcpyAsync(pcols, c.data(), c.size() * 2, cudaMemcpyHostToDevice, s));
     GA_CUDA(cudaMemcpyAsync(poffs, o.data(), o.size() * 4, cudaMemcpyHostToDevice, s));
     GA_CUDA(cudaMemcpyAsync(pcounts, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
     int rc = ebic_fitness(m, pcols, poffs, t, pcounts, pbm, pcols, poffs, pbm, t, 0, pfit, pov, s);
     if (rc != EBIC_OK) return rc;
     GA_CUDA(cudaMemcpyAsync(out, pov, (size_t)t * t * 4, cudaMemcpyDeviceToHost, s));
+    // the lists were built here, valid by construction; a device-side rejection would still
+    // show in the sticky status word that the next evaluation reads
     GA_CUDA(cudaStreamSynchronize(s));
-    return ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
+    return EBIC_OK;
   }
   int set_archive(const std::vector<int32_t>& src) override {
     std::vector<uint16_t> c;
     std::vector<uint32_t> o{0};
     for (size_t k = 0; k < src.size(); ++k) {
-      const uint32_t* from;
       if (src[k] >= 0) {
         const uint32_t i = (uint32_t)src[k];
         c.insert(c.end(), pop_cols.begin() + pop_offs[i], pop_cols.begin() + pop_offs[i + 1]);
-        from = dbm + (size_t)i * W;
       } else {
         const uint32_t a = (uint32_t)(-src[k] - 1);
         c.insert(c.end(), arch_cols.begin() + arch_offs[a], arch_cols.begin() + arch_offs[a + 1]);
-        from = abm + (size_t)a * W;
       }
       o.push_back((uint32_t)c.size());
-      GA_CUDA(cudaMemcpyAsync(abm_next + k * W, from, (size_t)W * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    // the new archive's rows, gathered from the population's and the old archive's bitmaps
+    if (!src.empty()) {
+      GA_CUDA(cudaMemcpyAsync(didx, src.data(), src.size() * 4, cudaMemcpyHostToDevice, s));
+      GA_CUDA(launch_gather_rows(dbm, abm, didx, (uint32_t)src.size(), W, abm_next, s));
     }
     std::swap(abm, abm_next);
     arch_cols = c;
@@ -504,8 +582,7 @@ struct GpuEvaluator : Evaluator {
     if (!c.empty())
       GA_CUDA(cudaMemcpyAsync(acols, c.data(), c.size() * 2, cudaMemcpyHostToDevice, s));
     GA_CUDA(cudaMemcpyAsync(aoffs, o.data(), o.size() * 4, cudaMemcpyHostToDevice, s));
-    GA_CUDA(cudaStreamSynchronize(s));  // host vectors c, o go out of scope
-    return EBIC_OK;
+    return EBIC_OK;  // stream-ordered before the next evaluation; sources already staged
   }
   bool has_bitmaps() const override { return true; }
   int archive_bitmaps(uint32_t* out, uint32_t k) override {
