@@ -216,14 +216,15 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
  * bitmap is then the AND of its consecutive pairs' rows (the reversed pairs for decreasing
  * trends), one 32-bit AND per 32 rows per column, instead of a compare per row per column.
  * The table takes cols * cols * W' * 4 bytes of device memory, W' = W rounded up to a multiple
- * of 128 (its rows are padded with zero words), and is built once, by the evaluator itself (on
+ * of 512 (its rows are padded with zero words), and is built once, by the evaluator itself (on
  * the population of all pairs), so results never change.
  *   ebic_matrix_build_pairs: build it if it needs at most max_bytes (else EBIC_ERR_UNSUPPORTED);
  *                            *bytes (may be NULL) receives the size. Synchronous.
  *   ebic_matrix_drop_pairs:  free it.
  * While a matrix has a table, ebic_eval_population and ebic_eval_fitness use it unless
  * EBIC_EVAL_DIRECT is given.
- * ebic_eval_population_noalloc and the batched calls always use the rank-code evaluator.
+ * ebic_eval_population_noalloc always uses the rank-code evaluator; the batched calls use the
+ * table for the requests on a matrix that has one.
  */
 int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, uint64_t* bytes);
 int ebic_matrix_drop_pairs(ebic_matrix* m);
