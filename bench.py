@@ -501,7 +501,7 @@ def traffic_record(name):
 
 def roofline_pairs(pops, R, m, launch_ms, clk, peaks, fused, K):
     """The pair-table evaluator: an HBM stream. Algorithmic bytes per launch: the table rows the
-    population needs (distinct consecutive column pairs, rows of W rounded up to 128 words;
+    population needs (distinct consecutive column pairs, rows of W rounded up to 512 words;
     each read once) and its counts, plus the bitmaps it writes (unfused) or the padded archive
     rows it reads (fused), against the measured HBM copy bandwidth."""
     W = m.words

@@ -750,6 +750,35 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
   return EBIC_OK;
 }
 
+// The fused route's outputs: the caller's overlaps from the paired layout, host copies, and
+// (when an output is on the host, so the call synchronizes) the call's error word.
+static int finish_fitness(uint32_t n_cand, uint32_t n_arch, uint32_t ov_stride,
+                          uint32_t* dcounts, uint32_t* dbm, uint64_t* dfit, uint32_t* dov,
+                          uint32_t* err, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
+                          uint32_t* overlaps, bool counts_host, bool bm_host, bool fit_host,
+                          int64_t words, int dev, cudaStream_t s) {
+  const bool ov_host = overlaps && n_arch > 0 && !on_device(overlaps, dev);
+  if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout
+    EBIC_CUDA(cudaMemcpy2DAsync(overlaps, (size_t)n_arch * 4, dov, (size_t)ov_stride * 4,
+                                (size_t)n_arch * 4, n_cand,
+                                ov_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  if (counts_host || bm_host || fit_host || ov_host) {
+    if (counts_host)
+      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
+    if (bm_host)
+      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbm, (size_t)n_cand * words * 4,
+                                cudaMemcpyDeviceToHost, s));
+    if (fit_host)
+      EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_eval_fitness");
+  }
+  return EBIC_OK;
+}
+
+
 int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
                       uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
                       const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
@@ -817,19 +846,19 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm, &bm_host));
   EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
 
-  // the call's working buffers, carved from one stream-ordered allocation; none needs zeroing
-  // before the preparation kernel (it writes every word the later kernels read)
   const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
   // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
   const uint32_t ov_stride = (n_arch + 1u) & ~1u;
   const uint32_t stride = m->pair_stride;
-  const uint32_t prep_blocks = fused_prepare_blocks(n_cand, n_arch, stride, m->num_sms);
   size_t total = 0;
   auto carve = [&total](size_t bytes) {
     const size_t off = total;
     total += (bytes + 255) & ~(size_t)255;
     return off;
   };
+  // the call's working buffers, carved from one stream-ordered allocation; none needs zeroing
+  // before the preparation kernel (it writes every word the later kernels read)
+  const uint32_t prep_blocks = fused_prepare_blocks(n_cand, n_arch, stride, m->num_sms);
   const size_t o_err = carve(sizeof(uint32_t));
   const size_t o_flags = carve((size_t)prep_blocks * 4);
   const size_t o_terms = carve((size_t)n_cand * term_slots(neg) * 4);
@@ -900,25 +929,9 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, ov_stride,
                                     darch_counts, dshare, dfit, err, !timing_on(), s));
   }
-  const bool ov_host = overlaps && n_arch > 0 && !on_device(overlaps, dev);
-  if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout
-    EBIC_CUDA(cudaMemcpy2DAsync(overlaps, (size_t)n_arch * 4, dov, (size_t)ov_stride * 4,
-                                (size_t)n_arch * 4, n_cand,
-                                ov_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-  if (counts_host || bm_host || fit_host || ov_host) {
-    if (counts_host)
-      EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
-    if (bm_host)
-      EBIC_CUDA(cudaMemcpyAsync(bitmaps, dbm, (size_t)n_cand * L.words * 4,
-                                cudaMemcpyDeviceToHost, s));
-    if (fit_host)
-      EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
-    uint32_t bits = 0;
-    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
-    EBIC_CUDA(cudaStreamSynchronize(s));
-    return status_code(bits, "ebic_eval_fitness");
-  }
-  return EBIC_OK;
+  return finish_fitness(n_cand, n_arch, ov_stride, dcounts, dbm, dfit, dov, err, counts,
+                        bitmaps, fitness, overlaps, counts_host, bm_host, fit_host, L.words, dev,
+                        s);
 }
 
 int ebic_matrix_status(ebic_matrix* m, void* stream) {

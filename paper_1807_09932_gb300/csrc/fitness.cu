@@ -15,84 +15,14 @@
 // tests each archive member's columns against it.
 #include <algorithm>
 
-#include "device_common.cuh"
-#include "ebic_internal.h"
+#include "prep_dev.cuh"
 
 namespace ebic {
 namespace {
 
-constexpr int kSetWords = (kMaxCols + 31) / 32;  // a column set as a bitset
+using namespace prepdev;
+
 constexpr int kPrepWarps = 8;
-
-// Warp-cooperative check of candidate i of a CSR list of n: offsets[0] == 0, 1 <= L <= 64, the
-// candidate ends at or before offsets[n] (so its columns lie inside cols[0 .. offsets[n]), the
-// caller's buffer), its columns are < ncols and distinct. Columns are read only when the offsets
-// pass, so reads stay in bounds whatever the other candidates' offsets are. Leaves the
-// candidate's column set in `set` (the warp's own shared-memory bitset; empty when the offsets
-// fail). Returns true on every lane when the candidate is invalid.
-__device__ bool check_candidate_span(const uint16_t* __restrict__ cols, uint32_t lo, uint32_t hi,
-                                     uint32_t total, bool first, int32_t ncols, uint32_t* set,
-                                     int lane) {
-  const bool bad = (first && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > total;
-  const int nw = (ncols + 31) / 32;
-  for (int w = lane; w < nw; w += 32) set[w] = 0u;
-  __syncwarp();
-  bool b = false;
-  if (!bad) {
-    for (uint32_t j = lo + lane; j < hi; j += 32) {
-      const uint32_t c = cols[j];
-      if (c >= (uint32_t)ncols) {
-        b = true;
-        continue;
-      }
-      const uint32_t bit = 1u << (c & 31u);
-      b |= (atomicOr(&set[c >> 5], bit) & bit) != 0u;  // seen before: a repeated column
-    }
-  }
-  __syncwarp();
-  return __any_sync(0xFFFFFFFFu, bad || b);
-}
-
-__device__ bool check_candidate_warp(const uint16_t* __restrict__ cols,
-                                     const uint32_t* __restrict__ offs, uint32_t n, uint32_t i,
-                                     int32_t ncols, uint32_t* set, int lane) {
-  return check_candidate_span(cols, offs[i], offs[i + 1], offs[n], i == 0, ncols, set, lane);
-}
-
-// The term list of one candidate (see kTermSlots), a warp per candidate. Its offsets must have
-// passed the check (lo < hi <= lo + 64, inside the caller's columns); a column >= C makes a
-// garbage offset, but the call is then rejected and no later kernel reads the list.
-__device__ void build_terms_warp(const uint16_t* __restrict__ cols, uint32_t lo, uint32_t hi,
-                                 uint32_t C, uint32_t S, bool negative, uint32_t* out,
-                                 int lane) {
-  const int L = (int)(hi - lo);
-  const uint32_t c_lo = lane < L ? cols[lo + lane] : 0u;
-  const uint32_t c_hi = lane + 32 < L ? cols[lo + 32 + lane] : 0u;
-  const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
-  const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
-  const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
-  const uint32_t next_lo = lane == 31 ? h0 : n_lo;  // c_{i+1} for i = lane
-  const int n_terms = L == 1 ? 1 : L - 1;
-  const bool t_lo = lane < n_terms, t_hi = lane + 32 < n_terms;
-  out[lane] = t_lo ? (L == 1 ? c_lo * C + c_lo : c_lo * C + next_lo) * S : 0u;
-  out[32 + lane] = lane == 31 ? (uint32_t)L : (t_hi ? (c_hi * C + n_hi) * S : 0u);
-  if (negative) {
-    out[64 + lane] = t_lo && L > 1 ? (next_lo * C + c_lo) * S : 0u;
-    out[96 + lane] = t_hi ? (n_hi * C + c_hi) * S : 0u;
-  }
-}
-
-__device__ __forceinline__ bool offsets_sane(uint32_t lo, uint32_t hi, uint32_t total,
-                                             bool first) {
-  return !(first && lo != 0u) && hi > lo && hi - lo <= (uint32_t)kMaxLen && hi <= total;
-}
-
-__device__ __forceinline__ void report_invalid(bool bad, uint32_t* err, uint32_t* status) {
-  if (bad) {
-    atomicOr(err, kErrInvalid);
-    if (status) atomicOr(status, kErrInvalid);
-  }
-}
 
 // Device-side check of up to two CSR candidate lists (a warp per candidate) and zeroing of up to
 // two outputs, in one launch.
@@ -125,120 +55,11 @@ __global__ void __launch_bounds__(kPrepWarps * 32) prepare_kernel(PrepareArgs a)
   if (lane == 0) report_invalid(bad, a.err, a.status);
 }
 
-// Preparation of the fused evaluation + overlap pass (see launch_fused_prepare). Three phases,
-// each a single round of independent loads: (A) archive offsets, the archive copy and the
-// warp's first candidate's offsets; (B) the archive members' columns; (C) the candidates'
-// columns.
+// Preparation of the fused evaluation + overlap pass (see launch_fused_prepare).
 __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPrepareArgs a) {
-  __shared__ uint32_t msets[kPairMaxArch][kSetWords];  // archive members' column sets
-  __shared__ uint32_t sets[kPrepWarps][kSetWords];
-  __shared__ uint32_t aoff_s[kPairMaxArch + 1];
+  __shared__ PrepShared<kPrepWarps> sh;
   dev::pdl_trigger();  // the pair-table pass may be scheduled; it waits for this grid
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t nthreads = (size_t)gridDim.x * blockDim.x;
-  const uint32_t gw = blockIdx.x * kPrepWarps + warp, nwarps = gridDim.x * kPrepWarps;
-  const int nw = (a.ncols + 31) / 32;
-  const uint32_t na = a.n_arch;
-
-  // (A)
-  if (threadIdx.x <= na && na) aoff_s[threadIdx.x] = a.aoffsets[threadIdx.x];
-  for (int i = threadIdx.x; i < (int)na * kSetWords; i += blockDim.x) (&msets[0][0])[i] = 0u;
-  uint32_t lo0 = 0, hi0 = 0, tot0 = 0;
-  if (gw < a.n_cand) {
-    lo0 = a.offsets[gw];
-    hi0 = a.offsets[gw + 1];
-    tot0 = a.offsets[a.n_cand];
-  }
-  {  // archive rows padded to the table stride (an even number of rows), four loads in flight
-    const uint32_t* __restrict__ src = a.arch_src;
-    uint32_t* __restrict__ dst = a.arch_pad;
-    const uint64_t n_pad = (uint64_t)((na + 1u) & ~1u) * a.stride;
-    const bool narrow = n_pad < (1ull << 32);  // 32-bit index arithmetic suffices
-    for (uint64_t i0 = tid; i0 < n_pad; i0 += 4 * nthreads) {
-      uint32_t v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint64_t i = i0 + k * nthreads;
-        uint64_t m, w;
-        if (narrow) {
-          const uint32_t i32 = (uint32_t)i;
-          m = i32 / a.stride;
-          w = i32 - (uint32_t)m * a.stride;
-        } else {
-          m = i / a.stride;
-          w = i - m * a.stride;
-        }
-        v[k] = i < n_pad && m < na && w < (uint64_t)a.W ? src[m * (uint64_t)a.W + w] : 0u;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint64_t i = i0 + k * nthreads;
-        if (i < n_pad) dst[i] = v[k];
-      }
-    }
-  }
-  for (size_t i = tid; i < na; i += nthreads) a.arch_counts[i] = 0u;
-  __syncthreads();
-
-  // (B) every block builds the members' column sets, one (member, position) per thread; a
-  // member whose offsets fail contributes none (the list is rejected below, and the pass that
-  // follows then does nothing)
-  const uint32_t atotal = na ? aoff_s[na] : 0u;
-  for (uint32_t t0 = threadIdx.x; t0 < na * (uint32_t)kMaxLen; t0 += 4 * blockDim.x) {
-    uint32_t c[4], m[4];
-    bool ok[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t t = t0 + k * blockDim.x;
-      m[k] = t / kMaxLen;
-      const uint32_t j = t % kMaxLen;
-      ok[k] = false;
-      c[k] = 0u;
-      if (m[k] < na) {
-        const uint32_t lo = aoff_s[m[k]], hi = aoff_s[m[k] + 1];
-        const bool sane = !(m[k] == 0 && lo != 0u) && hi > lo && hi - lo <= (uint32_t)kMaxLen &&
-                          hi <= atotal;
-        ok[k] = sane && j < hi - lo;
-        if (ok[k]) c[k] = a.acols[lo + j];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (ok[k] && c[k] < (uint32_t)a.ncols) atomicOr(&msets[m[k]][c[k] >> 5], 1u << (c[k] & 31u));
-  }
-  __syncthreads();
-
-  // (C) a warp per candidate: check, share mask, zeroed outputs
-  bool bad = false;
-  for (uint32_t i = gw; i < a.n_cand; i += nwarps) {
-    if (i != gw) {
-      lo0 = a.offsets[i];
-      hi0 = a.offsets[i + 1];
-    }
-    bad |= check_candidate_span(a.cols, lo0, hi0, tot0, i == 0, a.ncols, sets[warp], lane);
-    if (offsets_sane(lo0, hi0, tot0, i == 0))
-      build_terms_warp(a.cols, lo0, hi0, (uint32_t)a.ncols, a.stride, a.negative,
-                       a.terms + (size_t)i * term_slots(a.negative), lane);
-    uint32_t s0 = 0u, s1 = 0u;
-    for (int w = 0; w < nw; ++w) {
-      const uint32_t cw = sets[warp][w];
-      if ((uint32_t)lane < na) s0 |= cw & msets[lane][w];
-      if ((uint32_t)lane + 32u < na) s1 |= cw & msets[lane + 32][w];
-    }
-    const uint32_t lo_mask = __ballot_sync(0xFFFFFFFFu, s0 != 0u);
-    const uint32_t hi_mask = __ballot_sync(0xFFFFFFFFu, s1 != 0u);
-    if (lane == 0) {
-      if (a.share) a.share[i] = ((uint64_t)hi_mask << 32) | lo_mask;
-      a.counts[i] = 0u;
-    }
-    for (uint32_t m = lane; m < a.ov_stride; m += 32) a.overlaps[(size_t)i * a.ov_stride + m] = 0u;
-    __syncwarp();  // the set is rebuilt for the next candidate
-  }
-  if (a.check_arch)
-    for (uint32_t i = gw; i < na; i += nwarps)
-      bad |= check_candidate_span(a.acols, aoff_s[i], aoff_s[i + 1], atotal, i == 0, a.ncols,
-                                  sets[warp], lane);
+  const bool bad = fused_prepare_body<kPrepWarps>(a, sh, blockIdx.x, gridDim.x);
   // the block's verdict, stored (not accumulated) in its own flag: nothing needs zeroing first
   const bool block_bad = __syncthreads_or(bad) != 0;
   if (threadIdx.x == 0) {
@@ -247,8 +68,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
   }
 }
 
-// F_c for the fused pass: a warp per candidate, a lane per archive member; the share masks of the
-// preparation stand for the column-set test.
+// F_c for the fused pass: a warp per candidate, a lane per archive member.
 __global__ void __launch_bounds__(kPrepWarps * 32)
     fused_finalize_kernel(const uint32_t* __restrict__ offsets, uint32_t n_cand,
                           const uint32_t* __restrict__ counts,
@@ -266,21 +86,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   const uint32_t al1 = lane + 32 < (int)n_arch ? aoffsets[lane + 33] - aoffsets[lane + 32] : 0u;
   dev::pdl_wait();  // the pair-table pass is complete and visible
   if (*reinterpret_cast<const volatile uint32_t*>(err) != 0 || !live) return;
-  const uint32_t n = counts[c];
-  const uint32_t shift = (L < 33u ? L : 33u) - 1u;
-  const uint64_t qc = (uint64_t)n << shift;
-  const uint64_t sh = n_arch ? share[c] : 0ull;
-  uint32_t best = 0;
-  for (uint32_t m = lane; m < n_arch; m += 32) {
-    if (!((sh >> m) & 1ull)) continue;  // shares no column with the candidate
-    const uint32_t al = m < 32 ? al0 : al1;
-    const uint64_t qa = (uint64_t)arch_counts[m] << ((al < 33u ? al : 33u) - 1u);
-    if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
-    const uint32_t ov = overlaps[(size_t)c * ov_stride + m];
-    best = ov > best ? ov : best;
-  }
-  best = __reduce_max_sync(0xFFFFFFFFu, best);
-  if (lane == 0) fitness[c] = (uint64_t)(n - best) << shift;
+  fused_fitness_warp(c, L, al0, al1, n_arch, counts, overlaps, ov_stride, arch_counts,
+                            share, fitness, lane);
 }
 
 // Carry-save adder: a + b + c = 2 * carry + sum, bit by bit (two 3-input logic ops).

@@ -51,14 +51,10 @@ __device__ __forceinline__ void load_terms(const PairArgs& p, uint32_t cand, int
 // The term list of candidate `cand` of a checked CSR list, computed in registers (the batched
 // pass has no preparation kernel to build it): the same words the preparation writes, lane i
 // holding terms i and 32 + i, lane 31's hi word the length L.
+// From the candidate's L columns in registers (lane i: columns i and 32 + i).
 template <bool NEG>
-__device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ cols,
-                                                const uint32_t* __restrict__ offs, uint32_t cand,
-                                                uint32_t C, uint32_t S, int lane, Terms& t) {
-  const uint32_t o = offs[cand];
-  const int L = (int)(offs[cand + 1] - o);
-  const uint32_t c_lo = lane < L ? cols[o + lane] : 0u;
-  const uint32_t c_hi = lane + 32 < L ? cols[o + 32 + lane] : 0u;
+__device__ __forceinline__ void terms_from_cols(uint32_t c_lo, uint32_t c_hi, int L, uint32_t C,
+                                                uint32_t S, int lane, Terms& t) {
   const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
   const uint32_t n_hi = __shfl_down_sync(0xFFFFFFFFu, c_hi, 1);
   const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
@@ -71,6 +67,17 @@ __device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ col
     t.blo = t_lo && L > 1 ? (next_lo * C + c_lo) * S : 0u;
     t.bhi = t_hi ? (n_hi * C + c_hi) * S : 0u;
   }
+}
+
+template <bool NEG>
+__device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ cols,
+                                                const uint32_t* __restrict__ offs, uint32_t cand,
+                                                uint32_t C, uint32_t S, int lane, Terms& t) {
+  const uint32_t o = offs[cand];
+  const int L = (int)(offs[cand + 1] - o);
+  const uint32_t c_lo = lane < L ? cols[o + lane] : 0u;
+  const uint32_t c_hi = lane + 32 < L ? cols[o + 32 + lane] : 0u;
+  terms_from_cols<NEG>(c_lo, c_hi, L, C, S, lane, t);
 }
 
 // The candidate's bitmap words 4*lane .. 4*lane+3 of each 128-word part of the item whose first
@@ -145,7 +152,14 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
 }
 
 // An archive row segment: re-read by every warp of the CTA that scores a candidate of the same
-// range, so it is kept in L1 in preference to the streamed table rows.
+// range, so it is kept in L1 in preference to the streamed table rows. Archive rows are padded
+// with zero words to the table's stride, an even number of rows.
+__device__ __forceinline__ uint32_t ld_keep1(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 __device__ __forceinline__ uint4 ld_arch4(const uint32_t* p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::evict_last.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -165,11 +179,12 @@ __device__ __forceinline__ void add_pair(unsigned long long* ov2, int k, uint32_
 // Bitmap words and archive overlaps of candidate `cand` for the item at `rword`, from its words
 // x (lane holds words 4*lane .. 4*lane+3 of part q, i.e. item words 128q + 4*lane + j, in x[q])
 // and their warp total cnt.
+// `members`: the archive members whose overlaps are wanted (a bit per member below n_arch).
 template <bool BITMAPS, bool OVERLAP>
 __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, uint64_t rword,
                                               const uint4 (&x)[kParts], uint32_t cnt, uint32_t* st,
                                               int lane, uint32_t n_arch, int n_pairs,
-                                              uint64_t all_members) {
+                                              uint64_t members) {
   if constexpr (BITMAPS) {  // through shared memory, so each store instruction is coalesced
     uint32_t* out = p.bitmaps + (uint64_t)cand * (uint64_t)p.W;
 #pragma unroll
@@ -185,9 +200,8 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
     }
   }
   if constexpr (OVERLAP) {
-    if (cnt == 0) return;  // warp-uniform: nothing of this item overlaps anything
-    const uint64_t members = p.score ? p.score[cand] & all_members : all_members;
-    if (members == 0) return;
+    if (cnt == 0 || members == 0) return;  // warp-uniform: nothing to add
+    const uint64_t astride = p.stride;
     const uint32_t* abase = p.arch + rword;
     uint32_t* ov = p.overlaps + (uint64_t)cand * p.ov_stride;
     // the lane's eight words and where they sit in the item
@@ -227,14 +241,14 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
         // all, gathering its member's word at each; no warp reduction, one atomic per member
         const bool a0 = (members >> lane) & 1ull;
         const bool a1 = (members >> (lane + 32)) & 1ull;
-        const uint32_t* ar0 = abase + (uint64_t)lane * p.stride;
-        const uint32_t* ar1 = abase + (uint64_t)(lane + 32) * p.stride;
+        const uint32_t* ar0 = abase + (uint64_t)lane * astride;
+        const uint32_t* ar1 = abase + (uint64_t)(lane + 32) * astride;
         uint32_t o0 = 0, o1 = 0;
 #pragma unroll 4
         for (int i = 0; i < nz; ++i) {
           const uint32_t v = sv[i], w = si[i];
-          if (a0) o0 += __popc(v & __ldg(ar0 + w));
-          if (a1) o1 += __popc(v & __ldg(ar1 + w));
+          if (a0) o0 += __popc(v & ld_keep1(ar0 + w));
+          if (a1) o1 += __popc(v & ld_keep1(ar1 + w));
         }
         __syncwarp();
         if (o0) atomicAdd(&ov[lane], o0);
@@ -243,13 +257,14 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
         // a word per lane, two members per warp reduction (sums <= 1,024), one 64-bit atomic
         // per member pair
         unsigned long long* ov2 = reinterpret_cast<unsigned long long*>(ov);
-        const uint64_t S2 = 2ull * p.stride;  // from member 2k to 2k+2
+        const uint64_t S2 = 2ull * astride;  // from member 2k to 2k+2
         const uint32_t mv = lane < nz ? sv[lane] : 0u;
         const uint32_t* ab = abase + (lane < nz ? si[lane] : 0u);
         __syncwarp();
         for (int k = 0; k < n_pairs; ++k, ab += S2) {
           if (((members >> (2 * k)) & 3ull) == 0) continue;  // warp-uniform
-          const uint32_t w0 = __ldg(ab), w1 = __ldg(ab + p.stride);
+          // (an odd archive's last pair reads the zero padding row)
+          const uint32_t w0 = ld_keep1(ab), w1 = ld_keep1(ab + astride);
           const uint32_t r =
               __reduce_add_sync(0xFFFFFFFFu, __popc(mv & w0) + (__popc(mv & w1) << 16));
           add_pair(ov2, k, r, lane);
@@ -266,8 +281,8 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
         const int mb = mm ? __ffsll((long long)mm) - 1 : ma;
         const bool has_b = mm != 0ull;
         mm &= mm - 1ull;
-        const uint32_t* pa = ab + (uint64_t)ma * p.stride;
-        const uint32_t* pb = ab + (uint64_t)mb * p.stride;
+        const uint32_t* pa = ab + (uint64_t)ma * astride;
+        const uint32_t* pb = ab + (uint64_t)mb * astride;
         uint32_t sa = 0, sb = 0;
 #pragma unroll
         for (int q = 0; q < kParts; ++q) {
@@ -280,6 +295,63 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
         if (lane < 2 && v) atomicAdd(&ov[lane == 0 ? ma : mb], v);
       }
     }
+  }
+}
+
+// The pass over all (range, candidate group) items of one population, by a persistent grid of
+// kPairThreads-thread CTAs (see pairs.cu for the work order); `st` is the warp's kRangeWords-word
+// shared staging buffer.
+template <bool NEG, bool BITMAPS, bool OVERLAP>
+__device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
+  const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
+  const uint64_t n_items = (uint64_t)n_ranges * n_groups;
+  const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
+  const int n_pairs = (int)(n_arch + 1) >> 1;
+  const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
+  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
+  // the term list of the warp's next item is loaded while the current one is walked
+  const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
+  uint64_t it = blockIdx.x;
+  uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
+  Terms next;
+  if (it < n_items && grp * kPairWarps + warp < p.n_cand)
+    load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
+  while (it < n_items) {
+    const uint64_t rword = (uint64_t)range * kItemWords;  // first word of the item
+    const uint32_t cand = grp * kPairWarps + warp;
+    const uint32_t cur_grp = grp;
+    const Terms t = next;
+    it += gridDim.x;
+    range += d_range;
+    grp += d_grp;
+    if (grp >= n_groups) {
+      grp -= n_groups;
+      ++range;
+    }
+    if (it < n_items && grp * kPairWarps + warp < p.n_cand)
+      load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
+    if (OVERLAP && cur_grp == 0) {  // the archive members' own row counts, once per range
+      for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
+        const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
+        uint32_t pa = 0;
+#pragma unroll
+        for (int q = 0; q < kParts; ++q) pa += popc4(ld_arch4(ar + q * kRangeWords));
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, pa);
+        if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
+      }
+    }
+    if (cand >= p.n_cand) continue;  // warp-uniform
+    uint4 x[kParts];
+    pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
+    uint32_t pc = 0;
+#pragma unroll
+    for (int q = 0; q < kParts; ++q) pc += popc4(x[q]);
+    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
+    if (lane == 0 && c) atomicAdd(&p.counts[cand], c);
+    const uint64_t members = OVERLAP && p.score ? p.score[cand] & all_members : all_members;
+    item_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x, c, st, lane, n_arch, n_pairs, members);
   }
 }
 

@@ -63,57 +63,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   } else if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) {
     return;  // invalid input
   }
-  const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
-  const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
-  const uint64_t n_items = (uint64_t)n_ranges * n_groups;
-  const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
-  const int n_pairs = (int)(n_arch + 1) >> 1;
-  const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
-  uint32_t* st = stage[warp];
-  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
-  // the term list of the warp's next item is loaded while the current one is walked
-  const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
-  uint64_t it = blockIdx.x;
-  uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-  Terms next;
-  if (it < n_items && grp * kPairWarps + warp < p.n_cand)
-    load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
-  while (it < n_items) {
-    const uint64_t rword = (uint64_t)range * kItemWords;  // first word of the item
-    const uint32_t cand = grp * kPairWarps + warp;
-    const uint32_t cur_grp = grp;
-    const Terms t = next;
-    it += gridDim.x;
-    range += d_range;
-    grp += d_grp;
-    if (grp >= n_groups) {
-      grp -= n_groups;
-      ++range;
-    }
-    if (it < n_items && grp * kPairWarps + warp < p.n_cand)
-      load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
-    if (OVERLAP && cur_grp == 0) {  // the archive members' own row counts, once per range
-      for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
-        const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
-        uint32_t pa = 0;
-#pragma unroll
-        for (int q = 0; q < kParts; ++q)
-          pa += popc4(__ldg(reinterpret_cast<const uint4*>(ar + q * kRangeWords)));
-        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, pa);
-        if (lane == 0 && n) atomicAdd(&p.arch_counts[a], n);
-      }
-    }
-    if (cand >= p.n_cand) continue;  // warp-uniform
-    uint4 x[kParts];
-    pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
-    uint32_t pc = 0;
-#pragma unroll
-    for (int q = 0; q < kParts; ++q) pc += popc4(x[q]);
-    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
-    if (lane == 0 && c) atomicAdd(&p.counts[cand], c);
-    item_epilogue<BITMAPS, OVERLAP>(p, cand, rword, x, c, st, lane, n_arch, n_pairs,
-                                    all_members);
-  }
+  pair_items<NEG, BITMAPS, OVERLAP>(p, stage[warp]);
 }
 
 template <bool NEG, bool BITMAPS>

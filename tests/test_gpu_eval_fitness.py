@@ -1,7 +1,8 @@
 """ebic_eval_fitness (one generation's scoring in one call) against the oracle, bit for bit:
 counts, bitmaps, fitness and overlaps, on the fused pair-table pass (evaluation and archive
-overlaps in one kernel), on its fallbacks (EBIC_EVAL_DIRECT, no pair table, archives over 64
-members) and with device-resident inputs."""
+overlaps in one kernel),
+on its fallbacks (EBIC_EVAL_DIRECT, no pair table, archives over 64 members) and with
+device-resident inputs."""
 import numpy as np
 import pytest
 
@@ -115,8 +116,8 @@ def test_long_candidates_sparse_and_dense_ranges(ebic):
             m.build_pairs()
             c, b, f, ov = ebic.eval_fitness(m, cols, offs, acols, aoffs, abm, negative=negative,
                                             want_bitmaps=True, want_overlaps=True)
-        assert np.array_equal(c, ec) and np.array_equal(b, eb)
-        assert np.array_equal(f, ef) and np.array_equal(ov, eov)
+            assert np.array_equal(c, ec) and np.array_equal(b, eb)
+            assert np.array_equal(f, ef) and np.array_equal(ov, eov)
 
 
 def test_device_resident_inputs_and_outputs(ebic):
@@ -184,6 +185,49 @@ def test_invalid_lists_rejected(ebic):
         ef, _ = oracle.fitness(R, good_c, good_o, ec, eb, good_c, good_o, abm)
         c, _, f, _ = ebic.eval_fitness(m, good_c, good_o, good_c, good_o, abm)
         assert np.array_equal(c, ec) and np.array_equal(f, ef)
+
+
+def test_fused_route_back_to_back_calls(ebic):
+    """The fused route makes three kernel launches per call (preparation, pair pass, finalize);
+    40 calls queued back to back on one stream (stream-ordered scratch memory reused from call
+    to call, none of it zeroed by the host) on alternating populations and archives all give
+    the oracle's results."""
+    import torch
+    rng = np.random.default_rng(33)
+    R, C = 12000, 40
+    X = random_matrix(rng, R, C)
+    pops = []
+    for k in range(2):
+        cols, offs = synth.make_population(50 + k, 400 + 37 * k, C, 2, 14)
+        ec, eb = oracle.eval_population(X, cols, offs)
+        acols, aoffs, abm = make_archive(rng, 60 + k, cols, offs, eb, C, R, 12 + 8 * k)
+        ef, _ = oracle.fitness(R, cols, offs, ec, eb, acols, aoffs, abm)
+        pops.append((cols, offs, acols, aoffs, abm, ec, ef))
+    with ebic.Matrix(torch.from_numpy(X).cuda()) as m:
+        m.build_pairs()
+        dev = [tuple(dev_tensor(a) for a in p[:5]) for p in pops]
+        outs = []
+        for k in range(2):
+            n = len(pops[k][1]) - 1
+            outs.append((torch.zeros(n, dtype=torch.int32, device="cuda"),
+                         torch.zeros(n, dtype=torch.int64, device="cuda")))
+        before = ebic.ebic_launch_count()
+        rc = ebic.ebic_eval_fitness(m.handle, *dev[0][:2], len(pops[0][1]) - 1, 0, *dev[0][2:],
+                                    len(pops[0][3]) - 1, outs[0][0], None, outs[0][1], None)
+        assert rc == ebic.EBIC_OK
+        assert ebic.ebic_launch_count() - before == 3
+        for it in range(40):
+            k = it % 2
+            cnt, fit = outs[k]
+            cnt.zero_()
+            fit.zero_()
+            rc = ebic.ebic_eval_fitness(m.handle, *dev[k][:2], len(pops[k][1]) - 1, 0,
+                                        *dev[k][2:], len(pops[k][3]) - 1, cnt, None, fit, None)
+            assert rc == ebic.EBIC_OK
+            if it >= 38:
+                assert m.status() == ebic.EBIC_OK
+                assert np.array_equal(host(cnt, np.uint32), pops[k][5])
+                assert np.array_equal(host(fit, np.uint64), pops[k][6])
 
 
 def test_config3_full_size_sampled(ebic):
