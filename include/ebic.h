@@ -215,9 +215,10 @@ int ebic_matrix_set_tile(ebic_matrix* m, int32_t tile_slabs);
  * is not missing and b's value is >= a's; the diagonal holds "a not missing". A candidate's
  * bitmap is then the AND of its consecutive pairs' rows (the reversed pairs for decreasing
  * trends), one 32-bit AND per 32 rows per column, instead of a compare per row per column.
- * The table takes cols * cols * W' * 4 bytes of device memory, W' = W rounded up to a multiple
- * of 512 (its rows are padded with zero words), and is built once, by the evaluator itself (on
- * the population of all pairs), so results never change.
+ * The table takes cols * cols * W' * 4 + 512 bytes of device memory, W' = W rounded up to a
+ * multiple of 512 (its rows are padded with zero words; one all-ones row of 128 words follows
+ * them), and is built once, by the evaluator itself (on the population of all pairs), so results
+ * never change.
  *   ebic_matrix_build_pairs: build it if it needs at most max_bytes (else EBIC_ERR_UNSUPPORTED);
  *                            *bytes (may be NULL) receives the size. Synchronous.
  *   ebic_matrix_drop_pairs:  free it.

@@ -996,12 +996,13 @@ int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, ui
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
   const Layout& L = m->L;
   const int64_t stride = pair_stride(L.words);
-  const uint64_t need = (uint64_t)L.cols * (uint64_t)L.cols * (uint64_t)stride * 4ull;
+  const uint64_t rows = (uint64_t)L.cols * (uint64_t)L.cols * (uint64_t)stride * 4ull;
+  const uint64_t need = rows + (uint64_t)kOnesWords * 4ull;
   if (bytes) *bytes = need;
   if (need > max_bytes)
     return fail(EBIC_ERR_UNSUPPORTED, "the pair table needs " + std::to_string(need) +
                                           " bytes, more than max_bytes");
-  if (need / 4ull > 0xFFFFFFFFull)  // table rows are addressed with 32-bit word offsets
+  if (rows / 4ull > 0xFFFFFFFFull)  // table rows are addressed with 32-bit word offsets
     return fail(EBIC_ERR_UNSUPPORTED, "the pair table would exceed 2^32 words");
   DeviceGuard g(m->device);
   if (m->pairs) return EBIC_OK;
@@ -1021,7 +1022,9 @@ int ebic_matrix_build_pairs(ebic_matrix* m, uint64_t max_bytes, void* stream, ui
   uint32_t* counts = nullptr;
   cudaError_t e = cudaMalloc(&table, need);
   if (e == cudaSuccess) e = cudaMalloc(&counts, (size_t)n * 4);
-  if (e == cudaSuccess) e = cudaMemsetAsync(table, 0, need, s);  // the rows' padding words
+  if (e == cudaSuccess) e = cudaMemsetAsync(table, 0, rows, s);  // the rows' padding words
+  if (e == cudaSuccess)  // the all-ones row after the table
+    e = cudaMemsetAsync(reinterpret_cast<char*>(table) + rows, 0xFF, (size_t)kOnesWords * 4, s);
   if (e != cudaSuccess) {
     if (table) cudaFree(table);
     if (counts) cudaFree(counts);

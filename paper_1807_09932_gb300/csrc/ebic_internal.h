@@ -129,6 +129,13 @@ cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalA
 constexpr int kPairRangeWords = 512;  // table and padded archive row strides are multiples
 constexpr int kPairMaxArch = 64;      // archive members the fused overlap pass takes
 // Row stride (words) of the pair table and of padded archive bitmaps for W-word bitmaps.
+// A pair table allocation ends with one row of kOnesWords all-ones words (after the C*C
+// table rows): a chain step reads it in place of a part it no longer needs.
+constexpr int kOnesWords = 128;
+__host__ __device__ inline const uint32_t* pair_ones(const uint32_t* table, uint64_t cols,
+                                                    uint64_t stride) {
+  return table + cols * cols * stride;
+}
 inline int64_t pair_stride(int64_t words) {
   return (words + kPairRangeWords - 1) / kPairRangeWords * kPairRangeWords;
 }

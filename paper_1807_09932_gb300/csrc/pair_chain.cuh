@@ -84,20 +84,23 @@ __device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ col
 // table word is `base` (table + item*kItemWords): AND of its consecutive pairs' table rows, OR
 // the reversed pairs' AND with negative trends. Each step keeps the rows of several terms of
 // every part in flight; a part stops loading once every word of it in the warp is zero, and the
-// walk stops when all are (long chains match no row of most ranges).
+// walk stops when all are (long chains match no row of most ranges). `ones` is the lane's words
+// of the table's all-ones row: a step reads them in place of a part that is already zero or a
+// term past the end, so every load and AND of a step is unconditional.
 template <bool NEG>
-__device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base, int lane,
+__device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
+                                           const uint32_t* ones, int lane,
                                            uint4 (&out)[kParts]) {
   constexpr int kStep = NEG ? kStepTerms / 2 : kStepTerms;
   const int L = (int)__shfl_sync(0xFFFFFFFFu, t.hi, 31);
   const int n_terms = L == 1 ? 1 : L - 1;
   const bool two = NEG && L > 1;  // warp-uniform
-  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+  const uint4 all = make_uint4(~0u, ~0u, ~0u, ~0u);
   uint4 x[kParts], y[kParts];
   bool live[kParts];  // warp-uniform: the part still has a non-zero word
 #pragma unroll
   for (int q = 0; q < kParts; ++q) {
-    x[q] = y[q] = ones;
+    x[q] = y[q] = all;
     live[q] = true;
   }
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
@@ -107,19 +110,19 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
 #pragma unroll
       for (int k = 0; k < kStep; ++k) {
         const int i = i0 + k;
+        const bool has = i < t1;  // warp-uniform
+        const uint32_t* rf = base + __shfl_sync(0xFFFFFFFFu, offf, i & 31);
 #pragma unroll
-        for (int q = 0; q < kParts; ++q) v[k][q] = u[k][q] = ones;
-        if (i < t1) {  // warp-uniform
-          const uint32_t* rf = base + __shfl_sync(0xFFFFFFFFu, offf, i & 31);
+        for (int q = 0; q < kParts; ++q)
+          v[k][q] = __ldg(reinterpret_cast<const uint4*>(has && live[q] ? rf + q * kRangeWords
+                                                                        : ones));
+        if (NEG) {
+          const uint32_t* rb = base + __shfl_sync(0xFFFFFFFFu, offb, i & 31);
 #pragma unroll
           for (int q = 0; q < kParts; ++q)
-            if (live[q]) v[k][q] = __ldg(reinterpret_cast<const uint4*>(rf + q * kRangeWords));
-          if (two) {
-            const uint32_t* rb = base + __shfl_sync(0xFFFFFFFFu, offb, i & 31);
-#pragma unroll
-            for (int q = 0; q < kParts; ++q)
-              if (live[q]) u[k][q] = __ldg(reinterpret_cast<const uint4*>(rb + q * kRangeWords));
-          }
+            u[k][q] = __ldg(reinterpret_cast<const uint4*>(two && has && live[q]
+                                                               ? rb + q * kRangeWords
+                                                               : ones));
         }
       }
       bool any_live = false;
@@ -310,6 +313,7 @@ __device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
   const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
   const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
+  const uint32_t* ones = pair_ones(p.table, (uint64_t)p.C, p.stride) + 4 * lane;
   // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
   // the term list of the warp's next item is loaded while the current one is walked
   const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
@@ -344,7 +348,7 @@ __device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
     }
     if (cand >= p.n_cand) continue;  // warp-uniform
     uint4 x[kParts];
-    pair_chain<NEG>(t, p.table + rword + 4 * lane, lane, x);
+    pair_chain<NEG>(t, p.table + rword + 4 * lane, ones, lane, x);
     uint32_t pc = 0;
 #pragma unroll
     for (int q = 0; q < kParts; ++q) pc += popc4(x[q]);

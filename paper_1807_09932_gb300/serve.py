@@ -228,10 +228,11 @@ class GpuBackend:
 
     @staticmethod
     def pair_bytes(spec: RunSpec):
-        """Device bytes of the run matrix's pair table (C*C rows of W rounded up to 512 words)."""
+        """Device bytes of the run matrix's pair table (C*C rows of W rounded up to 512 words,
+        and one all-ones row of 128 words)."""
         R, C = spec.X.shape
         W = (R + 31) // 32
-        return C * C * ((W + 511) // 512 * 512) * 4
+        return C * C * ((W + 511) // 512 * 512) * 4 + 512
 
     def footprint(self, spec: RunSpec):
         R, C = spec.X.shape

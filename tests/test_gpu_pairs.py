@@ -27,7 +27,7 @@ def test_pairs_match_oracle_and_direct(ebic, R, C):
     cols, offs = synth.make_population(R * C, 120, C, 1, min(C, 64))
     with ebic.Matrix(X) as m:
         size = m.build_pairs()
-        assert size == C * C * ((m.words + 511) // 512 * 512) * 4
+        assert size == C * C * ((m.words + 511) // 512 * 512) * 4 + 512  # and the all-ones row
         for neg in (False, True):
             c, b = ebic.eval_population(m, cols, offs, negative=neg)
             ec, eb = oracle.eval_population(X, cols, offs, negative=neg)
@@ -56,7 +56,7 @@ def test_pair_table_limit_and_drop(ebic):
     X = np.random.default_rng(3).standard_normal((5000, 64)).astype(np.float32)
     cols, offs = synth.make_population(4, 50, 64, 2, 10)
     with ebic.Matrix(X) as m:
-        need = 64 * 64 * ((m.words + 511) // 512 * 512) * 4
+        need = 64 * 64 * ((m.words + 511) // 512 * 512) * 4 + 512  # and the all-ones row
         with pytest.raises(ebic.EbicError) as ei:
             m.build_pairs(max_bytes=need - 1)
         assert ei.value.code == ebic.EBIC_ERR_UNSUPPORTED
