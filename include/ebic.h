@@ -254,10 +254,22 @@ typedef struct ebic_eval_request {
   uint32_t flags;            /* EBIC_NEGATIVE_TRENDS or 0                                     */
   uint32_t* counts;          /* device [n_cand]                                               */
   uint32_t* bitmaps;         /* device [n_cand][W], or NULL for counts only                   */
+  /* Optional, for a matrix with a pair table (ebic_matrix_build_pairs): the overlap-penalised
+   * fitness of ebic_fitness against an archive, with the overlaps computed inside the batched
+   * pass (as ebic_eval_fitness does for one population). fitness NULL: none. */
+  const uint16_t* arch_cols;     /* device CSR columns of the archive (n_arch > 0)           */
+  const uint32_t* arch_offsets;  /* device [n_arch+1]                                         */
+  const uint32_t* arch_bitmaps;  /* device [n_arch][W]                                        */
+  uint32_t n_arch;               /* 0 .. 64                                                   */
+  uint64_t* fitness;             /* device [n_cand], or NULL                                  */
 } ebic_eval_request;
 
 /* Score all requests in one persistent launch (plus a check and a plan kernel), asynchronously on
- * `stream`. Row tiles and candidate chunks of all requests share one dynamic work queue. */
+ * `stream`. Row tiles and candidate chunks of all requests share one dynamic work queue; requests
+ * on matrices with a pair table run on the batched pair pass instead, and those with `fitness`
+ * also get their archive overlaps there and their fitness from one more kernel. A request asking
+ * for fitness on a matrix without a pair table is rejected (EBIC_ERR_UNSUPPORTED). Archive lists
+ * are checked on the device like candidate lists. */
 int ebic_eval_batch(const ebic_eval_request* reqs, uint32_t n_req, void* stream);
 
 /* The same batched launch, captured once in a CUDA graph and replayed. A batch holds device and

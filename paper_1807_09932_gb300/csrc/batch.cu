@@ -23,6 +23,7 @@
 #include "ebic.h"
 #include "eval_kernel.cuh"
 #include "pair_chain.cuh"
+#include "prep_dev.cuh"
 
 namespace ebic {
 namespace {
@@ -61,6 +62,17 @@ struct BatchReq {
   const uint32_t* pairs;  // the matrix's pair table: the request runs on the batched pair pass
   uint32_t pair_stride;
   int32_t pair_cols;
+  // fitness against an archive (pair-table requests only; fitness null: none)
+  uint64_t* fitness;
+  const uint16_t* arch_cols;
+  const uint32_t* arch_offsets;
+  const uint32_t* arch_src;         // the caller's [n_arch][words] archive
+  uint32_t* arch_pad;               // scratch: [ov_stride][pair_stride], zero padding
+  uint32_t* overlaps;               // scratch: [n_cand][ov_stride], zeroed by the check kernel
+  uint32_t* arch_counts;            // scratch: [n_arch], zeroed by the check kernel
+  unsigned long long* colmask;      // scratch: [pair_cols] members holding each column
+  uint32_t n_arch;
+  uint32_t ov_stride;               // n_arch rounded up to even
 };
 
 struct BatchHeader {
@@ -69,6 +81,8 @@ struct BatchHeader {
   unsigned long long next_item;   // work counter, reset by the plan kernel
   unsigned long long total_items;
   unsigned long long grab;        // consecutive items taken per grab (set by the plan kernel)
+  uint32_t* zero;                 // the fitness requests' counters, one block of n_zero words
+  unsigned long long n_zero;
 };
 
 __device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t n, uint32_t cand) {
@@ -118,30 +132,67 @@ __global__ void batch_check_kernel(const BatchReq* __restrict__ reqs,
       atomicOr(q.status, kErrInvalid);
     }
   }
+  // the fitness requests: counters zeroed, archives copied into rows of the table's stride, the
+  // column -> member masks, and the archive lists checked like candidate lists
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nthreads = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = tid; i < hdr->n_zero; i += nthreads) hdr->zero[i] = 0u;
+  for (uint32_t r = 0; r < n_req; ++r) {
+    const BatchReq& q = reqs[r];
+    if (!q.fitness || q.n_arch == 0) continue;
+    prepdev::copy_archive_padded(q.arch_src, q.arch_pad, q.n_arch, q.words, q.pair_stride, tid,
+                                 nthreads);
+    const uint32_t* ao = q.arch_offsets;
+    const uint32_t atot = ao[q.n_arch];
+    for (size_t c = tid; c < (size_t)q.pair_cols; c += nthreads) {
+      unsigned long long mask = 0ull;
+      for (uint32_t m = 0; m < q.n_arch; ++m) {
+        const uint32_t lo = ao[m], hi = ao[m + 1];
+        if (!prepdev::offsets_sane(lo, hi, atot, m == 0)) continue;  // rejected below
+        for (uint32_t j = lo; j < hi; ++j)
+          if (q.arch_cols[j] == c) mask |= 1ull << m;
+      }
+      q.colmask[c] = mask;
+    }
+    for (size_t m = tid; m < q.n_arch; m += nthreads) {
+      const uint32_t lo = ao[m], hi = ao[m + 1];
+      bool bad = !prepdev::offsets_sane(lo, hi, atot, m == 0);
+      if (!bad) {
+        for (uint32_t j = lo; j < hi; ++j) {
+          const uint16_t c = q.arch_cols[j];
+          bad |= c >= (uint32_t)q.pair_cols;
+          for (uint32_t t = lo; t < j; ++t) bad |= q.arch_cols[t] == c;
+        }
+      }
+      if (bad) {
+        atomicOr(&req_err[r], kErrInvalid);
+        atomicOr(q.status, kErrInvalid);
+      }
+    }
+  }
 }
 
 // Item ranges: request r owns items [start[r], start[r+1]) = chunks x row tiles. One thread.
 // Requests on matrices with a pair table get no items here: they own items of the batched pair
-// pass instead, [pstart[k][r], pstart[k][r+1]) for k = their negative-trend flag, one item per
-// (range of pairdev::kItemWords words, group of pairdev::kPairWarps candidates).
+// pass instead, [pstart[k][r], pstart[k][r+1]) for k = their negative-trend flag + 2 when they
+// have an archive to score against, one item per (range of pairdev::kItemWords words, group of
+// pairdev::kPairWarps candidates).
 __global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader* hdr,
                                   const uint32_t* __restrict__ req_err,
                                   unsigned long long* __restrict__ start,
                                   unsigned long long* __restrict__ pstart,
                                   uint32_t n_max, unsigned long long gridDim_eval) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  unsigned long long pacc[2] = {0ull, 0ull};
+  unsigned long long pacc[4] = {0ull, 0ull, 0ull, 0ull};
   for (uint32_t r = 0; r < hdr->n_req; ++r) {
-    pstart[r] = pacc[0];
-    pstart[n_max + 1 + r] = pacc[1];
+    for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + r] = pacc[k];
     const BatchReq& q = reqs[r];
     if (q.pairs == nullptr || q.n_cand == 0 || req_err[r] != 0u) continue;
     const unsigned long long ranges = (q.words + pairdev::kItemWords - 1) / pairdev::kItemWords;
     const unsigned long long groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
-    pacc[q.neg ? 1 : 0] += ranges * groups;
+    pacc[(q.neg ? 1 : 0) + (q.fitness && q.n_arch ? 2 : 0)] += ranges * groups;
   }
-  pstart[hdr->n_req] = pacc[0];
-  pstart[n_max + 1 + hdr->n_req] = pacc[1];
+  for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + hdr->n_req] = pacc[k];
   unsigned long long acc = 0;
   for (uint32_t r = 0; r < hdr->n_req; ++r) {
     start[r] = acc;
@@ -363,13 +414,23 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
+// The archive members holding any of a candidate's L columns (lane i holds columns i and
+// 32 + i): the OR of the columns' member masks, the same on every lane.
+__device__ __forceinline__ uint64_t share_of(const unsigned long long* colmask, uint32_t c_lo,
+                                             uint32_t c_hi, int L, int lane) {
+  const unsigned long long m =
+      (lane < L ? colmask[c_lo] : 0ull) | (lane + 32 < L ? colmask[c_hi] : 0ull);
+  return ((uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)(m >> 32)) << 32) |
+         __reduce_or_sync(0xFFFFFFFFu, (uint32_t)m);
+}
+
 // The batched pair-table pass: every request whose matrix has a pair table and whose negative-
 // trend flag is NEG, its items (range of kItemWords words, group of kPairWarps candidates) laid
 // end to end in request order and taken round-robin by a persistent grid, so the CTAs walk each
 // request's ranges in order and its table rows stay in L2 while its candidates read them. The
 // chain and epilogue are the single-population pass's (pair_chain.cuh); the term list is
 // computed in registers from the checked candidate list.
-template <bool NEG>
+template <bool NEG, bool FIT>
 __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
     batch_pair_kernel(const BatchReq* __restrict__ reqs, const BatchHeader* __restrict__ hdr,
                       const unsigned long long* __restrict__ pstart) {
@@ -384,11 +445,27 @@ __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
     const uint32_t n_groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
     const uint64_t range = local / n_groups, grp = local - range * n_groups;
     const uint32_t cand = (uint32_t)grp * pairdev::kPairWarps + warp;
-    if (cand >= q.n_cand) continue;  // warp-uniform
     const uint64_t rword = range * pairdev::kItemWords;
+    if (FIT && grp == 0) {  // the archive members' own row counts, once per range
+      for (uint32_t a = warp; a < q.n_arch; a += pairdev::kPairWarps) {
+        const uint32_t* ar = q.arch_pad + (uint64_t)a * q.pair_stride + rword + 4 * lane;
+        uint32_t pa4 = 0;
+#pragma unroll
+        for (int k = 0; k < pairdev::kParts; ++k)
+          pa4 += pairdev::popc4(pairdev::ld_arch4(ar + k * pairdev::kRangeWords));
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, pa4);
+        if (lane == 0 && n) atomicAdd(&q.arch_counts[a], n);
+      }
+    }
+    if (cand >= q.n_cand) continue;  // warp-uniform
+    // the candidate's columns (the list passed the check kernel): its term list and, with an
+    // archive, the members sharing one of its columns
+    const uint32_t o = q.cand_offsets[cand];
+    const int L = (int)(q.cand_offsets[cand + 1] - o);
+    const uint32_t c_lo = lane < L ? q.cand_cols[o + lane] : 0u;
+    const uint32_t c_hi = lane + 32 < L ? q.cand_cols[o + 32 + lane] : 0u;
     pairdev::Terms t;
-    pairdev::terms_from_list<NEG>(q.cand_cols, q.cand_offsets, cand, (uint32_t)q.pair_cols,
-                                  q.pair_stride, lane, t);
+    pairdev::terms_from_cols<NEG>(c_lo, c_hi, L, (uint32_t)q.pair_cols, q.pair_stride, lane, t);
     uint4 x[pairdev::kParts];
     pairdev::pair_chain<NEG>(t, q.pairs + rword + 4 * lane,
                              pair_ones(q.pairs, (uint64_t)q.pair_cols, q.pair_stride) + 4 * lane,
@@ -398,11 +475,56 @@ __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
     for (int k = 0; k < pairdev::kParts; ++k) pc += pairdev::popc4(x[k]);
     const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
     if (lane == 0 && c) atomicAdd(&q.counts[cand], c);
-    if (q.bitmaps) {  // warp-uniform
-      PairArgs pa;
-      pa.bitmaps = q.bitmaps;
-      pa.W = q.words;
+    PairArgs pa;
+    pa.bitmaps = q.bitmaps;
+    pa.W = q.words;
+    if constexpr (FIT) {
+      pa.arch = q.arch_pad;
+      pa.stride = q.pair_stride;
+      pa.n_arch = q.n_arch;
+      pa.overlaps = q.overlaps;
+      pa.ov_stride = q.ov_stride;
+      const int n_pairs = (int)(q.n_arch + 1) >> 1;
+      const uint64_t sh = share_of(q.colmask, c_lo, c_hi, L, lane);
+      if (q.bitmaps)  // warp-uniform
+        pairdev::item_epilogue<true, true>(pa, cand, rword, x, c, stage[warp], lane, q.n_arch,
+                                           n_pairs, sh);
+      else
+        pairdev::item_epilogue<false, true>(pa, cand, rword, x, c, stage[warp], lane, q.n_arch,
+                                            n_pairs, sh);
+    } else if (q.bitmaps) {  // warp-uniform
       pairdev::item_epilogue<true, false>(pa, cand, rword, x, c, stage[warp], lane, 0u, 0, 0ull);
+    }
+  }
+}
+
+// F_c of every candidate of the fitness requests, a warp per candidate (as ebic_eval_fitness's
+// finalize), after the batched pair pass. Requests that failed their check get no fitness.
+__global__ void batch_fitness_kernel(const BatchReq* __restrict__ reqs,
+                                     const BatchHeader* __restrict__ hdr,
+                                     const uint32_t* __restrict__ req_err) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_req = hdr->n_req;
+  const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+  const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (uint32_t r = 0; r < n_req; ++r) {
+    const BatchReq& q = reqs[r];
+    if (!q.fitness || req_err[r] != 0u) continue;  // the same for the whole grid
+    for (uint32_t i = gw; i < q.n_cand; i += nw) {
+      const uint32_t o = q.cand_offsets[i];
+      const uint32_t L = q.cand_offsets[i + 1] - o;
+      if (q.n_arch == 0) {
+        if (lane == 0) q.fitness[i] = (uint64_t)q.counts[i] << ((L < 33u ? L : 33u) - 1u);
+        continue;
+      }
+      const uint32_t c_lo = lane < (int)L ? q.cand_cols[o + lane] : 0u;
+      const uint32_t c_hi = lane + 32 < (int)L ? q.cand_cols[o + 32 + lane] : 0u;
+      const uint64_t sh = share_of(q.colmask, c_lo, c_hi, (int)L, lane);
+      const uint32_t* ao = q.arch_offsets;
+      const uint32_t al0 = lane < (int)q.n_arch ? ao[lane + 1] - ao[lane] : 0u;
+      const uint32_t al1 = lane + 32 < (int)q.n_arch ? ao[lane + 33] - ao[lane + 32] : 0u;
+      prepdev::fused_fitness_mask(i, L, al0, al1, q.n_arch, sh, q.counts, q.overlaps,
+                                  q.ov_stride, q.arch_counts, q.fitness, lane);
     }
   }
 }
@@ -426,7 +548,43 @@ struct HostPlan {
   int32_t chunk_cap = 0;
   int device = -1;
   int num_sms = 0;
+  size_t fit_bytes = 0;  // device scratch of the fitness requests (see place_fitness)
 };
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The fitness requests' scratch, in one block: first their counters, contiguous so that one loop
+// zeroes them (per request: overlaps [n_cand][ov_stride], then archive counts [ov_stride], so
+// every overlap row starts on 8 bytes), then the padded archives, then the column masks. With
+// base null only the size is computed (hp->fit_bytes); else the pointers are set, and the
+// counter block is reported in *zero / *n_zero.
+void place_fitness(HostPlan* hp, uint8_t* base, uint32_t** zero, unsigned long long* n_zero) {
+  size_t words = 0;
+  for (BatchReq& q : hp->reqs) {
+    if (!q.fitness || q.n_arch == 0) continue;
+    if (base) {
+      q.overlaps = reinterpret_cast<uint32_t*>(base) + words;
+      q.arch_counts = q.overlaps + (size_t)q.n_cand * q.ov_stride;
+    }
+    words += ((size_t)q.n_cand + 1) * q.ov_stride;
+  }
+  if (base) {
+    *zero = reinterpret_cast<uint32_t*>(base);
+    *n_zero = words;
+  }
+  size_t off = round_up(words * 4, 256);
+  for (BatchReq& q : hp->reqs) {
+    if (!q.fitness || q.n_arch == 0) continue;
+    if (base) q.arch_pad = reinterpret_cast<uint32_t*>(base + off);
+    off += round_up((size_t)q.ov_stride * q.pair_stride * 4, 256);
+  }
+  for (BatchReq& q : hp->reqs) {
+    if (!q.fitness || q.n_arch == 0) continue;
+    if (base) q.colmask = reinterpret_cast<unsigned long long*>(base + off);
+    off += round_up((size_t)q.pair_cols * 8, 256);
+  }
+  hp->fit_bytes = off;
+}
 
 bool is_dev(const void* p, int dev) {
   cudaPointerAttributes at;
@@ -467,6 +625,19 @@ int build_plan(const ebic_eval_request* reqs, uint32_t n, uint32_t fixed_stage_c
         return set_last_error(EBIC_ERR_INVALID_ARG,
                               ("request " + std::to_string(i) +
                                ": batched requests take device buffers only").c_str());
+    }
+    if (r.fitness) {
+      const std::string who = "request " + std::to_string(i) + ": ";
+      if (!v.pairs)
+        return set_last_error(EBIC_ERR_UNSUPPORTED,
+                              (who + "fitness in a batch needs the matrix's pair table").c_str());
+      if (r.n_arch > (uint32_t)kPairMaxArch)
+        return set_last_error(EBIC_ERR_INVALID_ARG, (who + "more than 64 archive members").c_str());
+      if ((r.n_cand > 0 && !is_dev(r.fitness, v.device)) ||
+          (r.n_arch > 0 && (!is_dev(r.arch_cols, v.device) || !is_dev(r.arch_offsets, v.device) ||
+                            !is_dev(r.arch_bitmaps, v.device))))
+        return set_last_error(EBIC_ERR_INVALID_ARG,
+                              (who + "the archive and fitness must be device buffers").c_str());
     }
     int rc = matrix_eval_plan(r.m, r.n_cand > 0 ? r.n_cand : 1, 0, &args[i], &cfgs[i], &maps[i],
                               batch_tile_cap(v.L, (r.flags & EBIC_NEGATIVE_TRENDS) != 0));
@@ -513,12 +684,21 @@ int build_plan(const ebic_eval_request* reqs, uint32_t n, uint32_t fixed_stage_c
     q.pairs = v.pairs;
     q.pair_stride = v.pair_stride;
     q.pair_cols = v.L.cols;
+    if (r.fitness) {
+      q.fitness = r.fitness;
+      q.n_arch = r.n_arch;
+      q.ov_stride = (r.n_arch + 1u) & ~1u;
+      q.arch_cols = r.arch_cols;
+      q.arch_offsets = r.arch_offsets;
+      q.arch_src = r.arch_bitmaps;
+    }
     hp->tmaps.push_back(*maps[i]);
     hp->ncols.push_back(v.L.cols);
     hp->reqs.push_back(q);
     base += r.n_cand;
   }
   hp->total_cand = base;
+  place_fitness(hp, nullptr, nullptr, nullptr);
   return EBIC_OK;
 }
 
@@ -541,7 +721,7 @@ struct DeviceBatch {
   int32_t* ncols = nullptr;
   uint32_t* req_err = nullptr;
   unsigned long long* start = nullptr;
-  unsigned long long* pstart = nullptr;  // [2][n_max + 1]: the pair pass's item starts
+  unsigned long long* pstart = nullptr;  // [4][n_max + 1]: the pair passes' item starts
   BatchHeader* hdr = nullptr;
   uint32_t* err = nullptr;
   uint32_t n_max = 0;
@@ -552,7 +732,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 size_t batch_bytes(uint32_t n_max) {
   return align256(sizeof(BatchReq) * n_max) + align256(sizeof(CUtensorMap) * n_max) +
          align256(4 * (size_t)n_max) + align256(4 * (size_t)n_max) +
-         align256(8 * ((size_t)n_max + 1)) + align256(16 * ((size_t)n_max + 1)) +
+         align256(8 * ((size_t)n_max + 1)) + align256(32 * ((size_t)n_max + 1)) +
          align256(sizeof(BatchHeader)) + 256;
 }
 
@@ -569,7 +749,7 @@ void carve(uint8_t* base, uint32_t n_max, DeviceBatch* d) {
   d->start = reinterpret_cast<unsigned long long*>(base + o);
   o += align256(8 * ((size_t)n_max + 1));
   d->pstart = reinterpret_cast<unsigned long long*>(base + o);
-  o += align256(16 * ((size_t)n_max + 1));
+  o += align256(32 * ((size_t)n_max + 1));
   d->hdr = reinterpret_cast<BatchHeader*>(base + o);
   o += align256(sizeof(BatchHeader));
   d->err = reinterpret_cast<uint32_t*>(base + o);
@@ -587,8 +767,8 @@ int ensure_batch_attr() {
   return EBIC_OK;
 }
 
-// The launches of a batch (check, plan, the rank-code pass, the two pair-table passes),
-// stream-ordered.
+// The launches of a batch (check, plan, the rank-code pass, the two pair-table passes, the
+// fitness), stream-ordered.
 int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, int num_sms,
                  cudaStream_t s) {
   const size_t smem = 2 * (size_t)stage_cap + 2 * ((size_t)chunk_cap + kChunkSlack) +
@@ -607,13 +787,28 @@ int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, in
                                                           stage_cap, chunk_cap, 1000000000ull,
                                                           d.err);
   B_CUDA(cudaGetLastError());
-  // the requests on matrices with a pair table (none: both grids exit at once)
+  // the requests on matrices with a pair table, by trend option and archive (an item space
+  // without requests: its grid exits at once)
+  const size_t ps = (size_t)d.n_max + 1;
   count_launch();
-  batch_pair_kernel<false><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr, d.pstart);
+  batch_pair_kernel<false, false><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
+                                                                           d.pstart);
   B_CUDA(cudaGetLastError());
   count_launch();
-  batch_pair_kernel<true><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
-                                                                    d.pstart + d.n_max + 1);
+  batch_pair_kernel<true, false><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
+                                                                          d.pstart + ps);
+  B_CUDA(cudaGetLastError());
+  count_launch();
+  batch_pair_kernel<false, true><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
+                                                                          d.pstart + 2 * ps);
+  B_CUDA(cudaGetLastError());
+  count_launch();
+  batch_pair_kernel<true, true><<<num_sms, pairdev::kPairThreads, 0, s>>>(d.reqs, d.hdr,
+                                                                         d.pstart + 3 * ps);
+  B_CUDA(cudaGetLastError());
+  // the fitness of the requests that asked for it (none: the grid finds no such request)
+  count_launch();
+  batch_fitness_kernel<<<4 * num_sms, 256, 0, s>>>(d.reqs, d.hdr, d.req_err);
   B_CUDA(cudaGetLastError());
   return EBIC_OK;
 }
@@ -637,6 +832,8 @@ struct ebic_batch {
   cudaEvent_t done = nullptr;
   bool pending = false;
   uint32_t last_n = 0;
+  uint8_t* fmem = nullptr;   // the fitness requests' scratch, grown when a run needs more
+  size_t fbytes = 0;
   std::mutex mu;
 };
 
@@ -654,11 +851,13 @@ int ebic_eval_batch(const ebic_eval_request* reqs, uint32_t n_req, void* stream)
   if (cudaGetDevice(&prev) != cudaSuccess) { (void)cudaGetLastError(); prev = -1; }
   if (prev != hp.device) B_CUDA(cudaSetDevice(hp.device));
   void* mem = nullptr;
-  B_CUDA(cudaMallocAsync(&mem, batch_bytes(n_req), s));
+  const size_t bb = round_up(batch_bytes(n_req), 256);
+  B_CUDA(cudaMallocAsync(&mem, bb + hp.fit_bytes, s));
   DeviceBatch d;
   carve(static_cast<uint8_t*>(mem), n_req, &d);
   BatchHeader h;
   fill_header(hp, n_req, &h);
+  place_fitness(&hp, static_cast<uint8_t*>(mem) + bb, &h.zero, &h.n_zero);
   cudaError_t e = cudaMemcpyAsync(d.reqs, hp.reqs.data(), sizeof(BatchReq) * n_req,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -754,13 +953,23 @@ int ebic_batch_run(ebic_batch* b, const ebic_eval_request* reqs, uint32_t n_req,
         kMaxChunkCols, (kSmemDynMax - 2 * (int64_t)kStageMax - 2 * (kChunkSlack + 1) - 256) / 4);
     for (auto& q : hp.reqs) q.chunk_cols = std::min<int32_t>(q.chunk_cols, (int32_t)(cc / 64 * 64));
   }
-  if (b->pending) B_CUDA(cudaEventSynchronize(b->done));  // the pinned block is read by the graph
+  // the pinned block and the fitness scratch are used by the previous replay until it ends
+  if (b->pending) B_CUDA(cudaEventSynchronize(b->done));
+  b->pending = false;
+  if (hp.fit_bytes > b->fbytes) {
+    if (b->fmem) B_CUDA(cudaFree(b->fmem));
+    b->fmem = nullptr;
+    b->fbytes = 0;
+    B_CUDA(cudaMalloc(&b->fmem, hp.fit_bytes));
+    b->fbytes = hp.fit_bytes;
+  }
+  fill_header(hp, n_req, b->h.hdr);
+  if (hp.fit_bytes) place_fitness(&hp, b->fmem, &b->h.hdr->zero, &b->h.hdr->n_zero);
   if (n_req > 0) {
     std::memcpy(b->h.reqs, hp.reqs.data(), sizeof(BatchReq) * n_req);
     std::memcpy(b->h.tmaps, hp.tmaps.data(), sizeof(CUtensorMap) * n_req);
     std::memcpy(b->h.ncols, hp.ncols.data(), 4 * (size_t)n_req);
   }
-  fill_header(hp, n_req, b->h.hdr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   B_CUDA(cudaGraphLaunch(b->exec, s));
   B_CUDA(cudaEventRecord(b->done, s));
@@ -789,6 +998,7 @@ int ebic_batch_free(ebic_batch* b) {
   if (b->pending) cudaEventSynchronize(b->done);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->fmem) cudaFree(b->fmem);
   cudaFree(b->dmem);
   cudaFreeHost(b->hmem);
   delete b;

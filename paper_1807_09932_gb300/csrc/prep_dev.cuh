@@ -292,20 +292,19 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
   return bad;
 }
 
-// F_c of candidate c of the fused pass, a lane per archive member; the share masks of the
-// preparation stand for the column-set test. L is the candidate's length and al0 / al1 the
-// lengths of members `lane` and `lane + 32` (0 when absent). Lane 0 stores the result.
-__device__ __forceinline__ void fused_fitness_warp(uint32_t c, uint32_t L, uint32_t al0,
-                                                   uint32_t al1, uint32_t n_arch,
+// F_c of candidate c of the fused pass, a lane per archive member; `sh` (the members sharing a
+// column with the candidate) stands for the column-set test. L is the candidate's length and
+// al0 / al1 the lengths of members `lane` and `lane + 32` (0 when absent). Lane 0 stores the
+// result.
+__device__ __forceinline__ void fused_fitness_mask(uint32_t c, uint32_t L, uint32_t al0,
+                                                   uint32_t al1, uint32_t n_arch, uint64_t sh,
                                                    const uint32_t* counts,
                                                    const uint32_t* overlaps, uint32_t ov_stride,
-                                                   const uint32_t* arch_counts,
-                                                   const uint64_t* share, uint64_t* fitness,
+                                                   const uint32_t* arch_counts, uint64_t* fitness,
                                                    int lane) {
   const uint32_t n = counts[c];
   const uint32_t shift = (L < 33u ? L : 33u) - 1u;
   const uint64_t qc = (uint64_t)n << shift;
-  const uint64_t sh = n_arch ? share[c] : 0ull;
   uint32_t best = 0;
   for (uint32_t m = lane; m < n_arch; m += 32) {
     if (!((sh >> m) & 1ull)) continue;  // shares no column with the candidate
@@ -317,6 +316,18 @@ __device__ __forceinline__ void fused_fitness_warp(uint32_t c, uint32_t L, uint3
   }
   best = __reduce_max_sync(0xFFFFFFFFu, best);
   if (lane == 0) fitness[c] = (uint64_t)(n - best) << shift;
+}
+
+// The same with the share masks of the preparation (share[c]).
+__device__ __forceinline__ void fused_fitness_warp(uint32_t c, uint32_t L, uint32_t al0,
+                                                   uint32_t al1, uint32_t n_arch,
+                                                   const uint32_t* counts,
+                                                   const uint32_t* overlaps, uint32_t ov_stride,
+                                                   const uint32_t* arch_counts,
+                                                   const uint64_t* share, uint64_t* fitness,
+                                                   int lane) {
+  fused_fitness_mask(c, L, al0, al1, n_arch, n_arch ? share[c] : 0ull, counts, overlaps,
+                     ov_stride, arch_counts, fitness, lane);
 }
 
 }  // namespace prepdev

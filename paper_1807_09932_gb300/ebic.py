@@ -118,7 +118,9 @@ class EbicEvaluator(ctypes.Structure):
 
 class EbicEvalRequest(ctypes.Structure):
     _fields_ = [("m", _P), ("cols", _P), ("offsets", _P), ("n_cand", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("counts", _P), ("bitmaps", _P)]
+                ("flags", ctypes.c_uint32), ("counts", _P), ("bitmaps", _P),
+                ("arch_cols", _P), ("arch_offsets", _P), ("arch_bitmaps", _P),
+                ("n_arch", ctypes.c_uint32), ("fitness", _P)]
 
 
 _lib_eval_batch = _sig("ebic_eval_batch", [ctypes.POINTER(EbicEvalRequest), _U32, _P])
@@ -287,10 +289,14 @@ def ebic_timing_read(kind):
 
 
 def make_requests(items):
-    """items: (handle, cols, offsets, n_cand, flags, counts, bitmaps) tuples -> ctypes array."""
+    """items: (handle, cols, offsets, n_cand, flags, counts, bitmaps) tuples, optionally followed
+    by (arch_cols, arch_offsets, arch_bitmaps, n_arch, fitness) -> ctypes array."""
     arr = (EbicEvalRequest * max(len(items), 1))()
-    for i, (h, c, o, n, f, cnt, bm) in enumerate(items):
-        arr[i] = EbicEvalRequest(h, _ptr(c), _ptr(o), n, f, _ptr(cnt), _ptr(bm))
+    for i, it in enumerate(items):
+        h, c, o, n, f, cnt, bm = it[:7]
+        ac, ao, ab, k, fit = it[7:] if len(it) > 7 else (None, None, None, 0, None)
+        arr[i] = EbicEvalRequest(h, _ptr(c), _ptr(o), n, f, _ptr(cnt), _ptr(bm), _ptr(ac),
+                                 _ptr(ao), _ptr(ab), k, _ptr(fit))
     return arr
 
 

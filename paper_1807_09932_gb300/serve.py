@@ -14,9 +14,9 @@ The server:
     throughput in candidate-row evals/s.
 
 The device work goes through a backend: ``GpuBackend`` (the C ABI: ebic_batch_run in a CUDA
-graph, then ebic_fitness per request against its run's resident archive) or, in tests, a fake
-one. ``plain_serve`` is the comparison point: the same arrivals served one request at a time
-with the per-population calls (ebic_eval_population + ebic_fitness), in arrival order.
+graph; a run with a pair table gets its fitness against its resident archive inside the batch,
+the others through ebic_fitness per request) or, in tests, a fake one. ``plain_serve`` is the comparison point: the same arrivals served one request at a time
+with the per-population call (ebic_eval_fitness), in arrival order.
 """
 from __future__ import annotations
 
@@ -252,11 +252,12 @@ class GpuBackend:
     def open_run(self, spec: RunSpec):
         torch = self.torch
         m = self.ebic.Matrix(spec.X, exclude_missing=spec.exclude_missing)
-        if 0 < self.pair_bytes(spec) <= self.pair_budget:
+        pairs = 0 < self.pair_bytes(spec) <= self.pair_budget
+        if pairs:
             m.build_pairs(max_bytes=self.pair_budget)
         W = m.words
         P = spec.max_cand
-        run = dict(m=m, P=P, W=W, rows=spec.X.shape[0],
+        run = dict(m=m, P=P, W=W, rows=spec.X.shape[0], pairs=pairs,
                    dcols=torch.empty(P * spec.max_len, dtype=torch.int16, device=self.dev),
                    doffs=torch.empty(P + 1, dtype=torch.int32, device=self.dev),
                    counts=torch.empty(P, dtype=torch.int32, device=self.dev),
@@ -300,8 +301,15 @@ class GpuBackend:
                 run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
                 run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
                 run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
-                items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
-                              run["counts"], run["bitmaps"]))
+                if run["pairs"]:  # fitness inside the batch, the overlaps fused there
+                    k = run["K"]
+                    items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+                                  run["counts"], None, run["acols"] if k else None,
+                                  run["aoffs"] if k else None, run["abm"] if k else None, k,
+                                  run["fit"]))
+                else:
+                    items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+                                  run["counts"], run["bitmaps"]))
             arr = ebic.make_requests(items)
             rc = ebic.ebic_batch_run(slot["batch"], arr, len(items), st.cuda_stream)
             if rc:
@@ -309,12 +317,13 @@ class GpuBackend:
             for r in reqs:
                 run = self.runs[r.run_id]
                 n = r.n_cand
-                rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n,
-                                       run["counts"], run["bitmaps"], run["acols"],
-                                       run["aoffs"], run["abm"], run["K"], 0, run["fit"], None,
-                                       st.cuda_stream)
-                if rc:
-                    raise ebic.EbicError(rc, "ebic_fitness")
+                if not run["pairs"]:  # the rank-code pass wrote bitmaps: the fitness call
+                    rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n,
+                                           run["counts"], run["bitmaps"], run["acols"],
+                                           run["aoffs"], run["abm"], run["K"], 0, run["fit"],
+                                           None, st.cuda_stream)
+                    if rc:
+                        raise ebic.EbicError(rc, "ebic_fitness")
                 run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
                 run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
             ev = torch.cuda.Event()
@@ -333,7 +342,7 @@ class GpuBackend:
             r.counts = run["hcounts"][:n].numpy().view(np.uint32).copy()
             r.fitness = run["hfit"][:n].numpy().view(np.uint64).copy()
 
-    # the comparison point: one request at a time, per-population calls
+    # the comparison point: one request at a time, one per-population call (ebic_eval_fitness)
     def plain(self, r, stream):
         torch, ebic = self.torch, self.ebic
         run = self.runs[r.run_id]
@@ -343,16 +352,12 @@ class GpuBackend:
             run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
             run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
             run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
-            rc = ebic.ebic_eval_population(run["m"].handle, run["dcols"], run["doffs"], n,
-                                           r.flags, run["counts"], run["bitmaps"],
-                                           stream.cuda_stream)
+            rc = ebic.ebic_eval_fitness(run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+                                        run["acols"], run["aoffs"], run["abm"], run["K"],
+                                        run["counts"], None, run["fit"], None,
+                                        stream.cuda_stream)
             if rc:
-                raise ebic.EbicError(rc, "ebic_eval_population")
-            rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n, run["counts"],
-                                   run["bitmaps"], run["acols"], run["aoffs"], run["abm"],
-                                   run["K"], 0, run["fit"], None, stream.cuda_stream)
-            if rc:
-                raise ebic.EbicError(rc, "ebic_fitness")
+                raise ebic.EbicError(rc, "ebic_eval_fitness")
             run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
             run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
         stream.synchronize()

@@ -200,3 +200,102 @@ def test_batch_with_pair_tables(ebic):
         _check_against_direct(ebic, reqs[1:])
     finally:
         ebic.ebic_batch_free(b)
+
+
+def _with_archives(ebic, reqs, seed, sizes=(0, 1, 7, 20, 64, 33)):
+    """Give every request an archive (sizes cycled; about half the members are candidates of the
+    request, so they overlap it and share its columns, the rest random column sets with random
+    bitmaps), a fitness output, and the oracle's expected fitness."""
+    import torch
+    rng = np.random.default_rng(seed)
+    for k, r in enumerate(reqs):
+        X = r["ds"].X
+        R, C = X.shape
+        K = sizes[k % len(sizes)]
+        n = r["n"]
+        cols, offs = r["cols"], r["offs"]
+        ec, eb = oracle.eval_population(X, cols, offs, negative=bool(r["flags"]))
+        k_pop = min(K // 2, n)
+        idx = rng.choice(n, size=k_pop, replace=False)
+        lists = [list(cols[offs[i]:offs[i + 1]]) for i in idx]
+        lists += [list(rng.choice(C, int(rng.integers(1, min(C, 8) + 1)), replace=False))
+                  for _ in range(K - k_pop)]
+        acols, aoffs = synth.population_from_lists(lists) if K else (
+            np.zeros(0, dtype=np.uint16), np.zeros(1, dtype=np.uint32))
+        abm = np.ascontiguousarray(np.concatenate(
+            [eb[idx], synth.random_bitmaps(seed + k, K - k_pop, R, 0.3)]) if K else
+            np.zeros((0, (R + 31) // 32), dtype=np.uint32), dtype=np.uint32)
+        ef, _ = oracle.fitness(R, cols, offs, ec, eb, acols, aoffs, abm)
+        r.update(acols=acols, aoffs=aoffs, abm=abm, K=K, exp_counts=ec, exp_fit=ef,
+                 dacols=_dev(acols) if K else None, daoffs=_dev(aoffs) if K else None,
+                 dabm=_dev(abm) if K else None,
+                 fit=torch.full((n,), -1, dtype=torch.int64, device="cuda"))
+
+
+def _fit_items(reqs):
+    return [(r["m"].handle, r["dcols"], r["doffs"], r["n"], r["flags"], r["counts"],
+             r["bitmaps"], r["dacols"], r["daoffs"], r["dabm"], r["K"], r["fit"]) for r in reqs]
+
+
+def _check_fitness(reqs):
+    for r in reqs:
+        assert np.array_equal(r["counts"].cpu().numpy().view(np.uint32), r["exp_counts"])
+        assert np.array_equal(r["fit"].cpu().numpy().view(np.uint64), r["exp_fit"])
+
+
+def test_batch_fitness_equals_oracle(ebic):
+    """Requests with an archive get ebic_eval_fitness's fitness from the batched pass (overlaps
+    fused there, 0 to 64 members, odd and even archive sizes, with and without bitmaps, both
+    trend options), directly and through the captured graph, equal to the oracle's; a request
+    without an archive in the same batch is unaffected; fitness on a matrix without a pair
+    table is refused; a request with a bad archive list fails alone."""
+    import torch
+    mats = _matrices(ebic)
+    _with_pairs(ebic, mats, lambda i: True)
+    reqs = _requests(ebic, mats, 24, seed=31)
+    _with_archives(ebic, reqs, seed=32)
+    plain = _requests(ebic, mats, 3, seed=33)   # no fitness, same batch
+    items = _fit_items(reqs) + _items(plain)
+    arr = ebic.make_requests(items)
+    assert ebic.ebic_eval_batch(arr, len(items)) == ebic.EBIC_OK, ebic.ebic_last_error()
+    torch.cuda.synchronize()
+    for _, m in mats:
+        assert m.status() == ebic.EBIC_OK
+    _check_fitness(reqs)
+    _check_against_direct(ebic, [r for r in reqs if r["bitmaps"] is not None] + plain)
+    b = ebic.ebic_batch_create(64)
+    try:
+        for seed in (34, 35):   # the graph, twice, on new compositions (scratch regrown)
+            reqs = _requests(ebic, mats, 40 if seed == 34 else 64, seed=seed)
+            _with_archives(ebic, reqs, seed=seed + 100, sizes=(20, 3, 64, 0, 2))
+            arr = ebic.make_requests(_fit_items(reqs))
+            assert ebic.ebic_batch_run(b, arr, len(reqs)) == ebic.EBIC_OK, ebic.ebic_last_error()
+            rc, st = ebic.ebic_batch_status(b, len(reqs))
+            assert rc == ebic.EBIC_OK and not any(st)
+            _check_fitness(reqs)
+        # a repeated column in one request's archive: that request fails alone
+        reqs = _requests(ebic, mats, 6, seed=36)
+        _with_archives(ebic, reqs, seed=136, sizes=(5,))
+        bad = reqs[0]
+        ac = bad["acols"].copy()
+        ac[1] = ac[0]
+        bad["dacols"] = _dev(ac)
+        arr = ebic.make_requests(_fit_items(reqs))
+        assert ebic.ebic_batch_run(b, arr, len(reqs)) == ebic.EBIC_OK
+        rc, st = ebic.ebic_batch_status(b, len(reqs))
+        assert rc == ebic.EBIC_ERR_INVALID_ARG
+        assert st[0] != 0 and all(s == 0 for i, s in enumerate(st) if i != 0)
+        assert bad["m"].status() == ebic.EBIC_ERR_INVALID_ARG
+        _check_fitness(reqs[1:])
+    finally:
+        ebic.ebic_batch_free(b)
+    # fitness needs the pair table
+    ds = synth.make_dataset(7, 500, 12, kind="normal")
+    with ebic.Matrix(ds.X) as m:
+        cols, offs = synth.make_population(8, 10, 12, 2, 5)
+        n = len(offs) - 1
+        cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+        fit = torch.zeros(n, dtype=torch.int64, device="cuda")
+        arr = ebic.make_requests([(m.handle, _dev(cols), _dev(offs), n, 0, cnt, None, None, None,
+                                   None, 0, fit)])
+        assert ebic.ebic_eval_batch(arr, 1) == ebic.EBIC_ERR_UNSUPPORTED

@@ -92,10 +92,14 @@ def test_one_request_in_flight_per_run_and_results_exact():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("pair_budget", [0, 1 << 30])
+def test_served_results_equal_alone(pair_budget):
+    """Served counts and fitness equal the per-population calls' and the oracle's counts, with
+    runs on the rank-code pass (fitness per request) and on pair tables (fitness inside the
+    batch)."""
     import torch
     from paper_1807_09932_gb300 import ebic
-    be = serve.GpuBackend(max_batch=16, max_inflight=2)
+    be = serve.GpuBackend(max_batch=16, max_inflight=2, pair_budget=pair_budget)
     try:
         srv = serve.Server(be, hbm_budget=8 << 30, max_batch=16, max_inflight=2)
         specs = []
