@@ -468,8 +468,8 @@ __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
     pairdev::terms_from_cols<NEG>(c_lo, c_hi, L, (uint32_t)q.pair_cols, q.pair_stride, lane, t);
     uint4 x[pairdev::kParts];
     pairdev::pair_chain<NEG>(t, q.pairs + rword + 4 * lane,
-                             pair_ones(q.pairs, (uint64_t)q.pair_cols, q.pair_stride) + 4 * lane,
-                             lane, x);
+                             pair_ones(q.pairs, (uint64_t)q.pair_cols, q.pair_stride), lane,
+                             x);
     uint32_t pc = 0;
 #pragma unroll
     for (int k = 0; k < pairdev::kParts; ++k) pc += pairdev::popc4(x[k]);

@@ -130,7 +130,8 @@ constexpr int kPairRangeWords = 512;  // table and padded archive row strides ar
 constexpr int kPairMaxArch = 64;      // archive members the fused overlap pass takes
 // Row stride (words) of the pair table and of padded archive bitmaps for W-word bitmaps.
 // A pair table allocation ends with one row of kOnesWords all-ones words (after the C*C
-// table rows): a chain step reads it in place of a part it no longer needs.
+// table rows): a lane of a chain step reads its first 16 bytes in place of a segment whose
+// words it has already zeroed.
 constexpr int kOnesWords = 128;
 __host__ __device__ inline const uint32_t* pair_ones(const uint32_t* table, uint64_t cols,
                                                     uint64_t stride) {

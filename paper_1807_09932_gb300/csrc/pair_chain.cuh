@@ -83,10 +83,10 @@ __device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ col
 // The candidate's bitmap words 4*lane .. 4*lane+3 of each 128-word part of the item whose first
 // table word is `base` (table + item*kItemWords): AND of its consecutive pairs' table rows, OR
 // the reversed pairs' AND with negative trends. Each step keeps the rows of several terms of
-// every part in flight; a part stops loading once every word of it in the warp is zero, and the
-// walk stops when all are (long chains match no row of most ranges). `ones` is the lane's words
-// of the table's all-ones row: a step reads them in place of a part that is already zero or a
-// term past the end, so every load and AND of a step is unconditional.
+// every part in flight. A lane whose own words of a part are all zero (they stay zero) reads the
+// table's all-ones chunk `ones` instead of its segment: every lane doing so reads the same 16
+// bytes, so the step's requests shrink to the lanes that still match rows, with no branch. The
+// walk stops when no lane has a non-zero word left (long chains match no row of most ranges).
 template <bool NEG>
 __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
                                            const uint32_t* ones, int lane,
@@ -97,12 +97,13 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
   const bool two = NEG && L > 1;  // warp-uniform
   const uint4 all = make_uint4(~0u, ~0u, ~0u, ~0u);
   uint4 x[kParts], y[kParts];
-  bool live[kParts];  // warp-uniform: the part still has a non-zero word
+  bool nzx[kParts], nzy[kParts];  // this lane's words of the part are not all zero
 #pragma unroll
   for (int q = 0; q < kParts; ++q) {
     x[q] = y[q] = all;
-    live[q] = true;
+    nzx[q] = nzy[q] = true;
   }
+  (void)lane;
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
   auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
     for (int i0 = t0; i0 < t1; i0 += kStep) {
@@ -114,44 +115,41 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
         const uint32_t* rf = base + __shfl_sync(0xFFFFFFFFu, offf, i & 31);
 #pragma unroll
         for (int q = 0; q < kParts; ++q)
-          v[k][q] = __ldg(reinterpret_cast<const uint4*>(has && live[q] ? rf + q * kRangeWords
-                                                                        : ones));
+          v[k][q] = __ldg(reinterpret_cast<const uint4*>(has && nzx[q] ? rf + q * kRangeWords
+                                                                       : ones));
         if (NEG) {
           const uint32_t* rb = base + __shfl_sync(0xFFFFFFFFu, offb, i & 31);
 #pragma unroll
           for (int q = 0; q < kParts; ++q)
-            u[k][q] = __ldg(reinterpret_cast<const uint4*>(two && has && live[q]
+            u[k][q] = __ldg(reinterpret_cast<const uint4*>(two && has && nzy[q]
                                                                ? rb + q * kRangeWords
                                                                : ones));
         }
       }
-      bool any_live = false;
+      bool lane_any = false;
 #pragma unroll
       for (int q = 0; q < kParts; ++q) {
 #pragma unroll
         for (int k = 0; k < kStep; ++k) x[q] = and4(x[q], v[k][q]);
-        uint32_t any = x[q].x | x[q].y | x[q].z | x[q].w;
-        if (NEG) {
+        nzx[q] = (x[q].x | x[q].y | x[q].z | x[q].w) != 0u;
+        lane_any |= nzx[q];
+        if (NEG && two) {
 #pragma unroll
           for (int k = 0; k < kStep; ++k) y[q] = and4(y[q], u[k][q]);
-          if (two) any |= y[q].x | y[q].y | y[q].z | y[q].w;
+          nzy[q] = (y[q].x | y[q].y | y[q].z | y[q].w) != 0u;
+          lane_any |= nzy[q];
         }
-        live[q] = __any_sync(0xFFFFFFFFu, any != 0u);
-        any_live |= live[q];
       }
-      if (!any_live) return false;  // all zero from here on
+      if (!__any_sync(0xFFFFFFFFu, lane_any)) return false;  // all zero from here on
     }
     return true;
   };
   if (walk(t.lo, t.blo, 0, n_terms < 32 ? n_terms : 32) && n_terms > 32)
     walk(t.hi, t.bhi, 32, n_terms);
 #pragma unroll
-  for (int q = 0; q < kParts; ++q) {
-    if (two) x[q] = make_uint4(x[q].x | y[q].x, x[q].y | y[q].y, x[q].z | y[q].z,
-                               x[q].w | y[q].w);
-    // a part that went all-zero stays zero (its remaining terms were not loaded)
-    out[q] = live[q] ? x[q] : make_uint4(0u, 0u, 0u, 0u);
-  }
+  for (int q = 0; q < kParts; ++q)
+    out[q] = two ? make_uint4(x[q].x | y[q].x, x[q].y | y[q].y, x[q].z | y[q].z, x[q].w | y[q].w)
+                 : x[q];
 }
 
 // An archive row segment: re-read by every warp of the CTA that scores a candidate of the same
@@ -313,7 +311,7 @@ __device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
   const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
   const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
-  const uint32_t* ones = pair_ones(p.table, (uint64_t)p.C, p.stride) + 4 * lane;
+  const uint32_t* ones = pair_ones(p.table, (uint64_t)p.C, p.stride);
   // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
   // the term list of the warp's next item is loaded while the current one is walked
   const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
