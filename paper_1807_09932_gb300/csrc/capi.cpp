@@ -109,6 +109,47 @@ bool foreign_device(const void* p, int dev) {
   return at.type == cudaMemoryTypeDevice && at.device != dev;
 }
 
+// A pointer's placement relative to device `dev`, from one attribute query.
+struct Where {
+  bool dev = false;      // device memory of `dev`, or managed
+  bool foreign = false;  // device memory of another device
+};
+
+Where where(const void* p, int dev) {
+  Where w;
+  if (!p) return w;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return w;
+  }
+  w.dev = at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
+  w.foreign = at.type == cudaMemoryTypeDevice && at.device != dev;
+  return w;
+}
+
+// to_device / out_buffer with the placement already known.
+template <class T>
+cudaError_t to_device_at(const T* p, size_t n, bool is_dev, Scratch& sc, const T** out) {
+  if (is_dev) { *out = p; return cudaSuccess; }
+  void* d = nullptr;
+  cudaError_t e = sc.alloc(&d, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpyAsync(d, p, n * sizeof(T), cudaMemcpyHostToDevice, sc.s);
+  *out = static_cast<const T*>(d);
+  return e;
+}
+
+template <class T>
+cudaError_t out_buffer_at(T* p, size_t n, bool is_dev, Scratch& sc, T** out, bool* host) {
+  if (is_dev) { *out = p; *host = false; return cudaSuccess; }
+  void* d = nullptr;
+  cudaError_t e = sc.alloc(&d, n * sizeof(T));
+  *out = static_cast<T*>(d);
+  *host = true;
+  return e;
+}
+
 template <class T>
 cudaError_t to_device(const T* p, size_t n, int dev, Scratch& sc, const T** out) {
   if (on_device(p, dev)) { *out = p; return cudaSuccess; }
@@ -145,14 +186,25 @@ void init_pool(int dev) {
 
 // Host-side check of a CSR candidate list: offsets[0] == 0, lengths in [1, 64], columns in
 // range and distinct. Returns an empty string when valid.
-std::string check_candidates_host(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
-                                  int32_t ncols) {
+// The offsets of a host-resident CSR list: offsets[0] == 0 and every length in [1, 64], so
+// offsets[n] bounds the columns a copy reads.
+std::string check_offsets_host(const uint32_t* offsets, uint32_t n) {
   if (offsets[0] != 0) return "offsets[0] must be 0";
-  std::vector<uint32_t> seen((size_t)ncols, 0xFFFFFFFFu);
   for (uint32_t i = 0; i < n; ++i) {
     const uint32_t a = offsets[i], b = offsets[i + 1];
     if (b <= a || b - a > (uint32_t)kMaxLen)
       return "candidate " + std::to_string(i) + " has length outside [1, 64]";
+  }
+  return "";
+}
+
+// The columns of a host-resident CSR list whose offsets passed check_offsets_host: each below
+// ncols and distinct within its candidate.
+std::string check_columns_host(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                               int32_t ncols) {
+  std::vector<uint32_t> seen((size_t)ncols, 0xFFFFFFFFu);
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t a = offsets[i], b = offsets[i + 1];
     for (uint32_t j = a; j < b; ++j) {
       const uint16_t c = cols[j];
       if (c >= (uint32_t)ncols)
@@ -164,6 +216,12 @@ std::string check_candidates_host(const uint16_t* cols, const uint32_t* offsets,
     }
   }
   return "";
+}
+
+std::string check_candidates_host(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
+                                  int32_t ncols) {
+  std::string why = check_offsets_host(offsets, n);
+  return why.empty() ? check_columns_host(cols, offsets, n, ncols) : why;
 }
 
 // Tensor map over the rank matrix: dims {32*VEC words, Q slabs, C columns}, box
@@ -756,8 +814,8 @@ static int finish_fitness(uint32_t n_cand, uint32_t n_arch, uint32_t ov_stride,
                           uint32_t* dcounts, uint32_t* dbm, uint64_t* dfit, uint32_t* dov,
                           uint32_t* err, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
                           uint32_t* overlaps, bool counts_host, bool bm_host, bool fit_host,
-                          int64_t words, int dev, cudaStream_t s) {
-  const bool ov_host = overlaps && n_arch > 0 && !on_device(overlaps, dev);
+                          int64_t words, bool ov_dev, cudaStream_t s) {
+  const bool ov_host = overlaps && n_arch > 0 && !ov_dev;
   if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout
     EBIC_CUDA(cudaMemcpy2DAsync(overlaps, (size_t)n_arch * 4, dov, (size_t)ov_stride * 4,
                                 (size_t)n_arch * 4, n_cand,
@@ -796,10 +854,13 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
   const int dev = m->device;
   const Layout& L = m->L;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
-                        (const void*)bitmaps, (const void*)arch_cols, (const void*)arch_offsets,
-                        (const void*)arch_bitmaps, (const void*)fitness, (const void*)overlaps})
-    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+  // each pointer's placement, queried once
+  const Where w_cols = where(cols, dev), w_offs = where(offsets, dev), w_cnt = where(counts, dev),
+              w_bm = where(bitmaps, dev), w_acols = where(arch_cols, dev),
+              w_aoffs = where(arch_offsets, dev), w_abm = where(arch_bitmaps, dev),
+              w_fit = where(fitness, dev), w_ov = where(overlaps, dev);
+  for (const Where& w : {w_cols, w_offs, w_cnt, w_bm, w_acols, w_aoffs, w_abm, w_fit, w_ov})
+    if (w.foreign) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
 
   const bool fused = m->pairs && !(flags & EBIC_EVAL_DIRECT) && n_arch <= (uint32_t)kPairMaxArch;
   if (!fused) {
@@ -813,38 +874,56 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
                         arch_bitmaps, n_arch, 0, fitness, overlaps, stream);
   }
 
-  const bool host_c = !on_device(cols, dev) && !on_device(offsets, dev);
-  if (host_c) {
-    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
-    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
-  }
-  const bool host_a = n_arch == 0 || (!on_device(arch_cols, dev) && !on_device(arch_offsets, dev));
-  if (n_arch > 0 && host_a) {
-    std::string why = check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
-    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
-  }
-  if ((!host_c && (!on_device(cols, dev) || !on_device(offsets, dev))) ||
-      (n_arch > 0 && !host_a && (!on_device(arch_cols, dev) || !on_device(arch_offsets, dev))))
+  const bool host_c = !w_cols.dev && !w_offs.dev;
+  const bool host_a = n_arch == 0 || (!w_acols.dev && !w_aoffs.dev);
+  if ((!host_c && (!w_cols.dev || !w_offs.dev)) ||
+      (n_arch > 0 && !host_a && (!w_acols.dev || !w_aoffs.dev)))
     return fail(EBIC_ERR_INVALID_ARG,
                 "a candidate list must have its columns and offsets in the same memory");
+  // host lists: the offsets (they bound what the copies read) before any launch; the columns
+  // too when the other list is device-resident, else while the kernels run (the device
+  // preparation checks them as well, without recording a deferred status, so a bad host list
+  // leaves every kernel a no-op and the call returns the host check's verdict)
+  const bool all_host = host_c && host_a;
+  if (host_c) {
+    std::string why = all_host ? check_offsets_host(offsets, n_cand)
+                               : check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+  }
+  if (n_arch > 0 && host_a) {
+    std::string why = all_host ? check_offsets_host(arch_offsets, n_arch)
+                               : check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
+  }
+  auto deferred_host_check = [&]() -> int {
+    if (!all_host) return EBIC_OK;
+    std::string why = check_columns_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+    if (n_arch > 0) {
+      why = check_columns_host(arch_cols, arch_offsets, n_arch, L.cols);
+      if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
+    }
+    return EBIC_OK;
+  };
 
   Scratch sc(s);
   const uint16_t *dcols = nullptr, *dacols = nullptr;
   const uint32_t *doffs = nullptr, *daoffs = nullptr, *dabm = nullptr;
-  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
-  EBIC_CUDA(to_device(cols, host_c ? (size_t)offsets[n_cand] : 0, dev, sc, &dcols));
+  EBIC_CUDA(to_device_at(offsets, (size_t)n_cand + 1, w_offs.dev, sc, &doffs));
+  EBIC_CUDA(to_device_at(cols, host_c ? (size_t)offsets[n_cand] : 0, w_cols.dev, sc, &dcols));
   if (n_arch > 0) {
-    EBIC_CUDA(to_device(arch_offsets, (size_t)n_arch + 1, dev, sc, &daoffs));
-    EBIC_CUDA(to_device(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, dev, sc, &dacols));
-    EBIC_CUDA(to_device(arch_bitmaps, (size_t)n_arch * L.words, dev, sc, &dabm));
+    EBIC_CUDA(to_device_at(arch_offsets, (size_t)n_arch + 1, w_aoffs.dev, sc, &daoffs));
+    EBIC_CUDA(to_device_at(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, w_acols.dev, sc,
+                           &dacols));
+    EBIC_CUDA(to_device_at(arch_bitmaps, (size_t)n_arch * L.words, w_abm.dev, sc, &dabm));
   }
   bool counts_host = false, bm_host = false, fit_host = false;
   uint32_t *dcounts = nullptr, *dbm = nullptr;
   uint64_t* dfit = nullptr;
-  EBIC_CUDA(out_buffer(counts, n_cand, dev, sc, &dcounts, &counts_host));
+  EBIC_CUDA(out_buffer_at(counts, n_cand, w_cnt.dev, sc, &dcounts, &counts_host));
   if (bitmaps)
-    EBIC_CUDA(out_buffer(bitmaps, (size_t)n_cand * L.words, dev, sc, &dbm, &bm_host));
-  EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
+    EBIC_CUDA(out_buffer_at(bitmaps, (size_t)n_cand * L.words, w_bm.dev, sc, &dbm, &bm_host));
+  EBIC_CUDA(out_buffer_at(fitness, n_cand, w_fit.dev, sc, &dfit, &fit_host));
 
   const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
   // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
@@ -898,7 +977,7 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     pa.terms = dterms;
     pa.negative = neg;
     pa.flags = dflags;
-    pa.status = m->status;
+    pa.status = all_host ? nullptr : m->status;  // host lists: the host check reports
     EBIC_CUDA(launch_fused_prepare(pa, prep_blocks, s));
   }
   {
@@ -929,9 +1008,11 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, ov_stride,
                                     darch_counts, dshare, dfit, err, !timing_on(), s));
   }
+  const int hc = deferred_host_check();
+  if (hc != EBIC_OK) return hc;
   return finish_fitness(n_cand, n_arch, ov_stride, dcounts, dbm, dfit, dov, err, counts,
-                        bitmaps, fitness, overlaps, counts_host, bm_host, fit_host, L.words, dev,
-                        s);
+                        bitmaps, fitness, overlaps, counts_host, bm_host, fit_host, L.words,
+                        w_ov.dev, s);
 }
 
 int ebic_matrix_status(ebic_matrix* m, void* stream) {
