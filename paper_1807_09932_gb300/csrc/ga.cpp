@@ -46,7 +46,49 @@ struct Rng {  // splitmix64 (Steele, Lea, Flood 2014), as a counter-based genera
   double unit() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
 };
 
-using Cand = std::vector<uint16_t>;
+// A candidate: up to kMaxLen columns held inline, so copying, crossing and mutating the
+// population allocates nothing. The members the GA uses behave as std::vector's do.
+struct Cand {
+  uint32_t n = 0;
+  uint16_t c[kMaxLen];
+  Cand() = default;
+  template <class It>
+  Cand(It b, It e) {
+    for (; b != e; ++b) c[n++] = (uint16_t)*b;
+  }
+  Cand(const Cand& o) : n(o.n) { std::memcpy(c, o.c, (size_t)n * 2); }
+  Cand& operator=(const Cand& o) {
+    n = o.n;
+    std::memcpy(c, o.c, (size_t)n * 2);
+    return *this;
+  }
+  size_t size() const { return n; }
+  uint16_t* begin() { return c; }
+  uint16_t* end() { return c + n; }
+  const uint16_t* begin() const { return c; }
+  const uint16_t* end() const { return c + n; }
+  uint16_t& operator[](size_t i) { return c[i]; }
+  uint16_t operator[](size_t i) const { return c[i]; }
+  void push_back(uint16_t x) { c[n++] = x; }
+  uint16_t* insert(uint16_t* pos, uint16_t x) {
+    std::memmove(pos + 1, pos, (size_t)(end() - pos) * 2);
+    *pos = x;
+    ++n;
+    return pos;
+  }
+  uint16_t* erase(uint16_t* pos) {
+    std::memmove(pos, pos + 1, (size_t)(end() - pos - 1) * 2);
+    --n;
+    return pos;
+  }
+  bool operator==(const Cand& o) const {
+    return n == o.n && std::memcmp(c, o.c, (size_t)n * 2) == 0;
+  }
+  bool operator!=(const Cand& o) const { return !(*this == o); }
+  bool operator<(const Cand& o) const {
+    return std::lexicographical_compare(begin(), end(), o.begin(), o.end());
+  }
+};
 
 struct CandHash {
   size_t operator()(const Cand& c) const {
@@ -67,8 +109,10 @@ class CandSet {
     ent_.clear();
   }
   size_t count(const Cand& c) const { return find(c, CandHash()(c)) ? 1 : 0; }
-  bool insert(const Cand& c) {
-    const uint64_t h = CandHash()(c);
+  bool insert(const Cand& c) { return insert(c, CandHash()(c)); }
+  // the same with the sequence's hash (CandHash) already computed
+  size_t count(const Cand& c, uint64_t h) const { return find(c, h) ? 1 : 0; }
+  bool insert(const Cand& c, uint64_t h) {
     if (find(c, h)) return false;
     if ((ent_.size() + 1) * 2 > slots_.size()) grow();
     ent_.push_back(Ent{(uint32_t)arena_.size(), (uint32_t)c.size(), h});
@@ -122,7 +166,27 @@ struct Evaluator {
   virtual ~Evaluator() = default;
   virtual int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs,
                        uint32_t n, uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) = 0;
+  // Scoring in two halves, so that the caller can work between them: begin issues the scoring
+  // (the lists must stay unchanged until end), end writes counts, fitness and overlaps. By
+  // default begin does it all.
+  virtual int evaluate_begin(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs,
+                             uint32_t n, uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) {
+    return evaluate(cols, offs, n, counts, fitness, overlaps);
+  }
+  virtual int evaluate_end() { return EBIC_OK; }
   virtual int pair_overlaps(const std::vector<uint32_t>& idx, uint32_t* out) = 0;
+  // The same in two halves, so that the caller can work between them: begin issues the work for
+  // `idx`, end (called once after each begin) writes the [t][t] overlaps to out. By default
+  // begin does it all.
+  virtual int pair_overlaps_begin(const std::vector<uint32_t>& idx) {
+    pending_.assign(idx.size() * idx.size(), 0u);
+    return idx.empty() ? EBIC_OK : pair_overlaps(idx, pending_.data());
+  }
+  virtual int pair_overlaps_end(uint32_t* out) {
+    std::copy(pending_.begin(), pending_.end(), out);
+    return EBIC_OK;
+  }
+  std::vector<uint32_t> pending_;
   virtual int set_archive(const std::vector<int32_t>& src) = 0;
   virtual bool has_bitmaps() const { return false; }
   virtual int archive_bitmaps(uint32_t* out, uint32_t k) { (void)out; (void)k; return EBIC_OK; }
@@ -249,13 +313,16 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
   Ga ga(p, ncols);
   CandSet tabu, in_archive, picked, in_next;
   std::vector<Cand> pop;
+  std::vector<uint64_t> pop_h;  // each candidate's CandHash, computed once
   pop.reserve(P);
+  pop_h.reserve(P);
   {
     CandSet seen;
     for (uint32_t i = 0; i < P; ++i) {
       Cand c = ga.random_candidate();
       for (int t = 0; t < 32 && seen.count(c); ++t) c = ga.random_candidate();
       seen.insert(c);
+      pop_h.push_back(CandHash()(c));
       pop.push_back(std::move(c));
     }
   }
@@ -263,7 +330,9 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
   std::vector<uint16_t> cols;
   std::vector<uint32_t> offs;
   std::vector<uint32_t> counts(P), overlaps((size_t)P * K), order(P), rank(P);
-  std::vector<uint64_t> fitness(P), head4(P);
+  std::vector<uint64_t> fitness(P), head4(P), qual(P);
+  std::vector<uint32_t> heap;
+  heap.reserve(P);
   uint64_t evaluated = 0;
   uint32_t gen = 0;
   for (; gen < p.generations; ++gen) {
@@ -273,10 +342,12 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
       cols.insert(cols.end(), c.begin(), c.end());
       offs.push_back((uint32_t)cols.size());
     }
-    int rc = ev.evaluate(cols, offs, P, counts.data(), fitness.data(), overlaps.data());
+    int rc = ev.evaluate_begin(cols, offs, P, counts.data(), fitness.data(), overlaps.data());
+    if (rc != EBIC_OK) return rc;
+    for (uint32_t i = 0; i < P; ++i) tabu.insert(pop[i], pop_h[i]);  // while the GPU scores
+    rc = ev.evaluate_end();
     if (rc != EBIC_OK) return rc;
     evaluated += P;
-    for (const Cand& c : pop) tabu.insert(c);
     const size_t K_eval = archive.size();  // overlaps is [P][K_eval]
 
     // lexicographic order of equal-length sequences: their first four columns packed high to low
@@ -307,24 +378,81 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     // being strictly worse; strictly worse members that overlap it that much are replaced.
     in_archive.clear();
     for (const Member& m : archive) in_archive.insert(m.cols);
+    // the offers in member_before order (ties between equal sequences by population index):
+    // candidates with rows popped from a heap until 2K distinct non-archived ones are taken, the
+    // same as sorting all of them after dropping later duplicates
     std::vector<Member> offers;
     {
+      for (uint32_t i = 0; i < P; ++i) qual[i] = quality(counts[i], pop[i].size());
+      auto after = [&](uint32_t a, uint32_t b) {  // heap order: true when a comes after b
+        if (qual[a] != qual[b]) return qual[a] < qual[b];
+        if (counts[a] != counts[b]) return counts[a] < counts[b];
+        if (pop[a].size() != pop[b].size()) return pop[a].size() < pop[b].size();
+        if (pop[a] != pop[b]) return pop[b] < pop[a];
+        return a > b;
+      };
+      heap.clear();
+      for (uint32_t i = 0; i < P; ++i)
+        if (counts[i] != 0) heap.push_back(i);
+      std::make_heap(heap.begin(), heap.end(), after);
       picked.clear();
-      for (uint32_t i = 0; i < P; ++i) {
-        if (counts[i] == 0 || in_archive.count(pop[i]) || picked.count(pop[i])) continue;
+      while (!heap.empty() && offers.size() < 2 * (size_t)K) {
+        std::pop_heap(heap.begin(), heap.end(), after);
+        const uint32_t i = heap.back();
+        heap.pop_back();
+        if (in_archive.count(pop[i]) || picked.count(pop[i])) continue;
         picked.insert(pop[i]);
-        offers.push_back(Member{pop[i], counts[i], quality(counts[i], pop[i].size()), (int32_t)i});
+        offers.push_back(Member{pop[i], counts[i], qual[i], (int32_t)i});
       }
-      std::stable_sort(offers.begin(), offers.end(), member_before);
-      if (offers.size() > 2 * (size_t)K) offers.resize(2 * (size_t)K);
     }
     std::vector<uint32_t> top;
     for (const Member& m : offers) top.push_back((uint32_t)m.src);
-    std::vector<uint32_t> pair((size_t)top.size() * top.size());
-    if (!top.empty()) {
-      rc = ev.pair_overlaps(top, pair.data());
-      if (rc != EBIC_OK) return rc;
+    // their pairwise overlaps are computed while the next population is built (it depends on
+    // neither the archive nor the overlaps, and the archive update draws no random numbers)
+    rc = ev.pair_overlaps_begin(top);
+    if (rc != EBIC_OK) return rc;
+    std::vector<Cand> next;
+    std::vector<uint64_t> next_h;
+    if (gen + 1 < p.generations) {
+      next.reserve(P);
+      next_h.reserve(P);
+      in_next.clear();
+      for (uint32_t r = 0; r < p.elite; ++r) {
+        next.push_back(pop[order[r]]);
+        next_h.push_back(pop_h[order[r]]);
+        in_next.insert(pop[order[r]], pop_h[order[r]]);
+      }
+      auto tournament = [&]() {
+        uint32_t best = ga.rng.below(P);
+        for (uint32_t t = 1; t < p.tournament; ++t) {
+          const uint32_t c = ga.rng.below(P);
+          if (rank[c] < rank[best]) best = c;
+        }
+        return best;
+      };
+      while (next.size() < P) {
+        const uint32_t a = tournament();
+        Cand child = pop[a];
+        if (ga.rng.unit() < p.p_crossover) child = ga.crossover(pop[a], pop[tournament()]);
+        if (ga.rng.unit() < p.p_mutation) ga.mutate(child);
+        uint64_t h = CandHash()(child);
+        auto taken = [&]() { return tabu.count(child, h) || in_next.count(child, h); };
+        for (uint32_t t = 0; t < p.tabu_retries && taken(); ++t) {
+          ga.mutate(child);
+          h = CandHash()(child);
+        }
+        for (int t = 0; t < 32 && taken(); ++t) {
+          child = ga.random_candidate();
+          h = CandHash()(child);
+        }
+        in_next.insert(child, h);
+        next_h.push_back(h);
+        next.push_back(std::move(child));
+      }
     }
+    std::vector<uint32_t> pair((size_t)top.size() * top.size());
+    rc = ev.pair_overlaps_end(pair.data());
+    if (rc != EBIC_OK) return rc;
     std::vector<bool> alive(archive.size(), true);
     std::vector<size_t> admitted;  // positions in `offers`
     for (size_t t = 0; t < offers.size(); ++t) {
@@ -364,36 +492,8 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     archive = merged;
 
     if (gen + 1 == p.generations) { ++gen; break; }
-
-    // ---- next population ----
-    std::vector<Cand> next;
-    next.reserve(P);
-    in_next.clear();
-    for (uint32_t r = 0; r < p.elite; ++r) {
-      next.push_back(pop[order[r]]);
-      in_next.insert(pop[order[r]]);
-    }
-    auto tournament = [&]() {
-      uint32_t best = ga.rng.below(P);
-      for (uint32_t t = 1; t < p.tournament; ++t) {
-        const uint32_t c = ga.rng.below(P);
-        if (rank[c] < rank[best]) best = c;
-      }
-      return best;
-    };
-    while (next.size() < P) {
-      const uint32_t a = tournament();
-      Cand child = pop[a];
-      if (ga.rng.unit() < p.p_crossover) child = ga.crossover(pop[a], pop[tournament()]);
-      if (ga.rng.unit() < p.p_mutation) ga.mutate(child);
-      for (uint32_t t = 0; t < p.tabu_retries && (tabu.count(child) || in_next.count(child)); ++t)
-        ga.mutate(child);
-      for (int t = 0; t < 32 && (tabu.count(child) || in_next.count(child)); ++t)
-        child = ga.random_candidate();
-      in_next.insert(child);
-      next.push_back(std::move(child));
-    }
-    pop.swap(next);
+    pop.swap(next);  // the next population, built above
+    pop_h.swap(next_h);
   }
 
   // ---- result ----
@@ -473,6 +573,14 @@ struct GpuEvaluator : Evaluator {
   uint64_t *dfit = nullptr, *pfit = nullptr;
   int32_t* didx = nullptr;  // rows to gather (population index, or -(archive index + 1))
   std::vector<int32_t> hidx;
+  uint32_t* hpov = nullptr;  // pinned [T][T]: the pair overlaps' copy-back
+  uint32_t pending_t = 0;
+  // pinned copy-backs of a generation's scores, and where evaluate_end puts them
+  uint32_t *hcnt = nullptr, *hov = nullptr;
+  uint64_t* hfit = nullptr;
+  uint32_t *out_counts = nullptr, *out_overlaps = nullptr;
+  uint64_t* out_fitness = nullptr;
+  uint32_t out_n = 0, out_k = 0;
   std::vector<uint16_t> pop_cols, arch_cols;
   std::vector<uint32_t> pop_offs, arch_offs{0}, host_counts;
   uint32_t n_arch = 0;
@@ -483,6 +591,10 @@ struct GpuEvaluator : Evaluator {
   ~GpuEvaluator() override {
     cudaStreamSynchronize(s);
     for (void* a : allocs) cudaFree(a);
+    if (hpov) cudaFreeHost(hpov);
+    if (hcnt) cudaFreeHost(hcnt);
+    if (hfit) cudaFreeHost(hfit);
+    if (hov) cudaFreeHost(hov);
   }
   template <class X>
   cudaError_t alloc(X** p, size_t n) {
@@ -510,12 +622,31 @@ struct GpuEvaluator : Evaluator {
     GA_CUDA(alloc(&pfit, T));
     GA_CUDA(alloc(&pov, (size_t)T * T));
     GA_CUDA(alloc(&didx, (size_t)std::max(T, K)));
+    GA_CUDA(cudaMallocHost(&hpov, (size_t)std::max(T, 1u) * std::max(T, 1u) * 4));
+    GA_CUDA(cudaMallocHost(&hcnt, (size_t)P * 4));
+    GA_CUDA(cudaMallocHost(&hfit, (size_t)P * 8));
+    GA_CUDA(cudaMallocHost(&hov, (size_t)P * std::max(K, 1u) * 4));
     return EBIC_OK;
   }
   int evaluate(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs, uint32_t n,
                uint32_t* counts, uint64_t* fitness, uint32_t* overlaps) override {
+    int rc = evaluate_begin(cols, offs, n, counts, fitness, overlaps);
+    return rc != EBIC_OK ? rc : evaluate_end();
+  }
+  int evaluate_end() override {
+    GA_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(out_counts, hcnt, (size_t)out_n * 4);
+    std::memcpy(out_fitness, hfit, (size_t)out_n * 8);
+    if (out_k) std::memcpy(out_overlaps, hov, (size_t)out_n * out_k * 4);
+    host_counts.assign(out_counts, out_counts + out_n);
+    return ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
+  }
+  int evaluate_begin(const std::vector<uint16_t>& cols, const std::vector<uint32_t>& offs,
+                     uint32_t n, uint32_t* counts, uint64_t* fitness,
+                     uint32_t* overlaps) override {
     pop_cols = cols;
     pop_offs = offs;
+    // pageable-source copies return once the source is staged
     GA_CUDA(cudaMemcpyAsync(dcols, cols.data(), cols.size() * 2, cudaMemcpyHostToDevice, s));
     GA_CUDA(cudaMemcpyAsync(doffs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, s));
     // one generation's scoring in one call: with a pair table on the matrix, the evaluation and
@@ -524,16 +655,30 @@ struct GpuEvaluator : Evaluator {
     int rc = ebic_eval_fitness(m, dcols, doffs, n, flags, acols, aoffs, abm, n_arch, dcounts, dbm,
                                dfit, n_arch ? dov : nullptr, s);
     if (rc != EBIC_OK) return rc;
-    GA_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-    GA_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaMemcpyAsync(hcnt, dcounts, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaMemcpyAsync(hfit, dfit, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     if (n_arch)
-      GA_CUDA(cudaMemcpyAsync(overlaps, dov, (size_t)n * n_arch * 4, cudaMemcpyDeviceToHost, s));
-    GA_CUDA(cudaStreamSynchronize(s));
-    host_counts.assign(counts, counts + n);
-    return ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
+      GA_CUDA(cudaMemcpyAsync(hov, dov, (size_t)n * n_arch * 4, cudaMemcpyDeviceToHost, s));
+    out_counts = counts;
+    out_fitness = fitness;
+    out_overlaps = overlaps;
+    out_n = n;
+    out_k = n_arch;
+    return EBIC_OK;
   }
   int pair_overlaps(const std::vector<uint32_t>& idx, uint32_t* out) override {
+    int rc = pair_overlaps_begin(idx);
+    return rc != EBIC_OK ? rc : pair_overlaps_end(out);
+  }
+  int pair_overlaps_end(uint32_t* out) override {
+    GA_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(out, hpov, (size_t)pending_t * pending_t * 4);
+    return EBIC_OK;
+  }
+  int pair_overlaps_begin(const std::vector<uint32_t>& idx) override {
     const uint32_t t = (uint32_t)idx.size();
+    pending_t = t;
+    if (t == 0) return EBIC_OK;
     std::vector<uint16_t> c;
     std::vector<uint32_t> o{0}, cn;
     hidx.assign(idx.begin(), idx.end());
@@ -551,10 +696,9 @@ struct GpuEvaluator : Evaluator {
     GA_CUDA(cudaMemcpyAsync(pcounts, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
     int rc = ebic_fitness(m, pcols, poffs, t, pcounts, pbm, pcols, poffs, pbm, t, 0, pfit, pov, s);
     if (rc != EBIC_OK) return rc;
-    GA_CUDA(cudaMemcpyAsync(out, pov, (size_t)t * t * 4, cudaMemcpyDeviceToHost, s));
+    GA_CUDA(cudaMemcpyAsync(hpov, pov, (size_t)t * t * 4, cudaMemcpyDeviceToHost, s));
     // the lists were built here, valid by construction; a device-side rejection would still
     // show in the sticky status word that the next evaluation reads
-    GA_CUDA(cudaStreamSynchronize(s));
     return EBIC_OK;
   }
   int set_archive(const std::vector<int32_t>& src) override {
