@@ -15,7 +15,8 @@ The server:
 
 The device work goes through a backend: ``GpuBackend`` (the C ABI: ebic_batch_run in a CUDA
 graph; a run with a pair table gets its fitness against its resident archive inside the batch,
-the others through ebic_fitness per request) or, in tests, a fake one. ``plain_serve`` is the comparison point: the same arrivals served one request at a time
+the others through ebic_fitness per request; a batch of a single pair-table request goes through
+ebic_eval_fitness instead, which launches less) or, in tests, a fake one. ``plain_serve`` is the comparison point: the same arrivals served one request at a time
 with the per-population call (ebic_eval_fitness), in arrival order.
 """
 from __future__ import annotations
@@ -292,6 +293,27 @@ class GpuBackend:
         slot = next(s for s in self.slots if not s["busy"])
         slot["busy"] = True
         st = slot["stream"]
+        if len(reqs) == 1 and self.runs[reqs[0].run_id]["pairs"]:
+            # a batch of one: the per-population fused call (three launches) costs less than the
+            # batch graph's fixed launches, with the same results
+            r = reqs[0]
+            run = self.runs[r.run_id]
+            n, tot = r.n_cand, int(r.offsets[-1])
+            with torch.cuda.stream(st):
+                run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
+                run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
+                run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
+                run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
+                rc = ebic.ebic_eval_fitness(run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+                                            run["acols"], run["aoffs"], run["abm"], run["K"],
+                                            run["counts"], None, run["fit"], None, st.cuda_stream)
+                if rc:
+                    raise ebic.EbicError(rc, "ebic_eval_fitness")
+                run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
+                run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+            return dict(slot=slot, event=ev)
         items = []
         with torch.cuda.stream(st):
             for r in reqs:

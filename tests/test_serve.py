@@ -92,11 +92,12 @@ def test_one_request_in_flight_per_run_and_results_exact():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("pair_budget", [0, 1 << 30])
-def test_served_results_equal_alone(pair_budget):
+@pytest.mark.parametrize("pair_budget,spacing", [(0, 0.0005), (1 << 30, 0.0005), (1 << 30, 0.0)])
+def test_served_results_equal_alone(pair_budget, spacing):
     """Served counts and fitness equal the per-population calls' and the oracle's counts, with
     runs on the rank-code pass (fitness per request) and on pair tables (fitness inside the
-    batch)."""
+    batch, or the fused call for a batch of one); spacing 0: every request arrives at once, so
+    batches hold many requests."""
     import torch
     from paper_1807_09932_gb300 import ebic
     be = serve.GpuBackend(max_batch=16, max_inflight=2, pair_budget=pair_budget)
@@ -120,7 +121,7 @@ def test_served_results_equal_alone(pair_budget):
             i = k % 6
             C = specs[i].X.shape[1]
             c, o = synth.make_population(900 + k, int(50 + 10 * k), C, 2, min(C, 64))
-            arr.append(serve.Request(run_id=i, cols=c, offsets=o, t_arrival=0.0005 * k,
+            arr.append(serve.Request(run_id=i, cols=c, offsets=o, t_arrival=spacing * k,
                                      flags=ebic.EBIC_NEGATIVE_TRENDS if k % 4 == 3 else 0))
         st = serve.drive(srv, arr, {s.run_id: s.X.shape[0] for s in specs})
         assert st["requests"] == 30
