@@ -378,7 +378,7 @@ def main():
             ho = torch.from_numpy(np.ascontiguousarray(o).view(np.int32)).pin_memory()
             hpops.append((hc, ho, len(o) - 1))
         hfit = torch.empty(P, dtype=torch.int64).pin_memory()
-        h2d = sum(hc.numel() * 2 + ho.numel() * 4 for hc, ho, _ in hpops) * 2 / N_POPS
+        h2d = sum(hc.numel() * 2 + ho.numel() * 4 for hc, ho, _ in hpops) / N_POPS
         d2h = P * 8 + 4
 
         def e2e_step(i):
@@ -416,8 +416,9 @@ def main():
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * et / args.e2e_steps,
                "path": ("ebic_eval_population + ebic_fitness" if args.unfused
                         else "ebic_eval_fitness") +
-                       ", population in pinned host memory, fitness read back to pinned host "
-                       "memory"}
+                       ", population in pinned host memory, fitness back in pinned host memory "
+                       "(the fused route's kernels read and write them in place over the "
+                       "host link)"}
 
     # ---- roofline of the dominant kernel (the evaluator) ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

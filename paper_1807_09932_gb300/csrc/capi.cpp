@@ -113,6 +113,7 @@ bool foreign_device(const void* p, int dev) {
 struct Where {
   bool dev = false;      // device memory of `dev`, or managed
   bool foreign = false;  // device memory of another device
+  void* mapped = nullptr;  // pinned host memory: the address kernels use for it
 };
 
 Where where(const void* p, int dev) {
@@ -125,7 +126,47 @@ Where where(const void* p, int dev) {
   }
   w.dev = at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
   w.foreign = at.type == cudaMemoryTypeDevice && at.device != dev;
+  if (at.type == cudaMemoryTypeHost) w.mapped = at.devicePointer;
   return w;
+}
+
+// A host word that kernels can write directly (pinned, mapped), one per host thread: the error
+// word of a call whose outputs are on the host reaches the host through it without a copy.
+struct MappedWord {
+  uint32_t* host = nullptr;
+  uint32_t* dev = nullptr;
+  ~MappedWord() {
+    if (host) (void)cudaFreeHost(host);
+  }
+  uint32_t* get() {
+    if (!dev) {
+      void* h = nullptr;
+      if (cudaHostAlloc(&h, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+      }
+      void* d = nullptr;
+      if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        (void)cudaFreeHost(h);
+        return nullptr;
+      }
+      host = static_cast<uint32_t*>(h);
+      dev = static_cast<uint32_t*>(d);
+    }
+    return dev;
+  }
+};
+thread_local MappedWord t_err_word;
+
+// A host input read in place by the kernels when it is pinned, else copied.
+template <class T>
+cudaError_t input_at(const T* p, size_t n, const Where& w, Scratch& sc, const T** out) {
+  if (!w.dev && w.mapped) {
+    *out = static_cast<const T*>(w.mapped);
+    return cudaSuccess;
+  }
+  return to_device_at(p, n, w.dev, sc, out);
 }
 
 // to_device / out_buffer with the placement already known.
@@ -810,17 +851,25 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
 
 // The fused route's outputs: the caller's overlaps from the paired layout, host copies, and
 // (when an output is on the host, so the call synchronizes) the call's error word.
+// `sync`: an output is on the host, so the call waits for the device and reports its error
+// word, which the finalize kernel mirrored into `err_mirror` (host) when it is not null;
+// counts_host / fit_host: those outputs still need a copy.
 static int finish_fitness(uint32_t n_cand, uint32_t n_arch, uint32_t ov_stride,
                           uint32_t* dcounts, uint32_t* dbm, uint64_t* dfit, uint32_t* dov,
                           uint32_t* err, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
                           uint32_t* overlaps, bool counts_host, bool bm_host, bool fit_host,
-                          int64_t words, bool ov_dev, cudaStream_t s) {
+                          int64_t words, bool ov_dev, bool sync,
+                          const volatile uint32_t* err_mirror, cudaStream_t s) {
   const bool ov_host = overlaps && n_arch > 0 && !ov_dev;
   if (overlaps && n_arch > 0)  // the caller's [n_cand][n_arch] from the paired layout
     EBIC_CUDA(cudaMemcpy2DAsync(overlaps, (size_t)n_arch * 4, dov, (size_t)ov_stride * 4,
                                 (size_t)n_arch * 4, n_cand,
                                 ov_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
-  if (counts_host || bm_host || fit_host || ov_host) {
+  if (sync && err_mirror && !counts_host && !bm_host && !fit_host && !ov_host) {
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(*err_mirror, "ebic_eval_fitness");
+  }
+  if (sync || counts_host || bm_host || fit_host || ov_host) {
     if (counts_host)
       EBIC_CUDA(cudaMemcpyAsync(counts, dcounts, (size_t)n_cand * 4, cudaMemcpyDeviceToHost, s));
     if (bm_host)
@@ -880,27 +929,25 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
       (n_arch > 0 && !host_a && (!w_acols.dev || !w_aoffs.dev)))
     return fail(EBIC_ERR_INVALID_ARG,
                 "a candidate list must have its columns and offsets in the same memory");
-  // host lists: the offsets (they bound what the copies read) before any launch; the columns
-  // too when the other list is device-resident, else while the kernels run (the device
-  // preparation checks them as well, without recording a deferred status, so a bad host list
-  // leaves every kernel a no-op and the call returns the host check's verdict)
-  const bool all_host = host_c && host_a;
+  // host lists: the offsets (they bound what the copies read) before any launch, the columns
+  // while the kernels run (the device preparation checks them as well, without recording a
+  // deferred status for a host list, so a bad host list leaves every kernel a no-op and the call
+  // returns the host check's verdict)
   if (host_c) {
-    std::string why = all_host ? check_offsets_host(offsets, n_cand)
-                               : check_candidates_host(cols, offsets, n_cand, L.cols);
+    std::string why = check_offsets_host(offsets, n_cand);
     if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
   }
   if (n_arch > 0 && host_a) {
-    std::string why = all_host ? check_offsets_host(arch_offsets, n_arch)
-                               : check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
+    std::string why = check_offsets_host(arch_offsets, n_arch);
     if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
   }
   auto deferred_host_check = [&]() -> int {
-    if (!all_host) return EBIC_OK;
-    std::string why = check_columns_host(cols, offsets, n_cand, L.cols);
-    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
-    if (n_arch > 0) {
-      why = check_columns_host(arch_cols, arch_offsets, n_arch, L.cols);
+    if (host_c) {
+      std::string why = check_columns_host(cols, offsets, n_cand, L.cols);
+      if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+    }
+    if (n_arch > 0 && host_a) {
+      std::string why = check_columns_host(arch_cols, arch_offsets, n_arch, L.cols);
       if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
     }
     return EBIC_OK;
@@ -909,21 +956,38 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
   Scratch sc(s);
   const uint16_t *dcols = nullptr, *dacols = nullptr;
   const uint32_t *doffs = nullptr, *daoffs = nullptr, *dabm = nullptr;
-  EBIC_CUDA(to_device_at(offsets, (size_t)n_cand + 1, w_offs.dev, sc, &doffs));
-  EBIC_CUDA(to_device_at(cols, host_c ? (size_t)offsets[n_cand] : 0, w_cols.dev, sc, &dcols));
+  // pinned host inputs are read in place by the kernels (over the host link), other host inputs
+  // are copied
+  EBIC_CUDA(input_at(offsets, (size_t)n_cand + 1, w_offs, sc, &doffs));
+  EBIC_CUDA(input_at(cols, host_c ? (size_t)offsets[n_cand] : 0, w_cols, sc, &dcols));
   if (n_arch > 0) {
-    EBIC_CUDA(to_device_at(arch_offsets, (size_t)n_arch + 1, w_aoffs.dev, sc, &daoffs));
-    EBIC_CUDA(to_device_at(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, w_acols.dev, sc,
-                           &dacols));
-    EBIC_CUDA(to_device_at(arch_bitmaps, (size_t)n_arch * L.words, w_abm.dev, sc, &dabm));
+    EBIC_CUDA(input_at(arch_offsets, (size_t)n_arch + 1, w_aoffs, sc, &daoffs));
+    EBIC_CUDA(input_at(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, w_acols, sc,
+                       &dacols));
+    EBIC_CUDA(input_at(arch_bitmaps, (size_t)n_arch * L.words, w_abm, sc, &dabm));
   }
+  // outputs: pinned host counts are written by the finalize kernel from the device accumulator,
+  // pinned host fitness in place; other host outputs go through scratch and a copy
   bool counts_host = false, bm_host = false, fit_host = false;
-  uint32_t *dcounts = nullptr, *dbm = nullptr;
+  uint32_t *dcounts = nullptr, *dbm = nullptr, *counts_mirror = nullptr;
   uint64_t* dfit = nullptr;
-  EBIC_CUDA(out_buffer_at(counts, n_cand, w_cnt.dev, sc, &dcounts, &counts_host));
+  if (!w_cnt.dev && w_cnt.mapped) {
+    EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&dcounts), (size_t)n_cand * 4));
+    counts_mirror = static_cast<uint32_t*>(w_cnt.mapped);
+  } else {
+    EBIC_CUDA(out_buffer_at(counts, n_cand, w_cnt.dev, sc, &dcounts, &counts_host));
+  }
   if (bitmaps)
     EBIC_CUDA(out_buffer_at(bitmaps, (size_t)n_cand * L.words, w_bm.dev, sc, &dbm, &bm_host));
-  EBIC_CUDA(out_buffer_at(fitness, n_cand, w_fit.dev, sc, &dfit, &fit_host));
+  if (!w_fit.dev && w_fit.mapped)
+    dfit = static_cast<uint64_t*>(w_fit.mapped);
+  else
+    EBIC_CUDA(out_buffer_at(fitness, n_cand, w_fit.dev, sc, &dfit, &fit_host));
+  // an output on the host: the call waits for the device and reports its error word, mirrored to
+  // the host by the finalize kernel
+  const bool sync = !w_cnt.dev || !w_fit.dev || (bitmaps && !w_bm.dev) ||
+                    (overlaps && n_arch > 0 && !w_ov.dev);
+  uint32_t* err_mirror = sync ? t_err_word.get() : nullptr;
 
   const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
   // overlaps are accumulated in pairs of adjacent counters: rows of an even number of members
@@ -977,7 +1041,8 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     pa.terms = dterms;
     pa.negative = neg;
     pa.flags = dflags;
-    pa.status = all_host ? nullptr : m->status;  // host lists: the host check reports
+    pa.status_cand = host_c ? nullptr : m->status;  // host lists: the host check reports
+    pa.status_arch = host_a ? nullptr : m->status;
     EBIC_CUDA(launch_fused_prepare(pa, prep_blocks, s));
   }
   {
@@ -1006,13 +1071,19 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
   {
     Timed t(EBIC_TIMING_FITNESS, s);
     EBIC_CUDA(launch_fused_finalize(doffs, n_cand, dcounts, daoffs, n_arch, dov, ov_stride,
-                                    darch_counts, dshare, dfit, err, !timing_on(), s));
+                                    darch_counts, dshare, dfit, err, counts_mirror, err_mirror,
+                                    !timing_on(), s));
   }
   const int hc = deferred_host_check();
-  if (hc != EBIC_OK) return hc;
+  if (hc != EBIC_OK) {
+    // the kernels (no-ops on these lists) may still write the caller's pinned outputs and this
+    // thread's error word: let them finish first
+    if (sync) (void)cudaStreamSynchronize(s);
+    return hc;
+  }
   return finish_fitness(n_cand, n_arch, ov_stride, dcounts, dbm, dfit, dov, err, counts,
                         bitmaps, fitness, overlaps, counts_host, bm_host, fit_host, L.words,
-                        w_ov.dev, s);
+                        w_ov.dev, sync, err_mirror ? t_err_word.host : nullptr, s);
 }
 
 int ebic_matrix_status(ebic_matrix* m, void* stream) {

@@ -202,18 +202,21 @@ struct FusedPrepareArgs {
   uint32_t* terms = nullptr;           // [n_cand][term_slots(negative)]
   bool negative = false;
   uint32_t* flags = nullptr;           // [blocks]: each block stores kErrInvalid or 0
-  uint32_t* status = nullptr;
+  uint32_t* status_cand = nullptr;     // ORed with kErrInvalid when the candidate list fails
+  uint32_t* status_arch = nullptr;     // ... when the archive list fails (null: not reported)
 };
 // Blocks of the fused preparation launch (and so the number of its flags).
 uint32_t fused_prepare_blocks(uint32_t n_cand, uint32_t n_arch, uint32_t stride, int num_sms);
 cudaError_t launch_fused_prepare(const FusedPrepareArgs& a, uint32_t blocks, cudaStream_t s);
-// F_c from counts, overlaps and the share masks of the fused preparation.
+// F_c from counts, overlaps and the share masks of the fused preparation. counts_out (or null)
+// receives a copy of the counts and err_out (or null) of the call's error word: both may be
+// pinned host memory, written by the kernel directly.
 cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, const uint32_t* counts,
                                   const uint32_t* arch_offsets, uint32_t n_arch,
                                   const uint32_t* overlaps, uint32_t ov_stride,
                                   const uint32_t* arch_counts, const uint64_t* share,
-                                  uint64_t* fitness, const uint32_t* err, bool pdl,
-                                  cudaStream_t s);
+                                  uint64_t* fitness, const uint32_t* err, uint32_t* counts_out,
+                                  uint32_t* err_out, bool pdl, cudaStream_t s);
 
 // Launch `kernel` with or without programmatic stream serialization.
 template <typename... Params, typename... Args>

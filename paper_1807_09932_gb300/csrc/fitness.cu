@@ -62,10 +62,7 @@ __global__ void __launch_bounds__(kPrepWarps * 32) fused_prepare_kernel(FusedPre
   const bool bad = fused_prepare_body<kPrepWarps>(a, sh, blockIdx.x, gridDim.x);
   // the block's verdict, stored (not accumulated) in its own flag: nothing needs zeroing first
   const bool block_bad = __syncthreads_or(bad) != 0;
-  if (threadIdx.x == 0) {
-    a.flags[blockIdx.x] = block_bad ? kErrInvalid : 0u;
-    if (block_bad && a.status) atomicOr(a.status, kErrInvalid);
-  }
+  if (threadIdx.x == 0) a.flags[blockIdx.x] = block_bad ? kErrInvalid : 0u;
 }
 
 // F_c for the fused pass: a warp per candidate, a lane per archive member.
@@ -76,7 +73,8 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
                           const uint32_t* __restrict__ overlaps, uint32_t ov_stride,
                           const uint32_t* __restrict__ arch_counts,
                           const uint64_t* __restrict__ share, uint64_t* __restrict__ fitness,
-                          const uint32_t* err) {
+                          const uint32_t* err, uint32_t* __restrict__ counts_out,
+                          uint32_t* err_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x * kPrepWarps + warp;
   // the call's inputs (written before the preparation ran) are read before the wait
@@ -85,9 +83,12 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   const uint32_t al0 = lane < (int)n_arch ? aoffsets[lane + 1] - aoffsets[lane] : 0u;
   const uint32_t al1 = lane + 32 < (int)n_arch ? aoffsets[lane + 33] - aoffsets[lane + 32] : 0u;
   dev::pdl_wait();  // the pair-table pass is complete and visible
-  if (*reinterpret_cast<const volatile uint32_t*>(err) != 0 || !live) return;
-  fused_fitness_warp(c, L, al0, al1, n_arch, counts, overlaps, ov_stride, arch_counts,
-                            share, fitness, lane);
+  const uint32_t e = *reinterpret_cast<const volatile uint32_t*>(err);
+  if (err_out && blockIdx.x == 0 && threadIdx.x == 0) *err_out = e;
+  if (e != 0 || !live) return;
+  fused_fitness_warp(c, L, al0, al1, n_arch, counts, overlaps, ov_stride, arch_counts, share,
+                     fitness, lane);
+  if (counts_out && lane == 0) counts_out[c] = counts[c];
 }
 
 // Carry-save adder: a + b + c = 2 * carry + sum, bit by bit (two 3-input logic ops).
@@ -317,14 +318,14 @@ cudaError_t launch_fused_finalize(const uint32_t* offsets, uint32_t n_cand, cons
                                   const uint32_t* arch_offsets, uint32_t n_arch,
                                   const uint32_t* overlaps, uint32_t ov_stride,
                                   const uint32_t* arch_counts, const uint64_t* share,
-                                  uint64_t* fitness, const uint32_t* err, bool pdl,
-                                  cudaStream_t s) {
+                                  uint64_t* fitness, const uint32_t* err, uint32_t* counts_out,
+                                  uint32_t* err_out, bool pdl, cudaStream_t s) {
   if (n_cand == 0) return cudaSuccess;
   count_launch();
   return launch_maybe_pdl(pdl, fused_finalize_kernel,
                           dim3((n_cand + kPrepWarps - 1) / kPrepWarps), dim3(kPrepWarps * 32), 0,
                           s, offsets, n_cand, counts, arch_offsets, n_arch, overlaps, ov_stride,
-                          arch_counts, share, fitness, err);
+                          arch_counts, share, fitness, err, counts_out, err_out);
 }
 
 cudaError_t launch_overlap(const uint32_t* bitmaps, uint32_t n_cand, const uint32_t* arch_bitmaps,

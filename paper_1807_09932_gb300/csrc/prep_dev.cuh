@@ -285,11 +285,18 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
     }
     __syncwarp();  // the set is rebuilt for the next candidate
   }
+  bool abad = false;
   if (a.check_arch)
     for (uint32_t i = gw; i < na; i += nwarps)
-      bad |= check_candidate_span(a.acols, sh.aoff[i], sh.aoff[i + 1], atotal, i == 0, a.ncols,
-                                  set, lane);
-  return bad;
+      abad |= check_candidate_span(a.acols, sh.aoff[i], sh.aoff[i + 1], atotal, i == 0, a.ncols,
+                                   set, lane);
+  // a failure reaches the deferred status only for a list that the caller keeps on the device
+  // (a host list's failure is the host check's to report)
+  if (lane == 0) {
+    if (bad && a.status_cand) atomicOr(a.status_cand, kErrInvalid);
+    if (abad && a.status_arch) atomicOr(a.status_arch, kErrInvalid);
+  }
+  return bad || abad;
 }
 
 // F_c of candidate c of the fused pass, a lane per archive member; `sh` (the members sharing a

@@ -258,3 +258,62 @@ def test_config3_full_size_sampled(ebic):
     ef, _ = oracle.fitness(R, sc, so, ec, eb, acols, aoffs, abm)
     assert np.array_equal(got_c[idx], ec)
     assert np.array_equal(got_f[idx], ef)
+
+
+def test_pinned_host_buffers_read_and_written_in_place(ebic):
+    """Pinned host lists, archive and outputs (the kernels read and write them over the host
+    link, no copies): the oracle's counts and fitness; an invalid pinned list is rejected with
+    no deferred status left behind; device outputs with pinned inputs work too."""
+    import torch
+    rng = np.random.default_rng(41)
+    R, C = 9000, 48
+    X = random_matrix(rng, R, C)
+    cols, offs = synth.make_population(42, 333, C, 2, 16)
+    ec, eb = oracle.eval_population(X, cols, offs)
+    acols, aoffs, abm = make_archive(rng, 43, cols, offs, eb, C, R, 11)
+    ef, _ = oracle.fitness(R, cols, offs, ec, eb, acols, aoffs, abm)
+    n, K = len(offs) - 1, len(aoffs) - 1
+
+    def pinned(a):
+        view = {np.dtype(np.uint16): np.int16, np.dtype(np.uint32): np.int32}[a.dtype]
+        return torch.from_numpy(np.ascontiguousarray(a).view(view)).pin_memory()
+
+    with ebic.Matrix(torch.from_numpy(X).cuda()) as m:
+        m.build_pairs()
+        hc, ho, hac, hao, hab = pinned(cols), pinned(offs), pinned(acols), pinned(aoffs), pinned(abm)
+        cnt = torch.full((n,), -1, dtype=torch.int32).pin_memory()
+        fit = torch.full((n,), -1, dtype=torch.int64).pin_memory()
+        for _ in range(3):
+            rc = ebic.ebic_eval_fitness(m.handle, hc, ho, n, 0, hac, hao, hab, K, cnt, None, fit,
+                                        None)
+            assert rc == ebic.EBIC_OK, ebic.ebic_last_error()
+            assert np.array_equal(cnt.numpy().view(np.uint32), ec)
+            assert np.array_equal(fit.numpy().view(np.uint64), ef)
+        # device outputs, pinned inputs (asynchronous call)
+        dcnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+        dfit = torch.zeros(n, dtype=torch.int64, device="cuda")
+        rc = ebic.ebic_eval_fitness(m.handle, hc, ho, n, 0, hac, hao, hab, K, dcnt, None, dfit,
+                                    None)
+        assert rc == ebic.EBIC_OK and m.status() == ebic.EBIC_OK
+        assert np.array_equal(host(dcnt, np.uint32), ec)
+        assert np.array_equal(host(dfit, np.uint64), ef)
+        # a repeated column in a pinned list
+        bad = cols.copy()
+        bad[offs[5] + 1] = bad[offs[5]]
+        rc = ebic.ebic_eval_fitness(m.handle, pinned(bad), ho, n, 0, hac, hao, hab, K, cnt, None,
+                                    fit, None)
+        assert rc == ebic.EBIC_ERR_INVALID_ARG
+        assert m.status() == ebic.EBIC_OK
+        # the same with the archive on the device: still the host check's verdict, no deferred
+        # status; then the device archive with the good pinned list
+        dac, dao, dab = dev_tensor(acols), dev_tensor(aoffs), dev_tensor(abm)
+        rc = ebic.ebic_eval_fitness(m.handle, pinned(bad), ho, n, 0, dac, dao, dab, K, cnt, None,
+                                    fit, None)
+        assert rc == ebic.EBIC_ERR_INVALID_ARG
+        assert m.status() == ebic.EBIC_OK
+        rc = ebic.ebic_eval_fitness(m.handle, hc, ho, n, 0, dac, dao, dab, K, cnt, None, fit, None)
+        assert rc == ebic.EBIC_OK
+        assert np.array_equal(fit.numpy().view(np.uint64), ef)
+        rc = ebic.ebic_eval_fitness(m.handle, hc, ho, n, 0, hac, hao, hab, K, cnt, None, fit, None)
+        assert rc == ebic.EBIC_OK
+        assert np.array_equal(fit.numpy().view(np.uint64), ef)
