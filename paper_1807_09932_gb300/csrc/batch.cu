@@ -71,8 +71,10 @@ struct BatchReq {
   uint32_t* overlaps;               // scratch: [n_cand][ov_stride], zeroed by the check kernel
   uint32_t* arch_counts;            // scratch: [n_arch], zeroed by the check kernel
   unsigned long long* colmask;      // scratch: [pair_cols] members holding each column
+  uint64_t* share;                  // scratch: [n_cand] members sharing a column with each
   uint32_t n_arch;
   uint32_t ov_stride;               // n_arch rounded up to even
+  uint32_t* terms;                  // pair-table requests: [n_cand][term_slots(neg)] scratch
 };
 
 struct BatchHeader {
@@ -83,7 +85,11 @@ struct BatchHeader {
   unsigned long long grab;        // consecutive items taken per grab (set by the plan kernel)
   uint32_t* zero;                 // the fitness requests' counters, one block of n_zero words
   unsigned long long n_zero;
+  uint32_t n_fit;                 // requests with a fitness output (set by the host)
 };
+
+constexpr int kCheckWarps = 8;     // warps per block of the check kernel
+constexpr int kPlanThreads = 256;  // threads per block of the plan kernel
 
 __device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t n, uint32_t cand) {
   uint32_t lo = 0, hi = n;  // last request with cand_base <= cand
@@ -106,31 +112,39 @@ __device__ __forceinline__ uint32_t find_item(const unsigned long long* start, u
 
 // Check every candidate of every request (same rules and bounds as the single-population
 // check) and zero the counts. Grid-stride, so the grid does not depend on the batch.
-__global__ void batch_check_kernel(const BatchReq* __restrict__ reqs,
-                                   const BatchHeader* __restrict__ hdr, int32_t* ncols_of,
-                                   uint32_t* __restrict__ req_err) {
+__global__ void __launch_bounds__(kCheckWarps * 32)
+    batch_check_kernel(const BatchReq* __restrict__ reqs, const BatchHeader* __restrict__ hdr,
+                       int32_t* ncols_of, uint32_t* __restrict__ req_err) {
+  __shared__ uint32_t sets[kCheckWarps][prepdev::kSetWords];
   const uint32_t n_req = hdr->n_req, total = hdr->total_cand;
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
-       g += gridDim.x * blockDim.x) {
-    const uint32_t r = find_request(reqs, n_req, g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // a warp per candidate: the single-population check (columns distinct through a bitset in
+  // shared memory) and, on a matrix with a pair table, its term list for the pair pass. Each
+  // warp takes a contiguous run of candidates, so it finds their request once and then steps.
+  const uint32_t nwarps = gridDim.x * kCheckWarps;
+  const uint32_t per = (total + nwarps - 1) / nwarps;
+  const uint32_t g0 = (blockIdx.x * kCheckWarps + warp) * per;
+  const uint32_t g1 = min(g0 + per, total);
+  uint32_t r = g0 < g1 ? find_request(reqs, n_req, g0) : 0u;
+  for (uint32_t g = g0; g < g1; ++g) {
+    while (r + 1 < n_req && reqs[r + 1].cand_base <= g) ++r;
     const BatchReq& q = reqs[r];
     const uint32_t i = g - q.cand_base;
-    q.counts[i] = 0u;
+    if (lane == 0) q.counts[i] = 0u;
     const uint32_t* offs = q.cand_offsets;
-    const uint32_t tot = offs[q.n_cand];
     const uint32_t lo = offs[i], hi = offs[i + 1];
-    bool bad = (i == 0 && lo != 0u) || hi <= lo || hi - lo > (uint32_t)kMaxLen || hi > tot;
-    if (!bad) {
-      for (uint32_t j = lo; j < hi; ++j) {
-        const uint16_t c = q.cand_cols[j];
-        bad |= c >= (uint32_t)ncols_of[r];
-        for (uint32_t t = lo; t < j; ++t) bad |= q.cand_cols[t] == c;
-      }
-    }
+    const bool bad = prepdev::check_candidate_span(q.cand_cols, lo, hi, offs[q.n_cand], i == 0,
+                                                   ncols_of[r], sets[warp], lane);
     if (bad) {
-      atomicOr(&req_err[r], kErrInvalid);
-      atomicOr(q.status, kErrInvalid);
+      if (lane == 0) {
+        atomicOr(&req_err[r], kErrInvalid);
+        atomicOr(q.status, kErrInvalid);
+      }
+    } else if (q.terms) {
+      prepdev::build_terms_warp(q.cand_cols, lo, hi, (uint32_t)q.pair_cols, q.pair_stride,
+                                q.neg != 0, q.terms + (size_t)i * term_slots(q.neg != 0), lane);
     }
+    __syncwarp();  // the bitset is rebuilt for the next candidate
   }
   // the fitness requests: counters zeroed, archives copied into rows of the table's stride, the
   // column -> member masks, and the archive lists checked like candidate lists
@@ -182,34 +196,76 @@ __global__ void batch_plan_kernel(const BatchReq* __restrict__ reqs, BatchHeader
                                   unsigned long long* __restrict__ start,
                                   unsigned long long* __restrict__ pstart,
                                   uint32_t n_max, unsigned long long gridDim_eval) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  unsigned long long pacc[4] = {0ull, 0ull, 0ull, 0ull};
-  for (uint32_t r = 0; r < hdr->n_req; ++r) {
-    for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + r] = pacc[k];
+  // every thread: the share masks of the fitness requests' candidates (the check kernel has
+  // built the column masks and rejected bad lists)
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < hdr->total_cand;
+       g += gridDim.x * blockDim.x) {
+    const uint32_t r = find_request(reqs, hdr->n_req, g);
     const BatchReq& q = reqs[r];
-    if (q.pairs == nullptr || q.n_cand == 0 || req_err[r] != 0u) continue;
-    const unsigned long long ranges = (q.words + pairdev::kItemWords - 1) / pairdev::kItemWords;
-    const unsigned long long groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
-    pacc[(q.neg ? 1 : 0) + (q.fitness && q.n_arch ? 2 : 0)] += ranges * groups;
+    if (!q.fitness || q.n_arch == 0 || req_err[r] != 0u) continue;
+    const uint32_t i = g - q.cand_base;
+    unsigned long long mask = 0ull;
+    for (uint32_t j = q.cand_offsets[i]; j < q.cand_offsets[i + 1]; ++j)
+      mask |= q.colmask[q.cand_cols[j]];
+    q.share[i] = mask;
   }
-  for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + hdr->n_req] = pacc[k];
-  unsigned long long acc = 0;
-  for (uint32_t r = 0; r < hdr->n_req; ++r) {
-    start[r] = acc;
+  // block 0: the plan, an exclusive scan of the requests' item counts in five spaces (the four
+  // pair passes, then the rank-code pass), each thread taking a contiguous run of requests
+  if (blockIdx.x != 0) return;
+  __shared__ unsigned long long part[kPlanThreads][5];
+  const uint32_t n = hdr->n_req;
+  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+  const uint32_t r0 = min(threadIdx.x * per, n), r1 = min(r0 + per, n);
+  auto items_of = [&](uint32_t r, unsigned long long (&sz)[5]) {
+    for (int k = 0; k < 5; ++k) sz[k] = 0ull;
     const BatchReq& q = reqs[r];
-    if (q.n_cand == 0 || req_err[r] != 0u || q.pairs != nullptr) continue;
-    const unsigned long long total = q.cand_offsets[q.n_cand];
-    const unsigned long long chunks = (total + q.chunk_cols - 1) / q.chunk_cols;
-    const unsigned long long tiles = (unsigned long long)((q.slabs + q.ts - 1) / q.ts);
-    acc += chunks * tiles;
+    if (q.n_cand == 0 || req_err[r] != 0u) return;
+    if (q.pairs != nullptr) {
+      const unsigned long long ranges = (q.words + pairdev::kItemWords - 1) / pairdev::kItemWords;
+      const unsigned long long groups =
+          (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
+      sz[(q.neg ? 1 : 0) + (q.fitness && q.n_arch ? 2 : 0)] = ranges * groups;
+    } else {
+      const unsigned long long total = q.cand_offsets[q.n_cand];
+      const unsigned long long chunks = (total + q.chunk_cols - 1) / q.chunk_cols;
+      const unsigned long long tiles = (unsigned long long)((q.slabs + q.ts - 1) / q.ts);
+      sz[4] = chunks * tiles;
+    }
+  };
+  unsigned long long acc[5] = {0ull, 0ull, 0ull, 0ull, 0ull}, sz[5];
+  for (uint32_t r = r0; r < r1; ++r) {
+    items_of(r, sz);
+    for (int k = 0; k < 5; ++k) acc[k] += sz[k];
   }
-  start[hdr->n_req] = acc;
-  hdr->total_items = acc;
-  hdr->next_item = 0ull;
+  for (int k = 0; k < 5; ++k) part[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive offsets of the threads' runs, and the totals
+    unsigned long long run[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+    for (uint32_t t = 0; t < blockDim.x; ++t)
+      for (int k = 0; k < 5; ++k) {
+        const unsigned long long v = part[t][k];
+        part[t][k] = run[k];
+        run[k] += v;
+      }
+    for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + n] = run[k];
+    start[n] = run[4];
+    hdr->total_items = run[4];
+    hdr->next_item = 0ull;
+  }
+  __syncthreads();
+  for (int k = 0; k < 5; ++k) acc[k] = part[threadIdx.x][k];
+  for (uint32_t r = r0; r < r1; ++r) {
+    for (int k = 0; k < 4; ++k) pstart[k * (n_max + 1) + r] = acc[k];
+    start[r] = acc[4];
+    items_of(r, sz);
+    for (int k = 0; k < 5; ++k) acc[k] += sz[k];
+  }
+  if (threadIdx.x != 0) return;
+  const unsigned long long acc_total = start[n];
   // runs of consecutive items (same candidate chunk, neighbouring row tiles) keep chunk restaging
   // and item decoding rare; about 8 runs per CTA keep the dynamic balance
   const unsigned long long runs = 8ull * gridDim_eval;
-  unsigned long long g = (acc + runs - 1) / runs;
+  unsigned long long g = (acc_total + runs - 1) / runs;
   hdr->grab = g < 1 ? 1 : (g > 64 ? 64 : g);
 }
 
@@ -414,39 +470,81 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
   }
 }
 
-// The archive members holding any of a candidate's L columns (lane i holds columns i and
-// 32 + i): the OR of the columns' member masks, the same on every lane.
-__device__ __forceinline__ uint64_t share_of(const unsigned long long* colmask, uint32_t c_lo,
-                                             uint32_t c_hi, int L, int lane) {
-  const unsigned long long m =
-      (lane < L ? colmask[c_lo] : 0ull) | (lane + 32 < L ? colmask[c_hi] : 0ull);
-  return ((uint64_t)__reduce_or_sync(0xFFFFFFFFu, (uint32_t)(m >> 32)) << 32) |
-         __reduce_or_sync(0xFFFFFFFFu, (uint32_t)m);
-}
-
 // The batched pair-table pass: every request whose matrix has a pair table and whose negative-
 // trend flag is NEG, its items (range of kItemWords words, group of kPairWarps candidates) laid
 // end to end in request order and taken round-robin by a persistent grid, so the CTAs walk each
 // request's ranges in order and its table rows stay in L2 while its candidates read them. The
 // chain and epilogue are the single-population pass's (pair_chain.cuh); the term list is
 // computed in registers from the checked candidate list.
+constexpr uint32_t kStartCache = 1024;  // item starts kept in shared memory (requests)
+
 template <bool NEG, bool FIT>
 __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
     batch_pair_kernel(const BatchReq* __restrict__ reqs, const BatchHeader* __restrict__ hdr,
                       const unsigned long long* __restrict__ pstart) {
   __shared__ __align__(16) uint32_t stage[pairdev::kPairWarps][pairdev::kRangeWords];
+  __shared__ unsigned long long starts[kStartCache + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t n_req = hdr->n_req;
-  const unsigned long long total = pstart[n_req];
-  for (unsigned long long it = blockIdx.x; it < total; it += gridDim.x) {
-    const uint32_t r = find_item(pstart, n_req, it);
-    const BatchReq& q = reqs[r];
-    const unsigned long long local = it - pstart[r];
+  // the item starts, searched once per item: from shared memory when they fit
+  const bool cached = n_req <= kStartCache;
+  if (cached)
+    for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) starts[i] = pstart[i];
+  __syncthreads();
+  const unsigned long long* ps = cached ? starts : pstart;
+  const unsigned long long total = ps[n_req];
+  // an item's request, row range and this warp's candidate in it
+  struct Item {
+    uint32_t r = 0, cand = 0xFFFFFFFFu;
+    uint64_t range = 0;
+    bool first_group = false;
+  };
+  auto decode = [&](unsigned long long it) {
+    Item m;
+    m.r = find_item(ps, n_req, it);
+    const BatchReq& q = reqs[m.r];
+    const unsigned long long local = it - ps[m.r];
     const uint32_t n_groups = (q.n_cand + pairdev::kPairWarps - 1) / pairdev::kPairWarps;
-    const uint64_t range = local / n_groups, grp = local - range * n_groups;
-    const uint32_t cand = (uint32_t)grp * pairdev::kPairWarps + warp;
-    const uint64_t rword = range * pairdev::kItemWords;
-    if (FIT && grp == 0) {  // the archive members' own row counts, once per range
+    m.range = local / n_groups;
+    const uint64_t grp = local - m.range * n_groups;
+    m.first_group = grp == 0;
+    m.cand = (uint32_t)grp * pairdev::kPairWarps + warp;
+    return m;
+  };
+  // the term list (written by the check kernel) and share mask of the warp's next item are
+  // loaded while the current one is walked
+  auto fetch = [&](const Item& m, pairdev::Terms& t, uint64_t& sh) {
+    const BatchReq& q = reqs[m.r];
+    if (m.cand >= q.n_cand) return;
+    const uint32_t* tp = q.terms + (uint64_t)m.cand * (NEG ? 2 * kTermSlots : kTermSlots);
+    t.lo = __ldg(tp + lane);
+    t.hi = __ldg(tp + 32 + lane);
+    if (NEG) {
+      t.blo = __ldg(tp + 64 + lane);
+      t.bhi = __ldg(tp + 96 + lane);
+    }
+    if (FIT) sh = __ldg(q.share + m.cand);
+  };
+  unsigned long long it = blockIdx.x;
+  Item nxt;
+  pairdev::Terms t_next;
+  uint64_t sh_next = 0;
+  if (it < total) {
+    nxt = decode(it);
+    fetch(nxt, t_next, sh_next);
+  }
+  while (it < total) {
+    const Item m = nxt;
+    const pairdev::Terms t = t_next;
+    const uint64_t sh = sh_next;
+    it += gridDim.x;
+    if (it < total) {
+      nxt = decode(it);
+      fetch(nxt, t_next, sh_next);
+    }
+    const BatchReq& q = reqs[m.r];
+    const uint64_t rword = m.range * pairdev::kItemWords;
+    if (FIT && m.first_group) {  // the archive members' own row counts, once per range
       for (uint32_t a = warp; a < q.n_arch; a += pairdev::kPairWarps) {
         const uint32_t* ar = q.arch_pad + (uint64_t)a * q.pair_stride + rword + 4 * lane;
         uint32_t pa4 = 0;
@@ -457,15 +555,8 @@ __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
         if (lane == 0 && n) atomicAdd(&q.arch_counts[a], n);
       }
     }
-    if (cand >= q.n_cand) continue;  // warp-uniform
-    // the candidate's columns (the list passed the check kernel): its term list and, with an
-    // archive, the members sharing one of its columns
-    const uint32_t o = q.cand_offsets[cand];
-    const int L = (int)(q.cand_offsets[cand + 1] - o);
-    const uint32_t c_lo = lane < L ? q.cand_cols[o + lane] : 0u;
-    const uint32_t c_hi = lane + 32 < L ? q.cand_cols[o + 32 + lane] : 0u;
-    pairdev::Terms t;
-    pairdev::terms_from_cols<NEG>(c_lo, c_hi, L, (uint32_t)q.pair_cols, q.pair_stride, lane, t);
+    if (m.cand >= q.n_cand) continue;  // warp-uniform
+    const uint32_t cand = m.cand;
     uint4 x[pairdev::kParts];
     pairdev::pair_chain<NEG>(t, q.pairs + rword + 4 * lane,
                              pair_ones(q.pairs, (uint64_t)q.pair_cols, q.pair_stride), lane,
@@ -485,7 +576,6 @@ __global__ void __launch_bounds__(pairdev::kPairThreads, 1)
       pa.overlaps = q.overlaps;
       pa.ov_stride = q.ov_stride;
       const int n_pairs = (int)(q.n_arch + 1) >> 1;
-      const uint64_t sh = share_of(q.colmask, c_lo, c_hi, L, lane);
       if (q.bitmaps)  // warp-uniform
         pairdev::item_epilogue<true, true>(pa, cand, rword, x, c, stage[warp], lane, q.n_arch,
                                            n_pairs, sh);
@@ -504,6 +594,7 @@ __global__ void batch_fitness_kernel(const BatchReq* __restrict__ reqs,
                                      const BatchHeader* __restrict__ hdr,
                                      const uint32_t* __restrict__ req_err) {
   const int lane = threadIdx.x & 31;
+  if (hdr->n_fit == 0) return;
   const uint32_t n_req = hdr->n_req;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -517,9 +608,7 @@ __global__ void batch_fitness_kernel(const BatchReq* __restrict__ reqs,
         if (lane == 0) q.fitness[i] = (uint64_t)q.counts[i] << ((L < 33u ? L : 33u) - 1u);
         continue;
       }
-      const uint32_t c_lo = lane < (int)L ? q.cand_cols[o + lane] : 0u;
-      const uint32_t c_hi = lane + 32 < (int)L ? q.cand_cols[o + 32 + lane] : 0u;
-      const uint64_t sh = share_of(q.colmask, c_lo, c_hi, (int)L, lane);
+      const uint64_t sh = q.share[i];
       const uint32_t* ao = q.arch_offsets;
       const uint32_t al0 = lane < (int)q.n_arch ? ao[lane + 1] - ao[lane] : 0u;
       const uint32_t al1 = lane + 32 < (int)q.n_arch ? ao[lane + 33] - ao[lane + 32] : 0u;
@@ -553,11 +642,12 @@ struct HostPlan {
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// The fitness requests' scratch, in one block: first their counters, contiguous so that one loop
-// zeroes them (per request: overlaps [n_cand][ov_stride], then archive counts [ov_stride], so
-// every overlap row starts on 8 bytes), then the padded archives, then the column masks. With
-// base null only the size is computed (hp->fit_bytes); else the pointers are set, and the
-// counter block is reported in *zero / *n_zero.
+// The batch's scratch, in one block: first the fitness requests' counters, contiguous so that
+// one loop zeroes them (per request: overlaps [n_cand][ov_stride], then archive counts
+// [ov_stride], so every overlap row starts on 8 bytes), then their padded archives, column
+// masks and share masks, then the term lists of every pair-table request. With base null only
+// the size is computed (hp->fit_bytes); else the pointers are set, and the counter block is
+// reported in *zero / *n_zero.
 void place_fitness(HostPlan* hp, uint8_t* base, uint32_t** zero, unsigned long long* n_zero) {
   size_t words = 0;
   for (BatchReq& q : hp->reqs) {
@@ -582,6 +672,13 @@ void place_fitness(HostPlan* hp, uint8_t* base, uint32_t** zero, unsigned long l
     if (!q.fitness || q.n_arch == 0) continue;
     if (base) q.colmask = reinterpret_cast<unsigned long long*>(base + off);
     off += round_up((size_t)q.pair_cols * 8, 256);
+    if (base) q.share = reinterpret_cast<uint64_t*>(base + off);
+    off += round_up((size_t)q.n_cand * 8, 256);
+  }
+  for (BatchReq& q : hp->reqs) {
+    if (!q.pairs || q.n_cand == 0) continue;
+    if (base) q.terms = reinterpret_cast<uint32_t*>(base + off);
+    off += round_up((size_t)q.n_cand * term_slots(q.neg != 0) * 4, 256);
   }
   hp->fit_bytes = off;
 }
@@ -776,11 +873,12 @@ int launch_batch(const DeviceBatch& d, uint32_t stage_cap, int32_t chunk_cap, in
   int rc = ensure_batch_attr();
   if (rc != EBIC_OK) return rc;
   count_launch();
-  batch_check_kernel<<<4 * num_sms, 256, 0, s>>>(d.reqs, d.hdr, d.ncols, d.req_err);
+  batch_check_kernel<<<8 * num_sms, kCheckWarps * 32, 0, s>>>(d.reqs, d.hdr, d.ncols, d.req_err);
   B_CUDA(cudaGetLastError());
   count_launch();
-  batch_plan_kernel<<<1, 32, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start, d.pstart, d.n_max,
-                                     (unsigned long long)num_sms);
+  batch_plan_kernel<<<4 * num_sms, kPlanThreads, 0, s>>>(d.reqs, d.hdr, d.req_err, d.start,
+                                                         d.pstart, d.n_max,
+                                                         (unsigned long long)num_sms);
   B_CUDA(cudaGetLastError());
   count_launch();
   batch_eval_kernel<<<num_sms, kBatchThreads, smem, s>>>(d.reqs, d.tmaps, d.hdr, d.start,
@@ -817,6 +915,7 @@ void fill_header(const HostPlan& hp, uint32_t n, BatchHeader* h) {
   std::memset(h, 0, sizeof(*h));
   h->n_req = n;
   h->total_cand = hp.total_cand;
+  for (const BatchReq& q : hp.reqs) h->n_fit += q.fitness != nullptr;
 }
 
 }  // namespace
