@@ -12,10 +12,11 @@
 // orders like the value (-0 folded onto +0, negatives bit-inverted, positives given the top bit),
 // so ties, signed zeros, infinities and subnormals are exact whatever the FTZ mode.
 //
-// One CTA per slab of rows (VEC row groups). Each warp takes one row at a time: it loads the
-// row's keys into its own shared buffer as (key << 32 | column) pairs, sorts them with a bitonic
-// network, and walks the sorted run with a warp prefix count of "first of a new key" flags to get
-// the dense rank of every column. Ranks are written as bytes/halves into a shared slab tile
+// One CTA per slab of rows (VEC row groups). Each warp takes one row at a time. Rows of up to 256
+// columns: the keys are sorted in registers and shuffles, and each column looks its key up in the
+// sorted run. Wider rows: (key << 32 | column) pairs are sorted in the warp's shared buffer and
+// walked. Either way a warp prefix count of "first of a new key" flags over the sorted run gives
+// the dense ranks. Ranks are written as bytes/halves into a shared slab tile
 // laid out as the HBM layout (with one padding word per column against bank conflicts), then the
 // tile is copied out with coalesced 32-bit stores, 128*VEC contiguous bytes per column.
 #include "ebic_internal.h"
@@ -126,9 +127,177 @@ __global__ void __launch_bounds__(512) rank_transform_kernel(const float* __rest
   }
 }
 
+// The same transform for rows of at most 32*E columns with the sort in registers: lane l holds
+// the row's sorted keys at positions l*E .. l*E+E-1 ("blocked" layout) after a bitonic network
+// whose exchanges are register min/max when partners share a lane (distance < E) and shuffles
+// otherwise. Only the 32-bit keys are sorted: the warp then writes the sorted keys and their
+// dense ranks to its shared buffer, and every lane finds the rank of each of its own columns by a
+// binary search of its key there. Each warp loads its next row while it ranks the current one.
+template <int E>
+__device__ __forceinline__ void bitonic_sort_keys(uint32_t (&x)[E], int lane) {
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      if (jj < E) {  // partners in this lane: elements e and e | jj
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (e & jj) continue;
+          const bool up = ((lane * E + e) & kk) == 0;
+          const uint32_t a = x[e], b = x[e | jj];
+          const uint32_t lo = min(a, b), hi = max(a, b);
+          x[e] = up ? lo : hi;
+          x[e | jj] = up ? hi : lo;
+        }
+      } else {  // partner in lane ^ (jj / E), same element
+        const int d = jj / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = lane * E + e;
+          const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x[e], d);
+          // the lower index of an ascending pair keeps the smaller key, and so on
+          const bool keep_min = ((i & jj) == 0) == ((i & kk) == 0);
+          x[e] = keep_min ? min(x[e], y) : max(x[e], y);
+        }
+      }
+    }
+  }
+}
+
+template <int WIDTH, int VEC, int E>
+__global__ void __launch_bounds__(512) rank_transform_reg_kernel(const float* __restrict__ X,
+                                                                int64_t R, int C, int64_t ld,
+                                                                int exclude, float fill,
+                                                                uint32_t* __restrict__ out,
+                                                                int64_t Q, int nwarps) {
+  constexpr int RPG = WIDTH == 8 ? 128 : 64;  // rows per group
+  constexpr int RPS = RPG * VEC;              // rows per slab
+  constexpr int N = 32 * E;
+  constexpr uint32_t MISSING = 0u;
+  constexpr int TROW = 32 * VEC + 1;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the warp's sorted keys and their dense ranks
+  uint32_t* skey = reinterpret_cast<uint32_t*>(
+                       smem + (((size_t)C * TROW * 4 + 15) & ~(size_t)15)) + (size_t)warp * 2 * N;
+  uint32_t* srank = skey + N;
+  const int64_t q = blockIdx.x;
+  // the row's values as loaded: element e of lane l is column e*32 + l (coalesced)
+  auto load_row = [&](int rho, float (&v)[E]) {
+    const int64_t r = q * RPS + rho;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int c = e * 32 + lane;
+      v[e] = (rho < RPS && r < R && c < C) ? __ldg(X + r * ld + c) : 0.0f;
+    }
+  };
+  float cur[E];
+  load_row(warp, cur);
+  for (int rho = warp; rho < RPS; rho += nwarps) {
+    const int64_t r = q * RPS + rho;
+    float nxt[E];
+    load_row(rho + nwarps, nxt);  // the warp's next row, while this one is ranked
+    const int j = rho / RPG, rr = rho % RPG, l = rr & 31, k = rr >> 5;
+    uint8_t* cell0 = reinterpret_cast<uint8_t*>(tile) + ((size_t)l * VEC + j) * 4 +
+                     (WIDTH == 8 ? k : 2 * k);
+    if (r >= R) {  // padding rows hold the missing code in every column
+      for (int c = lane; c < C; c += 32) {
+        uint8_t* cell = cell0 + (size_t)c * TROW * 4;
+        if (WIDTH == 8) *cell = (uint8_t)MISSING;
+        else *reinterpret_cast<uint16_t*>(cell) = (uint16_t)MISSING;
+      }
+    } else {
+      uint32_t v[E], x[E];  // keys of the lane's columns; the same, to be sorted
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        v[e] = e * 32 + lane < C ? order_key(cur[e], exclude, fill) : kMissingKey;
+        x[e] = v[e];
+      }
+      bitonic_sort_keys<E>(x, lane);
+      // dense rank of each sorted position: distinct keys up to and including it (the missing
+      // key, which also pads the row, sorts last and is never counted)
+      const uint32_t prev_last = __shfl_up_sync(0xFFFFFFFFu, x[E - 1], 1);
+      uint32_t fresh = 0, cnt = 0;  // fresh: bit e = position lane*E+e starts a new key
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t before = e > 0 ? x[e - 1] : prev_last;
+        const bool f = x[e] != kMissingKey && ((lane == 0 && e == 0) || before != x[e]);
+        fresh |= (uint32_t)f << e;
+        cnt += f;
+      }
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+      }
+      uint32_t run = incl - cnt;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        run += (fresh >> e) & 1u;
+        skey[lane * E + e] = x[e];
+        srank[lane * E + e] = run;
+      }
+      __syncwarp();
+      // each column's rank: the first sorted position holding its key (lower bound)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int c = e * 32 + lane;
+        if (c >= C) continue;
+        uint32_t rank = MISSING;
+        if (v[e] != kMissingKey) {
+          int pos = 0;
+#pragma unroll
+          for (int step = N / 2; step >= 1; step >>= 1)
+            if (skey[pos + step - 1] < v[e]) pos += step;
+          rank = srank[pos];  // 1-based dense rank
+        }
+        uint8_t* cell = cell0 + (size_t)c * TROW * 4;
+        if (WIDTH == 8) *cell = (uint8_t)rank;
+        else *reinterpret_cast<uint16_t*>(cell) = (uint16_t)rank;
+      }
+      __syncwarp();  // the buffer is rewritten for the next row
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) cur[e] = nxt[e];
+  }
+  __syncthreads();
+  // copy out: column c of slab q is 32*VEC contiguous words in HBM
+  const int wpc = 32 * VEC;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)C * wpc; idx += blockDim.x) {
+    const int64_t c = idx / wpc, i = idx % wpc;
+    out[(c * Q + q) * wpc + i] = tile[c * TROW + i];
+  }
+}
+
+template <int WIDTH, int VEC, int E>
+cudaError_t launch_rank_reg(const Layout& L, const float* dX, int64_t ld, int exclude, float fill,
+                            uint32_t* ranks, cudaStream_t s) {
+  const size_t tile = (((size_t)L.cols * (32 * VEC + 1) * 4) + 15) & ~(size_t)15;
+  const size_t per_warp = (size_t)2 * 32 * E * 4;  // sorted keys and their ranks
+  int nwarps = (int)((kSmemDynMax - tile) / per_warp);
+  if (nwarps > 16) nwarps = 16;
+  if (nwarps < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = tile + per_warp * nwarps;
+  auto kern = rank_transform_reg_kernel<WIDTH, VEC, E>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  kern<<<(unsigned)L.slabs, nwarps * 32, smem, s>>>(dX, L.rows, L.cols, ld, exclude, fill, ranks,
+                                                    L.slabs, nwarps);
+  return cudaGetLastError();
+}
+
 template <int WIDTH, int VEC>
 cudaError_t launch_rank_layout(const Layout& L, const float* dX, int64_t ld, int exclude,
                                float fill, uint32_t* ranks, cudaStream_t s) {
+  if (L.cols <= 32) return launch_rank_reg<WIDTH, VEC, 1>(L, dX, ld, exclude, fill, ranks, s);
+  if (L.cols <= 64) return launch_rank_reg<WIDTH, VEC, 2>(L, dX, ld, exclude, fill, ranks, s);
+  if (L.cols <= 128) return launch_rank_reg<WIDTH, VEC, 4>(L, dX, ld, exclude, fill, ranks, s);
+  if (L.cols <= 256) return launch_rank_reg<WIDTH, VEC, 8>(L, dX, ld, exclude, fill, ranks, s);
   int N = 32;
   while (N < L.cols) N <<= 1;
   const size_t tile_bytes = (((size_t)L.cols * (32 * VEC + 1) * 4) + 15) & ~(size_t)15;
