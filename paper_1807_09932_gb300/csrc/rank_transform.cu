@@ -12,11 +12,12 @@
 // orders like the value (-0 folded onto +0, negatives bit-inverted, positives given the top bit),
 // so ties, signed zeros, infinities and subnormals are exact whatever the FTZ mode.
 //
-// One CTA per slab of rows (VEC row groups). Each warp takes one row at a time. Rows of up to 256
-// columns: the keys are sorted in registers and shuffles, and each column looks its key up in the
-// sorted run. Wider rows: (key << 32 | column) pairs are sorted in the warp's shared buffer and
-// walked. Either way a warp prefix count of "first of a new key" flags over the sorted run gives
-// the dense ranks. Ranks are written as bytes/halves into a shared slab tile
+// One CTA per slab of rows (VEC row groups). Rows of up to 64 columns: one thread per row sorts
+// its (key, column) pairs with a compare-exchange network in registers and walks the sorted run.
+// Wider rows: each warp takes one row at a time. Up to 256 columns the keys are sorted in
+// registers and shuffles, and each column looks its key up in the sorted run; wider still,
+// (key << 32 | column) pairs are sorted in the warp's shared buffer and walked. In the warp forms
+// a warp prefix count of "first of a new key" flags over the sorted run gives the dense ranks. Ranks are written as bytes/halves into a shared slab tile
 // laid out as the HBM layout (with one padding word per column against bank conflicts), then the
 // tile is copied out with coalesced 32-bit stores, 128*VEC contiguous bytes per column.
 #include "ebic_internal.h"
@@ -272,6 +273,153 @@ __global__ void __launch_bounds__(512) rank_transform_reg_kernel(const float* __
   }
 }
 
+// Rows of at most 64 columns (8-bit codes): one thread per row. A compare-exchange network
+// sorts the thread's (key, column) pairs in registers: Batcher's odd-even merge sort (Batcher,
+// "Sorting networks and their applications", AFIPS 1968), 543 exchanges for 64 keys, 191 for 32,
+// each a compare, a min, a max and two selects, every index fixed at compile time so that the
+// arrays stay in registers. A walk over the sorted run then counts distinct keys and drops each
+// column's dense rank into the slab tile. Each chunk of 128 rows is staged in shared memory by
+// 4-byte cp.async copies (row stride N + 1 words, so that thread t reading its column c hits bank
+// (t + c) mod 32), the next chunk's copies in flight while the current one is sorted.
+__device__ __forceinline__ void compare_exchange(uint32_t& ka, uint32_t& kb, uint32_t& ca,
+                                                 uint32_t& cb) {
+  const bool swap = ka > kb;
+  const uint32_t lo = min(ka, kb), hi = max(ka, kb);
+  const uint32_t c0 = swap ? cb : ca, c1 = swap ? ca : cb;
+  ka = lo;
+  kb = hi;
+  ca = c0;
+  cb = c1;
+}
+
+// Batcher's merge of the elements at LO, LO+R, LO+2R, ... below LO+NN, whose two halves are each
+// sorted: merge the even and the odd subsequences (stride 2R), then exchange the neighbours
+// (i, i+R) for i = LO+R, LO+3R, ...
+template <int LO, int NN, int R, int N>
+struct OddEvenMerge {
+  static __device__ __forceinline__ void run(uint32_t (&k)[N], uint32_t (&c)[N]) {
+    if constexpr (2 * R < NN) {
+      OddEvenMerge<LO, NN, 2 * R, N>::run(k, c);
+      OddEvenMerge<LO + R, NN, 2 * R, N>::run(k, c);
+#pragma unroll
+      for (int i = LO + R; i + R < LO + NN; i += 2 * R) compare_exchange(k[i], k[i + R], c[i], c[i + R]);
+    } else {
+      compare_exchange(k[LO], k[LO + R], c[LO], c[LO + R]);
+    }
+  }
+};
+
+template <int LO, int NN, int N>
+struct OddEvenSort {
+  static __device__ __forceinline__ void run(uint32_t (&k)[N], uint32_t (&c)[N]) {
+    if constexpr (NN > 1) {
+      OddEvenSort<LO, NN / 2, N>::run(k, c);
+      OddEvenSort<LO + NN / 2, NN / 2, N>::run(k, c);
+      OddEvenMerge<LO, NN, 1, N>::run(k, c);
+    }
+  }
+};
+
+template <int N>
+__device__ __forceinline__ void oddeven_merge_sort(uint32_t (&k)[N], uint32_t (&c)[N]) {
+  OddEvenSort<0, N, N>::run(k, c);
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const float* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+constexpr int kRowThreads = 128;  // rows per chunk, one per thread
+
+template <int N>
+__global__ void __launch_bounds__(kRowThreads, 3) rank_transform_row_kernel(
+    const float* __restrict__ X, int64_t R, int C, int64_t ld, int exclude, float fill,
+    uint32_t* __restrict__ out, int64_t Q) {
+  constexpr int VEC = 4, RPG = 128, RPS = RPG * VEC;  // 8-bit codes: 512 rows per slab
+  constexpr int TROW = 32 * VEC + 1;
+  constexpr int SROW = N + 1;
+  constexpr int T = kRowThreads;
+  constexpr uint32_t MISSING = 0u;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* stage =
+      reinterpret_cast<uint32_t*>(smem + (((size_t)C * TROW * 4 + 15) & ~(size_t)15));
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int64_t q = blockIdx.x;
+  const int64_t r_base = q * RPS;
+  // chunk copies: warp w stages rows w, w+4, ..., columns lane, lane+32 (coalesced per row)
+  auto stage_chunk = [&](int cb) {
+    for (int rr = warp; rr < T; rr += T / 32) {
+      const int64_t r = r_base + cb + rr;
+      if (r >= R) break;
+      const float* row = X + r * ld;
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 32)
+        if (c0 + lane < C) cp_async4(stage + rr * SROW + c0 + lane, row + c0 + lane);
+    }
+    cp_async_commit();
+  };
+  stage_chunk(0);
+  for (int cb = 0; cb < RPS; cb += T) {
+    const int rho = cb + t;
+    const int64_t r = r_base + rho;
+    cp_async_wait_all();
+    __syncthreads();
+    uint32_t key[N], col[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      key[c] = (c < C && r < R) ? order_key(__uint_as_float(stage[t * SROW + c]), exclude, fill)
+                                : kMissingKey;
+      col[c] = c;
+    }
+    __syncthreads();  // the stage is free: the next chunk's copies overlap this one's sort
+    if (cb + T < RPS) stage_chunk(cb + T);
+    const int j = rho / RPG, rr = rho % RPG, l = rr & 31, k = rr >> 5;
+    uint8_t* cell0 = reinterpret_cast<uint8_t*>(tile) + ((size_t)l * VEC + j) * 4 + k;
+    if (r >= R) {  // padding rows hold the missing code in every column
+      for (int c = 0; c < C; ++c) cell0[(size_t)c * TROW * 4] = (uint8_t)MISSING;
+      continue;
+    }
+    oddeven_merge_sort<N>(key, col);
+    uint32_t run = 0;  // distinct non-missing keys so far: the 1-based dense rank
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+      run += key[p] != kMissingKey && (p == 0 || key[p] != key[p - 1]);
+      if (col[p] < (uint32_t)C)
+        cell0[(size_t)col[p] * TROW * 4] = (uint8_t)(key[p] == kMissingKey ? MISSING : run);
+    }
+  }
+  __syncthreads();
+  // copy out: column c of slab q is 32*VEC contiguous words in HBM
+  constexpr int wpc = 32 * VEC;
+  for (int idx = t; idx < C * wpc; idx += T) {
+    const int c = idx / wpc, i = idx % wpc;
+    out[((int64_t)c * Q + q) * wpc + i] = tile[c * TROW + i];
+  }
+}
+
+template <int N>
+cudaError_t launch_rank_row(const Layout& L, const float* dX, int64_t ld, int exclude, float fill,
+                            uint32_t* ranks, cudaStream_t s) {
+  const size_t tile = (((size_t)L.cols * (32 * 4 + 1) * 4) + 15) & ~(size_t)15;
+  const size_t smem = tile + (size_t)kRowThreads * (N + 1) * 4;
+  auto kern = rank_transform_row_kernel<N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  kern<<<(unsigned)L.slabs, kRowThreads, smem, s>>>(dX, L.rows, L.cols, ld, exclude, fill, ranks,
+                                                    L.slabs);
+  return cudaGetLastError();
+}
+
 template <int WIDTH, int VEC, int E>
 cudaError_t launch_rank_reg(const Layout& L, const float* dX, int64_t ld, int exclude, float fill,
                             uint32_t* ranks, cudaStream_t s) {
@@ -294,6 +442,10 @@ cudaError_t launch_rank_reg(const Layout& L, const float* dX, int64_t ld, int ex
 template <int WIDTH, int VEC>
 cudaError_t launch_rank_layout(const Layout& L, const float* dX, int64_t ld, int exclude,
                                float fill, uint32_t* ranks, cudaStream_t s) {
+  if (WIDTH == 8 && VEC == 4) {
+    if (L.cols <= 32) return launch_rank_row<32>(L, dX, ld, exclude, fill, ranks, s);
+    if (L.cols <= 64) return launch_rank_row<64>(L, dX, ld, exclude, fill, ranks, s);
+  }
   if (L.cols <= 32) return launch_rank_reg<WIDTH, VEC, 1>(L, dX, ld, exclude, fill, ranks, s);
   if (L.cols <= 64) return launch_rank_reg<WIDTH, VEC, 2>(L, dX, ld, exclude, fill, ranks, s);
   if (L.cols <= 128) return launch_rank_reg<WIDTH, VEC, 4>(L, dX, ld, exclude, fill, ranks, s);

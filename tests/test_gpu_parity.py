@@ -130,7 +130,7 @@ def test_tile_that_does_not_fit_is_rejected(ebic):
 
 def test_rank_export_matches_dense_ranks(ebic):
     from pins import tiny_matrix
-    for C in (5, 127, 128, 300):
+    for C in (1, 2, 5, 31, 32, 33, 63, 64, 65, 127, 128, 300):
         X = tiny_matrix(C, 700, C, nan_frac=0.1)
         rng = np.random.default_rng(C)
         X[:, : C // 2] += rng.standard_normal((700, C // 2)).astype(np.float32)
@@ -139,6 +139,25 @@ def test_rank_export_matches_dense_ranks(ebic):
                 got = m.ranks()
             want = oracle.dense_ranks(X, exclude_missing=exclude, fill_value=1.0)
             assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("C", [3, 32, 50, 64, 100, 300])
+def test_rank_transform_reads_strided_device_rows(ebic, C):
+    # a device matrix whose rows are further apart than its columns (ld > cols) is ranked in place
+    import torch
+    from pins import tiny_matrix
+    R, pad = 1100, 7
+    Xw = tiny_matrix(C + 11, R, C + pad, nan_frac=0.05)
+    Xw[:, : C // 2] += np.random.default_rng(C).standard_normal((R, C // 2)).astype(np.float32)
+    dXw = torch.from_numpy(Xw).cuda()
+    h = ebic.ebic_load_matrix(dXw, R, C, C + pad, ebic.EBIC_EXCLUDE_MISSING, 0.0)
+    try:
+        got = np.zeros((R, C), dtype=np.uint16)
+        ebic.ebic_matrix_ranks(h, got)
+    finally:
+        ebic.ebic_free_matrix(h)
+    want = oracle.dense_ranks(np.ascontiguousarray(Xw[:, :C]), exclude_missing=True, fill_value=0.0)
+    assert np.array_equal(got, want)
 
 
 def test_empty_population_is_a_noop(ebic):
