@@ -14,6 +14,7 @@ import os
 import shutil
 import subprocess
 import sys
+import sysconfig
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -25,6 +26,14 @@ LIB = os.path.join(LIB_DIR, "libebic_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", INCLUDE, "-I", CSRC]
+
+
+PYFAST_SRC = os.path.join(CSRC, "pyfast.c")
+
+
+def pyfast_path() -> str:
+    """Where the C marshalling module for the per-generation calls is built."""
+    return os.path.join(LIB_DIR, "_ebic_fast" + (sysconfig.get_config_var("EXT_SUFFIX") or ".so"))
 
 
 def nvcc() -> str:
@@ -84,9 +93,31 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, LIB)
+    _build_pyfast()
     if verbose_ptxas:
         sys.stderr.write("\n".join(logs))
     return LIB
+
+
+def _build_pyfast():
+    """The CPython module that converts the per-generation calls' arguments in C (linked to the
+    library beside it). Built only where the interpreter's headers are installed; without it the
+    binding converts the same arguments through ctypes."""
+    inc = sysconfig.get_paths().get("include") or ""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc or not os.path.exists(os.path.join(inc, "Python.h")):
+        return None
+    out = pyfast_path()
+    if not _stale(out, [PYFAST_SRC, os.path.join(INCLUDE, "ebic.h"), __file__, LIB]):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = [cc, "-shared", "-fPIC", "-O2", "-std=c11", "-Wall", "-I", inc, "-I", INCLUDE,
+           PYFAST_SRC, "-L", LIB_DIR, "-lebic_gb300", "-Wl,-rpath,$ORIGIN", "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"building the marshalling module failed:\n{r.stderr}")
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -36,6 +36,23 @@ if not os.path.exists(LIB_PATH):
                       "run `python -c 'import __graft_entry__ as g; g.build()'`")
 
 _lib = ctypes.CDLL(LIB_PATH)
+
+
+def _load_fast():
+    """The C marshalling module for the per-generation calls, when it was built (it links to the
+    library loaded above; the calls and their results are the same either way)."""
+    import importlib.util
+    import sysconfig
+    path = os.path.join(_PKG, "lib", "_ebic_fast" + (sysconfig.get_config_var("EXT_SUFFIX") or ".so"))
+    if not os.path.exists(path) or os.environ.get("EBIC_CTYPES_ONLY"):
+        return None
+    spec = importlib.util.spec_from_file_location("_ebic_fast", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+_fast = _load_fast()
 _P = ctypes.c_void_p
 _I32, _I64, _U32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
 
@@ -155,10 +172,18 @@ def _check(code, where):
         raise EbicError(code, where)
 
 
+_TENSOR = None  # torch.Tensor, once one has been seen (torch is not imported here)
+
+
 def _ptr(x):
     """Raw address of a numpy array (host) or torch tensor (its device or host memory)."""
+    global _TENSOR
     if x is None:
         return None
+    if type(x) is _TENSOR:  # the common case first: a plain torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
     if isinstance(x, np.ndarray):
         if not x.flags.c_contiguous:
             raise ValueError("arrays must be C-contiguous")
@@ -166,6 +191,8 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensors must be contiguous")
+        if type(x).__name__ == "Tensor" and type(x).__module__ == "torch":
+            _TENSOR = type(x)
         return x.data_ptr()
     if isinstance(x, int):
         return x
@@ -215,6 +242,9 @@ def ebic_matrix_ranks(h, out, stream=None):
 
 
 def ebic_eval_population(h, cols, offsets, n_cand, flags, counts, bitmaps, stream=None):
+    if _fast is not None:
+        return _fast.eval_population(h, cols, offsets, n_cand, flags, counts, bitmaps,
+                                     stream if stream is not None else _stream(None))
     return _lib_eval(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(counts), _ptr(bitmaps),
                      _stream(stream))
 
@@ -227,6 +257,10 @@ def ebic_eval_population_noalloc(h, cols, offsets, n_cand, flags, counts, bitmap
 
 def ebic_fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offsets,
                  arch_bitmaps, n_arch, flags, fitness, overlaps, stream=None):
+    if _fast is not None:
+        return _fast.fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offsets,
+                             arch_bitmaps, n_arch, flags, fitness, overlaps,
+                             stream if stream is not None else _stream(None))
     return _lib_fitness(h, _ptr(cols), _ptr(offsets), n_cand, _ptr(counts), _ptr(bitmaps),
                         _ptr(arch_cols), _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, flags,
                         _ptr(fitness), _ptr(overlaps), _stream(stream))
@@ -234,6 +268,10 @@ def ebic_fitness(h, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offs
 
 def ebic_eval_fitness(h, cols, offsets, n_cand, flags, arch_cols, arch_offsets, arch_bitmaps,
                       n_arch, counts, bitmaps, fitness, overlaps, stream=None):
+    if _fast is not None:
+        return _fast.eval_fitness(h, cols, offsets, n_cand, flags, arch_cols, arch_offsets,
+                                  arch_bitmaps, n_arch, counts, bitmaps, fitness, overlaps,
+                                  stream if stream is not None else _stream(None))
     return _lib_eval_fitness(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(arch_cols),
                              _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, _ptr(counts),
                              _ptr(bitmaps), _ptr(fitness), _ptr(overlaps), _stream(stream))

@@ -101,3 +101,55 @@ def test_no_device_is_reported_not_crashed(lib):
     rc = f(x.ctypes.data, 4, 3, 3, 1, 0.0, None, ctypes.byref(h))
     assert rc in (-6, -3), rc
     assert not h.value
+
+
+def test_c_marshalling_matches_ctypes_marshalling(lib):
+    """The C module that converts the per-generation calls' arguments gives the same statuses,
+    messages and argument errors as the ctypes path (both call the same library functions)."""
+    import torch
+    from paper_1807_09932_gb300 import ebic
+    fast = ebic._fast
+    if fast is None:
+        pytest.skip("the interpreter's headers are not installed: the binding uses ctypes only")
+    cols = np.zeros(6, np.uint16)
+    offs = np.array([0, 3, 6], np.uint32)
+    cnt = torch.zeros(2, dtype=torch.int32)
+    fit = torch.zeros(2, dtype=torch.int64)
+    calls = [
+        ("ebic_eval_fitness", lambda: fast.eval_fitness(None, cols, offs, 2, 0, None, None, None, 0,
+                                                        cnt, None, fit, None, 0),
+         lambda: ebic._lib_eval_fitness(None, cols.ctypes.data, offs.ctypes.data, 2, 0, None, None,
+                                        None, 0, cnt.data_ptr(), None, fit.data_ptr(), None, None)),
+        ("ebic_eval_population", lambda: fast.eval_population(ctypes.c_void_p(), cols, offs, 2, 0,
+                                                              cnt, None, 0),
+         lambda: ebic._lib_eval(None, cols.ctypes.data, offs.ctypes.data, 2, 0, cnt.data_ptr(),
+                                None, None)),
+        ("ebic_fitness", lambda: fast.fitness(0, cols, offs, 2, cnt, None, None, None, None, 0, 0,
+                                              fit, None, None),
+         lambda: ebic._lib_fitness(None, cols.ctypes.data, offs.ctypes.data, 2, cnt.data_ptr(),
+                                   None, None, None, None, 0, 0, fit.data_ptr(), None, None)),
+    ]
+    for name, via_c, via_ctypes in calls:
+        rc_c = via_c()
+        msg_c = ebic.ebic_last_error()
+        rc_t = via_ctypes()
+        msg_t = ebic.ebic_last_error()
+        assert rc_c == rc_t == ebic.EBIC_ERR_INVALID_ARG, name
+        assert msg_c == msg_t and "NULL" in msg_c, (name, msg_c, msg_t)
+    # argument errors are raised before the library is called
+    with pytest.raises(ValueError):
+        fast.eval_fitness(None, np.zeros((3, 4), np.uint16)[:, 1], offs, 2, 0, None, None, None, 0,
+                          cnt, None, fit, None, 0)
+    with pytest.raises(ValueError):
+        fast.eval_fitness(None, cols, offs, 2, 0, None, None, None, 0,
+                          torch.zeros(4, dtype=torch.int32)[::2], None, fit, None, 0)
+    with pytest.raises(TypeError):
+        fast.eval_fitness(None, "cols", offs, 2, 0, None, None, None, 0, cnt, None, fit, None, 0)
+    with pytest.raises(TypeError):
+        fast.eval_fitness(None, cols, offs, 2)
+    with pytest.raises(OverflowError):
+        fast.eval_fitness(None, cols, offs, 1 << 32, 0, None, None, None, 0, cnt, None, fit,
+                          None, 0)
+    # the module links to the library the binding loaded: one copy of its state
+    maps = {l.split()[-1] for l in open("/proc/self/maps") if "libebic_gb300" in l}
+    assert len(maps) == 1, maps

@@ -317,3 +317,36 @@ def test_pinned_host_buffers_read_and_written_in_place(ebic):
         rc = ebic.ebic_eval_fitness(m.handle, hc, ho, n, 0, hac, hao, hab, K, cnt, None, fit, None)
         assert rc == ebic.EBIC_OK
         assert np.array_equal(fit.numpy().view(np.uint64), ef)
+
+
+def test_c_and_ctypes_marshalling_give_the_same_scores(ebic):
+    # the per-generation call through the C marshalling module and through ctypes, on pinned host
+    # and device buffers: identical counts and fitness
+    import torch
+    if ebic._fast is None:
+        pytest.skip("the C marshalling module is not built here")
+    ds = synth.make_dataset(41, 6000, 30, kind="beta", planted=[(900, 6, False)], nan_frac=0.01)
+    cols, offs = synth.make_population(42, 300, 30, 2, 12)
+    acols, aoffs = synth.make_population(43, 5, 30, 3, 8)
+    with ebic.Matrix(ds.X, exclude_missing=True) as m:
+        m.build_pairs()
+        _, abm = ebic.eval_population(m, acols, aoffs)
+        got = []
+        for use_c in (True, False):
+            saved = ebic._fast
+            if not use_c:
+                ebic._fast = None
+            try:
+                hc = torch.from_numpy(cols.view(np.int16)).pin_memory()
+                ho = torch.from_numpy(offs.view(np.int32)).pin_memory()
+                cnt = torch.zeros(len(offs) - 1, dtype=torch.int32).pin_memory()
+                fit = torch.zeros(len(offs) - 1, dtype=torch.int64).pin_memory()
+                rc = ebic.ebic_eval_fitness(m.handle, hc, ho, len(offs) - 1, 0, acols, aoffs, abm,
+                                            len(aoffs) - 1, cnt, None, fit, None,
+                                            torch.cuda.current_stream())
+                assert rc == 0, ebic.ebic_last_error()
+                got.append((cnt.numpy().copy(), fit.numpy().copy()))
+            finally:
+                ebic._fast = saved
+        assert np.array_equal(got[0][0], got[1][0]) and np.array_equal(got[0][1], got[1][1])
+
