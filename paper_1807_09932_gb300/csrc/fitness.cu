@@ -83,12 +83,19 @@ __global__ void __launch_bounds__(kPrepWarps * 32)
   const uint32_t al0 = lane < (int)n_arch ? aoffsets[lane + 1] - aoffsets[lane] : 0u;
   const uint32_t al1 = lane + 32 < (int)n_arch ? aoffsets[lane + 33] - aoffsets[lane + 32] : 0u;
   dev::pdl_wait();  // the pair-table pass is complete and visible
+  // the error word is read alongside the scores; a failed call's scores are read but not stored
   const uint32_t e = *reinterpret_cast<const volatile uint32_t*>(err);
+  uint32_t n = 0;
+  uint64_t f = 0;
+  if (live) {
+    const uint64_t sh = n_arch ? share[c] : 0ull;
+    f = fused_fitness_value(c, L, al0, al1, n_arch, sh, counts, overlaps, ov_stride, arch_counts,
+                            lane, n);
+  }
   if (err_out && blockIdx.x == 0 && threadIdx.x == 0) *err_out = e;
-  if (e != 0 || !live) return;
-  fused_fitness_warp(c, L, al0, al1, n_arch, counts, overlaps, ov_stride, arch_counts, share,
-                     fitness, lane);
-  if (counts_out && lane == 0) counts_out[c] = counts[c];
+  if (!live || e != 0 || lane != 0) return;
+  fitness[c] = f;
+  if (counts_out) counts_out[c] = n;
 }
 
 // Carry-save adder: a + b + c = 2 * carry + sum, bit by bit (two 3-input logic ops).

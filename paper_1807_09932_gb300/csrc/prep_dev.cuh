@@ -299,42 +299,47 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
   return bad || abad;
 }
 
-// F_c of candidate c of the fused pass, a lane per archive member; `sh` (the members sharing a
-// column with the candidate) stands for the column-set test. L is the candidate's length and
-// al0 / al1 the lengths of members `lane` and `lane + 32` (0 when absent). Lane 0 stores the
-// result.
+// F_c of candidate c of the fused pass (at most 64 archive members), a lane per member (two for
+// members 32..63); `sh` (the members sharing a column with the candidate) stands for the
+// column-set test. L is the candidate's length and al0 / al1 the lengths of members `lane` and
+// `lane + 32` (0 when absent). Every load is issued before any comparison (none depends on
+// another), so the warp waits for one round of loads. Returns F_c in every lane, and the
+// candidate's row count in n.
+__device__ __forceinline__ uint64_t fused_fitness_value(uint32_t c, uint32_t L, uint32_t al0,
+                                                        uint32_t al1, uint32_t n_arch,
+                                                        uint64_t sh, const uint32_t* counts,
+                                                        const uint32_t* overlaps,
+                                                        uint32_t ov_stride,
+                                                        const uint32_t* arch_counts, int lane,
+                                                        uint32_t& n) {
+  const uint32_t m0 = (uint32_t)lane, m1 = (uint32_t)lane + 32u;
+  const bool in0 = m0 < n_arch, in1 = m1 < n_arch;
+  const size_t row = (size_t)c * ov_stride;
+  n = counts[c];
+  const uint32_t ac0 = in0 ? arch_counts[m0] : 0u, ac1 = in1 ? arch_counts[m1] : 0u;
+  const uint32_t ov0 = in0 ? overlaps[row + m0] : 0u, ov1 = in1 ? overlaps[row + m1] : 0u;
+  const bool has0 = in0 && ((sh >> m0) & 1ull), has1 = in1 && ((sh >> m1) & 1ull);
+  const uint32_t shift = (L < 33u ? L : 33u) - 1u;
+  const uint64_t qc = (uint64_t)n << shift;
+  // a strictly worse member (q(a) < q(c)) does not penalise the candidate
+  uint32_t best = 0;
+  if (has0 && ((uint64_t)ac0 << ((al0 < 33u ? al0 : 33u) - 1u)) >= qc) best = ov0;
+  if (has1 && ((uint64_t)ac1 << ((al1 < 33u ? al1 : 33u) - 1u)) >= qc) best = ov1 > best ? ov1 : best;
+  best = __reduce_max_sync(0xFFFFFFFFu, best);
+  return (uint64_t)(n - best) << shift;
+}
+
+// The same, stored by lane 0.
 __device__ __forceinline__ void fused_fitness_mask(uint32_t c, uint32_t L, uint32_t al0,
                                                    uint32_t al1, uint32_t n_arch, uint64_t sh,
                                                    const uint32_t* counts,
                                                    const uint32_t* overlaps, uint32_t ov_stride,
                                                    const uint32_t* arch_counts, uint64_t* fitness,
                                                    int lane) {
-  const uint32_t n = counts[c];
-  const uint32_t shift = (L < 33u ? L : 33u) - 1u;
-  const uint64_t qc = (uint64_t)n << shift;
-  uint32_t best = 0;
-  for (uint32_t m = lane; m < n_arch; m += 32) {
-    if (!((sh >> m) & 1ull)) continue;  // shares no column with the candidate
-    const uint32_t al = m < 32 ? al0 : al1;
-    const uint64_t qa = (uint64_t)arch_counts[m] << ((al < 33u ? al : 33u) - 1u);
-    if (qa < qc) continue;  // a strictly worse member does not penalise the candidate
-    const uint32_t ov = overlaps[(size_t)c * ov_stride + m];
-    best = ov > best ? ov : best;
-  }
-  best = __reduce_max_sync(0xFFFFFFFFu, best);
-  if (lane == 0) fitness[c] = (uint64_t)(n - best) << shift;
-}
-
-// The same with the share masks of the preparation (share[c]).
-__device__ __forceinline__ void fused_fitness_warp(uint32_t c, uint32_t L, uint32_t al0,
-                                                   uint32_t al1, uint32_t n_arch,
-                                                   const uint32_t* counts,
-                                                   const uint32_t* overlaps, uint32_t ov_stride,
-                                                   const uint32_t* arch_counts,
-                                                   const uint64_t* share, uint64_t* fitness,
-                                                   int lane) {
-  fused_fitness_mask(c, L, al0, al1, n_arch, n_arch ? share[c] : 0ull, counts, overlaps,
-                     ov_stride, arch_counts, fitness, lane);
+  uint32_t n;
+  const uint64_t f = fused_fitness_value(c, L, al0, al1, n_arch, sh, counts, overlaps, ov_stride,
+                                         arch_counts, lane, n);
+  if (lane == 0) fitness[c] = f;
 }
 
 }  // namespace prepdev
