@@ -288,7 +288,8 @@ int ebic_batch_free(ebic_batch* b);
  * The paper says EBIC uses evolutionary computation over a population of up to 65,535
  * candidates, with 1,600 or fewer usually enough to converge (Methods, "Support for Big Data").
  * It does not define the operators. The ones here are the project's definition: deterministic
- * given `seed` (a splitmix64 counter generator), tournament selection, an order-preserving
+ * given `seed` (splitmix64 counter generators: one for the initial population, one per child
+ * slot and generation), tournament selection, an order-preserving
  * crossover, four mutations (swap, substitute, insert, delete), a tabu list of evaluated column
  * sequences, and an elite archive of `archive_size` biclusters ranked by raw quality
  * n << (min(L,33)-1). A candidate enters the archive unless a member sharing a column overlaps
@@ -297,6 +298,9 @@ int ebic_batch_free(ebic_batch* b);
  * Each generation the population is scored with ebic_eval_fitness against the current archive
  * (device-resident rank matrix, bitmaps and archive); when the matrix has a pair table
  * (ebic_matrix_build_pairs) that is one fused pass. Results do not depend on the table.
+ * The children of a generation are bred by host threads (the environment variable
+ * EBIC_HOST_THREADS, 1..64, sets their number; by default the cores, at most 16, with at least
+ * 128 children each); results do not depend on their number either.
  */
 typedef struct ebic_params {
   uint32_t population;       /* candidates per generation (default 1600)                      */

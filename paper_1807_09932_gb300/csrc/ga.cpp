@@ -18,13 +18,23 @@
 //     candidates are offered, best quality first: one is admitted unless a member sharing a
 //     column overlaps it by more than overlap_threshold x its row count without being strictly
 //     worse; strictly worse members it overlaps that much are replaced by it.
-// Every random draw comes from one splitmix64 counter generator seeded with `seed`, and every
-// decision depends only on draws and exact integer scores, so a run is reproducible bit for bit
-// and independent of which evaluator produced the (identical) scores.
+// Random draws come from splitmix64 counter generators: the initial population from one seeded
+// with `seed`, and child slot j of generation g from its own, seeded from (seed, g, j). A child is
+// bred against the tabu list alone, so the children of a generation are bred in parallel (host
+// threads); a pass in slot order then gives a child that repeats an earlier one of the same new
+// population further mutations, or a random replacement, from its own generator. Every decision
+// depends only on draws and exact integer scores, so a run is reproducible bit for bit, whatever
+// the number of threads, and independent of which evaluator produced the (identical) scores.
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ebic.h"
@@ -45,6 +55,17 @@ struct Rng {  // splitmix64 (Steele, Lea, Flood 2014), as a counter-based genera
   uint32_t below(uint32_t n) { return (uint32_t)(next() % n); }
   double unit() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
 };
+
+// The generator of child slot `slot` of generation `gen`: its state is the splitmix64 output
+// function applied twice, over (seed, gen) and then the slot.
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+Rng child_stream(uint64_t seed, uint32_t gen, uint32_t slot) {
+  return Rng{mix64(mix64(seed + 0x9E3779B97F4A7C15ull * ((uint64_t)gen + 1)) + slot)};
+}
 
 // A candidate: up to kMaxLen columns held inline, so copying, crossing and mutating the
 // population allocates nothing. The members the GA uses behave as std::vector's do.
@@ -159,6 +180,41 @@ class CandSet {
   std::vector<uint32_t> slots_;  // entry index + 1, 0 = empty
 };
 
+// The sequences of the population being built, as indices into it (no copy): open addressing on
+// the sequences' FNV-1a hashes, the hashes kept beside the population.
+class SlotSet {
+ public:
+  void reset(size_t n_max) {
+    size_t cap = 64;
+    while (cap < 2 * n_max) cap <<= 1;
+    slots_.assign(cap, 0u);
+  }
+  bool contains(const Cand& c, uint64_t h, const std::vector<Cand>& seqs,
+                const std::vector<uint64_t>& hashes) const {
+    const size_t mask = slots_.size() - 1;
+    for (size_t i = spread(h) & mask;; i = (i + 1) & mask) {
+      const uint32_t s = slots_[i];
+      if (s == 0) return false;
+      if (hashes[s - 1] == h && seqs[s - 1] == c) return true;
+    }
+  }
+  void add(uint32_t index, uint64_t h) {  // the caller keeps the set at most half full
+    const size_t mask = slots_.size() - 1;
+    size_t i = spread(h) & mask;
+    while (slots_[i] != 0) i = (i + 1) & mask;
+    slots_[i] = index + 1;
+  }
+
+ private:
+  static size_t spread(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    return (size_t)h;
+  }
+  std::vector<uint32_t> slots_;  // index + 1, 0 = empty
+};
+
 uint64_t quality(uint32_t n, size_t L) { return (uint64_t)n << ((L < 33 ? L : 33) - 1); }
 
 // Scoring of one generation, implemented by the GPU (ebic_run) or by callbacks.
@@ -213,24 +269,29 @@ bool shares_column(const Cand& a, const Cand& b) {
   return false;
 }
 
-struct Ga {
+// The variation operators, drawing from `rng` (set per child). One Breeder per thread: the
+// column list is scratch.
+struct Breeder {
   const ebic_params& p;
   int32_t ncols;
   Rng rng;
-  std::vector<uint16_t> all_cols;
+  std::vector<uint16_t> all_cols;  // 0 .. ncols-1 between calls
 
-  Ga(const ebic_params& prm, int32_t nc) : p(prm), ncols(nc), rng{prm.seed} {
+  Breeder(const ebic_params& prm, int32_t nc) : p(prm), ncols(nc), rng{prm.seed} {
     all_cols.resize((size_t)nc);
     for (int32_t i = 0; i < nc; ++i) all_cols[(size_t)i] = (uint16_t)i;
   }
 
   Cand random_candidate() {
     const uint32_t L = p.min_len + rng.below(p.max_init_len - p.min_len + 1);
+    uint32_t js[kMaxLen];
     for (uint32_t i = 0; i < L; ++i) {  // partial Fisher-Yates over the column list
-      const uint32_t j = i + rng.below((uint32_t)ncols - i);
-      std::swap(all_cols[i], all_cols[j]);
+      js[i] = i + rng.below((uint32_t)ncols - i);
+      std::swap(all_cols[i], all_cols[js[i]]);
     }
-    return Cand(all_cols.begin(), all_cols.begin() + L);
+    Cand c(all_cols.begin(), all_cols.begin() + L);
+    for (uint32_t i = L; i-- > 0;) std::swap(all_cols[i], all_cols[js[i]]);  // back to 0..ncols-1
+    return c;
   }
 
   uint16_t unused_column(const Cand& c) {
@@ -290,6 +351,102 @@ struct Ga {
   }
 };
 
+// Host threads for the breeding of a generation: start(n, f) has the pool's threads call
+// f(i, worker) for i in [0, n) and returns at once, so the caller can issue other work; finish()
+// has the caller (worker 0) take the calls still left, and returns when all have returned.
+class Workers {
+ public:
+  explicit Workers(unsigned n) : n_(n < 1 ? 1 : n) {
+    for (unsigned w = 1; w < n_; ++w) threads_.emplace_back([this, w] { loop(w); });
+  }
+  ~Workers() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_ = true;
+      ++epoch_;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+  unsigned size() const { return n_; }
+  void start(uint32_t n, std::function<void(uint32_t, unsigned)> f) {
+    job_ = std::move(f);
+    n_items_ = n;
+    next_.store(0, std::memory_order_relaxed);
+    if (n_ == 1 || n < 2 * kChunk) {  // not worth waking the pool: finish() does it all
+      pooled_ = false;
+      return;
+    }
+    pooled_ = true;
+    {
+      std::lock_guard<std::mutex> g(m_);
+      busy_ = n_ - 1;
+      ++epoch_;
+    }
+    cv_.notify_all();
+  }
+  void finish() {
+    work(0);
+    if (pooled_) {
+      std::unique_lock<std::mutex> lk(m_);
+      done_cv_.wait(lk, [this] { return busy_ == 0; });
+    }
+    job_ = nullptr;
+  }
+
+ private:
+  static constexpr uint32_t kChunk = 16;
+  void work(unsigned w) {
+    for (;;) {
+      const uint32_t b = next_.fetch_add(kChunk, std::memory_order_relaxed);
+      if (b >= n_items_) return;
+      const uint32_t e = std::min(b + kChunk, n_items_);
+      for (uint32_t i = b; i < e; ++i) job_(i, w);
+    }
+  }
+  void loop(unsigned w) {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return epoch_ != seen; });
+        seen = epoch_;
+        if (stop_) return;
+      }
+      work(w);
+      {
+        std::lock_guard<std::mutex> g(m_);
+        if (--busy_ == 0) done_cv_.notify_one();
+      }
+    }
+  }
+  unsigned n_;
+  std::vector<std::thread> threads_;
+  std::mutex m_;
+  std::condition_variable cv_, done_cv_;
+  std::function<void(uint32_t, unsigned)> job_;  // set before the threads are woken
+  uint32_t n_items_ = 0;
+  bool pooled_ = false;
+  std::atomic<uint32_t> next_{0};
+  unsigned busy_ = 0;
+  uint64_t epoch_ = 0;
+  bool stop_ = false;
+};
+
+// Host threads that breed a generation: EBIC_HOST_THREADS when set (1 .. 64), else the cores (at
+// most 16) with at least 128 children each. The result does not depend on the count.
+unsigned breeding_threads(uint32_t population) {
+  if (const char* e = std::getenv("EBIC_HOST_THREADS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 1 && v <= 64) return (unsigned)v;
+  }
+  const unsigned hw = std::thread::hardware_concurrency();
+  unsigned n = hw == 0 ? 1 : (hw > 16 ? 16 : hw);
+  const unsigned by_size = population / 128;  // at least 128 children per thread
+  if (n > by_size) n = by_size;
+  return n < 1 ? 1 : n;
+}
+
 std::string check_params(const ebic_params& p, int32_t ncols) {
   if (p.population < 1) return "population must be >= 1";
   if (p.archive_size < 1 || p.archive_size > 4096) return "archive_size must be in [1, 4096]";
@@ -310,8 +467,13 @@ std::string check_params(const ebic_params& p, int32_t ncols) {
 
 int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebic_result** out) {
   const uint32_t P = p.population, K = p.archive_size;
-  Ga ga(p, ncols);
-  CandSet tabu, in_archive, picked, in_next;
+  Workers workers(breeding_threads(P));
+  std::vector<Breeder> breeders;
+  breeders.reserve(workers.size());
+  for (unsigned w = 0; w < workers.size(); ++w) breeders.emplace_back(p, ncols);
+  Breeder& ga = breeders[0];  // the initial population draws from the generator seeded with `seed`
+  CandSet tabu, in_archive, picked;
+  SlotSet in_next;  // the next population's sequences so far
   std::vector<Cand> pop;
   std::vector<uint64_t> pop_h;  // each candidate's CandHash, computed once
   pop.reserve(P);
@@ -329,10 +491,18 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
   std::vector<Member> archive;
   std::vector<uint16_t> cols;
   std::vector<uint32_t> offs;
-  std::vector<uint32_t> counts(P), overlaps((size_t)P * K), order(P), rank(P);
-  std::vector<uint64_t> fitness(P), head4(P), qual(P);
+  std::vector<uint32_t> counts(P), overlaps((size_t)P * K), elites;
+  std::vector<uint64_t> fitness(P), qual(P);
+  struct SortKey {
+    uint64_t fit, head4;
+    uint32_t count, len, idx;
+  };
+  std::vector<SortKey> skeys(P), top_keys;  // skeys[i]: candidate i's order key
   std::vector<uint32_t> heap;
   heap.reserve(P);
+  std::vector<Cand> kids;  // a generation's children before the pass in slot order
+  std::vector<uint64_t> kids_h;
+  std::vector<Rng> kids_rng;
   uint64_t evaluated = 0;
   uint32_t gen = 0;
   for (; gen < p.generations; ++gen) {
@@ -350,27 +520,36 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     evaluated += P;
     const size_t K_eval = archive.size();  // overlaps is [P][K_eval]
 
-    // lexicographic order of equal-length sequences: their first four columns packed high to low
-    // decide most comparisons; the rest of the sequence breaks the remaining ties
+    // The generation's order, best first: higher fitness, then more rows, longer, then the
+    // lexicographically smaller sequence (equal-length sequences compare their first four columns
+    // packed high to low, then the rest), then the lower index. It is a total order; tournaments
+    // compare with it directly and only the `elite` best are sorted out.
     for (uint32_t i = 0; i < P; ++i) {
-      order[i] = i;
       uint64_t k = 0;
       for (size_t j = 0; j < 4; ++j) k = (k << 16) | (j < pop[i].size() ? pop[i][j] : 0u);
-      head4[i] = k;
+      skeys[i] = SortKey{fitness[i], k, counts[i], (uint32_t)pop[i].size(), i};
     }
-    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
-      if (fitness[a] != fitness[b]) return fitness[a] > fitness[b];
-      if (counts[a] != counts[b]) return counts[a] > counts[b];
-      if (pop[a].size() != pop[b].size()) return pop[a].size() > pop[b].size();
-      if (head4[a] != head4[b]) return head4[a] < head4[b];
-      if (pop[a].size() > 4) {
-        const auto ta = pop[a].begin() + 4, tb = pop[b].begin() + 4;
-        if (!std::equal(ta, pop[a].end(), tb))
-          return std::lexicographical_compare(ta, pop[a].end(), tb, pop[b].end());
+    auto before = [&](const SortKey& a, const SortKey& b) {
+      if (a.fit != b.fit) return a.fit > b.fit;
+      if (a.count != b.count) return a.count > b.count;
+      if (a.len != b.len) return a.len > b.len;
+      if (a.head4 != b.head4) return a.head4 < b.head4;
+      if (a.len > 4) {
+        const Cand& ca = pop[a.idx];
+        const Cand& cb = pop[b.idx];
+        const auto ta = ca.begin() + 4, tb = cb.begin() + 4;
+        if (!std::equal(ta, ca.end(), tb))
+          return std::lexicographical_compare(ta, ca.end(), tb, cb.end());
       }
-      return a < b;
-    });
-    for (uint32_t r = 0; r < P; ++r) rank[order[r]] = r;
+      return a.idx < b.idx;
+    };
+    {
+      const uint32_t ne = std::min(p.elite, P);
+      top_keys = skeys;
+      std::partial_sort(top_keys.begin(), top_keys.begin() + ne, top_keys.end(), before);
+      elites.resize(ne);
+      for (uint32_t r = 0; r < ne; ++r) elites[r] = top_keys[r].idx;
+    }
 
     // ---- archive update ----
     // Offer up to 2K non-archived candidates with rows, best raw quality first. A candidate is
@@ -408,46 +587,84 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
     std::vector<uint32_t> top;
     for (const Member& m : offers) top.push_back((uint32_t)m.src);
     // their pairwise overlaps are computed while the next population is built (it depends on
-    // neither the archive nor the overlaps, and the archive update draws no random numbers)
-    rc = ev.pair_overlaps_begin(top);
-    if (rc != EBIC_OK) return rc;
+    // neither the archive nor the overlaps, and the archive update draws no random numbers):
+    // the host threads start breeding, then this thread issues the overlaps
     std::vector<Cand> next;
     std::vector<uint64_t> next_h;
-    if (gen + 1 < p.generations) {
+    const bool breed = gen + 1 < p.generations;
+    if (breed) {
       next.reserve(P);
       next_h.reserve(P);
-      in_next.clear();
-      for (uint32_t r = 0; r < p.elite; ++r) {
-        next.push_back(pop[order[r]]);
-        next_h.push_back(pop_h[order[r]]);
-        in_next.insert(pop[order[r]], pop_h[order[r]]);
+      in_next.reset(P);
+      for (uint32_t e : elites) {
+        in_next.add((uint32_t)next.size(), pop_h[e]);
+        next.push_back(pop[e]);
+        next_h.push_back(pop_h[e]);
       }
-      auto tournament = [&]() {
-        uint32_t best = ga.rng.below(P);
-        for (uint32_t t = 1; t < p.tournament; ++t) {
-          const uint32_t c = ga.rng.below(P);
-          if (rank[c] < rank[best]) best = c;
-        }
-        return best;
-      };
-      while (next.size() < P) {
+      // the children of slots elite .. P-1, each from its own generator and against the tabu
+      // list only (read-only here), in parallel
+      const uint32_t n_child = P - (uint32_t)next.size();
+      kids.resize(n_child);
+      kids_h.resize(n_child);
+      kids_rng.resize(n_child);
+      const uint32_t slot0 = (uint32_t)next.size();
+      workers.start(n_child, [&, slot0](uint32_t k, unsigned w) {
+        Breeder& b = breeders[w];
+        b.rng = child_stream(p.seed, gen, slot0 + k);
+        auto tournament = [&]() {
+          uint32_t best = b.rng.below(P);
+          for (uint32_t t = 1; t < p.tournament; ++t) {
+            const uint32_t c = b.rng.below(P);
+            if (before(skeys[c], skeys[best])) best = c;
+          }
+          return best;
+        };
         const uint32_t a = tournament();
         Cand child = pop[a];
-        if (ga.rng.unit() < p.p_crossover) child = ga.crossover(pop[a], pop[tournament()]);
-        if (ga.rng.unit() < p.p_mutation) ga.mutate(child);
+        if (b.rng.unit() < p.p_crossover) child = b.crossover(pop[a], pop[tournament()]);
+        if (b.rng.unit() < p.p_mutation) b.mutate(child);
         uint64_t h = CandHash()(child);
-        auto taken = [&]() { return tabu.count(child, h) || in_next.count(child, h); };
-        for (uint32_t t = 0; t < p.tabu_retries && taken(); ++t) {
-          ga.mutate(child);
+        for (uint32_t t = 0; t < p.tabu_retries && tabu.count(child, h); ++t) {
+          b.mutate(child);
           h = CandHash()(child);
         }
-        for (int t = 0; t < 32 && taken(); ++t) {
-          child = ga.random_candidate();
+        for (int t = 0; t < 32 && tabu.count(child, h); ++t) {
+          child = b.random_candidate();
           h = CandHash()(child);
         }
-        in_next.insert(child, h);
+        kids[k] = child;
+        kids_h[k] = h;
+        kids_rng[k] = b.rng;
+      });
+    }
+    rc = ev.pair_overlaps_begin(top);
+    if (breed) workers.finish();
+    if (rc != EBIC_OK) return rc;
+    if (breed) {
+      const uint32_t n_child = (uint32_t)kids.size();
+      // in slot order: a child that repeats one already in the new population is varied again
+      // from its own generator, like a tabu child
+      for (uint32_t k = 0; k < n_child; ++k) {
+        Cand& child = kids[k];
+        uint64_t h = kids_h[k];
+        if (in_next.contains(child, h, next, next_h)) {
+          Breeder& b = breeders[0];
+          b.rng = kids_rng[k];
+          auto taken = [&]() {
+            return tabu.count(child, h) || in_next.contains(child, h, next, next_h);
+          };
+          for (uint32_t t = 0; t < p.tabu_retries && taken(); ++t) {
+            b.mutate(child);
+            h = CandHash()(child);
+          }
+          for (int t = 0; t < 32 && taken(); ++t) {
+            child = b.random_candidate();
+            h = CandHash()(child);
+          }
+        }
+        in_next.add((uint32_t)next.size(), h);
         next_h.push_back(h);
-        next.push_back(std::move(child));
+        next.push_back(child);
       }
     }
     std::vector<uint32_t> pair((size_t)top.size() * top.size());
@@ -572,7 +789,10 @@ struct GpuEvaluator : Evaluator {
   uint32_t *poffs = nullptr, *pcounts = nullptr, *pbm = nullptr, *pov = nullptr;
   uint64_t *dfit = nullptr, *pfit = nullptr;
   int32_t* didx = nullptr;  // rows to gather (population index, or -(archive index + 1))
-  std::vector<int32_t> hidx;
+  // the offers' lists, staged in pinned memory and sent in one copy to a device block of the
+  // same layout: gather indices [T], columns [T * max_len], offsets [T + 1], counts [T]
+  char *hstage = nullptr, *dstage = nullptr;
+  size_t st_cols = 0, st_offs = 0, st_cnt = 0, st_bytes = 0;
   uint32_t* hpov = nullptr;  // pinned [T][T]: the pair overlaps' copy-back
   uint32_t pending_t = 0;
   // pinned copy-backs of a generation's scores, and where evaluate_end puts them
@@ -592,6 +812,7 @@ struct GpuEvaluator : Evaluator {
     cudaStreamSynchronize(s);
     for (void* a : allocs) cudaFree(a);
     if (hpov) cudaFreeHost(hpov);
+    if (hstage) cudaFreeHost(hstage);
     if (hcnt) cudaFreeHost(hcnt);
     if (hfit) cudaFreeHost(hfit);
     if (hov) cudaFreeHost(hov);
@@ -615,9 +836,16 @@ struct GpuEvaluator : Evaluator {
     GA_CUDA(alloc(&aoffs, (size_t)K + 1));
     GA_CUDA(alloc(&abm, (size_t)K * W));
     GA_CUDA(alloc(&abm_next, (size_t)K * W));
-    GA_CUDA(alloc(&pcols, (size_t)T * max_len));
-    GA_CUDA(alloc(&poffs, (size_t)T + 1));
-    GA_CUDA(alloc(&pcounts, T));
+    auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    st_cols = up16((size_t)T * 4);
+    st_offs = st_cols + up16((size_t)T * max_len * 2);
+    st_cnt = st_offs + up16(((size_t)T + 1) * 4);
+    st_bytes = st_cnt + up16((size_t)T * 4);
+    GA_CUDA(alloc(&dstage, st_bytes));
+    GA_CUDA(cudaMallocHost(&hstage, st_bytes));
+    pcols = reinterpret_cast<uint16_t*>(dstage + st_cols);
+    poffs = reinterpret_cast<uint32_t*>(dstage + st_offs);
+    pcounts = reinterpret_cast<uint32_t*>(dstage + st_cnt);
     GA_CUDA(alloc(&pbm, (size_t)T * W));
     GA_CUDA(alloc(&pfit, T));
     GA_CUDA(alloc(&pov, (size_t)T * T));
@@ -679,21 +907,23 @@ struct GpuEvaluator : Evaluator {
     const uint32_t t = (uint32_t)idx.size();
     pending_t = t;
     if (t == 0) return EBIC_OK;
-    std::vector<uint16_t> c;
-    std::vector<uint32_t> o{0}, cn;
-    hidx.assign(idx.begin(), idx.end());
+    // the staging block is free: the previous generation's copy completed before its
+    // pair_overlaps_end returned
+    int32_t* hi = reinterpret_cast<int32_t*>(hstage);
+    uint16_t* hc = reinterpret_cast<uint16_t*>(hstage + st_cols);
+    uint32_t* ho = reinterpret_cast<uint32_t*>(hstage + st_offs);
+    uint32_t* hn = reinterpret_cast<uint32_t*>(hstage + st_cnt);
+    ho[0] = 0;
     for (uint32_t k = 0; k < t; ++k) {
       const uint32_t i = idx[k];
-      c.insert(c.end(), pop_cols.begin() + pop_offs[i], pop_cols.begin() + pop_offs[i + 1]);
-      o.push_back((uint32_t)c.size());
-      cn.push_back(host_counts[i]);
+      hi[k] = (int32_t)i;
+      const uint32_t b = pop_offs[i], e = pop_offs[i + 1];
+      std::copy(pop_cols.begin() + b, pop_cols.begin() + e, hc + ho[k]);
+      ho[k + 1] = ho[k] + (e - b);
+      hn[k] = host_counts[i];
     }
-    // pageable-source copies return once the source is staged, so the vectors may go
-    GA_CUDA(cudaMemcpyAsync(didx, hidx.data(), (size_t)t * 4, cudaMemcpyHostToDevice, s));
-    GA_CUDA(launch_gather_rows(dbm, dbm, didx, t, W, pbm, s));
-    GA_CUDA(cudaMemcpyAsync(pcols, c.data(), c.size() * 2, cudaMemcpyHostToDevice, s));
-    GA_CUDA(cudaMemcpyAsync(poffs, o.data(), o.size() * 4, cudaMemcpyHostToDevice, s));
-    GA_CUDA(cudaMemcpyAsync(pcounts, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice, s));
+    GA_CUDA(cudaMemcpyAsync(dstage, hstage, st_bytes, cudaMemcpyHostToDevice, s));
+    GA_CUDA(launch_gather_rows(dbm, dbm, reinterpret_cast<const int32_t*>(dstage), t, W, pbm, s));
     int rc = ebic_fitness(m, pcols, poffs, t, pcounts, pbm, pcols, poffs, pbm, t, 0, pfit, pov, s);
     if (rc != EBIC_OK) return rc;
     GA_CUDA(cudaMemcpyAsync(hpov, pov, (size_t)t * t * 4, cudaMemcpyDeviceToHost, s));
