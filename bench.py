@@ -171,6 +171,20 @@ def oracle_sample(ds, pops, arch, target_s):
     return n, threads, run
 
 
+def combine_over_ranks(my_seconds, units_per_rank, dist=None, device=None):
+    """The job's time and throughput over all ranks: the time is the slowest rank's (max over
+    ranks), the value is the units every rank processed together divided by it. Every rank gets
+    both; without a process group this is the one rank's own."""
+    ws, t = 1, float(my_seconds)
+    if dist is not None:
+        import torch
+        ws = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, float(units_per_rank) * ws / t
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -364,13 +378,7 @@ def main():
     ebic.ebic_timing_enable(False)
     if m.status() != ebic.EBIC_OK:
         raise SystemExit("device status error in the kernel-timing pass")
-    my_time = tot_ms / 1000.0
-    if dist:
-        t = torch.tensor([my_time], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        my_time = float(t.item())
-    evals = float(P) * R * args.steps * ws
-    value = evals / my_time
+    my_time, value = combine_over_ranks(tot_ms / 1000.0, float(P) * R * args.steps, dist, dev)
     ms_per_step = 1000.0 * my_time / args.steps
 
     # ---- e2e: the same step through the public calls with pinned host inputs/outputs ----
@@ -410,12 +418,8 @@ def main():
             t0 = time.perf_counter()
             e2e_step(i)
             ts.append(time.perf_counter() - t0)
-        et = sum(ts)
-        if dist:
-            t = torch.tensor([et], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": float(P) * R * args.e2e_steps * ws / et,
+        et, e2e_value = combine_over_ranks(sum(ts), float(P) * R * args.e2e_steps, dist, dev)
+        e2e = {"value": e2e_value,
                "unit": "candidate-row evals/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * et / args.e2e_steps,
                "path": ("ebic_eval_population + ebic_fitness" if args.unfused
