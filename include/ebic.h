@@ -315,10 +315,15 @@ typedef struct ebic_params {
   float p_mutation;          /* mutation probability (default 0.7)                            */
   float overlap_threshold;   /* archive admission threshold (default 0.5)                     */
   uint32_t tabu_retries;     /* re-mutations of a tabu child before a random one (default 8)  */
-  uint32_t flags;            /* EBIC_NEGATIVE_TRENDS or 0                                     */
+  uint32_t flags;            /* EBIC_NEGATIVE_TRENDS, EBIC_RUN_ON_DEVICE, or 0               */
   uint32_t reserved;
   uint64_t seed;             /* default 1807099320                                            */
 } ebic_params;
+/* ebic_params.flags: the whole generation loop runs on the device (breeding, tabu list,
+ * duplicate handling, archive update), with no host round trip per generation; the archive is
+ * the same, bit for bit, as the host loop's. Takes archive_size <= 32 (else
+ * EBIC_ERR_UNSUPPORTED); ebic_run only. */
+#define EBIC_RUN_ON_DEVICE 0x2u
 
 typedef struct ebic_result {
   uint32_t n;                /* archive members, best first                                   */

@@ -24,6 +24,9 @@ namespace ebic {
 
 constexpr int kMaxCols = 832;
 constexpr int kMaxLen = 64;
+// The host and the device generation loops draw at most this many random columns when looking
+// for one not in a candidate, then take the smallest unused one (the same bound on both sides).
+constexpr uint32_t kUnusedDraws = 1u << 16;
 constexpr int kSmemLimit = 232448;            // 227 KB shared memory per CTA (static + dynamic)
 constexpr int kSmemDynMax = kSmemLimit - 2048;  // dynamic part: room for the kernels' static smem
 constexpr int kStageMax = 104 * 1024;         // per pipeline stage (two stages)
@@ -255,6 +258,8 @@ cudaError_t launch_gather_rows(const uint32_t* a, const uint32_t* b, const int32
 }  // namespace ebic
 
 struct ebic_matrix;
+struct ebic_params;
+struct ebic_result;
 
 namespace ebic {
 
@@ -274,6 +279,13 @@ int matrix_eval_plan(const ebic_matrix* m, uint32_t n_cand, int64_t total_cols_h
                      EvalArgs* a, EvalConfig* cfg, const CUtensorMap** tmap, int ts_cap = 0);
 // Record the calling thread's last-error message and return `code`.
 int set_last_error(int code, const char* msg);
+
+// The generation loop on the device (ga_device.cu), from the host loop's initial population:
+// init_cols [population][kMaxLen] (a candidate's columns first), init_n its lengths, init_h its
+// hashes. The archive is at most 32 members.
+int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t W,
+                     const ebic_params& p, cudaStream_t s, const uint16_t* init_cols,
+                     const uint32_t* init_n, const uint64_t* init_h, ebic_result** out);
 // Host-side check of a CSR candidate list; empty string when valid.
 const char* check_candidates_host_c(const uint16_t* cols, const uint32_t* offsets, uint32_t n,
                                     int32_t ncols);

@@ -294,11 +294,14 @@ struct Breeder {
     return c;
   }
 
-  uint16_t unused_column(const Cand& c) {
-    for (;;) {  // terminates: callers ensure c.size() < ncols
+  uint16_t unused_column(const Cand& c) {  // callers ensure c.size() < ncols
+    for (uint32_t t = 0; t < kUnusedDraws; ++t) {
       const uint16_t x = (uint16_t)rng.below((uint32_t)ncols);
       if (std::find(c.begin(), c.end(), x) == c.end()) return x;
     }
+    for (int32_t x = 0; x < ncols; ++x)  // after kUnusedDraws misses: the smallest unused one
+      if (std::find(c.begin(), c.end(), (uint16_t)x) == c.end()) return (uint16_t)x;
+    return 0;
   }
 
   Cand crossover(const Cand& a, const Cand& b) {
@@ -461,8 +464,25 @@ std::string check_params(const ebic_params& p, int32_t ncols) {
       !(p.p_mutation >= 0.f && p.p_mutation <= 1.f))
     return "probabilities must be in [0, 1]";
   if (!(p.overlap_threshold >= 0.f)) return "overlap_threshold must be >= 0";
-  if (p.flags & ~EBIC_NEGATIVE_TRENDS) return "unknown flag";
+  if (p.flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_RUN_ON_DEVICE)) return "unknown flag";
   return "";
+}
+
+// The initial population: random candidates from the generator seeded with `seed`, a repeat
+// drawn again (up to 32 times).
+void initial_population(const ebic_params& p, int32_t ncols, std::vector<Cand>& pop,
+                        std::vector<uint64_t>& pop_h) {
+  Breeder ga(p, ncols);
+  CandSet seen;
+  pop.clear();
+  pop_h.clear();
+  for (uint32_t i = 0; i < p.population; ++i) {
+    Cand c = ga.random_candidate();
+    for (int t = 0; t < 32 && seen.count(c); ++t) c = ga.random_candidate();
+    seen.insert(c);
+    pop_h.push_back(CandHash()(c));
+    pop.push_back(std::move(c));
+  }
 }
 
 int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebic_result** out) {
@@ -471,23 +491,13 @@ int run_ga(int64_t rows, int32_t ncols, const ebic_params& p, Evaluator& ev, ebi
   std::vector<Breeder> breeders;
   breeders.reserve(workers.size());
   for (unsigned w = 0; w < workers.size(); ++w) breeders.emplace_back(p, ncols);
-  Breeder& ga = breeders[0];  // the initial population draws from the generator seeded with `seed`
   CandSet tabu, in_archive, picked;
   SlotSet in_next;  // the next population's sequences so far
   std::vector<Cand> pop;
   std::vector<uint64_t> pop_h;  // each candidate's CandHash, computed once
   pop.reserve(P);
   pop_h.reserve(P);
-  {
-    CandSet seen;
-    for (uint32_t i = 0; i < P; ++i) {
-      Cand c = ga.random_candidate();
-      for (int t = 0; t < 32 && seen.count(c); ++t) c = ga.random_candidate();
-      seen.insert(c);
-      pop_h.push_back(CandHash()(c));
-      pop.push_back(std::move(c));
-    }
-  }
+  initial_population(p, ncols, pop, pop_h);
   std::vector<Member> archive;
   std::vector<uint16_t> cols;
   std::vector<uint32_t> offs;
@@ -806,7 +816,7 @@ struct GpuEvaluator : Evaluator {
   uint32_t n_arch = 0;
 
   GpuEvaluator(const ebic_matrix* mm, cudaStream_t st, const ebic_params& p, int64_t words)
-      : m(mm), s(st), flags(p.flags), P(p.population), K(p.archive_size),
+      : m(mm), s(st), flags(p.flags & EBIC_NEGATIVE_TRENDS), P(p.population), K(p.archive_size),
         T(2 * p.archive_size), max_len(p.max_len), W(words) {}
   ~GpuEvaluator() override {
     cudaStreamSynchronize(s);
@@ -999,6 +1009,8 @@ int ebic_run_custom(int64_t rows, int32_t cols, const ebic_params* p, const ebic
     return set_last_error(EBIC_ERR_INVALID_ARG, "rows/cols out of range");
   std::string why = check_params(*p, cols);
   if (!why.empty()) return set_last_error(EBIC_ERR_INVALID_ARG, why.c_str());
+  if (p->flags & EBIC_RUN_ON_DEVICE)
+    return set_last_error(EBIC_ERR_UNSUPPORTED, "EBIC_RUN_ON_DEVICE is for ebic_run");
   try {
     CallbackEvaluator e(ev);
     return run_ga(rows, cols, *p, e, out);
@@ -1019,9 +1031,24 @@ int ebic_run(const ebic_matrix* m, const ebic_params* p, void* stream, ebic_resu
   if (prev != v.device) (void)cudaSetDevice(v.device);
   int rc;
   try {
-    GpuEvaluator e(m, static_cast<cudaStream_t>(stream), *p, v.L.words);
-    rc = e.init();
-    if (rc == EBIC_OK) rc = run_ga(v.L.rows, v.L.cols, *p, e, out);
+    if (p->flags & EBIC_RUN_ON_DEVICE) {
+      std::vector<Cand> pop;
+      std::vector<uint64_t> pop_h;
+      initial_population(*p, v.L.cols, pop, pop_h);
+      std::vector<uint16_t> c((size_t)p->population * kMaxLen, 0);
+      std::vector<uint32_t> n(p->population);
+      for (uint32_t i = 0; i < p->population; ++i) {
+        n[i] = (uint32_t)pop[i].size();
+        std::copy(pop[i].begin(), pop[i].end(), c.begin() + (size_t)i * kMaxLen);
+      }
+      rc = run_ga_on_device(m, v.L.rows, v.L.cols, v.L.words, *p,
+                            static_cast<cudaStream_t>(stream), c.data(), n.data(), pop_h.data(),
+                            out);
+    } else {
+      GpuEvaluator e(m, static_cast<cudaStream_t>(stream), *p, v.L.words);
+      rc = e.init();
+      if (rc == EBIC_OK) rc = run_ga(v.L.rows, v.L.cols, *p, e, out);
+    }
   } catch (const std::bad_alloc&) {
     rc = set_last_error(EBIC_ERR_OOM, "host allocation failed");
   }

@@ -28,6 +28,7 @@ EBIC_ERR_NO_DEVICE = -6
 EBIC_EXCLUDE_MISSING = 0x1
 EBIC_NEGATIVE_TRENDS = 0x1
 EBIC_EVAL_DIRECT = 0x2
+EBIC_RUN_ON_DEVICE = 0x2  # ebic_params.flags
 EBIC_MAX_COLS = 832
 EBIC_MAX_CANDIDATE_LEN = 64
 

@@ -154,3 +154,44 @@ def test_gpu_run_equals_oracle_run(negative, pairs):
     cols, offs = synth.population_from_lists(got["members"])
     _, bm = oracle.eval_population(ds.X, cols, offs, negative=negative)
     assert np.array_equal(got["bitmaps"], bm)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("negative,pairs,population,generations,archive,max_len,threshold", [
+    (False, True, 120, 12, 6, 12, 0.5),
+    (True, True, 120, 12, 6, 12, 0.5),
+    (False, False, 120, 8, 6, 12, 0.5),
+    (False, True, 700, 10, 20, 16, 0.5),
+    (True, True, 400, 15, 32, 24, 0.25),
+    (False, True, 300, 20, 10, 12, 1.0),
+])
+def test_device_loop_equals_host_loop(negative, pairs, population, generations, archive, max_len,
+                                      threshold):
+    """The generation loop on the device (EBIC_RUN_ON_DEVICE) takes the host loop's decisions:
+    the same archive, bit for bit, with the same counts, qualities and bitmaps."""
+    ebic = _ebic()
+    ds = _small(seed=8)
+    flags = ebic.EBIC_NEGATIVE_TRENDS if negative else 0
+    kw = dict(population=population, generations=generations, archive_size=archive,
+              max_len=max_len, overlap_threshold=threshold)
+    with ebic.Matrix(ds.X) as m:
+        if pairs:
+            m.build_pairs()
+        host = ebic.ebic_run(m.handle, _params(ebic, flags=flags, **kw))
+        dev = ebic.ebic_run(m.handle, _params(ebic, flags=flags | ebic.EBIC_RUN_ON_DEVICE, **kw))
+    assert dev["members"] == host["members"]
+    assert np.array_equal(dev["counts"], host["counts"])
+    assert np.array_equal(dev["quality"], host["quality"])
+    assert np.array_equal(dev["bitmaps"], host["bitmaps"])
+    assert dev["generations_run"] == host["generations_run"] == generations
+    assert dev["candidates_evaluated"] == host["candidates_evaluated"]
+
+
+def test_device_loop_rejects_what_it_does_not_take():
+    ebic = _ebic()
+    ds = _small()
+    sc = OracleScorer(ds.X)
+    with pytest.raises(ebic.EbicError) as ei:
+        ebic.ebic_run_custom(ds.X.shape[0], ds.X.shape[1],
+                             _params(ebic, flags=ebic.EBIC_RUN_ON_DEVICE), sc.evaluator)
+    assert ei.value.code == ebic.EBIC_ERR_UNSUPPORTED
