@@ -65,8 +65,12 @@ def parse_args():
                    help="time ebic_eval_population + ebic_fitness instead of ebic_eval_fitness")
     p.add_argument("--pair-budget", type=int, default=8 << 30,
                    help="largest pair table to build, bytes")
-    p.add_argument("--workload", choices=["methylation", "batched", "served"],
+    p.add_argument("--workload", choices=["methylation", "batched", "served", "ga"],
                    default="methylation")
+    p.add_argument("--ga-generations", type=int, default=30,
+                   help="ga: generations of each ebic_run")
+    p.add_argument("--ga-loop", choices=["both", "host", "device"], default="both",
+                   help="ga: which generation loop(s) to time")
     p.add_argument("--load", type=float, default=0.7,
                    help="served: arrival rate as a fraction of the measured capacity")
     p.add_argument("--runs", type=int, default=32, help="served: concurrent EBIC runs")
@@ -250,6 +254,9 @@ def main():
         return
     if args.workload == "served":
         served_workload(args)
+        return
+    if args.workload == "ga":
+        ga_workload(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -604,6 +611,50 @@ def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
 
 
 # ---- config 4: batched vs plain per-population launches ----------------------------------------
+
+def ga_workload(args):
+    """The whole method on the methylation-shaped matrix: ebic_run (P = 1,600, archive 20,
+    candidates of up to 16 columns) with the generation loop on the host and on the device. A step
+    is one generation; the line reports ms per generation of each loop and whether their archives
+    are identical (they must be)."""
+    import torch
+    from paper_1807_09932_gb300 import ebic
+    torch.cuda.set_device(0)
+    ds, _, _ = make_workload()
+    R = ds.X.shape[0]
+    loops = {"host": 0, "device": ebic.EBIC_RUN_ON_DEVICE}
+    if args.ga_loop != "both":
+        loops = {args.ga_loop: loops[args.ga_loop]}
+    out, archives = {}, {}
+    with ebic.Matrix(torch.from_numpy(ds.X).cuda(), exclude_missing=True) as m:
+        if not args.no_pairs:
+            m.build_pairs(max_bytes=args.pair_budget)
+        for name, flag in loops.items():
+            ebic.ebic_run(m.handle, ebic.ebic_params_default(population=1600, generations=2,
+                                                             flags=flag))  # warm-up
+            params = ebic.ebic_params_default(population=1600, generations=args.ga_generations,
+                                              archive_size=20, max_len=16, flags=flag)
+            launches0 = ebic.ebic_launch_count()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = ebic.ebic_run(m.handle, params)
+            wall = time.perf_counter() - t0
+            out[name] = {"ms_per_generation": 1000.0 * wall / res["generations_run"],
+                         "generations": res["generations_run"],
+                         "gpu_launches": ebic.ebic_launch_count() - launches0}
+            archives[name] = res
+    line = {"metric": "ms per EBIC generation", "workload": "ga", "unit": "ms",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; ebic_run, population 1,600, archive 20, "
+                                   "candidates of 2-16 columns",
+                       "rows": R, "pair_table": not args.no_pairs},
+            "loops": out}
+    if len(archives) == 2:
+        a, b = archives["host"], archives["device"]
+        line["same_archive"] = bool(a["members"] == b["members"] and
+                                    np.array_equal(a["bitmaps"], b["bitmaps"]))
+    print(json.dumps(line), flush=True)
+
 
 def batched_workload(args):
     """8 datasets (5k-200k rows, 20-500 cols) and 64 populations (200-3,200 candidates of 2-64

@@ -364,8 +364,7 @@ struct Archive {  // members in order; `size` of them real, the rest (to K) empt
 // Up to 2K offers: candidates with rows in the offer order, skipping archived sequences. One
 // warp; lane a holds archive member a's hash.
 __global__ void offers_kernel(Pop pop, const uint32_t* offer_sorted, const uint32_t* n_offerable,
-                              Archive arch, uint32_t T, uint32_t* offers, uint32_t* n_offers,
-                              int32_t* gather_idx) {
+                              Archive arch, uint32_t T, uint32_t* offers, uint32_t* n_offers) {
   __shared__ uint64_t ah[kMaxArch];
   const int lane = threadIdx.x;
   const uint32_t ka = *arch.size;
@@ -395,7 +394,6 @@ __global__ void offers_kernel(Pop pop, const uint32_t* offer_sorted, const uint3
     if (t > T) t = T;
   }
   __syncwarp();
-  for (uint32_t k = lane; k < T; k += 32) gather_idx[k] = k < t ? (int32_t)offers[k] : 0;
   if (lane == 0) *n_offers = t;
 }
 
@@ -1066,9 +1064,9 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   GD_CUDA(b.get(&nxt.h, P));
   uint16_t* dcols;
   uint32_t *doffs, *dcounts, *dov, *dbm, *rank, *elites, *offer_sorted, *n_offerable, *offers,
-      *n_offers, *pbm, *pov, *pcnt, *zero;
+      *n_offers, *pov;
   uint64_t* dfit;
-  int32_t *gather_idx, *gather_src;
+  int32_t* gather_src;
   Rng* kid_rng;
   uint8_t* dup;
   GD_CUDA(b.get(&dcols, (size_t)P * kMaxLen));
@@ -1083,11 +1081,7 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   GD_CUDA(b.get(&n_offerable, 1));
   GD_CUDA(b.get(&offers, T));
   GD_CUDA(b.get(&n_offers, 1));
-  GD_CUDA(b.get(&gather_idx, T));
-  GD_CUDA(b.get(&pbm, (size_t)T * W));
   GD_CUDA(b.get(&pov, (size_t)T * T));
-  GD_CUDA(b.get(&pcnt, T));
-  GD_CUDA(b.get(&zero, 1));
   GD_CUDA(b.get(&kid_rng, P));
   GD_CUDA(b.get(&dup, ((size_t)P + 15) / 16 * 16));
   GD_CUDA(cudaMemsetAsync(dup, 0, ((size_t)P + 15) / 16 * 16, s));
@@ -1126,7 +1120,6 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   GD_CUDA(b.get(&gather_src, K));
   GD_CUDA(cudaMemsetAsync(tabu.slots, 0, cap_t * 4, s));
   GD_CUDA(cudaMemsetAsync(tabu.n_ent, 0, 4, s));
-  GD_CUDA(cudaMemsetAsync(zero, 0, 4, s));
   // the initial population and the empty archive (K members of one column, no rows)
   GD_CUDA(cudaMemcpyAsync(pop.c, init_cols, (size_t)P * kMaxLen * 2, cudaMemcpyHostToDevice, s));
   GD_CUDA(cudaMemcpyAsync(pop.n, init_n, (size_t)P * 4, cudaMemcpyHostToDevice, s));
@@ -1177,8 +1170,7 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
     count_launch();
     order_kernel<<<(unsigned)(((uint64_t)P * 32 + 255) / 256), 256, 0, s>>>(oa);
     count_launch();
-    offers_kernel<<<1, 32, 0, s>>>(pop, offer_sorted, n_offerable, arch[cur], T, offers, n_offers,
-                                   gather_idx);
+    offers_kernel<<<1, 32, 0, s>>>(pop, offer_sorted, n_offerable, arch[cur], T, offers, n_offers);
     GD_CUDA(cudaMemsetAsync(pov, 0, (size_t)T * T * 4, s));
     count_launch();
     offer_overlap_kernel<<<(unsigned)num_sms, 256, 0, s>>>(dbm, W, offers, n_offers, T, pov);
