@@ -241,9 +241,10 @@ __device__ void store_cand(const Pop& p, uint32_t i, const Cand& c, uint64_t h) 
 
 // ---- an exact set of sequences (the tabu list) -------------------------------------------------
 struct SeqSet {
-  uint32_t* slots;   // entry + 1, 0 = empty; mask + 1 of them, at most half used
+  // slot: the hash's high 32 bits (a tag) << 32 | entry + 1; 0 = empty; mask + 1 slots, at most
+  // half used. A probe that meets no equal tag costs one load.
+  unsigned long long* slots;
   uint64_t mask;
-  uint64_t* ent_h;
   uint32_t* ent_n;
   uint16_t* arena;   // entry e's sequence at arena + e * kMaxLen
   uint32_t* n_ent;
@@ -257,11 +258,14 @@ __device__ uint64_t spread(uint64_t h) {
 }
 
 __device__ bool set_contains(const SeqSet& s, const uint16_t* c, uint32_t n, uint64_t h) {
+  const uint32_t tag = (uint32_t)(h >> 32);
   uint64_t i = spread(h) & s.mask;
   for (uint64_t k = 0; k <= s.mask; ++k, i = (i + 1) & s.mask) {
-    const uint32_t e = *reinterpret_cast<volatile const uint32_t*>(s.slots + i);
-    if (e == 0) return false;
-    if (s.ent_h[e - 1] == h && equal_global(s.arena + (size_t)(e - 1) * kMaxLen, s.ent_n[e - 1], c, n))
+    const unsigned long long v = *reinterpret_cast<volatile const unsigned long long*>(s.slots + i);
+    if (v == 0) return false;
+    const uint32_t e = (uint32_t)v;
+    if ((uint32_t)(v >> 32) == tag &&
+        equal_global(s.arena + (size_t)(e - 1) * kMaxLen, s.ent_n[e - 1], c, n))
       return true;
   }
   return false;
@@ -270,13 +274,13 @@ __device__ bool set_contains(const SeqSet& s, const uint16_t* c, uint32_t n, uin
 // Inserts a sequence that is not in the set; concurrent inserts of distinct sequences are safe.
 __device__ void set_insert(const SeqSet& s, const uint16_t* c, uint32_t n, uint64_t h) {
   const uint32_t e = atomicAdd(s.n_ent, 1u);
-  s.ent_h[e] = h;
   s.ent_n[e] = n;
   for (uint32_t k = 0; k < n; ++k) s.arena[(size_t)e * kMaxLen + k] = c[k];
   __threadfence();  // the entry is complete before a slot points to it
+  const unsigned long long v = ((unsigned long long)(uint32_t)(h >> 32) << 32) | (e + 1u);
   uint64_t i = spread(h) & s.mask;
   for (uint64_t k = 0; k <= s.mask; ++k, i = (i + 1) & s.mask)
-    if (atomicCAS(s.slots + i, 0u, e + 1) == 0u) return;
+    if (atomicCAS(s.slots + i, 0ull, v) == 0ull) return;
 }
 
 // ---- kernels -----------------------------------------------------------------------------------
@@ -1100,7 +1104,6 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   SeqSet tabu;
   tabu.mask = cap_t - 1;
   GD_CUDA(b.get(&tabu.slots, cap_t));
-  GD_CUDA(b.get(&tabu.ent_h, cap_e));
   GD_CUDA(b.get(&tabu.ent_n, cap_e));
   GD_CUDA(b.get(&tabu.arena, cap_e * kMaxLen));
   GD_CUDA(b.get(&tabu.n_ent, 1));
@@ -1118,7 +1121,7 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
     GD_CUDA(cudaMemsetAsync(abm[k], 0, (size_t)(K + 1) * W * 4, s));
   }
   GD_CUDA(b.get(&gather_src, K));
-  GD_CUDA(cudaMemsetAsync(tabu.slots, 0, cap_t * 4, s));
+  GD_CUDA(cudaMemsetAsync(tabu.slots, 0, cap_t * 8, s));
   GD_CUDA(cudaMemsetAsync(tabu.n_ent, 0, 4, s));
   // the initial population and the empty archive (K members of one column, no rows)
   GD_CUDA(cudaMemcpyAsync(pop.c, init_cols, (size_t)P * kMaxLen * 2, cudaMemcpyHostToDevice, s));
