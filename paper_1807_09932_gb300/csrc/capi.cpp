@@ -357,6 +357,7 @@ int status_code(uint32_t bits, const char* where) {
 namespace ebic {
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 Layout make_layout(int64_t rows, int32_t cols) {
   Layout L;

@@ -55,6 +55,7 @@ struct Layout {
 
 // Diagnostics: every kernel launch of the library is counted (defined in capi.cpp).
 void count_launch();
+void count_launches(int64_t n);  // n kernels at once (a negative n takes back counted ones)
 
 // Choose width and VEC for a column count (host).
 Layout make_layout(int64_t rows, int32_t cols);

@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(256) offer_overlap_kernel(const uint32_t* __re
 
 struct BreedArgs {
   Ops o;
-  uint32_t gen;
+  const uint32_t* gen;  // the generation number (device memory, so a captured graph replays)
   Pop pop, next;
   const uint32_t* rank;
   const uint32_t* elites;
@@ -479,7 +479,7 @@ __global__ void breed_kernel(BreedArgs a) {
     store_cand(a.next, s, child, a.pop.h[e]);
     return;
   }
-  Rng r = child_stream(o.seed, a.gen, s);
+  Rng r = child_stream(o.seed, *a.gen, s);
   auto tournament = [&]() {
     uint32_t best = r.below(o.P);
     for (uint32_t t = 1; t < o.tournament; ++t) {
@@ -756,6 +756,8 @@ __global__ void commit_spec_kernel(uint32_t P, const uint8_t* dup, Spec sp, Pop 
   next.n[s] = n;
   next.h[s] = sp.seq.h[s];
 }
+
+__global__ void next_generation_kernel(uint32_t* gen) { ++*gen; }
 
 // The next population as the list the scoring reads.
 __global__ void pack_kernel(Pop pop, uint32_t P, uint16_t* cols, uint32_t* offs) {
@@ -1040,10 +1042,33 @@ uint64_t pow2_at_least(uint64_t x) {
 
 }  // namespace
 
+namespace {
+// The loop's own stream (it can be captured into a graph, which the legacy default stream cannot),
+// started after the caller's stream's pending work; released when the run returns.
+struct RunStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t e = nullptr;
+  ~RunStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    if (e) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
 int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t W,
-                     const ebic_params& p, cudaStream_t s, const uint16_t* init_cols,
+                     const ebic_params& p, cudaStream_t caller, const uint16_t* init_cols,
                      const uint32_t* init_n, const uint64_t* init_h, ebic_result** out) {
   using namespace gadev;
+  DeviceBuffers b;  // freed after the stream below is drained (declared first, destroyed last)
+  RunStream rs;
+  GD_CUDA(cudaStreamCreateWithFlags(&rs.s, cudaStreamNonBlocking));
+  GD_CUDA(cudaEventCreateWithFlags(&rs.e, cudaEventDisableTiming));
+  GD_CUDA(cudaEventRecord(rs.e, caller));
+  GD_CUDA(cudaStreamWaitEvent(rs.s, rs.e, 0));
+  cudaStream_t s = rs.s;
   const uint32_t P = p.population, K = p.archive_size, T = 2 * K, G = p.generations;
   if (K > kMaxArch)
     return set_last_error(EBIC_ERR_UNSUPPORTED, "the device loop takes archive_size <= 32");
@@ -1058,7 +1083,6 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
     GD_CUDA(cudaGetDevice(&dev));
     GD_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  DeviceBuffers b;
   Pop pop, nxt;
   GD_CUDA(b.get(&pop.c, (size_t)P * kMaxLen));
   GD_CUDA(b.get(&pop.n, P));
@@ -1156,59 +1180,104 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   o.p_crossover = p.p_crossover;
   o.p_mutation = p.p_mutation;
   o.seed = p.seed;
-  int cur = 0;
-  uint64_t evaluated = 0;
-  uint32_t gen = 0;
-  pack_kernel<<<1, 1024, 0, s>>>(pop, P, dcols, doffs);
-  GD_CUDA(cudaGetLastError());
-  for (; gen < G; ++gen) {
-    int rc = ebic_eval_fitness(m, dcols, doffs, P, eflags, arch[cur].csr_cols, arch[cur].csr_offs,
-                               abm[cur], K, dcounts, dbm, dfit, dov, s);
+  uint32_t* dgen;
+  GD_CUDA(b.get(&dgen, 1));
+  GD_CUDA(cudaMemsetAsync(dgen, 0, 4, s));
+  Pop pops[2] = {pop, nxt};
+  // One generation's work on the stream; the buffers alternate with the generation's parity, so
+  // two generations return to the same buffers (a graph of two replays unchanged).
+  auto issue = [&](int par, bool breed) -> int {
+    const Pop& cp = pops[par];
+    const Pop& np = pops[1 - par];
+    int rc = ebic_eval_fitness(m, dcols, doffs, P, eflags, arch[par].csr_cols, arch[par].csr_offs,
+                               abm[par], K, dcounts, dbm, dfit, dov, s);
     if (rc != EBIC_OK) return rc;
-    evaluated += P;
     count_launch();
-    tabu_insert_kernel<<<(P + 255) / 256, 256, 0, s>>>(tabu, pop, P);
+    tabu_insert_kernel<<<(P + 255) / 256, 256, 0, s>>>(tabu, cp, P);
     GD_CUDA(cudaMemsetAsync(n_offerable, 0, 4, s));
-    OrderArgs oa{pop, P, p.elite, dfit, dcounts, rank, elites, offer_sorted, n_offerable};
+    OrderArgs oa{cp, P, p.elite, dfit, dcounts, rank, elites, offer_sorted, n_offerable};
     count_launch();
     order_kernel<<<(unsigned)(((uint64_t)P * 32 + 255) / 256), 256, 0, s>>>(oa);
     count_launch();
-    offers_kernel<<<1, 32, 0, s>>>(pop, offer_sorted, n_offerable, arch[cur], T, offers, n_offers);
+    offers_kernel<<<1, 32, 0, s>>>(cp, offer_sorted, n_offerable, arch[par], T, offers, n_offers);
     GD_CUDA(cudaMemsetAsync(pov, 0, (size_t)T * T * 4, s));
     count_launch();
     offer_overlap_kernel<<<(unsigned)num_sms, 256, 0, s>>>(dbm, W, offers, n_offers, T, pov);
-    const bool breed = gen + 1 < G;
     if (breed) {
-      BreedArgs ba{o, gen, pop, nxt, rank, elites, tabu, kid_rng};
+      BreedArgs ba{o, dgen, cp, np, rank, elites, tabu, kid_rng};
       count_launch();
       breed_kernel<<<(P + 127) / 128, 128, 0, s>>>(ba);
       GD_CUDA(cudaMemsetAsync(table.v, 0, cap_n * 4, s));
       count_launch();
-      first_slot_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, nxt, P);
+      first_slot_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, np, P);
       count_launch();
-      dup_flag_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, nxt, P, dup);
+      dup_flag_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, np, P, dup);
       count_launch();
-      spec_kernel<<<(P + 63) / 64, 64, 0, s>>>(o, table, nxt, tabu, kid_rng, dup, spec);
+      spec_kernel<<<(P + 63) / 64, 64, 0, s>>>(o, table, np, tabu, kid_rng, dup, spec);
       count_launch();
-      settle_kernel<<<1, 32, 0, s>>>(o, table, nxt, tabu, kid_rng, dup, spec, acc_slot, acc_h);
+      settle_kernel<<<1, 32, 0, s>>>(o, table, np, tabu, kid_rng, dup, spec, acc_slot, acc_h);
       count_launch();
-      commit_spec_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dup, spec, nxt);
+      commit_spec_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dup, spec, np);
     }
-    AdmitArgs aa{pop, P, K, T, (uint32_t)(ncols + 31) / 32, p.overlap_threshold, dcounts, dov,
-                 pov, offers, n_offers, arch[cur], arch[1 - cur], gather_src};
+    AdmitArgs aa{cp, P, K, T, (uint32_t)(ncols + 31) / 32, p.overlap_threshold, dcounts, dov,
+                 pov, offers, n_offers, arch[par], arch[1 - par], gather_src};
     count_launch();
     admit_kernel<<<1, 32, 0, s>>>(aa);
-    GD_CUDA(launch_gather_rows(dbm, abm[cur], gather_src, K, W, abm[1 - cur], s));
-    GD_CUDA(cudaGetLastError());
-    cur = 1 - cur;
-    if (!breed) {
-      ++gen;
-      break;
+    GD_CUDA(launch_gather_rows(dbm, abm[par], gather_src, K, W, abm[1 - par], s));
+    if (breed) {
+      count_launch();
+      pack_kernel<<<1, 1024, 0, s>>>(np, P, dcols, doffs);
+      count_launch();
+      next_generation_kernel<<<1, 1, 0, s>>>(dgen);
     }
-    count_launch();
-    pack_kernel<<<1, 1024, 0, s>>>(nxt, P, dcols, doffs);
-    std::swap(pop, nxt);
+    GD_CUDA(cudaGetLastError());
+    return EBIC_OK;
+  };
+  pack_kernel<<<1, 1024, 0, s>>>(pops[0], P, dcols, doffs);
+  GD_CUDA(cudaGetLastError());
+  // the breeding generations 0 .. G-2 (two at a time from a captured graph when the stream can be
+  // captured), then the last one without breeding
+  uint32_t gen = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_launches = 0;  // kernels in the two-generation graph
+  if (G >= 5) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+      const int64_t c0 = ebic_launch_count();
+      const int rc0 = issue(0, true);
+      const int rc1 = rc0 == EBIC_OK ? issue(1, true) : rc0;
+      graph_launches = ebic_launch_count() - c0;
+      count_launches(-graph_launches);  // nothing ran while capturing
+      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+      if (rc1 == EBIC_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    (void)cudaGetLastError();  // a failed capture leaves the direct launches below
   }
+  if (exec) {
+    for (; gen + 2 <= G - 1; gen += 2) {
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        GD_CUDA(e);
+      }
+      count_launches(graph_launches);
+    }
+    cudaGraphExecDestroy(exec);
+  }
+  for (; gen + 1 < G; ++gen) {
+    const int rc = issue((int)(gen & 1u), true);
+    if (rc != EBIC_OK) return rc;
+  }
+  {
+    const int rc = issue((int)(gen & 1u), false);  // the last generation
+    if (rc != EBIC_OK) return rc;
+    ++gen;
+  }
+  const int cur = (int)(gen & 1u);  // the archive the last generation wrote
+  const uint64_t evaluated = (uint64_t)P * gen;
   GD_CUDA(cudaStreamSynchronize(s));
   int st = ebic_matrix_status(const_cast<ebic_matrix*>(m), s);
   if (st != EBIC_OK) return st;
