@@ -638,6 +638,8 @@ __global__ void spec_kernel(Ops o, SlotTable t, Pop next, SeqSet tabu, const Rng
 // are kept in shared memory (up to kAccMax; a longer list is read from the population itself).
 constexpr uint32_t kAccMax = 1024;
 constexpr uint32_t kFlagsMax = 16384;  // duplicate flags kept in shared memory up to this population
+constexpr uint32_t kListMax = 512;     // duplicate slots walked from a list up to this many
+constexpr uint32_t kExtraMax = 256;    // displaced slots waiting in the side list
 __global__ void settle_kernel(Ops o, SlotTable t, Pop next, SeqSet tabu, const Rng* kid_rng,
                               uint8_t* dup_g, Spec sp, uint32_t* acc_slot_g, uint64_t* acc_h_g) {
   __shared__ uint64_t acc_h[kAccMax];
@@ -654,87 +656,177 @@ __global__ void settle_kernel(Ops o, SlotTable t, Pop next, SeqSet tabu, const R
   }
   __syncwarp();
   uint32_t n_acc = 0;
-  // the window's phase-A keys, one slot per lane; the next window's are loaded ahead
-  auto keys = [&](uint32_t base, uint64_t& h, uint32_t& n, int32_t& d) {
-    const uint32_t s0 = base + lane;
-    h = 0;
-    n = 0;
-    d = -1;
-    if (s0 < o.P && dup[s0] == 1) {
-      h = sp.seq.h[s0];
-      n = sp.seq.n[s0];
-      d = sp.disp[s0];
+  // Slot s (kind 1: phase A ran, with its key h_j, length n_j and displacement disp_j; kind 2:
+  // displaced during this walk): the whole warp calls this; returns the slot it displaces, or -1.
+  auto settle_slot = [&](uint32_t s, uint8_t kind, uint64_t h_j, uint32_t n_j,
+                         int32_t disp_j) -> int32_t {
+    // does the phase-A result repeat a replacement taken before?
+    bool clash = false;
+    if (kind == 1) {
+      for (uint32_t k = lane; k < n_acc; k += 32) {
+        const uint64_t ah = k < kAccMax ? acc_h[k] : acc_h_g[k];
+        if (ah != h_j) continue;
+        const uint32_t as = k < kAccMax ? acc_slot[k] : acc_slot_g[k];
+        uint32_t na;
+        const uint16_t* ca = accepted_seq(as, next, sp.seq, na);
+        if (seq_equal(ca, na, sp.seq.c + (size_t)s * kMaxLen, n_j)) clash = true;
+      }
+      clash = __any_sync(0xFFFFFFFFu, clash);
     }
+    int32_t displaced = -1;
+    uint64_t h_acc = h_j;
+    uint32_t slot_acc = s | kInSpec;
+    if (kind == 1 && !clash) {
+      displaced = disp_j;  // the phase-A result stands; copied into place after the walk
+    } else if (lane == 0) {
+      Cand child;
+      load_cand(next, s, child);
+      uint64_t h = next.h[s];
+      Rng r = kid_rng[s - o.elite];
+      retry_chain(o, r, child, h, tabu, t, next, s, n_acc <= kAccMax ? acc_h : acc_h_g,
+                  n_acc <= kAccMax ? acc_slot : acc_slot_g, n_acc, sp.seq);
+      first_before(t, next, child.c, child.n, h, s, &displaced);
+      store_cand(next, s, child, h);
+      dup[s] = 3;  // settled here: no copy from the phase-A buffer
+      h_acc = h;
+      slot_acc = s;
+    }
+    h_acc = __shfl_sync(0xFFFFFFFFu, h_acc, 0);
+    slot_acc = __shfl_sync(0xFFFFFFFFu, slot_acc, 0);
+    displaced = __shfl_sync(0xFFFFFFFFu, displaced, 0);
+    if (lane == 0) {
+      if (n_acc < kAccMax) {
+        acc_h[n_acc] = h_acc;
+        acc_slot[n_acc] = slot_acc;
+      }
+      acc_h_g[n_acc] = h_acc;
+      acc_slot_g[n_acc] = slot_acc;
+    }
+    ++n_acc;
+    __syncwarp();
+    return displaced;
   };
-  uint64_t my_h, nx_h;
-  uint32_t my_n, nx_n;
-  int32_t my_disp, nx_disp;
-  keys(o.elite, my_h, my_n, my_disp);
-  for (uint32_t base = o.elite; base < o.P; base += 32) {
+  // the duplicate slots in order, compacted from the flags (shared memory), their phase-A keys
+  // loaded together; slots displaced on the way are merged from a small side list
+  __shared__ uint32_t list[kListMax];
+  __shared__ uint64_t list_h[kListMax];
+  __shared__ uint32_t list_n[kListMax];
+  __shared__ int32_t list_d[kListMax];
+  __shared__ uint32_t extra[kExtraMax];
+  uint32_t count = 0;
+  uint32_t walk_from = o.elite;
+  if (in_smem) {
+    for (uint32_t base = o.elite; base < o.P; base += 32) {
+      const uint32_t s0 = base + lane;
+      const bool d = s0 < o.P && dup[s0] == 1;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, d);
+      const uint32_t pos = count + __popc(m & ((1u << lane) - 1u));
+      if (d && pos < kListMax) list[pos] = s0;
+      count += __popc(m);
+    }
+  }
+  __syncwarp();
+  if (in_smem && count <= kListMax) {
+#pragma unroll 4
+    for (uint32_t k = lane; k < count; k += 32) {
+      const uint32_t s0 = list[k];
+      list_h[k] = sp.seq.h[s0];
+      list_n[k] = sp.seq.n[s0];
+      list_d[k] = sp.disp[s0];
+    }
+    uint32_t n_extra = 0;  // displaced slots not settled yet (unordered; usually none)
+    uint32_t i = 0;
+    bool overflow = false;
+    uint32_t resume = o.P;  // after an overflow: the slot the window walk resumes from
+    __syncwarp();
+    while (i < count || n_extra > 0) {
+      // the next slot: the list's next one or the smallest displaced one
+      uint32_t e_min = 0xFFFFFFFFu, e_at = 0;
+      for (uint32_t k = lane; k < n_extra; k += 32)
+        if (extra[k] < e_min) {
+          e_min = extra[k];
+          e_at = k;
+        }
+      for (int d = 16; d > 0; d >>= 1) {
+        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, e_min, d);
+        const uint32_t oa = __shfl_xor_sync(0xFFFFFFFFu, e_at, d);
+        if (om < e_min) {
+          e_min = om;
+          e_at = oa;
+        }
+      }
+      const uint32_t l_next = i < count ? list[i] : 0xFFFFFFFFu;
+      int32_t displaced;
+      uint32_t cur;
+      if (l_next < e_min) {
+        cur = l_next;
+        displaced = settle_slot(l_next, 1, list_h[i], list_n[i], list_d[i]);
+        ++i;
+      } else {
+        cur = e_min;
+        if (lane == 0) extra[e_at] = extra[n_extra - 1];
+        --n_extra;
+        __syncwarp();
+        displaced = settle_slot(e_min, 2, 0, 0, -1);
+      }
+      // a displaced slot's own sequence is now held by an earlier slot: settled in turn
+      if (displaced >= 0 && dup[displaced] != 2) {
+        if (lane == 0) {
+          dup[displaced] = 2;
+          if (n_extra < kExtraMax) extra[n_extra] = (uint32_t)displaced;
+        }
+        if (n_extra < kExtraMax) ++n_extra;
+        else overflow = true;
+      }
+      __syncwarp();
+      if (overflow) {  // every slot up to cur is settled; the rest are flagged 1 or 2
+        resume = cur + 1;
+        break;
+      }
+    }
+    if (!overflow) {
+      __syncwarp();
+      if (in_smem) {
+        const uint32_t nv = (o.P + 15) / 16;
+        for (uint32_t k = lane; k < nv; k += 32)
+          reinterpret_cast<uint4*>(dup_g)[k] = reinterpret_cast<const uint4*>(dup_s)[k];
+      }
+      return;
+    }
+    // more displaced slots than the side list holds: the window walk below settles the slots
+    // after `resume` in order (the flags say which: 1 or 2)
+    walk_from = resume;
+  }
+  // the window walk: every slot in order, the window's phase-A keys one slot per lane
+  for (uint32_t base = walk_from; base < o.P; base += 32) {
     __syncwarp();
     const uint32_t s0 = base + lane;
-    uint32_t mask = __ballot_sync(0xFFFFFFFFu, s0 < o.P && dup[s0] != 0);
-    keys(base + 32, nx_h, nx_n, nx_disp);
+    uint32_t mask = __ballot_sync(0xFFFFFFFFu, s0 < o.P && (dup[s0] == 1 || dup[s0] == 2));
+    if (!mask) continue;
+    uint64_t my_h = 0;
+    uint32_t my_n = 0;
+    int32_t my_disp = -1;
+    if (s0 < o.P && dup[s0] == 1) {
+      my_h = sp.seq.h[s0];
+      my_n = sp.seq.n[s0];
+      my_disp = sp.disp[s0];
+    }
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
       const uint32_t s = base + (uint32_t)j;
-      const uint8_t kind = dup[s];  // 1: phase A ran; 2: displaced during this walk
+      const uint8_t kind = dup[s];
       const uint64_t h_j = __shfl_sync(0xFFFFFFFFu, my_h, j);
       const int32_t disp_j = __shfl_sync(0xFFFFFFFFu, my_disp, j);
       const uint32_t n_j = __shfl_sync(0xFFFFFFFFu, my_n, j);
-      // does the phase-A result repeat a replacement taken before?
-      bool clash = false;
-      if (kind == 1) {
-        for (uint32_t k = lane; k < n_acc; k += 32) {
-          const uint64_t ah = k < kAccMax ? acc_h[k] : acc_h_g[k];
-          if (ah != h_j) continue;
-          const uint32_t as = k < kAccMax ? acc_slot[k] : acc_slot_g[k];
-          uint32_t na;
-          const uint16_t* ca = accepted_seq(as, next, sp.seq, na);
-          if (seq_equal(ca, na, sp.seq.c + (size_t)s * kMaxLen, n_j)) clash = true;
-        }
-        clash = __any_sync(0xFFFFFFFFu, clash);
+      const int32_t displaced = settle_slot(s, kind, h_j, n_j, disp_j);
+      if (displaced >= 0) {
+        if (lane == 0) dup[displaced] = 2;
+        __syncwarp();
+        if (displaced >= (int32_t)base && displaced < (int32_t)(base + 32))
+          mask |= 1u << (uint32_t)(displaced - (int32_t)base);
       }
-      int32_t displaced = -1;
-      uint64_t h_acc = h_j;
-      uint32_t slot_acc = s | kInSpec;
-      if (kind == 1 && !clash) {
-        displaced = disp_j;  // the phase-A result stands; copied into place after the walk
-      } else if (lane == 0) {
-        Cand child;
-        load_cand(next, s, child);
-        uint64_t h = next.h[s];
-        Rng r = kid_rng[s - o.elite];
-        retry_chain(o, r, child, h, tabu, t, next, s, n_acc <= kAccMax ? acc_h : acc_h_g,
-                    n_acc <= kAccMax ? acc_slot : acc_slot_g, n_acc, sp.seq);
-        first_before(t, next, child.c, child.n, h, s, &displaced);
-        store_cand(next, s, child, h);
-        dup[s] = 3;  // settled here: no copy from the phase-A buffer
-        h_acc = h;
-        slot_acc = s;
-      }
-      h_acc = __shfl_sync(0xFFFFFFFFu, h_acc, 0);
-      slot_acc = __shfl_sync(0xFFFFFFFFu, slot_acc, 0);
-      displaced = __shfl_sync(0xFFFFFFFFu, displaced, 0);
-      if (lane == 0) {
-        if (n_acc < kAccMax) {
-          acc_h[n_acc] = h_acc;
-          acc_slot[n_acc] = slot_acc;
-        }
-        acc_h_g[n_acc] = h_acc;
-        acc_slot_g[n_acc] = slot_acc;
-        // a displaced slot's own sequence is now held by s: it is a duplicate, settled in turn
-        if (displaced >= 0) dup[displaced] = 2;
-      }
-      ++n_acc;
-      if (displaced >= (int32_t)base && displaced < (int32_t)(base + 32))
-        mask |= 1u << (uint32_t)(displaced - (int32_t)base);
-      __syncwarp();
     }
-    my_h = nx_h;
-    my_n = nx_n;
-    my_disp = nx_disp;
   }
   __syncwarp();
   if (in_smem) {  // the flags back: 1 marks a phase-A result that stood (copied by the next kernel)
