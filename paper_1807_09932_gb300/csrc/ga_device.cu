@@ -370,30 +370,49 @@ struct Archive {  // members in order; `size` of them real, the rest (to K) empt
 __global__ void offers_kernel(Pop pop, const uint32_t* offer_sorted, const uint32_t* n_offerable,
                               Archive arch, uint32_t T, uint32_t* offers, uint32_t* n_offers) {
   __shared__ uint64_t ah[kMaxArch];
+  __shared__ uint64_t oh[kMaxOffers];
   const int lane = threadIdx.x;
   const uint32_t ka = *arch.size;
   if (lane < (int)ka) ah[lane] = cand_hash(arch.c + (size_t)lane * kMaxLen, arch.n[lane]);
   __syncwarp();
   const uint32_t no = *n_offerable;
   uint32_t t = 0;
-  // candidate r = base + lane checks itself against the archive; the non-archived ones are taken
-  // in order
+  // candidate r = base + lane is skipped when its sequence is archived, already offered, or held
+  // by an earlier candidate of the same 32 (a population can repeat a sequence when its retries
+  // ran out); the others are taken in order
   for (uint32_t base = 0; base < no && t < T; base += 32) {
     const uint32_t r = base + lane;
     bool take = false;
     uint32_t i = 0;
+    uint64_t h = 0;
+    const uint16_t* c = nullptr;
+    uint32_t n = 0;
     if (r < no) {
       i = offer_sorted[r];
-      const uint64_t h = pop.h[i];
+      h = pop.h[i];
+      c = pop.c + (size_t)i * kMaxLen;
+      n = pop.n[i];
       take = true;
       for (uint32_t a = 0; a < ka && take; ++a)
-        if (ah[a] == h && seq_equal(arch.c + (size_t)a * kMaxLen, arch.n[a],
-                                    pop.c + (size_t)i * kMaxLen, pop.n[i]))
+        if (ah[a] == h && seq_equal(arch.c + (size_t)a * kMaxLen, arch.n[a], c, n)) take = false;
+      for (uint32_t k = 0; k < t && take; ++k)
+        if (oh[k] == h && seq_equal(pop.c + (size_t)offers[k] * kMaxLen, pop.n[offers[k]], c, n))
           take = false;
+    }
+    for (int k = 0; k < 31; ++k) {  // an earlier candidate of the same 32 with this sequence
+      const uint64_t hk = __shfl_sync(0xFFFFFFFFu, h, k);
+      const uint32_t ik = __shfl_sync(0xFFFFFFFFu, i, k);
+      if (k < lane && take && base + k < no && hk == h &&
+          seq_equal(pop.c + (size_t)ik * kMaxLen, pop.n[ik], c, n))
+        take = false;
     }
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, take);
     const uint32_t before = __popc(m & ((1u << lane) - 1u));
-    if (take && t + before < T) offers[t + before] = i;
+    if (take && t + before < T) {
+      offers[t + before] = i;
+      oh[t + before] = h;
+    }
+    __syncwarp();
     t += __popc(m);
     if (t > T) t = T;
   }
@@ -555,9 +574,13 @@ __global__ void first_slot_kernel(SlotTable t, Pop next, uint32_t P) {
   }
 }
 
-__global__ void dup_flag_kernel(SlotTable t, Pop next, uint32_t P, uint8_t* dup) {
+__global__ void dup_flag_kernel(SlotTable t, Pop next, uint32_t P, uint32_t elite, uint8_t* dup) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P) return;
+  if (s < elite) {  // elites are kept as they are, repeats included (as on the host)
+    dup[s] = 0;
+    return;
+  }
   bool found;
   const uint64_t i = table_find(t, next, next.c + (size_t)s * kMaxLen, next.n[s], next.h[s], found);
   dup[s] = (found && t.v[i] != s + 1) ? 1 : 0;
@@ -837,11 +860,13 @@ __global__ void settle_kernel(Ops o, SlotTable t, Pop next, SeqSet tabu, const R
 }
 
 // The phase-A results that stood, copied into the population: a thread per slot.
-__global__ void commit_spec_kernel(uint32_t P, const uint8_t* dup, Spec sp, Pop next) {
+__global__ void commit_spec_kernel(uint32_t P, uint32_t elite, const uint8_t* dup, Spec sp,
+                                   Pop next) {
   const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= P || dup[s] != 1) return;
+  if (s >= P || s < elite || dup[s] != 1) return;
   uint4 v[kChunks];
   const uint32_t n = sp.seq.n[s];
+  if (n > (uint32_t)kMaxLen) return;  // never: phase A wrote this slot
   load_chunks(sp.seq.c + (size_t)s * kMaxLen, n, v);
   uint4* dst = reinterpret_cast<uint4*>(next.c + (size_t)s * kMaxLen);
   for (uint32_t k = 0; 8 * k < n; ++k) dst[k] = v[k];
@@ -1026,6 +1051,10 @@ __global__ void admit_kernel(AdmitArgs a) {
   uint32_t n_new = 0;
   for (uint32_t x = 0; x < n_items; ++x) n_new += live(x);
   n_new = n_new < a.K ? n_new : a.K;
+  // every row's source starts as the zero row (the items are distinct, so every position below
+  // n_new is then written; this only keeps the gather in bounds whatever happens)
+  for (uint32_t r = lane; r < a.K; r += 32) a.gather_src[r] = -(int32_t)a.K - 1;
+  __syncwarp();
   for (uint32_t x = lane; x < n_items; x += 32) {
     if (!live(x)) continue;
     const uint16_t* cx;
@@ -1303,13 +1332,13 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
       count_launch();
       first_slot_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, np, P);
       count_launch();
-      dup_flag_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, np, P, dup);
+      dup_flag_kernel<<<(P + 255) / 256, 256, 0, s>>>(table, np, P, p.elite, dup);
       count_launch();
       spec_kernel<<<(P + 63) / 64, 64, 0, s>>>(o, table, np, tabu, kid_rng, dup, spec);
       count_launch();
       settle_kernel<<<1, 32, 0, s>>>(o, table, np, tabu, kid_rng, dup, spec, acc_slot, acc_h);
       count_launch();
-      commit_spec_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, dup, spec, np);
+      commit_spec_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, p.elite, dup, spec, np);
     }
     AdmitArgs aa{cp, P, K, T, (uint32_t)(ncols + 31) / 32, p.overlap_threshold, dcounts, dov,
                  pov, offers, n_offers, arch[par], arch[1 - par], gather_src};

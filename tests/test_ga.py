@@ -195,3 +195,24 @@ def test_device_loop_rejects_what_it_does_not_take():
         ebic.ebic_run_custom(ds.X.shape[0], ds.X.shape[1],
                              _params(ebic, flags=ebic.EBIC_RUN_ON_DEVICE), sc.evaluator)
     assert ei.value.code == ebic.EBIC_ERR_UNSUPPORTED
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("population", [300, 900])
+def test_device_loop_equals_host_loop_when_sequences_run_out(population):
+    """Five columns allow 325 sequences of 2-5 columns: most children repeat a tabu sequence or an
+    earlier child, retries run out, and the slot-order pass settles hundreds of duplicates (the
+    device walks them from a list up to 512, window by window beyond). Host and device loops still
+    take the same decisions."""
+    ebic = _ebic()
+    ds = synth.make_dataset(19, 900, 5, kind="normal", planted=[(200, 4, False)], nan_frac=0.0)
+    kw = dict(population=population, generations=7, archive_size=4, max_len=5, max_init_len=4,
+              elite=4)
+    with ebic.Matrix(ds.X) as m:
+        m.build_pairs()
+        host = ebic.ebic_run(m.handle, _params(ebic, **kw))
+        dev = ebic.ebic_run(m.handle, _params(ebic, flags=ebic.EBIC_RUN_ON_DEVICE, **kw))
+    assert dev["members"] == host["members"]
+    assert np.array_equal(dev["counts"], host["counts"])
+    assert np.array_equal(dev["bitmaps"], host["bitmaps"])
+    assert dev["candidates_evaluated"] == host["candidates_evaluated"]
