@@ -216,3 +216,23 @@ def test_device_loop_equals_host_loop_when_sequences_run_out(population):
     assert np.array_equal(dev["counts"], host["counts"])
     assert np.array_equal(dev["bitmaps"], host["bitmaps"])
     assert dev["candidates_evaluated"] == host["candidates_evaluated"]
+
+
+@pytest.mark.gpu
+def test_device_loop_equals_host_loop_wide_rows_long_candidates_no_elites():
+    """120 columns (column sets over four words), candidates of up to 40 columns, a full 32-member
+    archive, no elites and a population that is not a multiple of 32."""
+    ebic = _ebic()
+    ds = synth.make_dataset(23, 2500, 120, kind="beta", planted=[(400, 12, False), (300, 8, True)],
+                            nan_frac=0.01)
+    kw = dict(population=333, generations=9, archive_size=32, max_len=40, max_init_len=10,
+              elite=0, tournament=2, overlap_threshold=0.3, flags=ebic.EBIC_NEGATIVE_TRENDS)
+    with ebic.Matrix(ds.X) as m:
+        m.build_pairs()
+        host = ebic.ebic_run(m.handle, _params(ebic, **kw))
+        kw["flags"] |= ebic.EBIC_RUN_ON_DEVICE
+        dev = ebic.ebic_run(m.handle, _params(ebic, **kw))
+    assert dev["members"] == host["members"]
+    assert np.array_equal(dev["counts"], host["counts"])
+    assert np.array_equal(dev["quality"], host["quality"])
+    assert np.array_equal(dev["bitmaps"], host["bitmaps"])
