@@ -1167,14 +1167,17 @@ namespace {
 // The loop's own stream (it can be captured into a graph, which the legacy default stream cannot),
 // started after the caller's stream's pending work; released when the run returns.
 struct RunStream {
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr, s2 = nullptr;  // s2: the branch that runs beside s within a generation
   cudaEvent_t e = nullptr;
+  cudaEvent_t fork0 = nullptr, tabu_done = nullptr, fork1 = nullptr, archive_done = nullptr;
   ~RunStream() {
-    if (s) {
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
-    }
-    if (e) cudaEventDestroy(e);
+    for (cudaStream_t x : {s, s2})
+      if (x) {
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+      }
+    for (cudaEvent_t x : {e, fork0, tabu_done, fork1, archive_done})
+      if (x) cudaEventDestroy(x);
   }
 };
 }  // namespace
@@ -1186,10 +1189,12 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   DeviceBuffers b;  // freed after the stream below is drained (declared first, destroyed last)
   RunStream rs;
   GD_CUDA(cudaStreamCreateWithFlags(&rs.s, cudaStreamNonBlocking));
-  GD_CUDA(cudaEventCreateWithFlags(&rs.e, cudaEventDisableTiming));
+  GD_CUDA(cudaStreamCreateWithFlags(&rs.s2, cudaStreamNonBlocking));
+  for (cudaEvent_t* x : {&rs.e, &rs.fork0, &rs.tabu_done, &rs.fork1, &rs.archive_done})
+    GD_CUDA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
   GD_CUDA(cudaEventRecord(rs.e, caller));
   GD_CUDA(cudaStreamWaitEvent(rs.s, rs.e, 0));
-  cudaStream_t s = rs.s;
+  cudaStream_t s = rs.s, s2 = rs.s2;
   const uint32_t P = p.population, K = p.archive_size, T = 2 * K, G = p.generations;
   if (K > kMaxArch)
     return set_last_error(EBIC_ERR_UNSUPPORTED, "the device loop takes archive_size <= 32");
@@ -1307,24 +1312,42 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
   Pop pops[2] = {pop, nxt};
   // One generation's work on the stream; the buffers alternate with the generation's parity, so
   // two generations return to the same buffers (a graph of two replays unchanged).
+  // Within a generation two branches run side by side: on s2 the tabu insert (beside the
+  // scoring), then, after the ranks, the archive chain (offers, their overlaps, admission, the
+  // new archive's rows); on s the scoring, the ranks and the breeding chain. They touch disjoint
+  // buffers; s waits for s2 before the generation ends.
   auto issue = [&](int par, bool breed) -> int {
     const Pop& cp = pops[par];
     const Pop& np = pops[1 - par];
+    GD_CUDA(cudaEventRecord(rs.fork0, s));
+    GD_CUDA(cudaStreamWaitEvent(s2, rs.fork0, 0));
+    count_launch();
+    tabu_insert_kernel<<<(P + 255) / 256, 256, 0, s2>>>(tabu, cp, P);
+    GD_CUDA(cudaEventRecord(rs.tabu_done, s2));
     int rc = ebic_eval_fitness(m, dcols, doffs, P, eflags, arch[par].csr_cols, arch[par].csr_offs,
                                abm[par], K, dcounts, dbm, dfit, dov, s);
     if (rc != EBIC_OK) return rc;
-    count_launch();
-    tabu_insert_kernel<<<(P + 255) / 256, 256, 0, s>>>(tabu, cp, P);
     GD_CUDA(cudaMemsetAsync(n_offerable, 0, 4, s));
     OrderArgs oa{cp, P, p.elite, dfit, dcounts, rank, elites, offer_sorted, n_offerable};
     count_launch();
     order_kernel<<<(unsigned)(((uint64_t)P * 32 + 255) / 256), 256, 0, s>>>(oa);
+    GD_CUDA(cudaEventRecord(rs.fork1, s));
+    // the archive chain, on s2
+    GD_CUDA(cudaStreamWaitEvent(s2, rs.fork1, 0));
     count_launch();
-    offers_kernel<<<1, 32, 0, s>>>(cp, offer_sorted, n_offerable, arch[par], T, offers, n_offers);
-    GD_CUDA(cudaMemsetAsync(pov, 0, (size_t)T * T * 4, s));
+    offers_kernel<<<1, 32, 0, s2>>>(cp, offer_sorted, n_offerable, arch[par], T, offers, n_offers);
+    GD_CUDA(cudaMemsetAsync(pov, 0, (size_t)T * T * 4, s2));
     count_launch();
-    offer_overlap_kernel<<<(unsigned)num_sms, 256, 0, s>>>(dbm, W, offers, n_offers, T, pov);
+    offer_overlap_kernel<<<(unsigned)num_sms, 256, 0, s2>>>(dbm, W, offers, n_offers, T, pov);
+    AdmitArgs aa{cp, P, K, T, (uint32_t)(ncols + 31) / 32, p.overlap_threshold, dcounts, dov,
+                 pov, offers, n_offers, arch[par], arch[1 - par], gather_src};
+    count_launch();
+    admit_kernel<<<1, 32, 0, s2>>>(aa);
+    GD_CUDA(launch_gather_rows(dbm, abm[par], gather_src, K, W, abm[1 - par], s2));
+    GD_CUDA(cudaEventRecord(rs.archive_done, s2));
+    // the breeding chain, on s (after the tabu insert)
     if (breed) {
+      GD_CUDA(cudaStreamWaitEvent(s, rs.tabu_done, 0));
       BreedArgs ba{o, dgen, cp, np, rank, elites, tabu, kid_rng};
       count_launch();
       breed_kernel<<<(P + 127) / 128, 128, 0, s>>>(ba);
@@ -1339,18 +1362,14 @@ int run_ga_on_device(const ebic_matrix* m, int64_t rows, int32_t ncols, int64_t 
       settle_kernel<<<1, 32, 0, s>>>(o, table, np, tabu, kid_rng, dup, spec, acc_slot, acc_h);
       count_launch();
       commit_spec_kernel<<<(P + 255) / 256, 256, 0, s>>>(P, p.elite, dup, spec, np);
-    }
-    AdmitArgs aa{cp, P, K, T, (uint32_t)(ncols + 31) / 32, p.overlap_threshold, dcounts, dov,
-                 pov, offers, n_offers, arch[par], arch[1 - par], gather_src};
-    count_launch();
-    admit_kernel<<<1, 32, 0, s>>>(aa);
-    GD_CUDA(launch_gather_rows(dbm, abm[par], gather_src, K, W, abm[1 - par], s));
-    if (breed) {
       count_launch();
       pack_kernel<<<1, 1024, 0, s>>>(np, P, dcols, doffs);
       count_launch();
       next_generation_kernel<<<1, 1, 0, s>>>(dgen);
+    } else {
+      GD_CUDA(cudaStreamWaitEvent(s, rs.tabu_done, 0));
     }
+    GD_CUDA(cudaStreamWaitEvent(s, rs.archive_done, 0));  // the generation ends on s
     GD_CUDA(cudaGetLastError());
     return EBIC_OK;
   };
