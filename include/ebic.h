@@ -125,20 +125,27 @@ int ebic_eval_population(const ebic_matrix* m, const uint16_t* cols, const uint3
 /*
  * Allocation-free variant of ebic_eval_population, for callers that cannot allocate device
  * memory while they evaluate: a serving loop that must not take the allocator's lock or meet an
- * out-of-memory error mid-request, a process whose device memory is owned by another caching
- * allocator, or code inside a stream capture. It has no counterpart in the paper; it computes
- * exactly what ebic_eval_population computes, with the same kernels.
+ * out-of-memory error mid-request, or a process whose device memory is already owned by another
+ * framework's caching allocator. It has no counterpart in the paper; it computes exactly what
+ * ebic_eval_population computes, with the same kernels.
  *   counts, bitmaps   must be device memory of the matrix's device (no staging buffer exists).
  *   cols, offsets     device memory (used in place, checked by a device kernel), or host memory
  *                     (checked on the host and copied into the library's fixed scratch; the
  *                     offsets rounded up to 256 bytes plus the columns must fit in 1 MiB minus
- *                     256 bytes, otherwise EBIC_ERR_UNSUPPORTED).
+ *                     256 bytes, otherwise EBIC_ERR_UNSUPPORTED). Both in the same placement.
+ *   Memory of another device, for any of the four, returns EBIC_ERR_INVALID_ARG.
  * Scratch: a fixed 1 MiB device array inside the library (held by every GPU that loads the
- * library until exit). Nothing is allocated or freed, by the library or by any library it calls.
- * The first call on each device looks up that array's device address; make it before any stream
- * capture. All calls share the array and its previous contents: the call clears its status word
- * itself, and calls that overlap on the GPU race on the array, so issue one at a time.
- * Always asynchronous on `stream`: device-side check failures are reported by
+ * library until exit). The library calls no allocation or free routine on this path. The first
+ * call on each device looks up that array's device address and loads the code of every kernel
+ * variant this call can launch on that device (under CUDA's lazy module loading, loading code is
+ * the one step in which the CUDA runtime itself reserves device memory); later calls load
+ * nothing. Make that first call before any stream capture. All calls share the array and its
+ * previous contents: the call clears its status word itself, and calls that overlap on the GPU
+ * race on the array, so issue one at a time.
+ * With device-resident lists the call is asynchronous on `stream`. Host-resident lists are
+ * copied with cudaMemcpyAsync: from pageable memory that copy has consumed the host buffer when
+ * the call returns; from pinned memory it is asynchronous, and the buffer must stay unchanged
+ * until the stream has run the call. Device-side check failures are reported by
  * ebic_matrix_status().
  */
 int ebic_eval_population_noalloc(const ebic_matrix* m, const uint16_t* cols,

@@ -128,6 +128,14 @@ cudaError_t launch_eval_w8v4(const EvalConfig&, const CUtensorMap*, const EvalAr
 cudaError_t launch_eval_w16v4(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w16v2(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
 cudaError_t launch_eval_w16v1(const EvalConfig&, const CUtensorMap*, const EvalArgs&, cudaStream_t);
+// Ready every evaluator instantiation of a layout on the current device (shared-memory limit
+// raised, code loaded).
+cudaError_t ready_eval_w8v4();
+cudaError_t ready_eval_w16v4();
+cudaError_t ready_eval_w16v2();
+cudaError_t ready_eval_w16v1();
+// Load the list-check kernel's code on the current device.
+cudaError_t ready_prepare();
 
 // ---- pair-table evaluation (optionally with the archive overlaps fused in) -----------------
 constexpr int kPairRangeWords = 512;  // table and padded archive row strides are multiples

@@ -29,6 +29,8 @@
 //     atomicAdd per candidate and tile.
 #pragma once
 
+#include <atomic>
+
 #include "device_common.cuh"
 #include "ebic_internal.h"
 
@@ -346,20 +348,44 @@ __global__ void __launch_bounds__(eval_threads<TS * VEC, NEG>(), 1)
   }
 }
 
+// The dynamic shared-memory limit of one instantiation, raised on the current device. The
+// attribute is a per-device property of the function, so it is set once per device (a bit per
+// device index, set after the call succeeded; concurrent first calls may both set it, which is
+// harmless). Setting it also loads the function's code on that device under lazy module loading.
+template <int WIDTH, int VEC, int TS, bool NEG, bool BITMAPS>
+cudaError_t ready_eval_variant() {
+  static std::atomic<uint64_t> ready_devices{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+  if (bit && (ready_devices.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(eval_population_kernel<WIDTH, VEC, TS, NEG, BITMAPS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDynMax);
+  if (e != cudaSuccess) return e;
+  if (bit) ready_devices.fetch_or(bit, std::memory_order_acq_rel);
+  return cudaSuccess;
+}
+
 template <int WIDTH, int VEC, int TS, bool NEG, bool BITMAPS>
 cudaError_t launch_eval_variant(int grid, const CUtensorMap* tmap, const EvalArgs& a,
                                 cudaStream_t s) {
-  auto kern = eval_population_kernel<WIDTH, VEC, TS, NEG, BITMAPS>;
-  static bool attr_set = false;  // one attribute call per instantiation and process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemDynMax);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = ready_eval_variant<WIDTH, VEC, TS, NEG, BITMAPS>();
+  if (e != cudaSuccess) return e;
   count_launch();
-  kern<<<grid, eval_threads<TS * VEC, NEG>(), a.smem_bytes, s>>>(*tmap, a);
+  eval_population_kernel<WIDTH, VEC, TS, NEG, BITMAPS>
+      <<<grid, eval_threads<TS * VEC, NEG>(), a.smem_bytes, s>>>(*tmap, a);
   return cudaGetLastError();
+}
+
+// Readies every (NEG, BITMAPS) instantiation of one tile shape on the current device.
+template <int WIDTH, int VEC, int TS>
+cudaError_t ready_eval_ts() {
+  cudaError_t e = ready_eval_variant<WIDTH, VEC, TS, false, false>();
+  if (e == cudaSuccess) e = ready_eval_variant<WIDTH, VEC, TS, false, true>();
+  if (e == cudaSuccess) e = ready_eval_variant<WIDTH, VEC, TS, true, false>();
+  if (e == cudaSuccess) e = ready_eval_variant<WIDTH, VEC, TS, true, true>();
+  return e;
 }
 
 template <int WIDTH, int VEC, int TS>
@@ -374,6 +400,16 @@ cudaError_t launch_eval_ts(const EvalConfig& c, const CUtensorMap* t, const Eval
 
 // 8-bit ranks (<= 127 columns) can stage 1, 2 or 4 slabs per stage; for 16-bit ranks VEC is
 // already chosen so that one slab fills a stage, so only TS = 1 is instantiated.
+template <int WIDTH, int VEC>
+cudaError_t ready_eval_layout() {
+  cudaError_t e = ready_eval_ts<WIDTH, VEC, 1>();
+  if constexpr (WIDTH == 8) {
+    if (e == cudaSuccess) e = ready_eval_ts<WIDTH, VEC, 2>();
+    if (e == cudaSuccess) e = ready_eval_ts<WIDTH, VEC, 4>();
+  }
+  return e;
+}
+
 template <int WIDTH, int VEC>
 cudaError_t launch_eval_layout(const EvalConfig& c, const CUtensorMap* t, const EvalArgs& a,
                                cudaStream_t s) {

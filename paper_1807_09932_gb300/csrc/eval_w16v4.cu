@@ -6,4 +6,5 @@ cudaError_t launch_eval_w16v4(const EvalConfig& c, const CUtensorMap* t, const E
                            cudaStream_t s) {
   return launch_eval_layout<16, 4>(c, t, a, s);
 }
+cudaError_t ready_eval_w16v4() { return ready_eval_layout<16, 4>(); }
 }  // namespace ebic

@@ -289,6 +289,11 @@ cudaError_t launch_gather_rows(const uint32_t* a, const uint32_t* b, const int32
   return cudaGetLastError();
 }
 
+cudaError_t ready_prepare() {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, prepare_kernel);
+}
+
 cudaError_t launch_prepare(const PrepareArgs& a, cudaStream_t s) {
   size_t warps = a.n[0] > a.n[1] ? a.n[0] : a.n[1];
   if (a.terms && a.n_terms_cand > warps) warps = a.n_terms_cand;

@@ -2,19 +2,21 @@
 //
 // Some callers cannot allocate device memory when they evaluate. Examples: a serving loop that
 // must never take the allocator's lock or risk an out-of-memory error in the middle of a
-// request; a process whose device memory is already carved up by another framework's caching
-// allocator; and code running inside a stream capture, where a new allocation would become part
-// of the captured graph. The regular entry point allocates small stream-ordered scratch on every
-// call (a status word, plus device copies of host inputs). This entry point uses a fixed
-// scratch area compiled into the library instead.
+// request; and a process whose device memory is already carved up by another framework's
+// caching allocator, so that a cudaMalloc of ours could fail or fragment its pool. The regular
+// entry point allocates small stream-ordered scratch on every call (a status word, plus device
+// copies of host inputs). This entry point uses a fixed scratch area compiled into the library
+// instead.
 //
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes (1 MiB). Every GPU that
 // loads this library holds it until the process exits. Host code cannot use the array's name as
 // a device address: in host code the symbol is only a host-side stand-in, and a kernel given it
 // would fault, or on a system where the GPU can reach host memory it would silently use the
-// wrong memory. So on the first call on each device (with that device current) the real device
-// address is fetched once with cudaGetSymbolAddress, checked, cached per device and passed to the
-// kernels. Make that first call before any stream capture.
+// wrong memory. So the first call on each device (with that device current) fetches the real
+// device address once with cudaGetSymbolAddress, checks it, caches it per device and passes it
+// to the kernels. The same first call also loads, on that device, the code of every kernel this
+// entry point can launch (every evaluator variant and the list check), so that no later call
+// makes the CUDA runtime load code. Make that first call before any stream capture.
 //
 // All calls share the one array, and it keeps the previous call's contents: the status word is
 // cleared at the start of every call. Calls that overlap on the GPU (different streams, or
@@ -37,7 +39,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 uint8_t* g_scratch_ptr[kMaxDevices] = {};
 
-// The scratch array's device address on `dev` (the current device), fetched once per device.
+// One-time set-up on `dev` (the current device): the scratch array's device address, and the
+// code of every kernel this entry point launches loaded (evaluator shared-memory limits raised).
 int scratch_address(int dev, uint8_t** out) {
   if (dev < 0 || dev >= kMaxDevices) return set_last_error(EBIC_ERR_UNSUPPORTED, "device index");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -50,19 +53,34 @@ int scratch_address(int dev, uint8_t** out) {
                             (std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
                              cudaGetErrorString(e)).c_str());
     }
+    e = ready_eval_w8v4();
+    if (e == cudaSuccess) e = ready_eval_w16v4();
+    if (e == cudaSuccess) e = ready_eval_w16v2();
+    if (e == cudaSuccess) e = ready_eval_w16v1();
+    if (e == cudaSuccess) e = ready_prepare();
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return set_last_error(EBIC_ERR_CUDA, (std::string("loading the evaluator kernels: ") +
+                                            cudaGetErrorString(e)).c_str());
+    }
     g_scratch_ptr[dev] = static_cast<uint8_t*>(p);
   }
   *out = g_scratch_ptr[dev];
   return EBIC_OK;
 }
 
-bool is_device_memory(const void* p, int dev) {
+// Where a caller's pointer lives, relative to device `dev`, from one attribute query.
+enum class Place { kHost, kDevice, kForeign };
+
+Place place_of(const void* p, int dev) {
   cudaPointerAttributes at;
   if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     (void)cudaGetLastError();
-    return false;
+    return Place::kHost;
   }
-  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == dev);
+  if (at.type == cudaMemoryTypeManaged) return Place::kDevice;
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev ? Place::kDevice : Place::kForeign;
+  return Place::kHost;
 }
 
 int cuda_error(cudaError_t e, const char* what) {
@@ -104,8 +122,17 @@ extern "C" int ebic_eval_population_noalloc(const ebic_matrix* m, const uint16_t
   const int dev = v.device;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
+  // Every pointer's placement, before anything is dereferenced on the host: memory of another
+  // device is rejected (the host could not read it, and the kernels must not).
+  const Place p_counts = place_of(counts, dev);
+  const Place p_bitmaps = bitmaps ? place_of(bitmaps, dev) : Place::kDevice;
+  const Place p_cols = place_of(cols, dev), p_offs = place_of(offsets, dev);
+  if (p_counts == Place::kForeign || p_bitmaps == Place::kForeign || p_cols == Place::kForeign ||
+      p_offs == Place::kForeign)
+    return set_last_error(EBIC_ERR_INVALID_ARG,
+                          "ebic_eval_population_noalloc: buffer on another device");
   // Outputs cannot be staged without an allocation: they must already be device memory.
-  if (!is_device_memory(counts, dev) || (bitmaps && !is_device_memory(bitmaps, dev)))
+  if (p_counts != Place::kDevice || p_bitmaps != Place::kDevice)
     return set_last_error(EBIC_ERR_INVALID_ARG,
                           "ebic_eval_population_noalloc: counts and bitmaps must be device "
                           "memory of the matrix's device");
@@ -114,7 +141,7 @@ extern "C" int ebic_eval_population_noalloc(const ebic_matrix* m, const uint16_t
   if (rc != EBIC_OK) return rc;
   uint32_t* err = reinterpret_cast<uint32_t*>(scratch);
 
-  const bool cols_dev = is_device_memory(cols, dev), offs_dev = is_device_memory(offsets, dev);
+  const bool cols_dev = p_cols == Place::kDevice, offs_dev = p_offs == Place::kDevice;
   if (cols_dev != offs_dev)
     return set_last_error(EBIC_ERR_INVALID_ARG,
                           "cols and offsets must both be host memory or both device memory");

@@ -3,10 +3,12 @@
 ebic_eval_population_noalloc exists for callers that cannot allocate device memory while they
 evaluate. Examples: a serving loop that must never wait on the allocator or hit an out-of-memory
 error mid-request; a process whose device memory another framework's caching allocator already
-owns; code running inside a stream capture. It uses a fixed scratch area inside the library
-instead of per-call allocations. This file checks it through the C ABI against
-ebic_eval_population on two calls in a row, bit for bit (results are integers). The file is
-named to be collected last, and it passes on its own in a fresh process too.
+owns. It uses a fixed scratch area inside the library instead of per-call allocations. This file
+checks it through the C ABI against ebic_eval_population on two calls in a row, bit for bit
+(results are integers), on the default stream and on a side stream; that a failed device-side
+list check is reported and does not leak into the next call through the shared scratch; and that
+memory of another device is refused. The file is named to be collected last, and it passes on
+its own in a fresh process too.
 """
 import numpy as np
 import pytest
@@ -89,3 +91,56 @@ def test_noalloc_rejects_what_it_cannot_do_without_allocating():
         rc = ebic.ebic_eval_population_noalloc(m.handle, small_c, small_o, 10, 0, host_counts,
                                                None)
         assert rc == ebic.EBIC_ERR_INVALID_ARG
+
+
+def test_noalloc_on_a_side_stream_and_after_a_failed_device_check():
+    import torch
+    from paper_1807_09932_gb300 import ebic
+    ds, cols, offs = synth.config3(rows=20011)
+    with ebic.Matrix(ds.X) as m:
+        n = len(offs) - 1
+        ref_c, ref_b = ebic.eval_population(m, cols, offs)
+        # a device-resident list with a column past the matrix: the device check reports it
+        # through the matrix status and the counts stay zero
+        bad = cols.copy()
+        bad[offs[3]] = m.cols + 5
+        got_c = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        rc = ebic.ebic_eval_population_noalloc(m.handle, _dev(bad), _dev(offs), n, 0, got_c, None)
+        assert rc == ebic.EBIC_OK, ebic.ebic_last_error()
+        assert m.status() == ebic.EBIC_ERR_INVALID_ARG
+        assert int(torch.count_nonzero(got_c)) == 0
+        # the next valid calls, on a side stream, start from a cleared status word
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        dcols, doffs = _dev(cols), _dev(offs)
+        for c_in, o_in in ((dcols, doffs), (cols, offs)):
+            with torch.cuda.stream(side):
+                got_c = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+                got_b = torch.full((n, m.words), -1, dtype=torch.int32, device="cuda")
+            rc = ebic.ebic_eval_population_noalloc(m.handle, c_in, o_in, n, 0, got_c, got_b,
+                                                   stream=side.cuda_stream)
+            assert rc == ebic.EBIC_OK, ebic.ebic_last_error()
+            assert m.status(side.cuda_stream) == ebic.EBIC_OK
+            assert np.array_equal(got_c.cpu().numpy().view(np.uint32), ref_c)
+            assert np.array_equal(got_b.cpu().numpy().view(np.uint32), ref_b)
+
+
+def test_noalloc_refuses_memory_of_another_device():
+    import torch
+    from paper_1807_09932_gb300 import ebic
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    X = np.random.default_rng(3).standard_normal((3000, 30)).astype(np.float32)
+    cols, offs = synth.make_population(4, 50, 30, 2, 6)
+    n = len(offs) - 1
+    with ebic.Matrix(X) as m:
+        here = torch.zeros(n, dtype=torch.int32, device="cuda:0")
+        with torch.cuda.device(1):
+            there_c = torch.from_numpy(cols.view(np.int16)).to("cuda:1")
+            there_o = torch.from_numpy(offs.view(np.int32)).to("cuda:1")
+            there_n = torch.zeros(n, dtype=torch.int32, device="cuda:1")
+        for args in ((there_c, there_o, here), (cols, offs, there_n)):
+            rc = ebic.ebic_eval_population_noalloc(m.handle, args[0], args[1], n, 0, args[2],
+                                                   None)
+            assert rc == ebic.EBIC_ERR_INVALID_ARG
+            assert "another device" in ebic.ebic_last_error()
