@@ -14,6 +14,11 @@ Inputs are resident in HBM when the timed region starts; L2 is flushed (512 MB w
 timed steps outside the timed events. ``e2e`` repeats the step through the same public calls
 with the population in pinned host memory and the fitness read back to pinned host memory.
 
+On one GPU the default run also measures the batched workload (8 matrices, 64 populations in
+one graph replay, against 64 plain per-population launches) and the served workload (32 runs,
+Poisson arrivals at 0.7 x the served capacity, against FIFO per-request calls), and reports them
+as the line's ``batched`` and ``served`` objects, each with its own plain arm and clock record.
+
 Under torchrun every rank runs the same workload on its own GPU (replicas, no collective on the
 data path); the value is all ranks' evals divided by the slowest rank's time.
 
@@ -75,6 +80,14 @@ def parse_args():
                    help="served: arrival rate as a fraction of the measured capacity")
     p.add_argument("--runs", type=int, default=32, help="served: concurrent EBIC runs")
     p.add_argument("--requests", type=int, default=1000, help="served: requests per trace")
+    p.add_argument("--main-only", action="store_true",
+                   help="default workload: skip the batched and served legs")
+    p.add_argument("--leg-steps", type=int, default=20,
+                   help="default workload: timed steps per arm of the batched leg")
+    p.add_argument("--leg-requests", type=int, default=500,
+                   help="default workload: requests per trace of the served leg")
+    p.add_argument("--leg-repeats", type=int, default=3,
+                   help="default workload: traces of the served leg at --load")
     return p.parse_args()
 
 
@@ -156,11 +169,11 @@ def oracle_sample(ds, pops, arch, target_s):
     import oracle
     X = ds.X
     R = X.shape[0]
-    cols, offs = pops[0]
     acols, aoffs, abm = arch
     threads = oracle.max_threads()
 
-    def run(n):
+    def run(n, i=0):
+        cols, offs = pops[i % len(pops)]   # the GPU arm's populations, cycled the same way
         sc = cols[: offs[n]]
         so = offs[: n + 1]
         t = time.perf_counter()
@@ -205,9 +218,9 @@ def reference_arm(args):
     arch = _archive_from(ds, ac, ao, cnt, bm, pbm)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     n, threads, run = oracle_sample(ds, pops, arch, min(per_step, args.cpu_seconds))
-    for _ in range(args.warmup):
-        run(n)
-    times = [run(n) for _ in range(args.steps)]
+    for i in range(args.warmup):
+        run(n, i)
+    times = [run(n, i) for i in range(args.steps)]
     ms = 1000 * statistics.mean(times)
     value = n * R / (ms / 1000)
     line = {"impl": "reference", "metric": "candidate-row evals/s", "value": value,
@@ -215,12 +228,13 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "rows": R, "cols": X.shape[1],
-                       "population": 1600, "archive": ARCHIVE,
+                       "population": 1600, "archive": ARCHIVE, "populations_cycled": N_POPS,
                        "sample_candidates_per_step": n},
             "cpu_baseline": {"value": value, "unit": "candidate-row evals/s", "cores": threads,
                              "kind": "oracle",
-                             "sample": f"{n} of 1,600 candidates x all {R} rows per step "
-                                       "(evaluation + fitness vs 20-member archive)"},
+                             "sample": f"the first {n} of the 1,600 candidates x all {R} rows "
+                                       f"per step, the {N_POPS} populations cycled (evaluation "
+                                       "+ fitness vs 20-member archive)"},
             "e2e": {"value": value, "unit": "candidate-row evals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -482,18 +496,30 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        n, threads, run = oracle_sample(ds, pops, (acols, aoffs, abm), args.cpu_seconds)
-        t = run(n)
-        line["cpu_baseline"] = {"value": n * R / t, "unit": "candidate-row evals/s",
+        n, threads, run = oracle_sample(ds, pops, (acols, aoffs, abm),
+                                        args.cpu_seconds / N_POPS)
+        t = sum(run(n, i) for i in range(N_POPS))
+        line["cpu_baseline"] = {"value": N_POPS * n * R / t, "unit": "candidate-row evals/s",
                                 "cores": threads, "kind": "oracle",
-                                "sample": f"{n} of 1,600 candidates x all {R} rows "
-                                          "(evaluation + fitness vs 20-member archive), once"}
+                                "sample": f"the first {n} of the 1,600 candidates of each of the "
+                                          f"{N_POPS} populations x all {R} rows (evaluation + "
+                                          "fitness vs 20-member archive), once each"}
+    m.close()
+    if ws == 1 and not args.main_only:
+        # the batched and served workloads, each against its plain per-population arm, with its
+        # own clock record (one process on one GPU; under torchrun the replicas line alone)
+        del counts, bitmaps, fit, flush, dpops
+        torch.cuda.empty_cache()
+        line["batched"] = batched_measure(args, args.leg_steps)
+        line["served"] = served_measure(args, [args.load], args.leg_requests, args.leg_repeats)
+        line["legs"] = ("batched: batched_measure, the config of its line; served: "
+                        f"served_measure, {args.leg_repeats} traces of {args.leg_requests} "
+                        f"requests at {args.load:.2f} x the served capacity, latencies pooled")
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    m.close()
 
 
 def traffic_record(name):
@@ -657,10 +683,15 @@ def ga_workload(args):
 
 
 def batched_workload(args):
+    print(json.dumps(batched_measure(args, max(3, min(args.steps, 50)))), flush=True)
+
+
+def batched_measure(args, steps):
     """8 datasets (5k-200k rows, 20-500 cols) and 64 populations (200-3,200 candidates of 2-64
     columns), round-robin over the datasets. One step = all 64 populations scored. Plain: one
     ebic_eval_population per population. Batched: one ebic_batch_run (CUDA-graph replay of the
-    check, plan and persistent kernels), with tile shapes from the autotuner."""
+    check, plan and persistent kernels), with tile shapes from the autotuner. `steps` timed steps
+    per arm. Returns the result line."""
     import torch
 
     from paper_1807_09932_gb300 import autotune, ebic, synth
@@ -736,7 +767,6 @@ def batched_workload(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / steps
 
-    steps = max(3, min(args.steps, 50))
     clocks = ClockSampler(0)
     clocks.start()
     launches0 = ebic.ebic_launch_count()
@@ -774,18 +804,25 @@ def batched_workload(args):
             "batched_over_plain": ms_plain / ms_batched,
             "rank_code_pass": rank_code,
             "gpu_launches": int(launches), "clocks": clk}
-    print(json.dumps(line), flush=True)
     for m in mats:
         m.close()
+    return line
 
 
 # ---- config 5: served (continuous batching) vs plain per-population launches -------------------
 
 def served_workload(args):
+    line = served_measure(args, sorted({0.25, 0.5, args.load, 1.0}), args.requests, 1)
+    print(json.dumps(line), flush=True)
+
+
+def served_measure(args, loads, requests, repeats):
     """32 concurrent EBIC runs on datasets of 10,000-436,444 rows x 20-200 cols, 1,600 candidates
-    per request (2-16 columns), Poisson arrivals at `--load` x the measured batched capacity.
+    per request (2-16 columns), Poisson arrivals at each of `loads` x the measured served
+    capacity (`repeats` traces of `requests` requests at `args.load`, one at each other load).
     Served: the continuous-batching server. Plain: the same arrivals, FIFO, one request at a time
-    through ebic_eval_population + ebic_fitness. Latency = completion - arrival (host clock)."""
+    through ebic_eval_fitness. Latency = completion - arrival (host clock). Returns the line; its
+    headline figures at `args.load` pool the latencies of all repeats."""
     import torch
 
     from paper_1807_09932_gb300 import serve, synth
@@ -845,11 +882,20 @@ def served_workload(args):
     clocks.start()
     sweep = []
     headline = None
-    for load in sorted({0.25, 0.5, args.load, 1.0}):
-        tr = trace(args.requests, load * capacity_rps)
-        sv = run_served(copy_trace(tr))
-        pl = serve.plain_serve(be, copy_trace(tr), rows_of, plain_stream)
-        entry = {"load": load, "rate_rps": load * capacity_rps, "served": sv, "plain": pl}
+    for load in loads:
+        reps = []
+        for _ in range(repeats if load == args.load else 1):
+            tr = trace(requests, load * capacity_rps)
+            a, b = copy_trace(tr), copy_trace(tr)
+            sv = run_served(a)
+            pl = serve.plain_serve(be, b, rows_of, plain_stream)
+            reps.append((sv, pl, [r.latency for r in a], [r.latency for r in b]))
+        entry = {"load": load, "rate_rps": load * capacity_rps,
+                 "served": pooled(reps, 0, 2), "plain": pooled(reps, 1, 3)}
+        if len(reps) > 1:
+            entry["repeats"] = [{"served_p50_ms": r[0]["p50_ms"], "served_p99_ms": r[0]["p99_ms"],
+                                 "plain_p50_ms": r[1]["p50_ms"], "plain_p99_ms": r[1]["p99_ms"]}
+                                for r in reps]
         sweep.append(entry)
         if load == args.load:
             headline = entry
@@ -866,13 +912,27 @@ def served_workload(args):
                                    "of 2-16 cols per request, archive of 20 per run, Poisson "
                                    f"arrivals at {args.load:.2f} x the served capacity",
                        "arrival_rate_rps": headline["rate_rps"], "capacity_rps": capacity_rps,
-                       "requests_per_trace": args.requests},
+                       "requests_per_trace": requests, "traces_at_headline_load": repeats},
             "served": served, "plain": plain,
             "saturated": {"served": sat_served, "plain": sat_plain,
                           "served_over_plain": sat_served["evals_per_s"] / sat_plain["evals_per_s"]},
             "sweep": sweep, "clocks": clk,
             "gpu_launches": int(ebic_launches())}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def pooled(reps, k, lat_k):
+    """One load's figures over its repeated traces: p50/p99 of all their latencies together,
+    evals/s over their summed wall time."""
+    from paper_1807_09932_gb300 import serve
+    if len(reps) == 1:
+        return reps[0][k]
+    lat = [x for r in reps for x in r[lat_k]]
+    wall = sum(r[k]["wall_s"] for r in reps)
+    evals = sum(r[k]["evals_per_s"] * r[k]["wall_s"] for r in reps)
+    return {"requests": len(lat), "p50_ms": 1000 * serve.percentile(lat, 50),
+            "p99_ms": 1000 * serve.percentile(lat, 99), "mean_ms": 1000 * sum(lat) / len(lat),
+            "evals_per_s": evals / wall, "wall_s": wall}
 
 
 def ebic_launches():
