@@ -80,6 +80,9 @@ def parse_args():
                    help="served: arrival rate as a fraction of the measured capacity")
     p.add_argument("--runs", type=int, default=32, help="served: concurrent EBIC runs")
     p.add_argument("--requests", type=int, default=1000, help="served: requests per trace")
+    p.add_argument("--shard-rows", action="store_true",
+                   help="methylation workload with its rows split over the ranks (one shard per "
+                        "GPU, one all-reduce per generation) instead of one replica per rank")
     p.add_argument("--main-only", action="store_true",
                    help="default workload: skip the batched and served legs")
     p.add_argument("--leg-steps", type=int, default=20,
@@ -271,6 +274,9 @@ def main():
         return
     if args.workload == "ga":
         ga_workload(args)
+        return
+    if args.shard_rows:
+        sharded_workload(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -520,6 +526,118 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def sharded_workload(args):
+    """The methylation workload with its rows spread over the ranks, as the paper spreads them
+    over GPUs (Abstract; Methods, "Support for Big Data"): rank r loads row shard r (32-row
+    aligned), builds its pair table, and every step is one generation's scoring -- the shard's
+    partials (ebic_eval_partials), one all-reduce of P + P*K + K values (NCCL under torchrun),
+    and the fitness from the sums (ebic_fitness_reduced). The total work is fixed as the ranks
+    grow ("scaling": "strong"); the value counts the whole matrix's rows."""
+    import torch
+    from paper_1807_09932_gb300 import ebic, shard
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ds, pops, arch_pool = make_workload()
+    X = ds.X
+    R, C = X.shape
+    o, r = shard.shard_ranges(R, ws)[rank]
+    m = ebic.Matrix(torch.from_numpy(np.ascontiguousarray(X[o:o + r])).to(dev),
+                    exclude_missing=True, row_offset=o, total_rows=R)
+    m.build_pairs(max_bytes=args.pair_budget)
+    allreduce = shard.reduce_sum(dist) if dist else (lambda b: None)
+
+    def d(a):
+        view = {np.dtype(np.uint16): np.int16, np.dtype(np.uint32): np.int32}[a.dtype]
+        return torch.from_numpy(np.ascontiguousarray(a).view(view)).to(dev)
+
+    # the archive, chosen from whole-matrix counts (the same choice on every rank); its bitmaps
+    # are this shard's rows of the members' bitmaps
+    ac, ao = arch_pool
+    acnt, abm = ebic.eval_population(m, ac, ao)
+    t = torch.from_numpy(acnt.astype(np.int32)).to(dev)
+    allreduce(t)
+    acnt = t.cpu().numpy().astype(np.uint32)
+    pc, po = synth_planted(ds)
+    _, pbm = ebic.eval_population(m, pc, po)
+    acols, aoffs, abm = _archive_from(ds, ac, ao, acnt, abm, pbm)
+    K = len(aoffs) - 1
+    dacols, daoffs, dabm = d(acols), d(aoffs), d(abm)
+    P = len(pops[0][1]) - 1
+    dpops = [(d(c), d(o_), len(o_) - 1) for c, o_ in pops]
+    stream = torch.cuda.current_stream(dev)
+    scorer = shard.ShardedScorer(m, P, K, allreduce, dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(i):
+        dc, do, n = dpops[i % N_POPS]
+        return scorer.score(dc, do, n, dacols, daoffs, dabm, K)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    check = None
+    if ws == 1:  # one shard is the whole matrix: the sharded fitness must be the fused call's
+        fit, _ = step(0)
+        ref = torch.empty(P, dtype=torch.int64, device=dev)
+        cnt = torch.empty(P, dtype=torch.int32, device=dev)
+        dc, do, n = dpops[0]
+        rc = ebic.ebic_eval_fitness(m.handle, dc, do, n, 0, dacols, daoffs, dabm, K, cnt, None,
+                                    ref, None, stream.cuda_stream)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_eval_fitness")
+        check = bool(torch.equal(fit, ref))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ebic.ebic_launch_count()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        step(i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ebic.ebic_launch_count() - launches0
+    clk = clocks.stop()
+    if m.status() != ebic.EBIC_OK:
+        raise SystemExit("device status error in the timed region")
+    tot_ms = sum(a.elapsed_time(b) for a, b in evs)
+    # strong scaling: every rank processed its shard of the same P x R evaluations, so the job's
+    # units are P x R per step in all; combine_over_ranks multiplies a rank's units by N
+    my_time, value = combine_over_ranks(tot_ms / 1000.0, float(P) * R * args.steps / ws, dist,
+                                        dev)
+    line = {"metric": "candidate-row evals/s", "value": value, "unit": "candidate-row evals/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * my_time / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "u8" if m.rank_bits == 8 else "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": R, "cols": C, "population": P,
+                       "archive": K, "populations_cycled": N_POPS,
+                       "parallelism": f"row shards x{ws} (32-row aligned), one all-reduce of "
+                                      f"{shard.packed_size(P, K)} uint32 per generation",
+                       "shard_rows": r, "step": "ebic_eval_partials + all-reduce + "
+                                                "ebic_fitness_reduced",
+                       "l2": "flushed between timed steps (512 MB write, outside the events)"},
+            "gpu_launches": int(launches), "clocks": clk,
+            "sharded_fitness_equals_fused_call": check}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
 
 
 def traffic_record(name):

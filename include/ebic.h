@@ -209,6 +209,74 @@ int ebic_eval_fitness(const ebic_matrix* m, const uint16_t* cols, const uint32_t
 int ebic_matrix_status(ebic_matrix* m, void* stream);
 
 /*
+ * ---- Row shards: one matrix spread over several GPUs by rows ----
+ * The paper's multi-GPU support (Abstract; Methods, "Support for Big Data"; Results, Fig. 1
+ * and Table 1: rows of one matrix spread over up to 8 GPUs) rests on rows being independent:
+ * a candidate's row count and its overlaps with archive members are sums over row ranges, and
+ * its bitmap is the concatenation of the ranges' bitmaps. Only the fitness needs the whole sums.
+ * So a sharded generation is: on every shard ebic_eval_partials; one sum over the shards of
+ * counts [n_cand], overlaps [n_cand][n_arch] and arch_counts [n_arch] (an all-reduce, all uint32:
+ * a sum is at most the total row count); then ebic_fitness_reduced on the sums. The fitness
+ * equals ebic_eval_fitness's on the whole matrix.
+ */
+
+/*
+ * Load rows [row_offset, row_offset + rows) of a matrix of total_rows rows; x points to the
+ * shard's first row (other arguments as for ebic_load_matrix). row_offset must be a multiple of
+ * 32 and every shard but the last must hold a multiple of 32 rows, so that a shard's bitmap word
+ * w is word row_offset / 32 + w of the whole matrix's bitmap. The shard is an ordinary matrix of
+ * `rows` rows for every call (bitmaps, archive bitmaps and counts are the shard's own), except
+ * ebic_run, which returns EBIC_ERR_UNSUPPORTED on a shard that is not the whole matrix.
+ * Errors: EBIC_ERR_INVALID_ARG for an offset or size outside those rules.
+ */
+int ebic_load_matrix_shard(const float* x, int64_t rows, int32_t cols, int64_t ld,
+                           int64_t row_offset, int64_t total_rows, uint32_t flags,
+                           float fill_value, void* stream, ebic_matrix** out);
+
+/* A matrix's place in the whole matrix: its first row, the whole matrix's rows and its first
+ * bitmap word (0, rows, 0 for a matrix loaded by ebic_load_matrix). Any pointer may be NULL. */
+int ebic_matrix_shard(const ebic_matrix* m, int64_t* row_offset, int64_t* total_rows,
+                      int64_t* word_offset);
+
+/*
+ * One shard's share of a generation's scoring (Methods, "Handling missing values": the search
+ * counts rows; the sums make the whole matrix's counts and overlaps).
+ *   cols, offsets, n_cand, flags  the population and flags, as for ebic_eval_population
+ *   arch_cols, arch_offsets, n_arch  the archive's column lists (the whole archive, every shard)
+ *   arch_bitmaps    uint32[n_arch][W]: the archive members' bitmaps over THIS shard's rows
+ *   counts          out: uint32[n_cand], the shard's matched rows per candidate
+ *   overlaps        out: uint32[n_cand][n_arch], the shard's popcount(M_c & M_a) for every
+ *                   member a that shares a column with c; entries of members sharing no column
+ *                   are 0 or that popcount (ebic_fitness_reduced never reads them). Needed, and
+ *                   arch_counts too, when n_arch > 0; otherwise unused.
+ *   arch_counts     out: uint32[n_arch], the shard's popcount of each member's bitmap
+ *   bitmaps         out: uint32[n_cand][W] over the shard's rows, or NULL
+ * Buffers may be host or device memory, as for ebic_eval_fitness; with all outputs on the device
+ * the call is asynchronous on `stream`.
+ */
+int ebic_eval_partials(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                       uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                       const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                       uint32_t n_arch, uint32_t* counts, uint32_t* overlaps,
+                       uint32_t* arch_counts, uint32_t* bitmaps, void* stream);
+
+/*
+ * The fitness of ebic_fitness from whole-matrix counts, overlaps and archive counts (the sums
+ * of every shard's ebic_eval_partials outputs), with no bitmap: q(x) = n_x << (min(L_x,33)-1),
+ * p_c = counts[c] - the largest overlaps[c][a] over members a that share a column with c and
+ * have q(a) >= q(c) (0 if none), fitness[c] = p_c << (min(L_c,33)-1).
+ *   m               any shard of the matrix (it gives the device and the column count)
+ *   counts          uint32[n_cand]; overlaps uint32[n_cand][n_arch]; arch_counts uint32[n_arch]
+ *   fitness         out: uint64[n_cand]
+ * flags is reserved (pass 0). Host or device buffers; asynchronous when fitness is on the device.
+ */
+int ebic_fitness_reduced(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                         uint32_t n_cand, const uint32_t* counts, const uint32_t* overlaps,
+                         const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                         const uint32_t* arch_counts, uint32_t n_arch, uint32_t flags,
+                         uint64_t* fitness, void* stream);
+
+/*
  * Row-tile height of the evaluator for this matrix, in slabs (1, 2 or 4), or 0 for the
  * built-in choice. A slab is 512 rows for 8-bit ranks and 256, 128 or 64 rows for 16-bit ranks
  * (ebic_matrix_get_tile reports it). The tile changes speed only, never results. The autotuner

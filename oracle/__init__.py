@@ -136,3 +136,28 @@ def dense_ranks(X, *, exclude_missing=True, fill_value=0.0):
     _load().oracle_dense_ranks(_ptr(X), R, C, C, int(exclude_missing), float(fill_value),
                                _ptr(out))
     return out
+
+
+def fitness_from_overlaps(cols, offsets, counts, overlaps, arch_cols, arch_offsets, arch_counts):
+    """D9 from row counts and overlaps alone (no bitmaps): the quantities a row-sharded run
+    sums over its shards. q(x) = n_x << (min(L_x, 33) - 1); p_c = n_c minus the largest
+    overlaps[c][a] over members a whose column set meets c's and with q(a) >= q(c), 0 if none;
+    F_c = p_c << (min(L_c, 33) - 1). Plain Python over candidates and members."""
+    P = len(offsets) - 1
+    K = len(arch_offsets) - 1
+    fit = np.zeros(P, dtype=np.uint64)
+    asets = [set(int(x) for x in arch_cols[arch_offsets[a]:arch_offsets[a + 1]])
+             for a in range(K)]
+    aq = [int(arch_counts[a]) << (min(int(arch_offsets[a + 1] - arch_offsets[a]), 33) - 1)
+          for a in range(K)]
+    for c in range(P):
+        cset = [int(x) for x in cols[offsets[c]:offsets[c + 1]]]
+        L = len(cset)
+        n = int(counts[c])
+        qc = n << (min(L, 33) - 1)
+        worst = 0
+        for a in range(K):
+            if aq[a] >= qc and asets[a] & set(cset):
+                worst = max(worst, int(overlaps[c][a]))
+        fit[c] = (n - worst) << (min(L, 33) - 1)
+    return fit

@@ -34,6 +34,8 @@ struct ebic_matrix {
   uint32_t* pairs = nullptr;   // pair table [cols*cols][pair_stride], padding zero, or null
   uint32_t pair_stride = 0;
   size_t pair_bytes = 0;
+  int64_t row_offset = 0;      // a row shard: its first row in the whole matrix (a multiple of 32)
+  int64_t total_rows = 0;      // and the whole matrix's rows (rows when not a shard)
 };
 
 namespace {
@@ -433,6 +435,8 @@ void matrix_view(const ebic_matrix* m, MatrixView* v) {
   v->num_sms = m->num_sms;
   v->pairs = m->pairs;
   v->pair_stride = m->pair_stride;
+  v->row_offset = m->row_offset;
+  v->total_rows = m->total_rows;
 }
 
 int matrix_eval_plan(const ebic_matrix* cm, uint32_t n_cand, int64_t total_cols_hint,
@@ -648,6 +652,7 @@ int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uin
   m->L = make_layout(rows, cols);
   m->flags = flags;
   m->fill = fill_value;
+  m->total_rows = rows;
   auto cleanup = [&](int code) {
     if (m->ranks) cudaFree(m->ranks);
     if (m->status) cudaFree(m->status);
@@ -742,11 +747,16 @@ int ebic_eval_population(const ebic_matrix* cm, const uint16_t* cols, const uint
                               stream);
 }
 
-int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
-                 uint32_t n_cand, const uint32_t* counts, const uint32_t* bitmaps,
-                 const uint16_t* arch_cols, const uint32_t* arch_offsets,
-                 const uint32_t* arch_bitmaps, uint32_t n_arch, uint32_t flags,
-                 uint64_t* fitness, uint32_t* overlaps, void* stream) {
+}  // extern "C"
+
+// ebic_fitness, and also the archive members' row counts into `arch_counts_out` (when not
+// null; [n_arch], device or host).
+static int fitness_impl(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                        uint32_t n_cand, const uint32_t* counts, const uint32_t* bitmaps,
+                        const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                        const uint32_t* arch_bitmaps, uint32_t n_arch, uint32_t flags,
+                        uint64_t* fitness, uint32_t* overlaps, uint32_t* arch_counts_out,
+                        void* stream) {
   ebic_matrix* m = const_cast<ebic_matrix*>(cm);
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
   if (flags != 0) return fail(EBIC_ERR_INVALID_ARG, "flags is reserved (pass 0)");
@@ -761,7 +771,8 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
                         (const void*)bitmaps, (const void*)arch_cols, (const void*)arch_offsets,
-                        (const void*)arch_bitmaps, (const void*)fitness, (const void*)overlaps})
+                        (const void*)arch_bitmaps, (const void*)fitness, (const void*)overlaps,
+                        (const void*)arch_counts_out})
     if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
 
   const bool host_c = !on_device(cols, dev) && !on_device(offsets, dev);
@@ -837,7 +848,11 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
     EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
                                       darch_counts, dfit, err, s));
   }
-  if (fit_host || ov_host) {
+  const bool ac_host = arch_counts_out && n_arch > 0 && !on_device(arch_counts_out, dev);
+  if (arch_counts_out && n_arch > 0)
+    EBIC_CUDA(cudaMemcpyAsync(arch_counts_out, darch_counts, (size_t)n_arch * 4,
+                              ac_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  if (fit_host || ov_host || ac_host) {
     if (fit_host)
       EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
     if (ov_host)
@@ -848,6 +863,15 @@ int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* of
     return status_code(bits, "ebic_fitness");
   }
   return EBIC_OK;
+}
+
+extern "C" int ebic_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                            uint32_t n_cand, const uint32_t* counts, const uint32_t* bitmaps,
+                            const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                            const uint32_t* arch_bitmaps, uint32_t n_arch, uint32_t flags,
+                            uint64_t* fitness, uint32_t* overlaps, void* stream) {
+  return fitness_impl(cm, cols, offsets, n_cand, counts, bitmaps, arch_cols, arch_offsets,
+                      arch_bitmaps, n_arch, flags, fitness, overlaps, nullptr, stream);
 }
 
 // The fused route's outputs: the caller's overlaps from the paired layout, host copies, and
@@ -887,11 +911,15 @@ static int finish_fitness(uint32_t n_cand, uint32_t n_arch, uint32_t ov_stride,
 }
 
 
-int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
-                      uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
-                      const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
-                      uint32_t n_arch, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
-                      uint32_t* overlaps, void* stream) {
+// ebic_eval_fitness, and also the archive members' row counts into `arch_counts_out` (when not
+// null). `sharing_only`: with `overlaps` asked for, the fused route may skip the members that
+// share no column with a candidate (their entries are then 0); the other route computes them.
+static int eval_fitness_impl(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                             uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                             const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                             uint32_t n_arch, uint32_t* counts, uint32_t* bitmaps,
+                             uint64_t* fitness, uint32_t* overlaps, uint32_t* arch_counts_out,
+                             bool sharing_only, void* stream) {
   ebic_matrix* m = const_cast<ebic_matrix*>(cm);
   if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
   if (flags & ~(EBIC_NEGATIVE_TRENDS | EBIC_EVAL_DIRECT))
@@ -908,8 +936,9 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
   const Where w_cols = where(cols, dev), w_offs = where(offsets, dev), w_cnt = where(counts, dev),
               w_bm = where(bitmaps, dev), w_acols = where(arch_cols, dev),
               w_aoffs = where(arch_offsets, dev), w_abm = where(arch_bitmaps, dev),
-              w_fit = where(fitness, dev), w_ov = where(overlaps, dev);
-  for (const Where& w : {w_cols, w_offs, w_cnt, w_bm, w_acols, w_aoffs, w_abm, w_fit, w_ov})
+              w_fit = where(fitness, dev), w_ov = where(overlaps, dev),
+              w_ac = where(arch_counts_out, dev);
+  for (const Where& w : {w_cols, w_offs, w_cnt, w_bm, w_acols, w_aoffs, w_abm, w_fit, w_ov, w_ac})
     if (w.foreign) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
 
   const bool fused = m->pairs && !(flags & EBIC_EVAL_DIRECT) && n_arch <= (uint32_t)kPairMaxArch;
@@ -920,8 +949,8 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     if (!bm) EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&bm), (size_t)n_cand * L.words * 4));
     int rc = ebic_eval_population(m, cols, offsets, n_cand, flags, counts, bm, stream);
     if (rc != EBIC_OK) return rc;
-    return ebic_fitness(m, cols, offsets, n_cand, counts, bm, arch_cols, arch_offsets,
-                        arch_bitmaps, n_arch, 0, fitness, overlaps, stream);
+    return fitness_impl(m, cols, offsets, n_cand, counts, bm, arch_cols, arch_offsets,
+                        arch_bitmaps, n_arch, 0, fitness, overlaps, arch_counts_out, stream);
   }
 
   const bool host_c = !w_cols.dev && !w_offs.dev;
@@ -987,7 +1016,8 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
   // an output on the host: the call waits for the device and reports its error word, mirrored to
   // the host by the finalize kernel
   const bool sync = !w_cnt.dev || !w_fit.dev || (bitmaps && !w_bm.dev) ||
-                    (overlaps && n_arch > 0 && !w_ov.dev);
+                    (overlaps && n_arch > 0 && !w_ov.dev) ||
+                    (arch_counts_out && n_arch > 0 && !w_ac.dev);
   uint32_t* err_mirror = sync ? t_err_word.get() : nullptr;
 
   const bool neg = (flags & EBIC_NEGATIVE_TRENDS) != 0;
@@ -1059,7 +1089,8 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     p.bitmaps = dbm;
     p.arch = n_arch > 0 ? dpad : nullptr;
     p.n_arch = n_arch;
-    p.score = overlaps ? nullptr : dshare;  // all members only when the caller reads them
+    // all members only when the caller reads all their overlaps
+    p.score = overlaps && !sharing_only ? nullptr : dshare;
     p.overlaps = dov;
     p.ov_stride = ov_stride;
     p.arch_counts = darch_counts;
@@ -1082,9 +1113,26 @@ int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_
     if (sync) (void)cudaStreamSynchronize(s);
     return hc;
   }
+  // the archive members' counts (a host destination makes the call synchronous above, so the
+  // synchronisation in finish_fitness also covers this copy)
+  if (arch_counts_out && n_arch > 0)
+    EBIC_CUDA(cudaMemcpyAsync(arch_counts_out, darch_counts, (size_t)n_arch * 4,
+                              w_ac.dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   return finish_fitness(n_cand, n_arch, ov_stride, dcounts, dbm, dfit, dov, err, counts,
                         bitmaps, fitness, overlaps, counts_host, bm_host, fit_host, L.words,
                         w_ov.dev, sync, err_mirror ? t_err_word.host : nullptr, s);
+}
+
+extern "C" {
+
+int ebic_eval_fitness(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                      uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                      const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                      uint32_t n_arch, uint32_t* counts, uint32_t* bitmaps, uint64_t* fitness,
+                      uint32_t* overlaps, void* stream) {
+  return eval_fitness_impl(cm, cols, offsets, n_cand, flags, arch_cols, arch_offsets,
+                           arch_bitmaps, n_arch, counts, bitmaps, fitness, overlaps, nullptr,
+                           false, stream);
 }
 
 int ebic_matrix_status(ebic_matrix* m, void* stream) {
@@ -1224,6 +1272,144 @@ int ebic_matrix_get_tile(const ebic_matrix* m, int32_t* tile_slabs, int32_t* row
   while (ts > 1 && ts > m->L.slabs) ts >>= 1;
   if (tile_slabs) *tile_slabs = ts;
   if (rows_per_slab) *rows_per_slab = (int32_t)m->L.rows_per_slab();
+  return EBIC_OK;
+}
+
+
+// ---- row shards (the paper's multi-GPU layout: rows spread over GPUs, Methods, "Support for Big
+// Data"; Abstract) ------------------------------------------------------------------------------
+
+int ebic_load_matrix_shard(const float* x, int64_t rows, int32_t cols, int64_t ld,
+                           int64_t row_offset, int64_t total_rows, uint32_t flags,
+                           float fill_value, void* stream, ebic_matrix** out) {
+  if (!out) return fail(EBIC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (total_rows < 1 || total_rows > 2147483647LL)
+    return fail(EBIC_ERR_INVALID_ARG, "total_rows must be in [1, 2^31-1]");
+  if (row_offset < 0 || row_offset % 32 != 0)
+    return fail(EBIC_ERR_INVALID_ARG, "row_offset must be a non-negative multiple of 32");
+  if (rows < 1 || row_offset + rows > total_rows)
+    return fail(EBIC_ERR_INVALID_ARG, "the shard must lie inside the whole matrix");
+  if (row_offset + rows != total_rows && rows % 32 != 0)
+    return fail(EBIC_ERR_INVALID_ARG,
+                "a shard that does not end the matrix must hold a multiple of 32 rows");
+  int rc = ebic_load_matrix(x, rows, cols, ld, flags, fill_value, stream, out);
+  if (rc != EBIC_OK) return rc;
+  (*out)->row_offset = row_offset;
+  (*out)->total_rows = total_rows;
+  return EBIC_OK;
+}
+
+int ebic_matrix_shard(const ebic_matrix* m, int64_t* row_offset, int64_t* total_rows,
+                      int64_t* word_offset) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (row_offset) *row_offset = m->row_offset;
+  if (total_rows) *total_rows = m->total_rows;
+  if (word_offset) *word_offset = m->row_offset / 32;
+  return EBIC_OK;
+}
+
+int ebic_eval_partials(const ebic_matrix* m, const uint16_t* cols, const uint32_t* offsets,
+                       uint32_t n_cand, uint32_t flags, const uint16_t* arch_cols,
+                       const uint32_t* arch_offsets, const uint32_t* arch_bitmaps,
+                       uint32_t n_arch, uint32_t* counts, uint32_t* overlaps,
+                       uint32_t* arch_counts, uint32_t* bitmaps, void* stream) {
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (n_cand == 0) return EBIC_OK;
+  if (n_arch > 0 && (!overlaps || !arch_counts))
+    return fail(EBIC_ERR_INVALID_ARG, "overlaps and arch_counts are needed with an archive");
+  DeviceGuard g(m->device);
+  // the shard's own fitness is of no use before the sum: it goes to scratch
+  Scratch sc(static_cast<cudaStream_t>(stream));
+  uint64_t* fit = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&fit), (size_t)n_cand * 8));
+  return eval_fitness_impl(m, cols, offsets, n_cand, flags, arch_cols, arch_offsets,
+                           arch_bitmaps, n_arch, counts, bitmaps, fit,
+                           n_arch ? overlaps : nullptr, n_arch ? arch_counts : nullptr, true,
+                           stream);
+}
+
+int ebic_fitness_reduced(const ebic_matrix* cm, const uint16_t* cols, const uint32_t* offsets,
+                         uint32_t n_cand, const uint32_t* counts, const uint32_t* overlaps,
+                         const uint16_t* arch_cols, const uint32_t* arch_offsets,
+                         const uint32_t* arch_counts, uint32_t n_arch, uint32_t flags,
+                         uint64_t* fitness, void* stream) {
+  ebic_matrix* m = const_cast<ebic_matrix*>(cm);
+  if (!m) return fail(EBIC_ERR_INVALID_ARG, "matrix is NULL");
+  if (flags != 0) return fail(EBIC_ERR_INVALID_ARG, "flags is reserved (pass 0)");
+  if (n_cand == 0) return EBIC_OK;
+  if (!cols || !offsets || !counts || !fitness) return fail(EBIC_ERR_INVALID_ARG, "NULL argument");
+  if (n_arch > 0 && (!arch_cols || !arch_offsets || !arch_counts || !overlaps))
+    return fail(EBIC_ERR_INVALID_ARG, "NULL archive argument");
+  DeviceGuard g(m->device);
+  const int dev = m->device;
+  const Layout& L = m->L;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const void* p : {(const void*)cols, (const void*)offsets, (const void*)counts,
+                        (const void*)overlaps, (const void*)arch_cols, (const void*)arch_offsets,
+                        (const void*)arch_counts, (const void*)fitness})
+    if (foreign_device(p, dev)) return fail(EBIC_ERR_INVALID_ARG, "buffer on another device");
+  const bool host_c = !on_device(cols, dev) && !on_device(offsets, dev);
+  if (!host_c && (!on_device(cols, dev) || !on_device(offsets, dev)))
+    return fail(EBIC_ERR_INVALID_ARG,
+                "a candidate list must have its columns and offsets in the same memory");
+  if (host_c) {
+    std::string why = check_candidates_host(cols, offsets, n_cand, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, why);
+  }
+  const bool host_a = n_arch == 0 || (!on_device(arch_cols, dev) && !on_device(arch_offsets, dev));
+  if (n_arch > 0 && !host_a && (!on_device(arch_cols, dev) || !on_device(arch_offsets, dev)))
+    return fail(EBIC_ERR_INVALID_ARG,
+                "a candidate list must have its columns and offsets in the same memory");
+  if (n_arch > 0 && host_a) {
+    std::string why = check_candidates_host(arch_cols, arch_offsets, n_arch, L.cols);
+    if (!why.empty()) return fail(EBIC_ERR_INVALID_ARG, "archive: " + why);
+  }
+  Scratch sc(s);
+  uint32_t* err = nullptr;
+  EBIC_CUDA(sc.alloc(reinterpret_cast<void**>(&err), sizeof(uint32_t)));
+  EBIC_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  const uint16_t *dcols = nullptr, *dacols = nullptr;
+  const uint32_t *doffs = nullptr, *daoffs = nullptr, *dcounts = nullptr, *dov = nullptr,
+                 *dacnt = nullptr;
+  EBIC_CUDA(to_device(offsets, (size_t)n_cand + 1, dev, sc, &doffs));
+  EBIC_CUDA(to_device(cols, host_c ? (size_t)offsets[n_cand] : 0, dev, sc, &dcols));
+  EBIC_CUDA(to_device(counts, n_cand, dev, sc, &dcounts));
+  if (n_arch > 0) {
+    EBIC_CUDA(to_device(arch_offsets, (size_t)n_arch + 1, dev, sc, &daoffs));
+    EBIC_CUDA(to_device(arch_cols, host_a ? (size_t)arch_offsets[n_arch] : 0, dev, sc, &dacols));
+    EBIC_CUDA(to_device(arch_counts, n_arch, dev, sc, &dacnt));
+    EBIC_CUDA(to_device(overlaps, (size_t)n_cand * n_arch, dev, sc, &dov));
+  }
+  bool fit_host = false;
+  uint64_t* dfit = nullptr;
+  EBIC_CUDA(out_buffer(fitness, n_cand, dev, sc, &dfit, &fit_host));
+  {
+    Timed t(EBIC_TIMING_PREPARE, s);
+    PrepareArgs pa;  // device-resident lists are checked here; nothing to zero
+    pa.cols[0] = dcols;
+    pa.offsets[0] = doffs;
+    pa.n[0] = host_c ? 0 : n_cand;
+    pa.cols[1] = dacols;
+    pa.offsets[1] = daoffs;
+    pa.n[1] = host_a ? 0 : n_arch;
+    pa.ncols = L.cols;
+    pa.err = err;
+    pa.status = m->status;
+    EBIC_CUDA(launch_prepare(pa, s));
+  }
+  {
+    Timed t(EBIC_TIMING_FITNESS, s);
+    EBIC_CUDA(launch_fitness_finalize(dcols, doffs, n_cand, dcounts, dacols, daoffs, n_arch, dov,
+                                      dacnt, dfit, err, s));
+  }
+  if (fit_host) {
+    EBIC_CUDA(cudaMemcpyAsync(fitness, dfit, (size_t)n_cand * 8, cudaMemcpyDeviceToHost, s));
+    uint32_t bits = 0;
+    EBIC_CUDA(cudaMemcpyAsync(&bits, err, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CUDA(cudaStreamSynchronize(s));
+    return status_code(bits, "ebic_fitness_reduced");
+  }
   return EBIC_OK;
 }
 

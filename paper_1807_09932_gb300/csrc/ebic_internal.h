@@ -279,6 +279,8 @@ struct MatrixView {
   int num_sms = 0;
   const uint32_t* pairs = nullptr;  // the matrix's pair table, or null
   uint32_t pair_stride = 0;
+  int64_t row_offset = 0;           // a row shard's first row in the whole matrix
+  int64_t total_rows = 0;           // the whole matrix's rows (L.rows when not a shard)
 };
 // Read-only view of a matrix handle's shape and device words.
 void matrix_view(const ebic_matrix* m, MatrixView* v);

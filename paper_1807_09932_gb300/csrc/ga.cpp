@@ -1024,6 +1024,9 @@ int ebic_run(const ebic_matrix* m, const ebic_params* p, void* stream, ebic_resu
   *out = nullptr;
   MatrixView v;
   matrix_view(m, &v);
+  if (v.total_rows != v.L.rows)
+    return set_last_error(EBIC_ERR_UNSUPPORTED,
+                          "ebic_run scores the whole matrix; this matrix is one row shard of it");
   std::string why = check_params(*p, v.L.cols);
   if (!why.empty()) return set_last_error(EBIC_ERR_INVALID_ARG, why.c_str());
   int prev = -1;

@@ -77,6 +77,14 @@ _lib_fitness = _sig("ebic_fitness", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32,
                                      _P])
 _lib_eval_fitness = _sig("ebic_eval_fitness", [_P, _P, _P, _U32, _U32, _P, _P, _P, _U32, _P,
                                                _P, _P, _P, _P])
+_lib_load_shard = _sig("ebic_load_matrix_shard", [_P, _I64, _I32, _I64, _I64, _I64, _U32,
+                                                  ctypes.c_float, _P, ctypes.POINTER(_P)])
+_lib_shard = _sig("ebic_matrix_shard", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                        ctypes.POINTER(_I64)])
+_lib_eval_partials = _sig("ebic_eval_partials", [_P, _P, _P, _U32, _U32, _P, _P, _P, _U32, _P,
+                                                 _P, _P, _P, _P])
+_lib_fitness_reduced = _sig("ebic_fitness_reduced", [_P, _P, _P, _U32, _P, _P, _P, _P, _P, _U32,
+                                                     _U32, _P, _P])
 _lib_status = _sig("ebic_matrix_status", [_P, _P])
 _lib_set_tile = _sig("ebic_matrix_set_tile", [_P, _I32])
 _lib_get_tile = _sig("ebic_matrix_get_tile", [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)])
@@ -225,6 +233,35 @@ def ebic_load_matrix(x, rows, cols, ld, flags, fill_value, stream=None):
     _check(_lib_load(_ptr(x), rows, cols, ld, flags, fill_value, _stream(stream),
                      ctypes.byref(h)), "ebic_load_matrix")
     return h
+
+
+def ebic_load_matrix_shard(x, rows, cols, ld, row_offset, total_rows, flags, fill_value,
+                           stream=None):
+    h = _P()
+    _check(_lib_load_shard(_ptr(x), rows, cols, ld, row_offset, total_rows, flags, fill_value,
+                           _stream(stream), ctypes.byref(h)), "ebic_load_matrix_shard")
+    return h
+
+
+def ebic_matrix_shard(h):
+    r, t, w = _I64(), _I64(), _I64()
+    _check(_lib_shard(h, ctypes.byref(r), ctypes.byref(t), ctypes.byref(w)), "ebic_matrix_shard")
+    return r.value, t.value, w.value
+
+
+def ebic_eval_partials(h, cols, offsets, n_cand, flags, arch_cols, arch_offsets, arch_bitmaps,
+                       n_arch, counts, overlaps, arch_counts, bitmaps, stream=None):
+    return _lib_eval_partials(h, _ptr(cols), _ptr(offsets), n_cand, flags, _ptr(arch_cols),
+                              _ptr(arch_offsets), _ptr(arch_bitmaps), n_arch, _ptr(counts),
+                              _ptr(overlaps), _ptr(arch_counts), _ptr(bitmaps), _stream(stream))
+
+
+def ebic_fitness_reduced(h, cols, offsets, n_cand, counts, overlaps, arch_cols, arch_offsets,
+                         arch_counts, n_arch, flags, fitness, stream=None):
+    return _lib_fitness_reduced(h, _ptr(cols), _ptr(offsets), n_cand, _ptr(counts),
+                                _ptr(overlaps), _ptr(arch_cols), _ptr(arch_offsets),
+                                _ptr(arch_counts), n_arch, flags, _ptr(fitness),
+                                _stream(stream))
 
 
 def ebic_free_matrix(h):
@@ -426,13 +463,22 @@ def words(rows):
 class Matrix:
     """A loaded matrix: its device-resident rank matrix stays on the GPU until ``close()``."""
 
-    def __init__(self, X, *, exclude_missing=True, fill_value=0.0, stream=None):
+    def __init__(self, X, *, exclude_missing=True, fill_value=0.0, stream=None, row_offset=None,
+                 total_rows=None):
+        """With row_offset / total_rows: X holds rows [row_offset, row_offset + len(X)) of a
+        matrix of total_rows rows (a row shard, ebic_load_matrix_shard)."""
         if isinstance(X, np.ndarray):
             X = np.ascontiguousarray(X, dtype=np.float32)
         rows, cols = X.shape
         flags = EBIC_EXCLUDE_MISSING if exclude_missing else 0
-        self.handle = ebic_load_matrix(X, rows, cols, cols, flags, float(fill_value), stream)
+        if row_offset is None and total_rows is None:
+            self.handle = ebic_load_matrix(X, rows, cols, cols, flags, float(fill_value), stream)
+        else:
+            self.handle = ebic_load_matrix_shard(
+                X, rows, cols, cols, int(row_offset or 0),
+                int(rows if total_rows is None else total_rows), flags, float(fill_value), stream)
         self.rows, self.cols, self.words, self.rank_bits = ebic_matrix_info(self.handle)
+        self.row_offset, self.total_rows, self.word_offset = ebic_matrix_shard(self.handle)
         self.exclude_missing = exclude_missing
 
     def close(self):
@@ -524,6 +570,37 @@ def eval_fitness(m: Matrix, cols, offsets, arch_cols, arch_offsets, arch_bitmaps
                            arch_bitmaps, k, counts, bitmaps, fit, overlaps, stream)
     _check(rc, "ebic_eval_fitness")
     return counts, bitmaps, fit, overlaps
+
+
+def eval_partials(m: Matrix, cols, offsets, arch_cols, arch_offsets, arch_bitmaps, *,
+                  negative=False, want_bitmaps=False, stream=None):
+    """One row shard's share of a generation's scoring (ebic_eval_partials): counts, overlaps
+    (or None without an archive), archive counts (or None) and bitmaps (or None), as host numpy
+    arrays. arch_bitmaps are the members' bitmaps over the shard's rows."""
+    n = len(offsets) - 1
+    k = len(arch_offsets) - 1
+    counts = np.zeros(n, dtype=np.uint32)
+    overlaps = np.zeros((n, k), dtype=np.uint32) if k else None
+    acounts = np.zeros(k, dtype=np.uint32) if k else None
+    bitmaps = np.zeros((n, m.words), dtype=np.uint32) if want_bitmaps else None
+    rc = ebic_eval_partials(m.handle, cols, offsets, n, EBIC_NEGATIVE_TRENDS if negative else 0,
+                            arch_cols, arch_offsets, arch_bitmaps, k, counts, overlaps, acounts,
+                            bitmaps, stream)
+    _check(rc, "ebic_eval_partials")
+    return counts, overlaps, acounts, bitmaps
+
+
+def fitness_reduced(m: Matrix, cols, offsets, counts, overlaps, arch_cols, arch_offsets,
+                    arch_counts, stream=None):
+    """The fitness from whole-matrix sums of the shards' partials (ebic_fitness_reduced)."""
+    n = len(offsets) - 1
+    k = len(arch_offsets) - 1
+    fit = np.zeros(n, dtype=np.uint64)
+    rc = ebic_fitness_reduced(m.handle, cols, offsets, n, counts, overlaps if k else None,
+                              arch_cols, arch_offsets, arch_counts if k else None, k, 0, fit,
+                              stream)
+    _check(rc, "ebic_fitness_reduced")
+    return fit
 
 
 # ---- text input and bicluster output ------------------------------------------------------------
