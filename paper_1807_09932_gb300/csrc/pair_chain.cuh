@@ -80,6 +80,22 @@ __device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ col
   terms_from_cols<NEG>(c_lo, c_hi, L, C, S, lane, t);
 }
 
+// L2 prefetch of the item segments (kParts parts of kRangeWords words: 2 KB, sixteen 128-byte
+// lines) of two table rows, at word offsets off_a and off_b from `item` (the item's first table
+// word): lanes 0-15 take row a's lines, lanes 16-31 row b's, one line per lane, only in the parts
+// whose bit is set in part_mask. A prefetch holds no register, so a warp keeps the next step's
+// rows on their way from HBM while its registers wait on the current step's.
+__device__ __forceinline__ void prefetch_rows2(const uint32_t* item, uint32_t off_a, bool has_a,
+                                               uint32_t off_b, bool has_b, uint32_t part_mask,
+                                               int lane) {
+  const int line = lane & 15;
+  const bool b = lane >= 16;
+  if ((b ? has_b : has_a) && ((part_mask >> (line >> 2)) & 1u)) {
+    const uint32_t* ptr = item + (b ? off_b : off_a) + line * 32;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+  }
+}
+
 // The candidate's bitmap words 4*lane .. 4*lane+3 of each 128-word part of the item whose first
 // table word is `base` (table + item*kItemWords): AND of its consecutive pairs' table rows, OR
 // the reversed pairs' AND with negative trends. Each step keeps the rows of several terms of
@@ -103,10 +119,20 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
     x[q] = y[q] = all;
     nzx[q] = nzy[q] = true;
   }
-  (void)lane;
+  const uint32_t* item = base - 4 * lane;
+  uint32_t parts = (1u << kParts) - 1u;  // parts in which some lane still has a non-zero word
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
   auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
     for (int i0 = t0; i0 < t1; i0 += kStep) {
+      // the next step's rows, prefetched while this step's are loaded (the parts still alive
+      // after the previous step: at most one step's rows are fetched in vain)
+      if (!NEG) {  // (measured slower with negative trends: one term per step there)
+        const int j = i0 + kStep;
+        const uint32_t fa = __shfl_sync(0xFFFFFFFFu, offf, j & 31);
+        const uint32_t fb = NEG ? __shfl_sync(0xFFFFFFFFu, offb, j & 31)
+                                : __shfl_sync(0xFFFFFFFFu, offf, (j + 1) & 31);
+        prefetch_rows2(item, fa, j < t1, fb, NEG ? (two && j < t1) : (j + 1 < t1), parts, lane);
+      }
       uint4 v[kStep][kParts], u[kStep][kParts];
 #pragma unroll
       for (int k = 0; k < kStep; ++k) {
@@ -126,21 +152,22 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
                                                                : ones));
         }
       }
-      bool lane_any = false;
+      uint32_t lane_parts = 0;
 #pragma unroll
       for (int q = 0; q < kParts; ++q) {
 #pragma unroll
         for (int k = 0; k < kStep; ++k) x[q] = and4(x[q], v[k][q]);
         nzx[q] = (x[q].x | x[q].y | x[q].z | x[q].w) != 0u;
-        lane_any |= nzx[q];
+        lane_parts |= nzx[q] ? 1u << q : 0u;
         if (NEG && two) {
 #pragma unroll
           for (int k = 0; k < kStep; ++k) y[q] = and4(y[q], u[k][q]);
           nzy[q] = (y[q].x | y[q].y | y[q].z | y[q].w) != 0u;
-          lane_any |= nzy[q];
+          lane_parts |= nzy[q] ? 1u << q : 0u;
         }
       }
-      if (!__any_sync(0xFFFFFFFFu, lane_any)) return false;  // all zero from here on
+      parts = __reduce_or_sync(0xFFFFFFFFu, lane_parts);
+      if (parts == 0u) return false;  // all zero from here on
     }
     return true;
   };
@@ -301,41 +328,62 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
 
 // The pass over all (range, candidate group) items of one population, by a persistent grid of
 // kPairThreads-thread CTAs (see pairs.cu for the work order); `st` is the warp's kRangeWords-word
-// shared staging buffer.
+// shared staging buffer. CTA b owns items b, b + G, b + 2G, ... (G = gridDim.x); an item's
+// kPairWarps candidates are its units, and the CTA's warps take units in that order from the
+// CTA's shared counter `next_unit` (zero at entry) as each becomes free, so a warp that drew
+// short candidates takes more of them and the CTA ends when its work ends, not when its unluckiest
+// warp does. The units of one item still run side by side on one SM, so the table rows they
+// share meet in its L1.
 template <bool NEG, bool BITMAPS, bool OVERLAP>
-__device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st, uint32_t* next_unit) {
+  const int lane = threadIdx.x & 31;
   const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
   const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
   const uint64_t n_items = (uint64_t)n_ranges * n_groups;
+  const bool narrow = n_items <= 0xFFFFFFFFull;  // 32-bit item arithmetic suffices
   const uint32_t n_arch = OVERLAP ? p.n_arch : 0u;
   const int n_pairs = (int)(n_arch + 1) >> 1;
   const uint64_t all_members = n_arch >= 64 ? ~0ull : ((1ull << n_arch) - 1ull);
   const uint32_t* ones = pair_ones(p.table, (uint64_t)p.C, p.stride);
-  // item `it` is (range, group) = (it / n_groups, it % n_groups), stepped without a division;
-  // the term list of the warp's next item is loaded while the current one is walked
-  const uint32_t d_range = gridDim.x / n_groups, d_grp = gridDim.x % n_groups;
-  uint64_t it = blockIdx.x;
-  uint32_t range = blockIdx.x / n_groups, grp = blockIdx.x % n_groups;
-  Terms next;
-  if (it < n_items && grp * kPairWarps + warp < p.n_cand)
-    load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
-  while (it < n_items) {
-    const uint64_t rword = (uint64_t)range * kItemWords;  // first word of the item
-    const uint32_t cand = grp * kPairWarps + warp;
-    const uint32_t cur_grp = grp;
-    const Terms t = next;
-    it += gridDim.x;
-    range += d_range;
-    grp += d_grp;
-    if (grp >= n_groups) {
-      grp -= n_groups;
-      ++range;
+  struct Unit {
+    uint64_t it;
+    uint32_t range, grp, slot, cand;
+  };
+  // the CTA's next unit: its item, range, group, slot and candidate
+  auto take = [&]() {
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(next_unit, 1u);
+    u = __shfl_sync(0xFFFFFFFFu, u, 0);
+    Unit x;
+    x.slot = u % kPairWarps;
+    x.it = blockIdx.x + (uint64_t)(u / kPairWarps) * gridDim.x;
+    x.range = x.grp = x.cand = 0;
+    if (x.it < n_items) {
+      if (narrow) {
+        x.range = (uint32_t)x.it / n_groups;
+        x.grp = (uint32_t)x.it - x.range * n_groups;
+      } else {
+        x.range = (uint32_t)(x.it / n_groups);
+        x.grp = (uint32_t)(x.it - (uint64_t)x.range * n_groups);
+      }
+      x.cand = x.grp * kPairWarps + x.slot;
     }
-    if (it < n_items && grp * kPairWarps + warp < p.n_cand)
-      load_terms<NEG>(p, grp * kPairWarps + warp, lane, next);
-    if (OVERLAP && cur_grp == 0) {  // the archive members' own row counts, once per range
-      for (uint32_t a = warp; a < n_arch; a += kPairWarps) {
+    return x;
+  };
+  Unit cur = take();
+  Terms next;
+  if (cur.it < n_items && cur.cand < p.n_cand) load_terms<NEG>(p, cur.cand, lane, next);
+  while (cur.it < n_items) {
+    const uint64_t rword = (uint64_t)cur.range * kItemWords;  // first word of the item
+    const uint32_t cand = cur.cand;
+    const Terms t = next;
+    const bool arch_share = OVERLAP && cur.grp == 0;  // this range's archive counts, slot's share
+    const uint32_t slot = cur.slot;
+    // the next unit, and its term list, requested before this one is walked
+    cur = take();
+    if (cur.it < n_items && cur.cand < p.n_cand) load_terms<NEG>(p, cur.cand, lane, next);
+    if (arch_share) {  // the archive members' own row counts, once per range
+      for (uint32_t a = slot; a < n_arch; a += kPairWarps) {
         const uint32_t* ar = p.arch + (uint64_t)a * p.stride + rword + 4 * lane;
         uint32_t pa = 0;
 #pragma unroll
@@ -347,6 +395,15 @@ __device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st) {
     if (cand >= p.n_cand) continue;  // warp-uniform
     uint4 x[kParts];
     pair_chain<NEG>(t, p.table + rword + 4 * lane, ones, lane, x);
+    // the next unit's first step, prefetched while this unit's epilogue runs (its term list has
+    // arrived during the walk)
+    if (!NEG && cur.it < n_items && cur.cand < p.n_cand) {
+      const int Ln = (int)__shfl_sync(0xFFFFFFFFu, next.hi, 31);
+      const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, next.lo, 0);
+      const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, next.lo, 1);
+      prefetch_rows2(p.table + (uint64_t)cur.range * kItemWords, a0, true, a1, Ln > 2,
+                     (1u << kParts) - 1u, lane);
+    }
     uint32_t pc = 0;
 #pragma unroll
     for (int q = 0; q < kParts; ++q) pc += popc4(x[q]);

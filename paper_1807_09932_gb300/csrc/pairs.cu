@@ -22,14 +22,17 @@
 // Work order: items are (range of 512 words = 16,384 rows, group of 24 candidates), taken
 // round-robin by a persistent grid in range-major order, so all CTAs work on the same few row
 // ranges at a time and the table rows of those ranges stay in L2 while every candidate reads
-// them; each table word comes from HBM about once per evaluation. Each warp takes one candidate
-// of its item. The preparation kernel has already turned the candidate into its term list (the
-// table-row offsets of its consecutive pairs), which the warp loads while it walks its previous
-// item. The chain goes two pairs per step, each step keeping eight 512-byte warp loads in flight
-// (two pairs x four parts; with negative trends one pair, both orders). A part stops loading
-// once all its words are zero and the walk stops when all are: long chains match no row of
-// most ranges. Larger items amortise the per-item work (the term list, the reductions and
-// atomics of the epilogue) over more rows.
+// them; each table word comes from HBM about once per evaluation. A CTA's items are fixed
+// (round-robin), but its warps take the items' candidates in order from a counter of the CTA as
+// each warp becomes free, so a warp that drew short candidates takes more of them. The
+// preparation kernel has already turned the candidate into its term list (the table-row offsets
+// of its consecutive pairs), which the warp loads while it walks its previous candidate. The
+// chain goes two pairs per step, each step keeping eight 512-byte warp loads in flight (two
+// pairs x four parts; with negative trends one pair, both orders), and the next step's rows
+// prefetched into L2 (prefetches hold no registers); the next candidate's first step is
+// prefetched before the epilogue. A part stops loading once all its words are zero and the walk
+// stops when all are: long chains match no row of most ranges. Larger items amortise the
+// per-item work (the term list, the reductions and atomics of the epilogue) over more rows.
 //
 // Fused overlaps (the fitness's o(c, a) = popcount(M_c & M_a), Methods, "Handling missing
 // values" and the archive rule of the fitness): the warp that has just built a candidate's words
@@ -51,6 +54,8 @@ template <bool NEG, bool BITMAPS, bool OVERLAP>
 __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairArgs p) {
   // per warp: 128 words for the coalesced bitmap store, or its compacted non-zero words
   __shared__ __align__(16) uint32_t stage[kPairWarps][kRangeWords];
+  __shared__ uint32_t next_unit;  // the CTA's next (item, candidate) unit
+  if (threadIdx.x == 0) next_unit = 0u;
   dev::pdl_wait();     // the preparation (checks, zeroed outputs) is complete and visible
   dev::pdl_trigger();  // the finalize launch may be scheduled now; it waits for this grid itself
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -63,7 +68,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   } else if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) {
     return;  // invalid input
   }
-  pair_items<NEG, BITMAPS, OVERLAP>(p, stage[warp]);
+  __syncthreads();  // next_unit is set
+  pair_items<NEG, BITMAPS, OVERLAP>(p, stage[warp], &next_unit);
 }
 
 template <bool NEG, bool BITMAPS>
