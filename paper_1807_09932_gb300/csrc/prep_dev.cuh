@@ -153,17 +153,19 @@ __device__ __forceinline__ uint64_t share_mask(const uint32_t* set,
 }
 
 // The archive's rows (src, [na][W]) copied into rows of `stride` words with zero padding, an
-// even number of rows (dst), by threads tid of nthreads, four loads in flight each.
+// even number of rows (dst), by threads tid of nthreads, eight loads in flight each (so a
+// preparation grid copies a 20-member archive of 436,444 rows in one round of loads).
 __device__ __forceinline__ void copy_archive_padded(const uint32_t* __restrict__ src,
                                                     uint32_t* __restrict__ dst, uint32_t na,
                                                     int64_t W, uint32_t stride, size_t tid,
                                                     size_t nthreads) {
+  constexpr int kInFlight = 8;
   const uint64_t n_pad = (uint64_t)((na + 1u) & ~1u) * stride;
   const bool narrow = n_pad < (1ull << 32);  // 32-bit index arithmetic suffices
-  for (uint64_t i0 = tid; i0 < n_pad; i0 += 4 * nthreads) {
-    uint32_t v[4];
+  for (uint64_t i0 = tid; i0 < n_pad; i0 += kInFlight * nthreads) {
+    uint32_t v[kInFlight];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kInFlight; ++k) {
       const uint64_t i = i0 + k * nthreads;
       uint64_t m, w;
       if (narrow) {
@@ -177,7 +179,7 @@ __device__ __forceinline__ void copy_archive_padded(const uint32_t* __restrict__
       v[k] = i < n_pad && m < na && w < (uint64_t)W ? src[m * (uint64_t)W + w] : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kInFlight; ++k) {
       const uint64_t i = i0 + k * nthreads;
       if (i < n_pad) dst[i] = v[k];
     }
@@ -187,8 +189,9 @@ __device__ __forceinline__ void copy_archive_padded(const uint32_t* __restrict__
 // The fused preparation's work for block `blk` of `nblk` blocks of WARPS warps (see
 // FusedPrepareArgs): checks, term lists, share masks, zeroed outputs and the padded archive copy.
 // Two rounds of global loads: (A) archive offsets, the warp's first candidate's offsets and the
-// archive copy, with every zeroing store; (B) the archive members' columns and the first
-// candidate's columns together, then its check and term list from registers; (C) share masks
+// archive copy, with every zeroing store; (B) the archive members' columns (checked there, when
+// the caller keeps the archive list on the device) and the first candidate's columns together,
+// then its check and term list from registers; (C) share masks
 // (shared memory only), then any further candidates of the warp one by one. Every thread of the
 // block calls it; returns true on a thread that found an invalid list (the caller reduces the
 // verdict over the block).
@@ -229,6 +232,14 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
   uint32_t c_lo = 0, c_hi = 0;
   if (first_sane) load_cols_regs(a.cols, lo0, hi0, lane, c_lo, c_hi);
   const uint32_t atotal = na ? sh.aoff[na] : 0u;
+  // the archive list is checked on the way (when the caller keeps it on the device): offsets, a
+  // column out of range, a column repeated within a member (seen by the atomic OR)
+  bool abad = false;
+  if (a.check_arch)
+    for (uint32_t m = threadIdx.x; m < na; m += blockDim.x) {
+      const uint32_t lo = sh.aoff[m], hi = sh.aoff[m + 1];
+      abad |= !offsets_sane(lo, hi, atotal, m == 0);
+    }
   for (uint32_t t0 = threadIdx.x; t0 < na * (uint32_t)kMaxLen; t0 += 4 * blockDim.x) {
     uint32_t c[4], m[4];
     bool ok[4];
@@ -249,8 +260,15 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (ok[k] && c[k] < (uint32_t)a.ncols)
-        atomicOr(&sh.msets[m[k]][c[k] >> 5], 1u << (c[k] & 31u));
+      if (ok[k]) {
+        if (c[k] < (uint32_t)a.ncols) {
+          const uint32_t bit = 1u << (c[k] & 31u);
+          const bool seen = (atomicOr(&sh.msets[m[k]][c[k] >> 5], bit) & bit) != 0u;
+          abad |= a.check_arch && seen;
+        } else {
+          abad |= a.check_arch;
+        }
+      }
   }
   bool bad = false;
   if (gw < a.n_cand) {
@@ -285,13 +303,10 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
     }
     __syncwarp();  // the set is rebuilt for the next candidate
   }
-  bool abad = false;
-  if (a.check_arch)
-    for (uint32_t i = gw; i < na; i += nwarps)
-      abad |= check_candidate_span(a.acols, sh.aoff[i], sh.aoff[i + 1], atotal, i == 0, a.ncols,
-                                   set, lane);
   // a failure reaches the deferred status only for a list that the caller keeps on the device
-  // (a host list's failure is the host check's to report)
+  // (a host list's failure is the host check's to report); the archive verdict was found by
+  // single threads, so the warp agrees on it first
+  abad = __any_sync(0xFFFFFFFFu, abad);
   if (lane == 0) {
     if (bad && a.status_cand) atomicOr(a.status_cand, kErrInvalid);
     if (abad && a.status_arch) atomicOr(a.status_arch, kErrInvalid);

@@ -174,7 +174,11 @@ def test_invalid_lists_rejected(ebic):
         n = 2
         cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
         fit = torch.zeros(n, dtype=torch.int64, device="cuda")
-        for cc, oo, ac, ao in ((bad_c, bad_o, good_c, good_o), (good_c, good_o, bad_c, bad_o)):
+        far_c, far_o = synth.population_from_lists([[0, 1], [3, C + 7]])  # column out of range
+        gap_c = good_c.copy()
+        gap_o = np.array([0, 2, 1], dtype=np.uint32)                        # offsets go backwards
+        for cc, oo, ac, ao in ((bad_c, bad_o, good_c, good_o), (good_c, good_o, bad_c, bad_o),
+                               (good_c, good_o, far_c, far_o), (good_c, good_o, gap_c, gap_o)):
             rc = ebic.ebic_eval_fitness(m.handle, dev_tensor(cc), dev_tensor(oo), n, 0,
                                         dev_tensor(ac), dev_tensor(ao), dev_tensor(abm), 2,
                                         cnt, None, fit, None)

@@ -141,6 +141,49 @@ def test_rank_export_matches_dense_ranks(ebic):
             assert np.array_equal(got, want)
 
 
+def _near_equal_rows(seed, R, C):
+    """Rows whose values crowd into a few groups of float32 bit patterns one unit apart (so many
+    share all but their lowest key bits), with exact ties, signed zeros, infinities and NaN."""
+    rng = np.random.default_rng(seed)
+    X = np.empty((R, C), dtype=np.float32)
+    for r in range(R):
+        groups = int(rng.integers(1, 5))
+        bases = rng.integers(0x00800000, 0x7F000000, size=groups).astype(np.uint64)
+        bases[rng.random(groups) < 0.4] |= 0x80000000  # negative values
+        pick = rng.integers(0, groups, size=C)
+        spread = int(rng.choice([1, 2, 4, 64, 200]))
+        bits = (bases[pick] + rng.integers(0, spread, size=C).astype(np.uint64)) & 0xFFFFFFFF
+        X[r] = bits.astype(np.uint32).view(np.float32)
+        special = rng.random(C)
+        X[r, special < 0.03] = np.float32(0.0)
+        X[r, (special >= 0.03) & (special < 0.06)] = np.float32(-0.0)
+        X[r, (special >= 0.06) & (special < 0.08)] = np.float32(np.inf)
+        X[r, (special >= 0.08) & (special < 0.10)] = np.float32(np.nan)
+        if r % 7 == 0:
+            X[r, :] = X[r, 0]  # a row of one value
+    return X
+
+
+@pytest.mark.parametrize("C", [2, 5, 31, 32, 33, 48, 64])
+def test_rank_transform_near_equal_values(ebic, C):
+    """The packed-key sort of rows up to 64 columns keeps the top 26 key bits and re-checks ties of
+    them with the full keys: runs of equal values, two values one key unit apart in either order,
+    and longer runs of near-equal values (the exact recount) all give the oracle's dense ranks, and
+    the evaluation on them gives the oracle's counts."""
+    X = _near_equal_rows(C, 1500, C)
+    for exclude in (True, False):
+        with ebic.Matrix(X, exclude_missing=exclude, fill_value=0.0) as m:
+            got = m.ranks()
+            want = oracle.dense_ranks(X, exclude_missing=exclude, fill_value=0.0)
+            assert np.array_equal(got, want)
+            cols, offs = synth.make_population(C + 1, 200, C, 1, min(C, 8))
+            for neg in (False, True):
+                c, b = ebic.eval_population(m, cols, offs, negative=neg, direct=True)
+                ec, eb = oracle.eval_population(X, cols, offs, exclude_missing=exclude,
+                                                fill_value=0.0, negative=neg)
+                assert np.array_equal(c, ec) and np.array_equal(b, eb)
+
+
 @pytest.mark.parametrize("C", [3, 32, 50, 64, 100, 300])
 def test_rank_transform_reads_strided_device_rows(ebic, C):
     # a device matrix whose rows are further apart than its columns (ld > cols) is ranked in place
