@@ -91,6 +91,8 @@ def parse_args():
                    help="default workload: requests per trace of the served leg")
     p.add_argument("--leg-repeats", type=int, default=3,
                    help="default workload: traces of the served leg at --load")
+    p.add_argument("--leg-generations", type=int, default=20,
+                   help="default workload: generations of each ebic_run of the ga leg")
     return p.parse_args()
 
 
@@ -455,6 +457,44 @@ def main():
                        "(the fused route's kernels read and write them in place over the "
                        "host link)"}
 
+    # ---- the rank-code route on the same matrix and populations (context for the other
+    # kernels' roofs): the evaluator with counts and bitmaps, then the overlap kernel and the
+    # fitness; the library's events around each launch, L2 flushed between steps ----
+    rc_steps = 0 if args.no_pairs or args.unfused else min(args.steps, 20)
+    rc_ms = None
+    if rc_steps:
+        def rc_step(i):
+            dc, do, n = dpops[i % N_POPS]
+            rc = ebic.ebic_eval_population(h, dc, do, n, ebic.EBIC_EVAL_DIRECT, counts, bitmaps,
+                                           sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_eval_population")
+            rc = ebic.ebic_fitness(h, dc, do, n, counts, bitmaps, dacols, daoffs, dabm, K, 0,
+                                   fit, None, sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_fitness")
+        for i in range(3):
+            rc_step(i)
+        torch.cuda.synchronize()
+        ebic.ebic_timing_enable(True)
+        for kind in (ebic.EBIC_TIMING_EVALUATE, ebic.EBIC_TIMING_OVERLAP):
+            ebic.ebic_timing_read(kind)
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        rc_tot = 0.0
+        for i in range(rc_steps):
+            flush.fill_(i & 0xFF)
+            a_ev.record(stream)
+            rc_step(i)
+            b_ev.record(stream)
+            torch.cuda.synchronize()
+            rc_tot += a_ev.elapsed_time(b_ev)
+        rc_eval_ms, rc_eval_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_EVALUATE)
+        rc_ov_ms, rc_ov_n = ebic.ebic_timing_read(ebic.EBIC_TIMING_OVERLAP)
+        ebic.ebic_timing_enable(False)
+        rc_ms = rc_tot / rc_steps
+        if m.status() != ebic.EBIC_OK:
+            raise SystemExit("device status error in the rank-code pass")
+
     # ---- roofline of the dominant kernel (the evaluator) ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
@@ -468,7 +508,16 @@ def main():
                                                   not args.unfused, K)
     if eval_n:
         kernels["evaluate"] = roofline_eval(pops, R, m, eval_launch_ms, sms, clk, peaks)
+    # the step's kernel with the largest share is the dominant one; the rank-code route's
+    # kernels (timed beside the step, not in it) are reported among the others
     dominant = max(kernels, key=lambda k: kernels[k]["launch_ms"])
+    if rc_ms is not None:
+        if rc_eval_n:
+            kernels["evaluate (rank-code route)"] = roofline_eval(
+                pops, R, m, rc_eval_ms / rc_eval_n, sms, clk, peaks)
+        if rc_ov_n:
+            kernels["overlap (rank-code route)"] = roofline_overlap(pops, K, m, rc_ov_ms / rc_ov_n,
+                                                                    sms, clk)
     roof = dict(kernels[dominant])
     roof["kernel_role"] = dominant
     roof["other_kernels"] = {k: v for k, v in kernels.items() if k != dominant}
@@ -499,6 +548,13 @@ def main():
                              "each launch on its stream, kernels not chained there",
             "rank_transform_ms": rank_ms,
             "wall_s": wall}
+    if rc_ms is not None:
+        line["rank_code_route"] = {
+            "ms_per_step": rc_ms, "value": float(P) * R / (rc_ms / 1000.0),
+            "steps": rc_steps,
+            "path": "ebic_eval_population (EBIC_EVAL_DIRECT: the rank-code evaluator, counts and "
+                    "bitmaps) + ebic_fitness (overlap kernel, fitness), device buffers, L2 flushed "
+                    "between steps; kernel figures in roofline.other_kernels"}
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -518,6 +574,7 @@ def main():
         torch.cuda.empty_cache()
         line["batched"] = batched_measure(args, args.leg_steps)
         line["served"] = served_measure(args, [args.load], args.leg_requests, args.leg_repeats)
+        line["ga"] = ga_measure(args, args.leg_generations)
         line["legs"] = ("batched: batched_measure, the config of its line; served: "
                         f"served_measure, {args.leg_repeats} traces of {args.leg_requests} "
                         f"requests at {args.load:.2f} x the served capacity, latencies pooled")
@@ -757,6 +814,10 @@ def roofline_eval(pops, R, m, launch_ms, sms, clk, peaks):
 # ---- config 4: batched vs plain per-population launches ----------------------------------------
 
 def ga_workload(args):
+    print(json.dumps(ga_measure(args, args.ga_generations)), flush=True)
+
+
+def ga_measure(args, generations):
     """The whole method on the methylation-shaped matrix: ebic_run (P = 1,600, archive 20,
     candidates of up to 16 columns) with the generation loop on the host and on the device. A step
     is one generation; the line reports ms per generation of each loop and whether their archives
@@ -776,7 +837,7 @@ def ga_workload(args):
         for name, flag in loops.items():
             ebic.ebic_run(m.handle, ebic.ebic_params_default(population=1600, generations=2,
                                                              flags=flag))  # warm-up
-            params = ebic.ebic_params_default(population=1600, generations=args.ga_generations,
+            params = ebic.ebic_params_default(population=1600, generations=generations,
                                               archive_size=20, max_len=16, flags=flag)
             launches0 = ebic.ebic_launch_count()
             torch.cuda.synchronize()
@@ -797,7 +858,7 @@ def ga_workload(args):
         a, b = archives["host"], archives["device"]
         line["same_archive"] = bool(a["members"] == b["members"] and
                                     np.array_equal(a["bitmaps"], b["bitmaps"]))
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def batched_workload(args):

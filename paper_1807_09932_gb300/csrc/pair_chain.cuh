@@ -83,8 +83,9 @@ __device__ __forceinline__ void terms_from_list(const uint16_t* __restrict__ col
 // L2 prefetch of the item segments (kParts parts of kRangeWords words: 2 KB, sixteen 128-byte
 // lines) of two table rows, at word offsets off_a and off_b from `item` (the item's first table
 // word): lanes 0-15 take row a's lines, lanes 16-31 row b's, one line per lane, only in the parts
-// whose bit is set in part_mask. A prefetch holds no register, so a warp keeps the next step's
-// rows on their way from HBM while its registers wait on the current step's.
+// whose bit is set in part_mask. A prefetch holds no register: the pass issues one for the next
+// candidate's first step before the current candidate's epilogue. (Prefetching each chain
+// step's next rows as well measured slower, most for long candidates.)
 __device__ __forceinline__ void prefetch_rows2(const uint32_t* item, uint32_t off_a, bool has_a,
                                                uint32_t off_b, bool has_b, uint32_t part_mask,
                                                int lane) {
@@ -119,20 +120,11 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
     x[q] = y[q] = all;
     nzx[q] = nzy[q] = true;
   }
-  const uint32_t* item = base - 4 * lane;
-  uint32_t parts = (1u << kParts) - 1u;  // parts in which some lane still has a non-zero word
   // terms [t0, t1) with t0 in {0, 32}: lane (i - t0) holds term i's offsets
   auto walk = [&](uint32_t offf, uint32_t offb, int t0, int t1) -> bool {
     for (int i0 = t0; i0 < t1; i0 += kStep) {
       // the next step's rows, prefetched while this step's are loaded (the parts still alive
       // after the previous step: at most one step's rows are fetched in vain)
-      if (!NEG) {  // (measured slower with negative trends: one term per step there)
-        const int j = i0 + kStep;
-        const uint32_t fa = __shfl_sync(0xFFFFFFFFu, offf, j & 31);
-        const uint32_t fb = NEG ? __shfl_sync(0xFFFFFFFFu, offb, j & 31)
-                                : __shfl_sync(0xFFFFFFFFu, offf, (j + 1) & 31);
-        prefetch_rows2(item, fa, j < t1, fb, NEG ? (two && j < t1) : (j + 1 < t1), parts, lane);
-      }
       uint4 v[kStep][kParts], u[kStep][kParts];
 #pragma unroll
       for (int k = 0; k < kStep; ++k) {
@@ -152,22 +144,21 @@ __device__ __forceinline__ void pair_chain(const Terms& t, const uint32_t* base,
                                                                : ones));
         }
       }
-      uint32_t lane_parts = 0;
+      bool lane_any = false;
 #pragma unroll
       for (int q = 0; q < kParts; ++q) {
 #pragma unroll
         for (int k = 0; k < kStep; ++k) x[q] = and4(x[q], v[k][q]);
         nzx[q] = (x[q].x | x[q].y | x[q].z | x[q].w) != 0u;
-        lane_parts |= nzx[q] ? 1u << q : 0u;
+        lane_any |= nzx[q];
         if (NEG && two) {
 #pragma unroll
           for (int k = 0; k < kStep; ++k) y[q] = and4(y[q], u[k][q]);
           nzy[q] = (y[q].x | y[q].y | y[q].z | y[q].w) != 0u;
-          lane_parts |= nzy[q] ? 1u << q : 0u;
+          lane_any |= nzy[q];
         }
       }
-      parts = __reduce_or_sync(0xFFFFFFFFu, lane_parts);
-      if (parts == 0u) return false;  // all zero from here on
+      if (!__any_sync(0xFFFFFFFFu, lane_any)) return false;  // all zero from here on
     }
     return true;
   };
