@@ -80,7 +80,7 @@ SPLITS = {
 
 
 @pytest.mark.parametrize("pairs", [True, False])
-@pytest.mark.parametrize("K", [0, 20, 70])
+@pytest.mark.parametrize("K", [0, 7, 20, 33, 70])
 @pytest.mark.parametrize("split", sorted(SPLITS))
 def test_shards_sum_to_the_whole_matrix(ebic, split, K, pairs):
     R, C = 20011, 40
