@@ -685,7 +685,7 @@ int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uin
     {
       Timed t(EBIC_TIMING_RANK_TRANSFORM, s);
       e = launch_rank_transform(m->L, dx, dld, (flags & EBIC_EXCLUDE_MISSING) ? 1 : 0,
-                                fill_value, m->ranks, s);
+                                fill_value, m->ranks, m->num_sms, s);
     }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform launch"));
   }

@@ -20,6 +20,10 @@
 // a warp prefix count of "first of a new key" flags over the sorted run gives the dense ranks. Ranks are written as bytes/halves into a shared slab tile
 // laid out as the HBM layout (with one padding word per column against bank conflicts), then the
 // tile is copied out with coalesced 32-bit stores, 128*VEC contiguous bytes per column.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
 #include "ebic_internal.h"
 
 namespace ebic {
@@ -273,23 +277,41 @@ __global__ void __launch_bounds__(512) rank_transform_reg_kernel(const float* __
   }
 }
 
-// Rows of at most 64 columns (8-bit codes): one thread per row. A compare-exchange network
-// sorts the thread's (key, column) pairs in registers: Batcher's odd-even merge sort (Batcher,
-// "Sorting networks and their applications", AFIPS 1968), 543 exchanges for 64 keys, 191 for 32,
-// each a compare, a min, a max and two selects, every index fixed at compile time so that the
-// arrays stay in registers. A walk over the sorted run then counts distinct keys and drops each
-// column's dense rank into the slab tile. Each chunk of 128 rows is staged in shared memory by
-// 4-byte cp.async copies (row stride N + 1 words, so that thread t reading its column c hits bank
-// (t + c) mod 32), the next chunk's copies in flight while the current one is sorted.
-__device__ __forceinline__ void compare_exchange(uint32_t& ka, uint32_t& kb, uint32_t& ca,
-                                                 uint32_t& cb) {
-  const bool swap = ka > kb;
-  const uint32_t lo = min(ka, kb), hi = max(ka, kb);
-  const uint32_t c0 = swap ? cb : ca, c1 = swap ? ca : cb;
-  ka = lo;
-  kb = hi;
-  ca = c0;
-  cb = c1;
+// Rows of at most 64 columns (8-bit codes): one thread per row sorts single words, each value's
+// order key with its low B bits (B = log2 N: 6 for 64 columns, 5 for 32) replaced by its column,
+// so that a compare-exchange is one min and one max and the sorted words still carry their
+// columns. The network is Batcher's odd-even merge sort (Batcher, "Sorting networks and their
+// applications", AFIPS 1968): 543 exchanges for 64 keys, 191 for 32, every index fixed at
+// compile time so that the words stay in registers. Words whose top 32 - B bits differ are in
+// the values' order, so the walk over the sorted words gives each column its code, the number of
+// distinct top-bit values up to its word. Two adjacent words with the same top bits hold one
+// value twice (a tie: one code, as the walk gives) or two values within 2^B key units, whose
+// order the sort did not see. A lane whose walk met such a pair hands its sorted words to its
+// warp, which recounts that row from the full keys: lane l takes sorted positions l and 32 + l,
+// a ballot marks each key's first position within its group of equal top bits, and a position's
+// code is 1 + the first positions of lower groups (a popcount) + the distinct keys of its own
+// group below its key (a walk over the group, a few words long). About 1.2 % of the rows of a
+// methylation-shaped matrix (beta values) are recounted, at about a hundred warp instructions
+// each.
+//
+// Keys: adding +0.0 (round to nearest, subnormals kept) folds -0 onto +0 and turns every NaN into
+// the canonical NaN 0x7FFFFFFF, whose key 0xFFFFFFFF is the missing key (exclusion on; with
+// exclusion off it is replaced by the fill value). A negative value's key is its bits inverted,
+// a positive value's its bits with the top bit set. Missing values sort last; the walk counts
+// them as one more value, and their columns, known from a bit mask, get code 0 afterwards.
+//
+// Work: each CTA ranks whole slabs of 512 rows. Warp w takes the slab's 32-row batches w and
+// w + 8 (batch b: rows 128 (b / 4) + 32 (b % 4) + lane), loads each lane's row straight into
+// registers (16-byte loads where the rows allow), and drops the codes as bytes into a shared slab
+// tile laid out [column][chunk][lane], so that lane l always writes bank l, whatever the column;
+// columns C..N-1 take the padding words. The tile is copied out with 16-byte stores into the HBM
+// layout (word 4 l + chunk of a column's 128 words of the slab); two tiles, one barrier per slab.
+// (Staging each warp's next rows in shared memory by cp.async measured no faster: the network,
+// integer-pipe work, is the bound.)
+__device__ __forceinline__ void compare_exchange(uint32_t& a, uint32_t& b) {
+  const uint32_t lo = min(a, b);
+  b = max(a, b);
+  a = lo;
 }
 
 // Batcher's merge of the elements at LO, LO+R, LO+2R, ... below LO+NN, whose two halves are each
@@ -297,128 +319,233 @@ __device__ __forceinline__ void compare_exchange(uint32_t& ka, uint32_t& kb, uin
 // (i, i+R) for i = LO+R, LO+3R, ...
 template <int LO, int NN, int R, int N>
 struct OddEvenMerge {
-  static __device__ __forceinline__ void run(uint32_t (&k)[N], uint32_t (&c)[N]) {
+  static __device__ __forceinline__ void run(uint32_t (&k)[N]) {
     if constexpr (2 * R < NN) {
-      OddEvenMerge<LO, NN, 2 * R, N>::run(k, c);
-      OddEvenMerge<LO + R, NN, 2 * R, N>::run(k, c);
+      OddEvenMerge<LO, NN, 2 * R, N>::run(k);
+      OddEvenMerge<LO + R, NN, 2 * R, N>::run(k);
 #pragma unroll
-      for (int i = LO + R; i + R < LO + NN; i += 2 * R) compare_exchange(k[i], k[i + R], c[i], c[i + R]);
+      for (int i = LO + R; i + R < LO + NN; i += 2 * R) compare_exchange(k[i], k[i + R]);
     } else {
-      compare_exchange(k[LO], k[LO + R], c[LO], c[LO + R]);
+      compare_exchange(k[LO], k[LO + R]);
     }
   }
 };
 
 template <int LO, int NN, int N>
 struct OddEvenSort {
-  static __device__ __forceinline__ void run(uint32_t (&k)[N], uint32_t (&c)[N]) {
+  static __device__ __forceinline__ void run(uint32_t (&k)[N]) {
     if constexpr (NN > 1) {
-      OddEvenSort<LO, NN / 2, N>::run(k, c);
-      OddEvenSort<LO + NN / 2, NN / 2, N>::run(k, c);
-      OddEvenMerge<LO, NN, 1, N>::run(k, c);
+      OddEvenSort<LO, NN / 2, N>::run(k);
+      OddEvenSort<LO + NN / 2, NN / 2, N>::run(k);
+      OddEvenMerge<LO, NN, 1, N>::run(k);
     }
   }
 };
 
-template <int N>
-__device__ __forceinline__ void oddeven_merge_sort(uint32_t (&k)[N], uint32_t (&c)[N]) {
-  OddEvenSort<0, N, N>::run(k, c);
+constexpr int kRankThreads = 256;   // 8 warps a CTA, two CTAs an SM
+constexpr int kRankBlocksPerSM = 2;
+constexpr int kRankSlabRows = 512;  // the 8-bit layout's slab: 4 chunks of 128 rows
+
+// A value's bits as its key sees them: -0 folded onto +0 and every NaN made 0x7FFFFFFF (the sum
+// with +0.0 in round-to-nearest without flushing subnormals), then a NaN replaced by the fill
+// value when exclusion is off. `nan` says whether the value was a NaN.
+template <bool EXCL>
+__device__ __forceinline__ uint32_t value_bits(float x, uint32_t fill_bits, bool& nan) {
+  float y;
+  asm("add.rn.f32 %0, %1, 0f00000000;" : "=f"(y) : "f"(x));
+  const uint32_t b = __float_as_uint(y);
+  nan = b == 0x7FFFFFFFu;
+  return !EXCL && nan ? fill_bits : b;
 }
 
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const float* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+template <bool EXCL>
+__device__ __forceinline__ uint32_t full_key(float x, uint32_t fill_bits) {
+  bool nan;
+  const uint32_t b = value_bits<EXCL>(x, fill_bits, nan);
+  return b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
 }
 
-constexpr int kRowThreads = 128;  // rows per chunk, one per thread
-
-template <int N>
-__global__ void __launch_bounds__(kRowThreads, 3) rank_transform_row_kernel(
-    const float* __restrict__ X, int64_t R, int C, int64_t ld, int exclude, float fill,
+template <int N, bool EXCL, bool VEC16>
+__global__ void __launch_bounds__(kRankThreads, kRankBlocksPerSM) rank_rows_packed_kernel(
+    const float* __restrict__ X, int64_t R, int C, int64_t ld, uint32_t fill_bits,
     uint32_t* __restrict__ out, int64_t Q) {
-  constexpr int VEC = 4, RPG = 128, RPS = RPG * VEC;  // 8-bit codes: 512 rows per slab
-  constexpr int TROW = 32 * VEC + 1;
-  constexpr int SROW = N + 1;
-  constexpr int T = kRowThreads;
-  constexpr uint32_t MISSING = 0u;
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* tile = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* stage =
-      reinterpret_cast<uint32_t*>(smem + (((size_t)C * TROW * 4 + 15) & ~(size_t)15));
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t q = blockIdx.x;
-  const int64_t r_base = q * RPS;
-  // chunk copies: warp w stages rows w, w+4, ..., columns lane, lane+32 (coalesced per row)
-  auto stage_chunk = [&](int cb) {
-    for (int rr = warp; rr < T; rr += T / 32) {
-      const int64_t r = r_base + cb + rr;
-      if (r >= R) break;
-      const float* row = X + r * ld;
+  constexpr int B = N == 64 ? 6 : 5;  // column bits of a word
+  constexpr uint32_t CM = (1u << B) - 1u;
+  constexpr uint32_t kTopMissing = kMissingKey >> B;
+  constexpr int kWarps = kRankThreads / 32;
+  constexpr int tile_words = N * 128;
+  static_assert(N == 32 || N == 64, "packed words carry a 5- or 6-bit column");
+  extern __shared__ __align__(16) uint32_t tiles[];  // two tiles of [N][4 chunks][32 lanes] words
+  __shared__ uint32_t sorted_w[kWarps][N];  // one lane's sorted words, for its warp
+  __shared__ uint32_t sorted_k[kWarps][N];  // the full keys of those words' values
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int buf = 0;
+  for (int64_t q = blockIdx.x; q < Q; q += gridDim.x, buf ^= 1) {
+    uint32_t* tile = tiles + buf * tile_words;
+    for (int b = warp; b < kRankSlabRows / 32; b += kWarps) {
+      const int j = b >> 2, k = b & 3;  // chunk, and the byte of the word
+      const int64_t r0 = q * kRankSlabRows + j * 128 + k * 32;
+      const int64_t r = r0 + lane;
+      const bool live = r < R;  // a padding row is ranked as a row of missing values
+      uint8_t* cell = reinterpret_cast<uint8_t*>(tile + j * 32 + lane) + k;  // + 512 per column
+      const float* row = X + (live ? r : 0) * ld;
+      uint32_t v[N];
+      uint64_t missing = 0;  // columns with a missing value
+      auto word_of = [&](int c, float x) {
+        bool nan;
+        const uint32_t bits = value_bits<EXCL>(x, fill_bits, nan);
+        if (EXCL && nan) missing |= 1ull << c;
+        // (key & ~CM) | c with key = bits ^ (sign ? 0xFFFFFFFF : 0x80000000); the sign is taken
+        // by the multiply pipe (the high word of 2 * bits)
+        const uint32_t sign = __umulhi(bits, 2u);
+        return (bits & ~CM) ^ (sign * (0x7FFFFFFFu & ~CM)) ^ (0x80000000u | (uint32_t)c);
+      };
+      if (VEC16) {
 #pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 32)
-        if (c0 + lane < C) cp_async4(stage + rr * SROW + c0 + lane, row + c0 + lane);
+        for (int c4 = 0; c4 < N / 4; ++c4) {
+          if (4 * c4 < C) {
+            const float4 f = live ? __ldg(reinterpret_cast<const float4*>(row) + c4)
+                                  : make_float4(NAN, NAN, NAN, NAN);
+            v[4 * c4] = word_of(4 * c4, f.x);
+            v[4 * c4 + 1] = word_of(4 * c4 + 1, f.y);
+            v[4 * c4 + 2] = word_of(4 * c4 + 2, f.z);
+            v[4 * c4 + 3] = word_of(4 * c4 + 3, f.w);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[4 * c4 + e] = ~CM | (uint32_t)(4 * c4 + e);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < N; ++c)
+          v[c] = c < C ? word_of(c, live ? __ldg(row + c) : NAN) : (~CM | (uint32_t)c);
+      }
+      if (!EXCL && !live) {  // the fill would rank a padding row: its codes are all missing
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = ~CM | (uint32_t)c;
+        missing = C >= 64 ? ~0ull : ((1ull << C) - 1ull);
+      }
+      OddEvenSort<0, N, N>::run(v);
+      // the walk: code = distinct top-bit values up to this word
+      uint32_t run = 1;
+      cell[(v[0] & CM) * 512] = 1u;
+#pragma unroll
+      for (int p = 1; p < N; ++p) {
+        run += (v[p] ^ v[p - 1]) > CM;
+        cell[(v[p] & CM) * 512] = (uint8_t)run;
+      }
+      // words that repeated their predecessor's top bits: the missing and padding words after the
+      // first of them, and any pair of values within 2^B key units
+      const int n_last = (N - C) + __popcll(missing);
+      const int repeats = N - (int)run - (n_last > 1 ? n_last - 1 : 0);
+      // rare: a lane whose row repeated top bits hands its sorted words to the warp, which
+      // recomputes that row's codes from the full keys (a group of words with the same top bits
+      // may hold ties and values the sort could not order)
+      uint32_t need = __ballot_sync(0xFFFFFFFFu, repeats > 0);
+      while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1u;
+        if (lane == src) {
+#pragma unroll
+          for (int p = 0; p < N; ++p) sorted_w[warp][p] = v[p];
+        }
+        __syncwarp();
+        const float* srow = X + (r0 + src) * ld;
+        uint32_t wp[N / 32], kp[N / 32];
+#pragma unroll
+        for (int h = 0; h < N / 32; ++h) {
+          wp[h] = sorted_w[warp][lane + 32 * h];
+          kp[h] = (wp[h] >> B) == kTopMissing ? kMissingKey
+                                               : full_key<EXCL>(__ldg(srow + (wp[h] & CM)),
+                                                                fill_bits);
+          sorted_k[warp][lane + 32 * h] = kp[h];
+        }
+        __syncwarp();
+        // each position's group (same top bits) start, and whether its key first occurs there
+        int g0[N / 32];
+        uint64_t first = 0;
+#pragma unroll
+        for (int h = 0; h < N / 32; ++h) {
+          const int p = lane + 32 * h;
+          int g = p;
+          while (g > 0 && (sorted_w[warp][g - 1] ^ wp[h]) <= CM) --g;
+          bool f = kp[h] != kMissingKey;
+          for (int i = g; i < p && f; ++i) f = sorted_k[warp][i] != kp[h];
+          g0[h] = g;
+          first |= (uint64_t)__ballot_sync(0xFFFFFFFFu, f) << (32 * h);
+        }
+        uint8_t* scell = reinterpret_cast<uint8_t*>(tile + j * 32 + src) + k;
+#pragma unroll
+        for (int h = 0; h < N / 32; ++h) {
+          // 1 + distinct keys in lower groups + distinct keys of its group below its own
+          uint32_t code = 1u + (uint32_t)__popcll(first & ((1ull << g0[h]) - 1ull));
+          for (int i = g0[h]; i < N && (sorted_w[warp][i] ^ wp[h]) <= CM; ++i)
+            code += ((first >> i) & 1ull) && sorted_k[warp][i] < kp[h];
+          scell[(wp[h] & CM) * 512] = (uint8_t)(kp[h] == kMissingKey ? 0u : code);
+        }
+        __syncwarp();  // the buffers are rewritten for the next lane
+      }
+      while (missing) {
+        const int c = __ffsll((long long)missing) - 1;
+        missing &= missing - 1ull;
+        cell[c * 512] = 0u;
+      }
     }
-    cp_async_commit();
-  };
-  stage_chunk(0);
-  for (int cb = 0; cb < RPS; cb += T) {
-    const int rho = cb + t;
-    const int64_t r = r_base + rho;
-    cp_async_wait_all();
     __syncthreads();
-    uint32_t key[N], col[N];
-#pragma unroll
-    for (int c = 0; c < N; ++c) {
-      key[c] = (c < C && r < R) ? order_key(__uint_as_float(stage[t * SROW + c]), exclude, fill)
-                                : kMissingKey;
-      col[c] = c;
+    // copy out: column c of slab q is 128 contiguous words; word 4 l + j is tile word 32 j + l
+    for (int i = threadIdx.x; i < C * 32; i += kRankThreads) {
+      const int c = i >> 5, l = i & 31;
+      const uint32_t* t = tile + c * 128 + l;
+      const uint4 w = make_uint4(t[0], t[32], t[64], t[96]);
+      *reinterpret_cast<uint4*>(out + ((int64_t)c * Q + q) * 128 + 4 * l) = w;
     }
-    __syncthreads();  // the stage is free: the next chunk's copies overlap this one's sort
-    if (cb + T < RPS) stage_chunk(cb + T);
-    const int j = rho / RPG, rr = rho % RPG, l = rr & 31, k = rr >> 5;
-    uint8_t* cell0 = reinterpret_cast<uint8_t*>(tile) + ((size_t)l * VEC + j) * 4 + k;
-    if (r >= R) {  // padding rows hold the missing code in every column
-      for (int c = 0; c < C; ++c) cell0[(size_t)c * TROW * 4] = (uint8_t)MISSING;
-      continue;
-    }
-    oddeven_merge_sort<N>(key, col);
-    uint32_t run = 0;  // distinct non-missing keys so far: the 1-based dense rank
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-      run += key[p] != kMissingKey && (p == 0 || key[p] != key[p - 1]);
-      if (col[p] < (uint32_t)C)
-        cell0[(size_t)col[p] * TROW * 4] = (uint8_t)(key[p] == kMissingKey ? MISSING : run);
-    }
-  }
-  __syncthreads();
-  // copy out: column c of slab q is 32*VEC contiguous words in HBM
-  constexpr int wpc = 32 * VEC;
-  for (int idx = t; idx < C * wpc; idx += T) {
-    const int c = idx / wpc, i = idx % wpc;
-    out[((int64_t)c * Q + q) * wpc + i] = tile[c * TROW + i];
   }
 }
 
-template <int N>
-cudaError_t launch_rank_row(const Layout& L, const float* dX, int64_t ld, int exclude, float fill,
-                            uint32_t* ranks, cudaStream_t s) {
-  const size_t tile = (((size_t)L.cols * (32 * 4 + 1) * 4) + 15) & ~(size_t)15;
-  const size_t smem = tile + (size_t)kRowThreads * (N + 1) * 4;
-  auto kern = rank_transform_row_kernel<N>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+uint32_t fill_bits_host(float fill) {
+  uint32_t b;
+  std::memcpy(&b, &fill, 4);
+  return b == 0x80000000u ? 0u : b;  // -0 -> +0 (fill is never NaN)
+}
+
+int rank_grid(const Layout& L, int num_sms) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(L.slabs, kRankBlocksPerSM * (int64_t)num_sms));
+}
+
+template <int N, bool EXCL, bool VEC16>
+cudaError_t launch_rank_packed_as(const Layout& L, const float* dX, int64_t ld, float fill,
+                                  uint32_t* ranks, int num_sms, cudaStream_t s) {
+  constexpr size_t smem = (size_t)2 * N * 128 * 4;
+  auto kern = rank_rows_packed_kernel<N, EXCL, VEC16>;
+  static std::atomic<uint64_t> ready{0};  // a bit per device: the attribute is set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev >= 64) return cudaErrorInvalidDevice;
+  if (!((ready.load() >> dev) & 1u)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ready.fetch_or(1ull << dev);
+  }
+  const int grid = rank_grid(L, num_sms);
   count_launch();
-  kern<<<(unsigned)L.slabs, kRowThreads, smem, s>>>(dX, L.rows, L.cols, ld, exclude, fill, ranks,
-                                                    L.slabs);
+  kern<<<grid, kRankThreads, smem, s>>>(dX, L.rows, L.cols, ld, fill_bits_host(fill), ranks,
+                                        L.slabs);
   return cudaGetLastError();
 }
+
+template <int N>
+cudaError_t launch_rank_packed(const Layout& L, const float* dX, int64_t ld, int exclude,
+                               float fill, uint32_t* ranks, int num_sms, cudaStream_t s) {
+  const bool vec16 = ld % 4 == 0 && L.cols % 4 == 0 &&
+                     (reinterpret_cast<uintptr_t>(dX) & 15u) == 0;
+  if (exclude)
+    return vec16 ? launch_rank_packed_as<N, true, true>(L, dX, ld, fill, ranks, num_sms, s)
+                 : launch_rank_packed_as<N, true, false>(L, dX, ld, fill, ranks, num_sms, s);
+  return vec16 ? launch_rank_packed_as<N, false, true>(L, dX, ld, fill, ranks, num_sms, s)
+               : launch_rank_packed_as<N, false, false>(L, dX, ld, fill, ranks, num_sms, s);
+}
+
 
 template <int WIDTH, int VEC, int E>
 cudaError_t launch_rank_reg(const Layout& L, const float* dX, int64_t ld, int exclude, float fill,
@@ -441,10 +568,12 @@ cudaError_t launch_rank_reg(const Layout& L, const float* dX, int64_t ld, int ex
 
 template <int WIDTH, int VEC>
 cudaError_t launch_rank_layout(const Layout& L, const float* dX, int64_t ld, int exclude,
-                               float fill, uint32_t* ranks, cudaStream_t s) {
+                               float fill, uint32_t* ranks, int num_sms, cudaStream_t s) {
   if (WIDTH == 8 && VEC == 4) {
-    if (L.cols <= 32) return launch_rank_row<32>(L, dX, ld, exclude, fill, ranks, s);
-    if (L.cols <= 64) return launch_rank_row<64>(L, dX, ld, exclude, fill, ranks, s);
+    if (L.cols <= 32)
+      return launch_rank_packed<32>(L, dX, ld, exclude, fill, ranks, num_sms, s);
+    if (L.cols <= 64)
+      return launch_rank_packed<64>(L, dX, ld, exclude, fill, ranks, num_sms, s);
   }
   if (L.cols <= 32) return launch_rank_reg<WIDTH, VEC, 1>(L, dX, ld, exclude, fill, ranks, s);
   if (L.cols <= 64) return launch_rank_reg<WIDTH, VEC, 2>(L, dX, ld, exclude, fill, ranks, s);
@@ -471,12 +600,12 @@ cudaError_t launch_rank_layout(const Layout& L, const float* dX, int64_t ld, int
 }  // namespace
 
 cudaError_t launch_rank_transform(const Layout& L, const float* dX, int64_t ld, int exclude,
-                                  float fill, uint32_t* ranks, cudaStream_t s) {
-  if (L.width == 8) return launch_rank_layout<8, 4>(L, dX, ld, exclude, fill, ranks, s);
+                                  float fill, uint32_t* ranks, int num_sms, cudaStream_t s) {
+  if (L.width == 8) return launch_rank_layout<8, 4>(L, dX, ld, exclude, fill, ranks, num_sms, s);
   switch (L.vec) {
-    case 4: return launch_rank_layout<16, 4>(L, dX, ld, exclude, fill, ranks, s);
-    case 2: return launch_rank_layout<16, 2>(L, dX, ld, exclude, fill, ranks, s);
-    case 1: return launch_rank_layout<16, 1>(L, dX, ld, exclude, fill, ranks, s);
+    case 4: return launch_rank_layout<16, 4>(L, dX, ld, exclude, fill, ranks, num_sms, s);
+    case 2: return launch_rank_layout<16, 2>(L, dX, ld, exclude, fill, ranks, num_sms, s);
+    case 1: return launch_rank_layout<16, 1>(L, dX, ld, exclude, fill, ranks, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -166,10 +166,11 @@ def _near_equal_rows(seed, R, C):
 
 @pytest.mark.parametrize("C", [2, 5, 31, 32, 33, 48, 64])
 def test_rank_transform_near_equal_values(ebic, C):
-    """The packed-key sort of rows up to 64 columns keeps the top 26 key bits and re-checks ties of
-    them with the full keys: runs of equal values, two values one key unit apart in either order,
-    and longer runs of near-equal values (the exact recount) all give the oracle's dense ranks, and
-    the evaluation on them gives the oracle's counts."""
+    """Rows of up to 64 columns are sorted on words that keep the top 26 (or 27) key bits beside
+    the column, and rows whose sort could not order two values are ranked again exactly: runs of
+    equal values, two values one key unit apart in either order, and longer runs of near-equal
+    values all give the oracle's dense ranks, and the evaluation on them gives the oracle's
+    counts."""
     X = _near_equal_rows(C, 1500, C)
     for exclude in (True, False):
         with ebic.Matrix(X, exclude_missing=exclude, fill_value=0.0) as m:
@@ -184,12 +185,14 @@ def test_rank_transform_near_equal_values(ebic, C):
                 assert np.array_equal(c, ec) and np.array_equal(b, eb)
 
 
-@pytest.mark.parametrize("C", [3, 32, 50, 64, 100, 300])
-def test_rank_transform_reads_strided_device_rows(ebic, C):
+@pytest.mark.parametrize("pad", [7, 4])
+@pytest.mark.parametrize("C", [3, 32, 48, 50, 64, 100, 300])
+def test_rank_transform_reads_strided_device_rows(ebic, C, pad):
     # a device matrix whose rows are further apart than its columns (ld > cols) is ranked in place
+    # (pad 4 keeps rows of a multiple of four columns on 16-byte boundaries: the vector loads)
     import torch
     from pins import tiny_matrix
-    R, pad = 1100, 7
+    R = 1100
     Xw = tiny_matrix(C + 11, R, C + pad, nan_frac=0.05)
     Xw[:, : C // 2] += np.random.default_rng(C).standard_normal((R, C // 2)).astype(np.float32)
     dXw = torch.from_numpy(Xw).cuda()
@@ -200,6 +203,65 @@ def test_rank_transform_reads_strided_device_rows(ebic, C):
     finally:
         ebic.ebic_free_matrix(h)
     want = oracle.dense_ranks(np.ascontiguousarray(Xw[:, :C]), exclude_missing=True, fill_value=0.0)
+    assert np.array_equal(got, want)
+
+
+def test_rank_transform_every_nan_pattern(ebic):
+    """Every float32 NaN bit pattern (both signs, quiet and signalling payloads) is a missing value
+    with exclusion on and takes the fill value's code with exclusion off, beside real values."""
+    pos = np.arange(0x7F800001, 0x80000000, dtype=np.uint64)
+    nans = np.concatenate([pos, pos | 0x80000000]).astype(np.uint32)
+    per_row = 48
+    R = (nans.size + per_row - 1) // per_row
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((R, 64)).astype(np.float32)
+    flat = np.full(R * per_row, 0x7FC00000, np.uint32)
+    flat[:nans.size] = nans
+    X[:, :per_row] = flat.reshape(R, per_row).view(np.float32)
+    with ebic.Matrix(X, exclude_missing=True) as m:
+        got = m.ranks()
+    assert (got[:, :per_row] == 0xFFFF).all()
+    sample = rng.choice(R, 3000, replace=False)
+    want = oracle.dense_ranks(np.ascontiguousarray(X[sample]), exclude_missing=True)
+    assert np.array_equal(got[sample], want)
+    with ebic.Matrix(X, exclude_missing=False, fill_value=0.25) as m:
+        got = m.ranks()
+    assert (got[:, :per_row] == got[:, :1]).all()
+    want = oracle.dense_ranks(np.ascontiguousarray(X[sample]), exclude_missing=False,
+                              fill_value=0.25)
+    assert np.array_equal(got[sample], want)
+
+
+@pytest.mark.parametrize("C", [17, 32, 64])
+def test_rank_transform_subnormals_and_signed_zeros(ebic, C):
+    """Subnormals of both signs, the smallest normals, and both zeros keep their order and ties."""
+    rng = np.random.default_rng(C)
+    bits = np.concatenate([
+        rng.integers(1, 0x00800000, size=8).astype(np.uint32),             # positive subnormals
+        rng.integers(1, 0x00800000, size=8).astype(np.uint32) | 0x80000000,  # negative subnormals
+        np.array([0x00800000, 0x80800000, 0x00000000, 0x80000000, 0x00000001, 0x80000001],
+                 np.uint32)])
+    X = bits[rng.integers(0, bits.size, size=(5000, C))].view(np.float32)
+    for exclude in (True, False):
+        with ebic.Matrix(X, exclude_missing=exclude, fill_value=-0.0) as m:
+            got = m.ranks()
+        want = oracle.dense_ranks(X, exclude_missing=exclude, fill_value=-0.0)
+        assert np.array_equal(got, want)
+
+
+def test_rank_transform_many_slabs_per_cta(ebic):
+    """A matrix of several slabs per CTA of the ranking launch (330,001 rows of 64 beta values,
+    one row in twenty near-equal), on device memory: each CTA's list of rows to rank exactly is
+    kept apart and every row gets the oracle's ranks."""
+    import torch
+    R, C = 330001, 64
+    ds = synth.make_dataset(5, R, C, kind="beta", planted=[(4000, 8, False)], nan_frac=0.01)
+    X = ds.X.copy()
+    rows = np.random.default_rng(6).choice(R, R // 20, replace=False)
+    X[rows] = _near_equal_rows(7, rows.size, C)
+    with ebic.Matrix(torch.from_numpy(X).cuda(), exclude_missing=True) as m:
+        got = m.ranks()
+    want = oracle.dense_ranks(X, exclude_missing=True)
     assert np.array_equal(got, want)
 
 
