@@ -325,8 +325,11 @@ __device__ __forceinline__ void item_epilogue(const PairArgs& p, uint32_t cand, 
 // short candidates takes more of them and the CTA ends when its work ends, not when its unluckiest
 // warp does. The units of one item still run side by side on one SM, so the table rows they
 // share meet in its L1.
-template <bool NEG, bool BITMAPS, bool OVERLAP>
-__device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st, uint32_t* next_unit) {
+// `valid()` (warp-uniform) is asked after the warp's first term list is requested and before any
+// table row is read; false ends the pass.
+template <bool NEG, bool BITMAPS, bool OVERLAP, class Valid>
+__device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st, uint32_t* next_unit,
+                                           Valid valid) {
   const int lane = threadIdx.x & 31;
   const uint32_t n_ranges = (uint32_t)((p.W + kItemWords - 1) / kItemWords);
   const uint32_t n_groups = (p.n_cand + kPairWarps - 1) / kPairWarps;
@@ -364,6 +367,7 @@ __device__ __forceinline__ void pair_items(const PairArgs& p, uint32_t* st, uint
   Unit cur = take();
   Terms next;
   if (cur.it < n_items && cur.cand < p.n_cand) load_terms<NEG>(p, cur.cand, lane, next);
+  if (!valid()) return;
   while (cur.it < n_items) {
     const uint64_t rword = (uint64_t)cur.range * kItemWords;  // first word of the item
     const uint32_t cand = cur.cand;

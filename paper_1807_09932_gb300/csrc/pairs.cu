@@ -59,17 +59,21 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_eval_kernel(const PairAr
   dev::pdl_wait();     // the preparation (checks, zeroed outputs) is complete and visible
   dev::pdl_trigger();  // the finalize launch may be scheduled now; it waits for this grid itself
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (p.flags) {  // the preparation's per-block verdicts; CTA 0 records the call's error word
-    uint32_t f = 0;
+  // the preparation's verdicts (per block, or the call's error word), requested here and checked
+  // once the warp's first term list is requested too: the two loads are in flight together, and
+  // no table row is read before the check
+  uint32_t f = 0;
+  if (p.flags) {
     for (uint32_t i = lane; i < p.n_flags; i += 32) f |= p.flags[i];
-    f = __reduce_or_sync(0xFFFFFFFFu, f);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.err_out = f;
-    if (f) return;  // invalid input
-  } else if (*reinterpret_cast<const volatile uint32_t*>(p.err) != 0) {
-    return;  // invalid input
+  } else if (lane == 0) {
+    f = *reinterpret_cast<const volatile uint32_t*>(p.err);
   }
   __syncthreads();  // next_unit is set
-  pair_items<NEG, BITMAPS, OVERLAP>(p, stage[warp], &next_unit);
+  pair_items<NEG, BITMAPS, OVERLAP>(p, stage[warp], &next_unit, [&]() {
+    f = __reduce_or_sync(0xFFFFFFFFu, f);
+    if (p.flags && blockIdx.x == 0 && threadIdx.x == 0) *p.err_out = f;  // CTA 0 records it
+    return f == 0u;  // else invalid input: nothing is evaluated
+  });
 }
 
 template <bool NEG, bool BITMAPS>
