@@ -685,12 +685,19 @@ int ebic_load_matrix(const float* x, int64_t rows, int32_t cols, int64_t ld, uin
     {
       Timed t(EBIC_TIMING_RANK_TRANSFORM, s);
       e = launch_rank_transform(m->L, dx, dld, (flags & EBIC_EXCLUDE_MISSING) ? 1 : 0,
-                                fill_value, m->ranks, m->num_sms, s);
+                                fill_value, m->ranks, m->status, m->num_sms, s);
     }
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform launch"));
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform"));
+  {  // a bounded wait of the transform that expired leaves the matrix unusable
+    uint32_t bits = 0;
+    e = cudaMemcpy(&bits, m->status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "rank transform status"));
+    if (bits & kErrTimeout)
+      return cleanup(fail(EBIC_ERR_DEVICE_TIMEOUT, "rank transform: a bounded device wait expired"));
+  }
   *out = m;
   return EBIC_OK;
 }

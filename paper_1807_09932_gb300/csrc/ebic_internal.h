@@ -61,9 +61,11 @@ void count_launches(int64_t n);  // n kernels at once (a negative n takes back c
 Layout make_layout(int64_t rows, int32_t cols);
 
 // ---- rank transform ------------------------------------------------------------------------
-// `num_sms`: the device's SM count (the ranking grid of rows up to 64 columns).
+// `num_sms`: the device's SM count (the ranking grid of rows up to 64 columns); `status`: a
+// device word that receives kErrTimeout if a bounded wait of the transform expired.
 cudaError_t launch_rank_transform(const Layout& L, const float* dX, int64_t ld, int exclude,
-                                  float fill, uint32_t* ranks, int num_sms, cudaStream_t s);
+                                  float fill, uint32_t* ranks, uint32_t* status, int num_sms,
+                                  cudaStream_t s);
 
 // ---- population preparation (device-side argument checks, zeroing) ----------------------------
 // One launch checks up to two CSR candidate lists (n[l] == 0 skips list l) against ncols and
