@@ -1081,6 +1081,7 @@ static int eval_fitness_impl(const ebic_matrix* cm, const uint16_t* cols, const 
     pa.flags = dflags;
     pa.status_cand = host_c ? nullptr : m->status;  // host lists: the host check reports
     pa.status_arch = host_a ? nullptr : m->status;
+    pa.table = m->pairs;
     EBIC_CUDA(launch_fused_prepare(pa, prep_blocks, s));
   }
   {

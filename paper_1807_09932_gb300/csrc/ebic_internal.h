@@ -219,6 +219,9 @@ struct FusedPrepareArgs {
   uint32_t* flags = nullptr;           // [blocks]: each block stores kErrInvalid or 0
   uint32_t* status_cand = nullptr;     // ORed with kErrInvalid when the candidate list fails
   uint32_t* status_arch = nullptr;     // ... when the archive list fails (null: not reported)
+  // the pair table (or null): each candidate's first chain step in the first two row ranges is
+  // prefetched into L2 for the pass's first wave
+  const uint32_t* table = nullptr;
 };
 // Blocks of the fused preparation launch (and so the number of its flags).
 uint32_t fused_prepare_blocks(uint32_t n_cand, uint32_t n_arch, uint32_t stride, int num_sms);

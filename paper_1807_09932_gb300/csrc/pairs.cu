@@ -29,7 +29,9 @@
 // of its consecutive pairs), which the warp loads while it walks its previous candidate. The
 // chain goes two pairs per step, each step keeping eight 512-byte warp loads in flight (two
 // pairs x four parts; with negative trends one pair, both orders); the next candidate's first
-// step is prefetched into L2 before the epilogue (a prefetch holds no registers). A part stops
+// step is prefetched into L2 before the epilogue (a prefetch holds no registers), and the
+// preparation kernel, which builds the term lists while DRAM is otherwise idle, prefetches every
+// candidate's first step in the first two ranges, the rows of the pass's first wave. A part stops
 // loading once all its words are zero and the walk
 // stops when all are: long chains match no row of most ranges. Larger items amortise the
 // per-item work (the term list, the reductions and atomics of the epilogue) over more rows.

@@ -278,6 +278,23 @@ __device__ bool fused_prepare_body(const FusedPrepareArgs& a, PrepShared<WARPS>&
       bad = cols_bad_regs(c_lo, c_hi, L, a.ncols, set, lane);
       build_terms_regs(c_lo, c_hi, (int)L, (uint32_t)a.ncols, a.stride, a.negative,
                        a.terms + (size_t)gw * slots, lane);
+      if (a.table && !bad && !a.negative) {
+        // the first chain step (terms 0 and 1) of the candidate's first two 16,384-row ranges:
+        // lanes 0-15 the lines of term 0's rows, lanes 16-31 term 1's (the pass reads them first)
+        const uint32_t n_lo = __shfl_down_sync(0xFFFFFFFFu, c_lo, 1);
+        const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, c_hi, 0);
+        const uint32_t nxt = lane == 31 ? h0 : n_lo;
+        const uint32_t term = (L == 1 ? c_lo * (uint32_t)a.ncols + c_lo
+                                      : c_lo * (uint32_t)a.ncols + nxt) * a.stride;
+        const uint32_t t0 = __shfl_sync(0xFFFFFFFFu, term, 0);
+        const uint32_t t1 = __shfl_sync(0xFFFFFFFFu, term, 1);
+        const bool has = lane < 16 || L > 2;
+        const uint32_t* row = a.table + (lane < 16 ? t0 : t1) + (lane & 15) * 32;
+        if (has) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+          if (a.W > 512) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 512));
+        }
+      }
     }
   }
   __syncthreads();
