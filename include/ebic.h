@@ -483,6 +483,17 @@ int ebic_free_text_matrix(ebic_text_matrix* m);
 int ebic_write_biclusters(const char* path, const char* title, const ebic_result* r,
                           const ebic_text_matrix* names);
 
+/* ---- staging ---------------------------------------------------------------------------- */
+/* A copy of `bytes` bytes from src to dst, ordered on `stream` (cudaMemcpyDefault: either side
+ * may be device memory, pinned host memory or pageable host memory). The paper has no
+ * counterpart. A caller that packs many requests' lists into one buffer uses it to move them, or
+ * the requests' outputs, in one copy without a framework's tensor calls. Pinned and device
+ * buffers: asynchronous on `stream`, and both must stay valid until the stream reaches the
+ * copy. Pageable host memory: the call returns once the host side has been read or written.
+ * bytes == 0 does nothing. Returns EBIC_ERR_INVALID_ARG for a NULL buffer and EBIC_ERR_CUDA
+ * when the runtime rejects the copy. */
+int ebic_copy_async(void* dst, const void* src, size_t bytes, void* stream);
+
 /* ---- diagnostics ----------------------------------------------------------------------- */
 /* Kernels launched by this library in this process so far (every launch is counted). */
 int64_t ebic_launch_count(void);

@@ -1154,6 +1154,14 @@ int ebic_matrix_status(ebic_matrix* m, void* stream) {
   return status_code(bits, "deferred device status");
 }
 
+int ebic_copy_async(void* dst, const void* src, size_t bytes, void* stream) {
+  if (bytes == 0) return EBIC_OK;
+  if (!dst || !src) return fail(EBIC_ERR_INVALID_ARG, "copy: NULL buffer");
+  EBIC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault,
+                            static_cast<cudaStream_t>(stream)));
+  return EBIC_OK;
+}
+
 int64_t ebic_launch_count(void) { return g_launches.load(); }
 
 int ebic_timing_enable(int on) {

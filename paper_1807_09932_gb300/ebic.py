@@ -94,6 +94,7 @@ _lib_build_pairs = _sig("ebic_matrix_build_pairs", [_P, ctypes.c_uint64, _P,
 _lib_drop_pairs = _sig("ebic_matrix_drop_pairs", [_P])
 _lib_last_error = _sig("ebic_last_error", [], ctypes.c_char_p)
 _lib_launch_count = _sig("ebic_launch_count", [], ctypes.c_int64)
+_lib_copy_async = _sig("ebic_copy_async", [_P, _P, ctypes.c_size_t, _P])
 _lib_timing_enable = _sig("ebic_timing_enable", [ctypes.c_int])
 _lib_timing_read = _sig("ebic_timing_read", [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(_I64)])
@@ -352,6 +353,12 @@ EBIC_TIMING_KINDS = 6
 
 def ebic_launch_count():
     return int(_lib_launch_count())
+
+
+def ebic_copy_async(dst, src, nbytes, stream=None):
+    """A stream-ordered copy of nbytes bytes between any two buffers (addresses, arrays or
+    tensors); see include/ebic.h."""
+    return _lib_copy_async(_ptr(dst), _ptr(src), nbytes, _stream(stream))
 
 
 def ebic_timing_enable(on):

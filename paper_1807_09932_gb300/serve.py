@@ -216,8 +216,61 @@ class GpuBackend:
         self.pair_budget = int(pair_budget)
         self.dev = torch.device("cuda", device)
         self.runs = {}
+        # each slot stages a whole batch: every request's lists packed into one pinned buffer and
+        # sent with one copy, every request's counts and fitness brought back with one copy
         self.slots = [dict(stream=torch.cuda.Stream(self.dev), batch=ebic.ebic_batch_create(max_batch),
-                           busy=False) for _ in range(max_inflight)]
+                           busy=False, event=torch.cuda.Event(), hin=None, din=None, hout=None,
+                           dout=None) for _ in range(max_inflight)]
+        # the plain arm's pinned lists and outputs, read and written in place by the fused call
+        self.plain_io = dict(hin=None, hout=None)
+
+    _ALIGN = 256  # every staged array starts on this boundary
+
+    @classmethod
+    def _layout(cls, reqs):
+        """Byte offsets of each request's columns and offsets in the input staging, and of its
+        counts (uint32) and fitness (uint64) in the output staging; the two sizes."""
+        a = cls._ALIGN
+
+        def up(x):
+            return (x + a - 1) // a * a
+
+        ins, outs, i_off, o_off = [], [], 0, 0
+        for r in reqs:
+            n = r.n_cand
+            oc = i_off
+            i_off = up(i_off + 2 * int(r.offsets[-1]))
+            oo = i_off
+            i_off = up(i_off + 4 * (n + 1))
+            ins.append((oc, oo))
+            cnt = o_off
+            o_off = up(o_off + 4 * n)
+            fit = o_off
+            o_off = up(o_off + 8 * n)
+            outs.append((cnt, fit))
+        return ins, outs, max(i_off, a), max(o_off, a)
+
+    def _pinned(self, nbytes):
+        t = self.torch.empty(nbytes, dtype=self.torch.uint8).pin_memory()
+        return t, t.numpy()
+
+    def _staging(self, slot, in_bytes, out_bytes):
+        """The slot's staging buffers, grown (never shrunk) to the sizes asked for."""
+        torch = self.torch
+        if slot["hin"] is None or slot["hin"][0].numel() < in_bytes:
+            slot["hin"] = self._pinned(2 * in_bytes)
+            slot["din"] = torch.empty(2 * in_bytes, dtype=torch.uint8, device=self.dev)
+        if slot["hout"] is None or slot["hout"][0].numel() < out_bytes:
+            slot["hout"] = self._pinned(2 * out_bytes)
+            slot["dout"] = torch.empty(2 * out_bytes, dtype=torch.uint8, device=self.dev)
+
+    @staticmethod
+    def _pack(hin_np, reqs, ins):
+        for r, (oc, oo) in zip(reqs, ins):
+            c = np.ascontiguousarray(r.cols, dtype=np.uint16).view(np.uint8)
+            o = np.ascontiguousarray(r.offsets, dtype=np.uint32).view(np.uint8)
+            hin_np[oc:oc + c.size] = c
+            hin_np[oo:oo + o.size] = o
 
     def close(self):
         for s in self.slots:
@@ -243,8 +296,10 @@ class GpuBackend:
         if 0 < pb <= self.pair_budget:
             rank_bytes += pb
         k = 0 if spec.archive_offsets is None else len(spec.archive_offsets) - 1
-        per_run = (spec.max_cand * (spec.max_len * 2 + 4 + 4 + 8 + W * 4)
-                   + k * (W * 4 + 64 * 2 + 4) + 4096)
+        # row bitmaps for the fitness call when the run has no pair table; the archive's lists
+        # and bitmaps (the requests' lists and outputs live in the shared batch staging)
+        per_run = (0 if 0 < pb <= self.pair_budget else spec.max_cand * W * 4) \
+            + k * (W * 4 + 64 * 2 + 4) + 4096
         return int(rank_bytes + per_run)
 
     def now(self):
@@ -258,16 +313,10 @@ class GpuBackend:
             m.build_pairs(max_bytes=self.pair_budget)
         W = m.words
         P = spec.max_cand
+        # the rank-code pass writes row bitmaps for the fitness call; pair-table runs need none
         run = dict(m=m, P=P, W=W, rows=spec.X.shape[0], pairs=pairs,
-                   dcols=torch.empty(P * spec.max_len, dtype=torch.int16, device=self.dev),
-                   doffs=torch.empty(P + 1, dtype=torch.int32, device=self.dev),
-                   counts=torch.empty(P, dtype=torch.int32, device=self.dev),
-                   bitmaps=torch.empty((P, W), dtype=torch.int32, device=self.dev),
-                   fit=torch.empty(P, dtype=torch.int64, device=self.dev),
-                   hcols=torch.empty(P * spec.max_len, dtype=torch.int16).pin_memory(),
-                   hoffs=torch.empty(P + 1, dtype=torch.int32).pin_memory(),
-                   hcounts=torch.empty(P, dtype=torch.int32).pin_memory(),
-                   hfit=torch.empty(P, dtype=torch.int64).pin_memory())
+                   bitmaps=None if pairs else torch.empty((P, W), dtype=torch.int32,
+                                                          device=self.dev))
         # resident archive: its members scored once on this matrix
         if spec.archive_offsets is not None and len(spec.archive_offsets) > 1:
             ac, ao = spec.archive_cols, spec.archive_offsets
@@ -289,102 +338,99 @@ class GpuBackend:
         run["m"].close()
 
     def launch(self, reqs):
-        torch, ebic = self.torch, self.ebic
+        ebic = self.ebic
         slot = next(s for s in self.slots if not s["busy"])
         slot["busy"] = True
         st = slot["stream"]
+        sp = st.cuda_stream
+        ins, outs, in_bytes, out_bytes = self._layout(reqs)
+        self._staging(slot, in_bytes, out_bytes)
+        self._pack(slot["hin"][1], reqs, ins)
+        hin = slot["hin"][0].data_ptr()
+        din, dout = slot["din"].data_ptr(), slot["dout"].data_ptr()
         if len(reqs) == 1 and self.runs[reqs[0].run_id]["pairs"]:
             # a batch of one: the per-population fused call (three launches) costs less than the
-            # batch graph's fixed launches, with the same results
+            # batch graph's fixed launches, with the same results; its kernels read the pinned
+            # lists in place, so nothing is uploaded
             r = reqs[0]
             run = self.runs[r.run_id]
-            n, tot = r.n_cand, int(r.offsets[-1])
-            with torch.cuda.stream(st):
-                run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
-                run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
-                run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
-                run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
-                rc = ebic.ebic_eval_fitness(run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
-                                            run["acols"], run["aoffs"], run["abm"], run["K"],
-                                            run["counts"], None, run["fit"], None, st.cuda_stream)
-                if rc:
-                    raise ebic.EbicError(rc, "ebic_eval_fitness")
-                run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
-                run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(st)
-            return dict(slot=slot, event=ev)
-        items = []
-        with torch.cuda.stream(st):
-            for r in reqs:
-                run = self.runs[r.run_id]
-                n, tot = r.n_cand, int(r.offsets[-1])
-                run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
-                run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
-                run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
-                run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
-                if run["pairs"]:  # fitness inside the batch, the overlaps fused there
-                    k = run["K"]
-                    items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
-                                  run["counts"], None, run["acols"] if k else None,
-                                  run["aoffs"] if k else None, run["abm"] if k else None, k,
-                                  run["fit"]))
-                else:
-                    items.append((run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
-                                  run["counts"], run["bitmaps"]))
-            arr = ebic.make_requests(items)
-            rc = ebic.ebic_batch_run(slot["batch"], arr, len(items), st.cuda_stream)
-            if rc:
-                raise ebic.EbicError(rc, "ebic_batch_run")
-            for r in reqs:
-                run = self.runs[r.run_id]
-                n = r.n_cand
-                if not run["pairs"]:  # the rank-code pass wrote bitmaps: the fitness call
-                    rc = ebic.ebic_fitness(run["m"].handle, run["dcols"], run["doffs"], n,
-                                           run["counts"], run["bitmaps"], run["acols"],
-                                           run["aoffs"], run["abm"], run["K"], 0, run["fit"],
-                                           None, st.cuda_stream)
-                    if rc:
-                        raise ebic.EbicError(rc, "ebic_fitness")
-                run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
-                run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(st)
-        return dict(slot=slot, event=ev)
-
-    def done(self, token):
-        return token["event"].query()
-
-    def collect(self, token, reqs):
-        token["event"].synchronize()
-        token["slot"]["busy"] = False
-        for r in reqs:
-            run = self.runs[r.run_id]
-            n = r.n_cand
-            r.counts = run["hcounts"][:n].numpy().view(np.uint32).copy()
-            r.fitness = run["hfit"][:n].numpy().view(np.uint64).copy()
-
-    # the comparison point: one request at a time, one per-population call (ebic_eval_fitness)
-    def plain(self, r, stream):
-        torch, ebic = self.torch, self.ebic
-        run = self.runs[r.run_id]
-        n, tot = r.n_cand, int(r.offsets[-1])
-        with torch.cuda.stream(stream):
-            run["hcols"][:tot].numpy()[:] = r.cols.view(np.int16)
-            run["hoffs"][:n + 1].numpy()[:] = r.offsets.view(np.int32)
-            run["dcols"][:tot].copy_(run["hcols"][:tot], non_blocking=True)
-            run["doffs"][:n + 1].copy_(run["hoffs"][:n + 1], non_blocking=True)
-            rc = ebic.ebic_eval_fitness(run["m"].handle, run["dcols"], run["doffs"], n, r.flags,
+            (oc, oo), (cnt, fit) = ins[0], outs[0]
+            rc = ebic.ebic_eval_fitness(run["m"].handle, hin + oc, hin + oo, r.n_cand, r.flags,
                                         run["acols"], run["aoffs"], run["abm"], run["K"],
-                                        run["counts"], None, run["fit"], None,
-                                        stream.cuda_stream)
+                                        dout + cnt, None, dout + fit, None, sp)
             if rc:
                 raise ebic.EbicError(rc, "ebic_eval_fitness")
-            run["hcounts"][:n].copy_(run["counts"][:n], non_blocking=True)
-            run["hfit"][:n].copy_(run["fit"][:n], non_blocking=True)
-        stream.synchronize()
-        r.counts = run["hcounts"][:n].numpy().view(np.uint32).copy()
-        r.fitness = run["hfit"][:n].numpy().view(np.uint64).copy()
+        else:
+            items = []
+            for r, (oc, oo), (cnt, fit) in zip(reqs, ins, outs):
+                run = self.runs[r.run_id]
+                if run["pairs"]:  # fitness inside the batch, the overlaps fused there
+                    k = run["K"]
+                    items.append((run["m"].handle, din + oc, din + oo, r.n_cand, r.flags,
+                                  dout + cnt, None, run["acols"] if k else None,
+                                  run["aoffs"] if k else None, run["abm"] if k else None, k,
+                                  dout + fit))
+                else:
+                    items.append((run["m"].handle, din + oc, din + oo, r.n_cand, r.flags,
+                                  dout + cnt, run["bitmaps"]))
+            rc = ebic.ebic_copy_async(din, hin, in_bytes, sp)  # every list in one copy
+            if rc:
+                raise ebic.EbicError(rc, "ebic_copy_async")
+            rc = ebic.ebic_batch_run(slot["batch"], ebic.make_requests(items), len(items), sp)
+            if rc:
+                raise ebic.EbicError(rc, "ebic_batch_run")
+            for r, (oc, oo), (cnt, fit) in zip(reqs, ins, outs):
+                run = self.runs[r.run_id]
+                if not run["pairs"]:  # the rank-code pass wrote bitmaps: the fitness call
+                    rc = ebic.ebic_fitness(run["m"].handle, din + oc, din + oo, r.n_cand,
+                                           dout + cnt, run["bitmaps"], run["acols"],
+                                           run["aoffs"], run["abm"], run["K"], 0, dout + fit,
+                                           None, sp)
+                    if rc:
+                        raise ebic.EbicError(rc, "ebic_fitness")
+        # every request's counts and fitness back in one copy
+        rc = ebic.ebic_copy_async(slot["hout"][0].data_ptr(), dout, out_bytes, sp)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_copy_async")
+        slot["event"].record(st)
+        return dict(slot=slot, outs=outs)
+
+    def done(self, token):
+        return token["slot"]["event"].query()
+
+    def collect(self, token, reqs):
+        slot = token["slot"]
+        slot["event"].synchronize()
+        hout = slot["hout"][1]
+        for r, (cnt, fit) in zip(reqs, token["outs"]):
+            n = r.n_cand
+            r.counts = hout[cnt:cnt + 4 * n].view(np.uint32).copy()
+            r.fitness = hout[fit:fit + 8 * n].view(np.uint64).copy()
+        slot["busy"] = False
+
+    # the comparison point: one request at a time, one per-population call (ebic_eval_fitness);
+    # its lists and outputs are pinned host memory that the call's kernels read and write in
+    # place (a call with host outputs returns once they are written)
+    def plain(self, r, stream):
+        ebic = self.ebic
+        run = self.runs[r.run_id]
+        ins, outs, in_bytes, out_bytes = self._layout([r])
+        io = self.plain_io
+        if io["hin"] is None or io["hin"][0].numel() < in_bytes:
+            io["hin"] = self._pinned(2 * in_bytes)
+        if io["hout"] is None or io["hout"][0].numel() < out_bytes:
+            io["hout"] = self._pinned(2 * out_bytes)
+        self._pack(io["hin"][1], [r], ins)
+        hin, hout = io["hin"][0].data_ptr(), io["hout"][0].data_ptr()
+        (oc, oo), (cnt, fit) = ins[0], outs[0]
+        rc = ebic.ebic_eval_fitness(run["m"].handle, hin + oc, hin + oo, r.n_cand, r.flags,
+                                    run["acols"], run["aoffs"], run["abm"], run["K"],
+                                    hout + cnt, None, hout + fit, None, stream.cuda_stream)
+        if rc:
+            raise ebic.EbicError(rc, "ebic_eval_fitness")
+        h = io["hout"][1]
+        r.counts = h[cnt:cnt + 4 * r.n_cand].view(np.uint32).copy()
+        r.fitness = h[fit:fit + 8 * r.n_cand].view(np.uint64).copy()
 
 
 def plain_serve(backend, arrivals, rows_of, stream):

@@ -85,6 +85,17 @@ def test_calls_reject_null_matrix(lib):
     assert lib.ebic_free_matrix(None) == 0
 
 
+def test_copy_rejects_null_buffers_and_skips_empty_copies(lib):
+    P = ctypes.c_void_p
+    f = lib.ebic_copy_async
+    f.argtypes = [P, P, ctypes.c_size_t, P]
+    buf = np.zeros(4, np.uint8)
+    assert f(None, buf.ctypes.data, 4, None) == -1
+    assert f(buf.ctypes.data, None, 4, None) == -1
+    assert "NULL" in _last_error(lib)
+    assert f(None, None, 0, None) == 0  # nothing to copy: no runtime call
+
+
 def test_no_device_is_reported_not_crashed(lib):
     try:
         import torch

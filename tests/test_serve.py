@@ -136,5 +136,13 @@ def test_served_results_equal_alone(pair_budget, spacing):
             assert np.array_equal(r.fitness, f)
             ec, eb = oracle.eval_population(s.X, r.cols, r.offsets, negative=bool(r.flags))
             assert np.array_equal(r.counts, ec)
+        # the plain arm (pinned lists and outputs read and written in place) agrees
+        stream = torch.cuda.Stream()
+        for r in srv.done[:12]:
+            p = serve.Request(run_id=r.run_id, cols=r.cols, offsets=r.offsets, t_arrival=0.0,
+                              flags=r.flags)
+            be.plain(p, stream)
+            assert np.array_equal(p.counts, r.counts)
+            assert np.array_equal(p.fitness, r.fitness)
     finally:
         be.close()
