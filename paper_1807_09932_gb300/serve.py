@@ -22,6 +22,7 @@ with the per-population call (ebic_eval_fitness), in arrival order.
 from __future__ import annotations
 
 import collections
+import ctypes
 import dataclasses
 import time
 
@@ -223,6 +224,9 @@ class GpuBackend:
                            dout=None) for _ in range(max_inflight)]
         # the plain arm's pinned lists and outputs, read and written in place by the fused call
         self.plain_io = dict(hin=None, hout=None)
+        # a batch's request table as a numpy record array laid out like ebic_eval_request
+        self._req_dtype = np.dtype(ebic.EbicEvalRequest)
+        self._req_ptr = ctypes.POINTER(ebic.EbicEvalRequest)
 
     _ALIGN = 256  # every staged array starts on this boundary
 
@@ -330,6 +334,12 @@ class GpuBackend:
             run["aoffs"] = torch.zeros(1, dtype=torch.int32, device=self.dev)
             run["abm"] = torch.zeros((1, W), dtype=torch.int32, device=self.dev)
             run["K"] = 0
+        # the run's fixed fields of a batch request, as addresses (0: none)
+        k = run["K"]
+        run["req"] = (m.handle.value, run["bitmaps"].data_ptr() if not pairs else 0,
+                      run["acols"].data_ptr() if pairs and k else 0,
+                      run["aoffs"].data_ptr() if pairs and k else 0,
+                      run["abm"].data_ptr() if pairs and k else 0, k if pairs else 0)
         self.runs[spec.run_id] = run
 
     def close_run(self, run_id):
@@ -361,22 +371,29 @@ class GpuBackend:
             if rc:
                 raise ebic.EbicError(rc, "ebic_eval_fitness")
         else:
-            items = []
-            for r, (oc, oo), (cnt, fit) in zip(reqs, ins, outs):
-                run = self.runs[r.run_id]
-                if run["pairs"]:  # fitness inside the batch, the overlaps fused there
-                    k = run["K"]
-                    items.append((run["m"].handle, din + oc, din + oo, r.n_cand, r.flags,
-                                  dout + cnt, None, run["acols"] if k else None,
-                                  run["aoffs"] if k else None, run["abm"] if k else None, k,
-                                  dout + fit))
-                else:
-                    items.append((run["m"].handle, din + oc, din + oo, r.n_cand, r.flags,
-                                  dout + cnt, run["bitmaps"]))
+            # the batch's request table, filled column by column (a pair-table run gets its
+            # fitness inside the batch; the others write bitmaps for the fitness call)
+            n = len(reqs)
+            req = np.zeros(n, dtype=self._req_dtype)
+            fixed = np.array([self.runs[r.run_id]["req"] for r in reqs], dtype=np.uint64)
+            place = np.array([io + oo_ for io, oo_ in zip(ins, outs)], dtype=np.uint64)
+            pairs = np.array([self.runs[r.run_id]["pairs"] for r in reqs], dtype=bool)
+            req["m"] = fixed[:, 0]
+            req["cols"] = din + place[:, 0]
+            req["offsets"] = din + place[:, 1]
+            req["n_cand"] = [r.n_cand for r in reqs]
+            req["flags"] = [r.flags for r in reqs]
+            req["counts"] = dout + place[:, 2]
+            req["bitmaps"] = fixed[:, 1]
+            req["arch_cols"] = fixed[:, 2]
+            req["arch_offsets"] = fixed[:, 3]
+            req["arch_bitmaps"] = fixed[:, 4]
+            req["n_arch"] = fixed[:, 5]
+            req["fitness"] = np.where(pairs, dout + place[:, 3], 0)
             rc = ebic.ebic_copy_async(din, hin, in_bytes, sp)  # every list in one copy
             if rc:
                 raise ebic.EbicError(rc, "ebic_copy_async")
-            rc = ebic.ebic_batch_run(slot["batch"], ebic.make_requests(items), len(items), sp)
+            rc = ebic.ebic_batch_run(slot["batch"], req.ctypes.data_as(self._req_ptr), n, sp)
             if rc:
                 raise ebic.EbicError(rc, "ebic_batch_run")
             for r, (oc, oo), (cnt, fit) in zip(reqs, ins, outs):
