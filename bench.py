@@ -28,6 +28,7 @@ bounded sample of the same workload: the comparison arm, not a target.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -134,7 +135,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={CLOCK_QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -367,6 +368,10 @@ def main():
     # ---- timed region: K steps, L2 flushed between steps outside the events ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    # the timed regions run with the garbage collector paused: a full collection in the middle
+    # of a step would hold back its launches after its start event
+    gc.collect()
+    gc.disable()
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -496,6 +501,8 @@ def main():
         rc_ms = rc_tot / rc_steps
         if m.status() != ebic.EBIC_OK:
             raise SystemExit("device status error in the rank-code pass")
+
+    gc.enable()
 
     # ---- roofline of the dominant kernel (the evaluator) ----
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -656,6 +663,8 @@ def sharded_workload(args):
         check = bool(torch.equal(fit, ref))
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    gc.collect()
+    gc.disable()
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
@@ -670,6 +679,7 @@ def sharded_workload(args):
     torch.cuda.synchronize()
     launches = ebic.ebic_launch_count() - launches0
     clk = clocks.stop()
+    gc.enable()
     if m.status() != ebic.EBIC_OK:
         raise SystemExit("device status error in the timed region")
     tot_ms = sum(a.elapsed_time(b) for a, b in evs)
@@ -937,6 +947,8 @@ def batched_measure(args, steps):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        gc.collect()
+        gc.disable()
         evs = []
         for i in range(steps):
             flush.fill_(i & 0xFF)
@@ -946,6 +958,7 @@ def batched_measure(args, steps):
             b.record(stream)
             evs.append((a, b))
         torch.cuda.synchronize()
+        gc.enable()
         return sum(a.elapsed_time(b) for a, b in evs) / steps
 
     clocks = ClockSampler(0)
@@ -1059,9 +1072,14 @@ def served_measure(args, loads, requests, repeats):
     serve.drive(srv, trace(2 * len(specs), 0.0), rows_of)
     serve.plain_serve(be, trace(len(specs), 0.0), rows_of, plain_stream)
     sat_trace = trace(4 * len(specs), 0.0)
+    gc.collect()
+    gc.disable()
     sat_served = run_served(copy_trace(sat_trace))
     sat_plain = serve.plain_serve(be, copy_trace(sat_trace), rows_of, plain_stream)
+    gc.enable()
     capacity_rps = sat_served["evals_per_s"] / mean_evals
+    gc.collect()
+    gc.disable()
     clocks = ClockSampler(0)
     clocks.start()
     sweep = []
@@ -1084,6 +1102,7 @@ def served_measure(args, loads, requests, repeats):
         if load == args.load:
             headline = entry
     clk = clocks.stop()
+    gc.enable()
     be.close()
     served, plain = headline["served"], headline["plain"]
     line = {"metric": "candidate-row evals/s", "value": served["evals_per_s"],
