@@ -120,31 +120,74 @@ __global__ void __launch_bounds__(kCheckWarps * 32)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a warp per candidate: the single-population check (columns distinct through a bitset in
   // shared memory) and, on a matrix with a pair table, its term list for the pair pass. Each
-  // warp takes a contiguous run of candidates, so it finds their request once and then steps.
+  // warp takes a contiguous run of candidates. Its lanes load the offsets of up to 32 of them in
+  // one round (lane k: candidate k of the chunk, with its request and counter); the columns of
+  // two candidates at a time are then loaded into registers together, checked and turned into
+  // term lists from there.
   const uint32_t nwarps = gridDim.x * kCheckWarps;
   const uint32_t per = (total + nwarps - 1) / nwarps;
   const uint32_t g0 = (blockIdx.x * kCheckWarps + warp) * per;
   const uint32_t g1 = min(g0 + per, total);
+  uint32_t* const set = sets[warp];
   uint32_t r = g0 < g1 ? find_request(reqs, n_req, g0) : 0u;
-  for (uint32_t g = g0; g < g1; ++g) {
-    while (r + 1 < n_req && reqs[r + 1].cand_base <= g) ++r;
-    const BatchReq& q = reqs[r];
-    const uint32_t i = g - q.cand_base;
-    if (lane == 0) q.counts[i] = 0u;
-    const uint32_t* offs = q.cand_offsets;
-    const uint32_t lo = offs[i], hi = offs[i + 1];
-    const bool bad = prepdev::check_candidate_span(q.cand_cols, lo, hi, offs[q.n_cand], i == 0,
-                                                   ncols_of[r], sets[warp], lane);
-    if (bad) {
-      if (lane == 0) {
-        atomicOr(&req_err[r], kErrInvalid);
-        atomicOr(q.status, kErrInvalid);
-      }
-    } else if (q.terms) {
-      prepdev::build_terms_warp(q.cand_cols, lo, hi, (uint32_t)q.pair_cols, q.pair_stride,
-                                q.neg != 0, q.terms + (size_t)i * term_slots(q.neg != 0), lane);
+  for (uint32_t c0 = g0; c0 < g1; c0 += 32) {
+    const uint32_t cnt = min(32u, g1 - c0);
+    // lane k: candidate c0 + k
+    uint32_t rk = r, ik = 0, lok = 0, hik = 0, totk = 0;
+    if ((uint32_t)lane < cnt) {
+      const uint32_t g = c0 + lane;
+      while (rk + 1 < n_req && reqs[rk + 1].cand_base <= g) ++rk;
+      const BatchReq& q = reqs[rk];
+      ik = g - q.cand_base;
+      const uint32_t* offs = q.cand_offsets;
+      lok = offs[ik];
+      hik = offs[ik + 1];
+      totk = offs[q.n_cand];
+      q.counts[ik] = 0u;
     }
-    __syncwarp();  // the bitset is rebuilt for the next candidate
+    r = __shfl_sync(0xFFFFFFFFu, rk, cnt - 1);  // the request of the chunk's last candidate
+    for (uint32_t j = 0; j < cnt; j += 2) {
+      // candidates j and j + 1 (when there is one): offsets from their lanes, columns loaded
+      // for both before either is checked
+      uint32_t ra[2], ia[2], lo[2], hi[2], ca_lo[2], ca_hi[2];
+      bool sane[2], has[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const uint32_t src = min(j + t, cnt - 1);
+        has[t] = j + t < cnt;
+        ra[t] = __shfl_sync(0xFFFFFFFFu, rk, src);
+        ia[t] = __shfl_sync(0xFFFFFFFFu, ik, src);
+        lo[t] = __shfl_sync(0xFFFFFFFFu, lok, src);
+        hi[t] = __shfl_sync(0xFFFFFFFFu, hik, src);
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, totk, src);
+        sane[t] = has[t] && prepdev::offsets_sane(lo[t], hi[t], tot, ia[t] == 0);
+        ca_lo[t] = ca_hi[t] = 0u;
+        if (sane[t])
+          prepdev::load_cols_regs(reqs[ra[t]].cand_cols, lo[t], hi[t], lane, ca_lo[t], ca_hi[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (!has[t]) continue;  // warp-uniform
+        const BatchReq& q = reqs[ra[t]];
+        const int32_t nc = ncols_of[ra[t]];
+        for (int w = lane; w < (nc + 31) / 32; w += 32) set[w] = 0u;
+        __syncwarp();
+        const uint32_t L = hi[t] - lo[t];
+        const bool bad =
+            !sane[t] || prepdev::cols_bad_regs(ca_lo[t], ca_hi[t], L, nc, set, lane);
+        if (bad) {
+          if (lane == 0) {
+            atomicOr(&req_err[ra[t]], kErrInvalid);
+            atomicOr(q.status, kErrInvalid);
+          }
+        } else if (q.terms) {
+          prepdev::build_terms_regs(ca_lo[t], ca_hi[t], (int)L, (uint32_t)q.pair_cols,
+                                    q.pair_stride, q.neg != 0,
+                                    q.terms + (size_t)ia[t] * term_slots(q.neg != 0), lane);
+        }
+        __syncwarp();  // the bitset is rebuilt for the next candidate
+      }
+    }
   }
   // the fitness requests: counters zeroed, archives copied into rows of the table's stride, the
   // column -> member masks, and the archive lists checked like candidate lists
