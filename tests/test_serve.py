@@ -146,3 +146,29 @@ def test_served_results_equal_alone(pair_budget, spacing):
             assert np.array_equal(p.fitness, r.fitness)
     finally:
         be.close()
+
+
+def test_batch_staging_layout_packs_every_list_on_aligned_offsets():
+    """The GPU backend's host staging (no device needed): each request's columns and offsets sit
+    on 256-byte boundaries without overlap, unpack to the request's own lists, and the outputs'
+    counts and fitness slots are aligned, disjoint and sized for the request."""
+    reqs = [_req(i % 3, 0.0, 40 + i, n=[1, 7, 33, 200][i % 4], cols=50) for i in range(9)]
+    ins, outs, in_bytes, out_bytes = serve.GpuBackend._layout(reqs)
+    a = serve.GpuBackend._ALIGN
+    spans = []
+    for r, (oc, oo), (cnt, fit) in zip(reqs, ins, outs):
+        assert oc % a == 0 and oo % a == 0 and cnt % a == 0 and fit % a == 0
+        spans.append(("in", oc, oc + 2 * int(r.offsets[-1])))
+        spans.append(("in", oo, oo + 4 * (r.n_cand + 1)))
+        spans.append(("out", cnt, cnt + 4 * r.n_cand))
+        spans.append(("out", fit, fit + 8 * r.n_cand))
+    for side, size in (("in", in_bytes), ("out", out_bytes)):
+        s = sorted((lo, hi) for k, lo, hi in spans if k == side)
+        assert all(h0 <= l1 for (_, h0), (l1, _) in zip(s, s[1:]))  # disjoint
+        assert s[-1][1] <= size
+    buf = np.zeros(in_bytes, dtype=np.uint8)
+    serve.GpuBackend._pack(buf, reqs, ins)
+    for r, (oc, oo) in zip(reqs, ins):
+        tot = int(r.offsets[-1])
+        assert np.array_equal(buf[oc:oc + 2 * tot].view(np.uint16), r.cols)
+        assert np.array_equal(buf[oo:oo + 4 * (r.n_cand + 1)].view(np.uint32), r.offsets)
