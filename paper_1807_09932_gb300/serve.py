@@ -164,7 +164,14 @@ class Server:
             for r in batch:
                 r.t_launch = t
                 self.busy_runs.add(r.run_id)
-            self.inflight.append((self.be.launch(batch), batch))
+            try:
+                token = self.be.launch(batch)
+            except Exception:
+                # the batch never ran: its runs may send again, and the caller sees the error
+                for r in batch:
+                    self.busy_runs.discard(r.run_id)
+                raise
+            self.inflight.append((token, batch))
             self.batches += 1
         return finished
 
@@ -352,9 +359,19 @@ class GpuBackend:
         run["m"].close()
 
     def launch(self, reqs):
-        ebic = self.ebic
         slot = next(s for s in self.slots if not s["busy"])
         slot["busy"] = True
+        try:
+            return self._launch(slot, reqs)
+        except Exception:
+            # nothing of this batch is waited for: let the stream finish what was queued, then
+            # give the slot back
+            slot["stream"].synchronize()
+            slot["busy"] = False
+            raise
+
+    def _launch(self, slot, reqs):
+        ebic = self.ebic
         st = slot["stream"]
         sp = st.cuda_stream
         ins, outs, in_bytes, out_bytes = self._layout(reqs)

@@ -91,6 +91,38 @@ def test_one_request_in_flight_per_run_and_results_exact():
         assert r.t_done >= r.t_launch >= r.t_arrival
 
 
+def test_failed_launch_frees_its_runs():
+    """A batch whose launch raises never ran: the error reaches the caller, its runs are not left
+    marked busy, and the same requests go through on the next pump."""
+    clock = FakeClock()
+    be = FakeBackend(clock, fixed=0.1, per_eval=0.0)
+    srv = serve.Server(be, hbm_budget=1 << 40, max_batch=4, max_inflight=1)
+    for i in range(2):
+        srv.add_run(_spec(i))
+    real, calls = be.launch, []
+
+    def flaky(reqs):
+        calls.append(len(reqs))
+        if len(calls) == 1:
+            raise RuntimeError("launch failed")
+        return real(reqs)
+
+    be.launch = flaky
+    reqs = [_req(0, 0.0, 70), _req(1, 0.0, 71)]
+    for r in reqs:
+        srv.submit(r)
+    with pytest.raises(RuntimeError):
+        srv.pump()
+    assert not srv.busy_runs and not srv.inflight and not srv.queue
+    for r in reqs:  # the failed batch's requests are the caller's to send again
+        srv.submit(r)
+    srv.pump()
+    assert len(srv.inflight) == 1 and srv.busy_runs == {0, 1}
+    clock.t = 1.0
+    done = srv.pump()
+    assert sorted(r.run_id for r in done) == [0, 1] and not srv.busy_runs
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("pair_budget,spacing", [(0, 0.0005), (1 << 30, 0.0005), (1 << 30, 0.0)])
 def test_served_results_equal_alone(pair_budget, spacing):
