@@ -204,3 +204,36 @@ def test_batch_staging_layout_packs_every_list_on_aligned_offsets():
         tot = int(r.offsets[-1])
         assert np.array_equal(buf[oc:oc + 2 * tot].view(np.uint16), r.cols)
         assert np.array_equal(buf[oo:oo + 4 * (r.n_cand + 1)].view(np.uint32), r.offsets)
+
+
+@pytest.mark.gpu
+def test_served_lone_request_error_frees_the_slot():
+    """A lone request whose list the library rejects (a column outside the matrix) raises from the
+    pump; the slot it took is free again and the next request is served correctly."""
+    from paper_1807_09932_gb300 import ebic
+    be = serve.GpuBackend(max_batch=4, max_inflight=1, pair_budget=1 << 30)
+    try:
+        srv = serve.Server(be, hbm_budget=8 << 30, max_batch=4, max_inflight=1)
+        ds = synth.make_dataset(720, 5000, 40, planted=synth.planted_specs_for(720, 5000, 40),
+                                nan_frac=0.01)
+        ac, ao = synth.population_from_lists([[0, 1, 2], [3, 4]])
+        srv.add_run(serve.RunSpec(run_id=0, X=ds.X, max_cand=300, max_len=16,
+                                  archive_cols=ac, archive_offsets=ao))
+        c, o = synth.make_population(721, 100, 40, 2, 8)
+        bad_c = c.copy()
+        bad_c[5] = 40  # no such column
+        srv.submit(serve.Request(run_id=0, cols=bad_c, offsets=o, t_arrival=0.0))
+        with pytest.raises(ebic.EbicError):
+            srv.pump()
+        assert not srv.busy_runs and not any(s["busy"] for s in be.slots)
+        good = serve.Request(run_id=0, cols=c, offsets=o, t_arrival=0.0)
+        srv.submit(good)
+        while not srv.done:
+            srv.pump()
+        ec, eb = oracle.eval_population(ds.X, c, o)
+        _, abm = oracle.eval_population(ds.X, ac, ao)
+        ef, _ = oracle.fitness(ds.X.shape[0], c, o, ec, eb, ac, ao, abm, want_overlaps=False)
+        assert np.array_equal(good.counts, ec)
+        assert np.array_equal(good.fitness, ef)
+    finally:
+        be.close()
