@@ -141,6 +141,28 @@ def test_rank_export_matches_dense_ranks(ebic):
             assert np.array_equal(got, want)
 
 
+def test_rank_export_matches_dense_ranks_past_one_round_of_slabs(ebic):
+    """Matrices of more 512-row slabs than the GPU has SMs: several rounds of slabs per CTA, a
+    partial last round, a ragged last slab and one almost all padding; rows on 16-byte
+    boundaries (the staged form) and not."""
+    from pins import tiny_matrix
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cases = [(sms * 512 + 44 * 512 + 37, 64, True),     # a short last round
+             (sms * 512 + 130 * 512 + 3, 32, True),     # a long last round
+             (sms * 512 + 130 * 512 + 3, 64, False),
+             (2 * sms * 512 + 1, 36, True),             # one padding chunk, mostly empty
+             (sms * 512 + 77 * 512, 61, True)]          # rows not on 16-byte boundaries
+    for R, C, exclude in cases:
+        X = tiny_matrix(R + C, R, C, nan_frac=0.02)
+        rng = np.random.default_rng(R)
+        X[:, : C // 2] += rng.standard_normal((R, C // 2)).astype(np.float32)
+        with ebic.Matrix(X, exclude_missing=exclude, fill_value=1.0) as m:
+            got = m.ranks()
+        want = oracle.dense_ranks(X, exclude_missing=exclude, fill_value=1.0)
+        assert np.array_equal(got, want), (R, C, exclude)
+
+
 def _near_equal_rows(seed, R, C):
     """Rows whose values crowd into a few groups of float32 bit patterns one unit apart (so many
     share all but their lowest key bits), with exact ties, signed zeros, infinities and NaN."""
