@@ -581,9 +581,20 @@ def main():
         # own clock record (one process on one GPU; under torchrun the replicas line alone)
         del counts, bitmaps, fit, flush, dpops
         torch.cuda.empty_cache()
-        line["batched"] = batched_measure(args, args.leg_steps)
-        line["served"] = served_measure(args, [args.load], args.leg_requests, args.leg_repeats)
-        line["ga"] = ga_measure(args, args.leg_generations)
+        # a leg that fails records its error in its own key; the headline above stands
+        legs = (("batched", lambda: batched_measure(args, args.leg_steps)),
+                ("served", lambda: served_measure(args, [args.load], args.leg_requests,
+                                                  args.leg_repeats)),
+                ("ga", lambda: ga_measure(args, args.leg_generations)))
+        for name, fn in legs:
+            try:
+                line[name] = fn()
+            except Exception as e:  # noqa: BLE001 - reported in the line, not swallowed
+                gc.enable()
+                line[name] = {"error": f"{type(e).__name__}: {e}"}
+                print(f"bench: the {name} leg failed: {e!r}", file=sys.stderr, flush=True)
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
         line["legs"] = ("batched: batched_measure, the config of its line; served: "
                         f"served_measure, {args.leg_repeats} traces of {args.leg_requests} "
                         f"requests at {args.load:.2f} x the served capacity, latencies pooled")
