@@ -194,36 +194,42 @@ __global__ void __launch_bounds__(kCheckWarps * 32)
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nthreads = (size_t)gridDim.x * blockDim.x;
   for (size_t i = tid; i < hdr->n_zero; i += nthreads) hdr->zero[i] = 0u;
-  for (uint32_t r = 0; r < n_req; ++r) {
-    const BatchReq& q = reqs[r];
-    if (!q.fitness || q.n_arch == 0) continue;
-    prepdev::copy_archive_padded(q.arch_src, q.arch_pad, q.n_arch, q.words, q.pair_stride, tid,
-                                 nthreads);
-    const uint32_t* ao = q.arch_offsets;
-    const uint32_t atot = ao[q.n_arch];
-    for (size_t c = tid; c < (size_t)q.pair_cols; c += nthreads) {
-      unsigned long long mask = 0ull;
-      for (uint32_t m = 0; m < q.n_arch; ++m) {
-        const uint32_t lo = ao[m], hi = ao[m + 1];
-        if (!prepdev::offsets_sane(lo, hi, atot, m == 0)) continue;  // rejected below
-        for (uint32_t j = lo; j < hi; ++j)
-          if (q.arch_cols[j] == c) mask |= 1ull << m;
-      }
-      q.colmask[c] = mask;
-    }
-    for (size_t m = tid; m < q.n_arch; m += nthreads) {
-      const uint32_t lo = ao[m], hi = ao[m + 1];
-      bool bad = !prepdev::offsets_sane(lo, hi, atot, m == 0);
-      if (!bad) {
-        for (uint32_t j = lo; j < hi; ++j) {
-          const uint16_t c = q.arch_cols[j];
-          bad |= c >= (uint32_t)q.pair_cols;
-          for (uint32_t t = lo; t < j; ++t) bad |= q.arch_cols[t] == c;
+  // the requests with an archive, found 32 at a time (a lane per request, one ballot) rather
+  // than by one dependent load per request; every warp finds the same ones
+  for (uint32_t r0 = 0; r0 < n_req; r0 += 32) {
+    const uint32_t rl = r0 + lane;
+    const bool has = rl < n_req && reqs[rl].fitness != nullptr && reqs[rl].n_arch != 0;
+    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, has); todo; todo &= todo - 1u) {
+      const uint32_t r = r0 + (uint32_t)(__ffs(todo) - 1);
+      const BatchReq& q = reqs[r];
+      prepdev::copy_archive_padded(q.arch_src, q.arch_pad, q.n_arch, q.words, q.pair_stride, tid,
+                                   nthreads);
+      const uint32_t* ao = q.arch_offsets;
+      const uint32_t atot = ao[q.n_arch];
+      for (size_t c = tid; c < (size_t)q.pair_cols; c += nthreads) {
+        unsigned long long mask = 0ull;
+        for (uint32_t m = 0; m < q.n_arch; ++m) {
+          const uint32_t lo = ao[m], hi = ao[m + 1];
+          if (!prepdev::offsets_sane(lo, hi, atot, m == 0)) continue;  // rejected below
+          for (uint32_t j = lo; j < hi; ++j)
+            if (q.arch_cols[j] == c) mask |= 1ull << m;
         }
+        q.colmask[c] = mask;
       }
-      if (bad) {
-        atomicOr(&req_err[r], kErrInvalid);
-        atomicOr(q.status, kErrInvalid);
+      for (size_t m = tid; m < q.n_arch; m += nthreads) {
+        const uint32_t lo = ao[m], hi = ao[m + 1];
+        bool bad = !prepdev::offsets_sane(lo, hi, atot, m == 0);
+        if (!bad) {
+          for (uint32_t j = lo; j < hi; ++j) {
+            const uint16_t c = q.arch_cols[j];
+            bad |= c >= (uint32_t)q.pair_cols;
+            for (uint32_t t = lo; t < j; ++t) bad |= q.arch_cols[t] == c;
+          }
+        }
+        if (bad) {
+          atomicOr(&req_err[r], kErrInvalid);
+          atomicOr(q.status, kErrInvalid);
+        }
       }
     }
   }
