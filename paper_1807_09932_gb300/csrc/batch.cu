@@ -196,41 +196,48 @@ __global__ void __launch_bounds__(kCheckWarps * 32)
   for (size_t i = tid; i < hdr->n_zero; i += nthreads) hdr->zero[i] = 0u;
   // the requests with an archive, found 32 at a time (a lane per request, one ballot) rather
   // than by one dependent load per request; every warp finds the same ones
+  // The archive copy of a request takes every thread; its column -> member masks and its list
+  // check take one block (the request's ordinal among them, modulo the grid), which loads every
+  // (member, position) of the list in one round and builds the masks in shared memory.
+  __shared__ unsigned long long cmask[kMaxCols];
+  uint32_t ordinal = 0;
   for (uint32_t r0 = 0; r0 < n_req; r0 += 32) {
     const uint32_t rl = r0 + lane;
     const bool has = rl < n_req && reqs[rl].fitness != nullptr && reqs[rl].n_arch != 0;
-    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, has); todo; todo &= todo - 1u) {
+    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, has); todo; todo &= todo - 1u, ++ordinal) {
       const uint32_t r = r0 + (uint32_t)(__ffs(todo) - 1);
       const BatchReq& q = reqs[r];
       prepdev::copy_archive_padded(q.arch_src, q.arch_pad, q.n_arch, q.words, q.pair_stride, tid,
                                    nthreads);
+      if (ordinal % gridDim.x != blockIdx.x) continue;  // block-uniform
       const uint32_t* ao = q.arch_offsets;
-      const uint32_t atot = ao[q.n_arch];
-      for (size_t c = tid; c < (size_t)q.pair_cols; c += nthreads) {
-        unsigned long long mask = 0ull;
-        for (uint32_t m = 0; m < q.n_arch; ++m) {
-          const uint32_t lo = ao[m], hi = ao[m + 1];
-          if (!prepdev::offsets_sane(lo, hi, atot, m == 0)) continue;  // rejected below
-          for (uint32_t j = lo; j < hi; ++j)
-            if (q.arch_cols[j] == c) mask |= 1ull << m;
-        }
-        q.colmask[c] = mask;
-      }
-      for (size_t m = tid; m < q.n_arch; m += nthreads) {
+      const uint32_t na = q.n_arch, atot = ao[na];
+      const int pc = q.pair_cols;
+      for (int c = threadIdx.x; c < pc; c += blockDim.x) cmask[c] = 0ull;
+      __syncthreads();
+      bool bad = false;
+      for (uint32_t t = threadIdx.x; t < na * (uint32_t)kMaxLen; t += blockDim.x) {
+        const uint32_t m = t / kMaxLen, j = t % kMaxLen;
         const uint32_t lo = ao[m], hi = ao[m + 1];
-        bool bad = !prepdev::offsets_sane(lo, hi, atot, m == 0);
-        if (!bad) {
-          for (uint32_t j = lo; j < hi; ++j) {
-            const uint16_t c = q.arch_cols[j];
-            bad |= c >= (uint32_t)q.pair_cols;
-            for (uint32_t t = lo; t < j; ++t) bad |= q.arch_cols[t] == c;
-          }
+        if (!prepdev::offsets_sane(lo, hi, atot, m == 0)) {
+          bad |= j == 0;  // once per member
+          continue;
         }
-        if (bad) {
-          atomicOr(&req_err[r], kErrInvalid);
-          atomicOr(q.status, kErrInvalid);
+        if (j >= hi - lo) continue;
+        const uint32_t c = q.arch_cols[lo + j];
+        if (c >= (uint32_t)pc) {
+          bad = true;
+          continue;
         }
+        const unsigned long long bit = 1ull << m;
+        bad |= (atomicOr(&cmask[c], bit) & bit) != 0ull;  // the member holds c twice
       }
+      if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        atomicOr(&req_err[r], kErrInvalid);
+        atomicOr(q.status, kErrInvalid);
+      }
+      for (int c = threadIdx.x; c < pc; c += blockDim.x) q.colmask[c] = cmask[c];
+      __syncthreads();  // the masks are rebuilt for the block's next request
     }
   }
 }
